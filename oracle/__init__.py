@@ -1,0 +1,134 @@
+"""CPU oracle for the simplex workloads of arXiv 2208.11617 (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may load this module; the product package never
+imports it.  The arithmetic lives in ``simplex_oracle.c`` (plain nested loops
+over x_1 + ... + x_m <= n, Eq. 1); this file only compiles it with gcc and
+marshals numpy arrays through ctypes.
+
+Arrays are dense with side D = n + 1 and x_m fastest (row-major).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "simplex_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile simplex_oracle.c into liboracle.so (OpenMP if gcc supports it)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True, text=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        i64, u32, i32, u64 = ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint64
+        lib.oracle_splitmix32.argtypes = [u32]
+        lib.oracle_splitmix32.restype = u32
+        lib.oracle_num_threads.argtypes = []
+        lib.oracle_num_threads.restype = i32
+        lib.oracle_count_cells.argtypes = [i32, i64]
+        lib.oracle_count_cells.restype = u64
+        lib.oracle_write.argtypes = [i32, i64, u32, u32p]
+        lib.oracle_write.restype = u64
+        lib.oracle_ca_init.argtypes = [i32, i64, u32, u32, u8p]
+        lib.oracle_ca_init.restype = u64
+        lib.oracle_ca_step.argtypes = [i32, i64, u32, u32, u8p, u8p]
+        lib.oracle_ca_step.restype = u64
+        lib.oracle_ca_run.argtypes = [i32, i64, i32, u32, u32, u8p, u8p, u64p]
+        lib.oracle_ca_run.restype = None
+        lib.oracle_block_indicator.argtypes = [i32, i64, i32, u32p]
+        lib.oracle_block_indicator.restype = None
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def splitmix32(z: int) -> int:
+    return int(_load().oracle_splitmix32(z & 0xFFFFFFFF))
+
+
+def count_cells(m: int, n: int) -> int:
+    """|Delta_n^m| by enumeration (Eq. 1)."""
+    return int(_load().oracle_count_cells(m, n))
+
+
+def dense_shape(m: int, n: int) -> tuple:
+    return (n + 1,) * m
+
+
+def write(m: int, n: int, seed: int) -> np.ndarray:
+    """Coordinate-write test: dense uint32 array, simplex cells hashed, rest 0."""
+    out = np.zeros(dense_shape(m, n), dtype=np.uint32)
+    c = _load().oracle_write(m, n, seed & 0xFFFFFFFF, _ptr(out, ctypes.c_uint32))
+    assert c == count_cells(m, n) or m not in (2, 3, 4)
+    return out
+
+
+def ca_init(m: int, n: int, seed: int, threshold: int) -> np.ndarray:
+    """Seeded Bernoulli state: simplex cells alive iff splitmix32(seed ^ lin) < threshold."""
+    g = np.zeros(dense_shape(m, n), dtype=np.uint8)
+    _load().oracle_ca_init(m, n, seed & 0xFFFFFFFF, threshold & 0xFFFFFFFF, _ptr(g, ctypes.c_uint8))
+    return g
+
+
+def ca_step(m: int, n: int, birth: int, survive: int, grid: np.ndarray):
+    """One synchronous step; returns (new grid, live count)."""
+    src = np.ascontiguousarray(grid, dtype=np.uint8)
+    dst = np.zeros_like(src)
+    live = _load().oracle_ca_step(m, n, birth, survive, _ptr(src, ctypes.c_uint8),
+                                  _ptr(dst, ctypes.c_uint8))
+    return dst, int(live)
+
+
+def ca_run(m: int, n: int, steps: int, birth: int, survive: int, grid: np.ndarray):
+    """`steps` synchronous steps; returns (final grid, live counts [steps + 1])."""
+    a = np.array(grid, dtype=np.uint8, order="C", copy=True)
+    b = np.zeros_like(a)
+    live = np.zeros(steps + 1, dtype=np.uint64)
+    _load().oracle_ca_run(m, n, steps, birth, survive, _ptr(a, ctypes.c_uint8),
+                          _ptr(b, ctypes.c_uint8), _ptr(live, ctypes.c_uint64))
+    return (a if steps % 2 == 0 else b), live
+
+
+def block_indicator(m: int, n: int, rho: int) -> np.ndarray:
+    """1 for every tile of side rho that holds a simplex cell, found cell by cell."""
+    nb = (n + rho) // rho
+    ind = np.zeros((nb,) * m, dtype=np.uint32)
+    _load().oracle_block_indicator(m, n, rho, _ptr(ind, ctypes.c_uint32))
+    return ind

@@ -1,0 +1,71 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds workload definitions only -- sizes, seeds, rule masks and
+Bernoulli thresholds -- and none of the method's arithmetic.  Both the CUDA path
+and the CPU oracle receive these numbers as plain arguments.
+
+The paper measures on synthetic n-sweeps (Sec. 5.1, Table 1) and publishes no
+dataset; the workloads below are the same shapes: dense n^m arrays holding the
+discrete orthogonal m-simplex x_1 + ... + x_m <= n.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from fractions import Fraction
+
+DEFAULT_SEED = 0x22081161
+
+# Automaton rules as (birth, survive) bit masks: bit k = "k live neighbours".
+B3S23 = (1 << 3, (1 << 2) | (1 << 3))          # Conway's Life, Moore-8 (m = 2)
+B5S45 = (1 << 5, (1 << 4) | (1 << 5))          # Moore-26 rule used for m = 3
+
+
+def bernoulli_threshold(p) -> int:
+    """floor(p * 2^32) computed exactly from the decimal value of p (0 <= p < 1)."""
+    q = Fraction(str(p))
+    if not (0 <= q < 1):
+        raise ValueError("p must be in [0, 1)")
+    return int(q * (1 << 32))
+
+
+@dataclass(frozen=True)
+class WriteWorkload:
+    name: str
+    m: int
+    n: int
+    block: int
+    seed: int = DEFAULT_SEED
+
+
+@dataclass(frozen=True)
+class CAWorkload:
+    name: str
+    m: int
+    n: int
+    block: int
+    steps: int
+    p: float
+    rule: tuple
+    seed: int = DEFAULT_SEED
+
+    @property
+    def threshold(self) -> int:
+        return bernoulli_threshold(self.p)
+
+
+# Write test on the 2-simplex: n = 1023 (524,800 cells) in a 1024^2 uint32 array,
+# 16 x 16 tiles.
+WRITE_M2 = WriteWorkload("write m=2 n=1023 rho=16", m=2, n=1023, block=16)
+# Write test on the 4-simplex: n = 127 (11,716,640 cells) in a 128^4 uint32 array.
+WRITE_M4 = WriteWorkload("write m=4 n=127 rho=4", m=4, n=127, block=4)
+# Automaton on the 2-simplex: n = 32767 in a 32768^2 uint8 array, Bernoulli(0.5),
+# B3/S23, 100 steps; the same run at n = 4095 is the size the oracle finishes in
+# seconds.
+CA_M2 = CAWorkload("ca m=2 n=32767 B3/S23", m=2, n=32767, block=128, steps=100,
+                   p=0.5, rule=B3S23)
+CA_M2_SMALL = CAWorkload("ca m=2 n=4095 B3/S23", m=2, n=4095, block=128, steps=100,
+                         p=0.5, rule=B3S23)
+# Automaton on the 3-simplex: n = 1023 in a 1024^3 uint8 array, Bernoulli(0.3),
+# B5/S45, 50 steps.
+CA_M3 = CAWorkload("ca m=3 n=1023 B5/S45", m=3, n=1023, block=32, steps=50,
+                   p=0.3, rule=B5S45)
