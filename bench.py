@@ -1,0 +1,401 @@
+"""Benchmark of the simplex automaton hot path (one JSON line on rank 0).
+
+Default workload: the automaton on the 2-simplex, n = 32767 (536,887,296 cells)
+in a dense 32768^2 uint8 grid, Bernoulli(0.5), B3/S23, 100 steps, 128 x 128
+tiles mapped by H.  One benchmark step = one simplex_ca_run of the 100
+automaton steps (CUDA-graph replay, per-step live counts) on device-resident
+grids; the grids (1 GiB each) are far larger than L2, so no flush is needed
+between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ca2|ca3|write2|write4]
+
+--impl reference times the CPU oracle on this host's cores on a bounded
+sample of the same workload (the reference arm).  Under torchrun (N > 1) every
+rank runs an independent replica (the path is not sharded); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2208_11617_gb300 import inputs  # noqa: E402
+
+METRIC = "simplex cells/s & HBM-roofline % of H vs bounding-box map; serve p99 latency"
+UNIT = "cell-updates/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed
+def _dist_init():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(units_per_rank: float, seconds: float, world: int):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([seconds, units_per_rank], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        return float(sm[1].item()) / float(mx[0].item()), float(mx[0].item())
+    return units_per_rank / seconds, seconds
+
+
+# ---------------------------------------------------------------- our arm
+def _workload(name):
+    if name == "ca2":
+        return inputs.CA_M2
+    if name == "ca3":
+        return inputs.CA_M3
+    if name == "write2":
+        return inputs.WRITE_M2
+    if name == "write4":
+        return inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _time_region(fn, steps, warmup, world):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    _barrier(world)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    _barrier(world)
+    return s.elapsed_time(e) / 1e3
+
+
+def _per_launch_ms(launch, reps):
+    """Average device duration of one kernel launch, CUDA events on the launching stream."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    launch()
+    torch.cuda.synchronize()
+    for s, e in evs:
+        s.record()
+        launch()
+        e.record()
+    torch.cuda.synchronize()
+    ts = sorted(s.elapsed_time(e) for s, e in evs)
+    return statistics.mean(ts), statistics.median(ts)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2208_11617_gb300 import simplex as sx
+
+    torch.cuda.set_device(local)
+    wl = _workload(args.workload)
+    hbm_peak, peak_kind = _peaks()
+    res = {}
+    if isinstance(wl, inputs.CAWorkload):
+        mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block)
+        info = sx.simplex_map_info(mp)
+        cells = info["cells"]
+        a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
+        b = torch.zeros_like(a)
+        sx.simplex_ca_init(mp, a, wl.seed, wl.threshold)
+        live = torch.zeros(wl.steps + 1, dtype=torch.int64, device="cuda")
+        birth, survive = wl.rule
+
+        def step(mode):
+            return lambda: sx.simplex_ca_run(mp, a, b, wl.steps, birth, survive, live, True, mode)
+
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        secs = _time_region(step(sx.SIMPLEX_MODE_H), args.steps, args.warmup, world)
+        clk = clocks.stop()
+        secs_bb = _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
+        units = cells * wl.steps * args.steps
+        value, tmax = aggregate(units, secs, world)
+        value_bb, _ = aggregate(units, secs_bb, world)
+        # dominant kernel: one automaton step; its average launch duration
+        nxt = torch.zeros_like(a)
+        mean_ms, med_ms = _per_launch_ms(lambda: sx.simplex_ca_step(mp, a, nxt, birth, survive, None), 20)
+        mean_bb, _ = _per_launch_ms(
+            lambda: sx.simplex_ca_step(mp, a, nxt, birth, survive, None, sx.SIMPLEX_MODE_BB), 20)
+        alg_bytes = 2 * cells
+        achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
+        res.update(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="u8", data="synthetic",
+            config={"workload": wl.name, "m": wl.m, "n": wl.n, "array": f"{mp.side}^{wl.m} uint8",
+                    "tile": f"{wl.block}^{wl.m}", "ca_steps_per_step": wl.steps, "p": wl.p,
+                    "rule": "B3/S23" if wl.m == 2 else "B5/S45", "map": "H (r=1/2, beta=2)",
+                    "cells": cells, "parallelism": "replicas" if world > 1 else "single",
+                    "l2": "inputs 1 GiB per grid >> 129 MB L2, no flush"},
+            roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                      "kernel": f"ca{wl.m}_step_kernel<{wl.block}>", "alg_bytes_per_launch": alg_bytes,
+                      "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
+            clocks=clk,
+            gpu_launches=args.steps * (wl.steps + 1),
+            bb={"value": value_bb, "speedup_h_over_bb": value / value_bb, "launch_ms_mean": mean_bb,
+                "kernel_speedup_h_over_bb": mean_bb / mean_ms},
+            blocks={"h": info["h_blocks"], "bb": info["bb_blocks"], "useful": info["useful_blocks"],
+                    "wasted_frac_h": 1 - info["useful_blocks"] / info["h_blocks"],
+                    "wasted_frac_bb": 1 - info["useful_blocks"] / info["bb_blocks"]},
+        )
+        # end to end through the C ABI from pinned host memory
+        e2e_steps = max(1, min(3, args.steps))
+        h_in = torch.empty(mp.numel, dtype=torch.uint8).pin_memory()
+        h_in.copy_(a.cpu())
+        h_out = torch.empty_like(h_in).pin_memory()
+        h_live = torch.zeros(wl.steps + 1, dtype=torch.int64)
+        sx.simplex_ca_run_host(mp, h_in, h_out, a, b, wl.steps, birth, survive, live, h_live)
+        torch.cuda.synchronize()
+        _barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sx.simplex_ca_run_host(mp, h_in, h_out, a, b, wl.steps, birth, survive, live, h_live)
+        t1 = time.perf_counter()
+        e2e_val, _ = aggregate(cells * wl.steps * e2e_steps, t1 - t0, world)
+        res["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": mp.numel,
+                      "d2h_bytes_per_step": mp.numel + 8 * (wl.steps + 1)}
+        assert sx.simplex_device_status() == 0
+    else:
+        beta = 2 if wl.m <= 3 else wl.m
+        mp = sx.simplex_map_create(wl.m, wl.n, 2, beta, wl.block)
+        info = sx.simplex_map_info(mp)
+        cells = info["cells"]
+        out = torch.zeros(mp.numel, dtype=torch.int32, device="cuda")
+        # many launches per benchmark step: the write of one array is a few microseconds
+        reps = 100
+
+        def step(mode):
+            def f():
+                for _ in range(reps):
+                    sx.simplex_write(mp, out, wl.seed, mode)
+            return f
+
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        secs = _time_region(step(sx.SIMPLEX_MODE_H), args.steps, args.warmup, world)
+        clk = clocks.stop()
+        secs_bb = _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
+        units = cells * reps * args.steps
+        value, tmax = aggregate(units, secs, world)
+        value_bb, _ = aggregate(units, secs_bb, world)
+        mean_ms, med_ms = _per_launch_ms(lambda: sx.simplex_write(mp, out, wl.seed), 50)
+        mean_bb, _ = _per_launch_ms(lambda: sx.simplex_write(mp, out, wl.seed, sx.SIMPLEX_MODE_BB), 50)
+        alg_bytes = 4 * cells
+        achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
+        res.update(
+            metric=METRIC, value=value, unit="cells/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="u32", data="synthetic",
+            config={"workload": wl.name, "m": wl.m, "n": wl.n, "array": f"{mp.side}^{wl.m} uint32",
+                    "tile": f"{wl.block}^{wl.m}", "writes_per_step": reps, "cells": cells,
+                    "parallelism": "replicas" if world > 1 else "single",
+                    "l2": "array re-written back to back (L2-resident when it fits)"},
+            roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                      "kernel": f"write_kernel<{wl.m}>", "alg_bytes_per_launch": alg_bytes,
+                      "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
+            clocks=clk, gpu_launches=args.steps * reps,
+            bb={"value": value_bb, "speedup_h_over_bb": value / value_bb, "launch_ms_mean": mean_bb,
+                "kernel_speedup_h_over_bb": mean_bb / mean_ms},
+            blocks={"h": info["h_blocks"], "bb": info["bb_blocks"], "useful": info["useful_blocks"]},
+        )
+        # end to end: write on the device, read the array back to pinned host memory
+        h_out = torch.empty(mp.numel, dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            sx.simplex_write(mp, out, wl.seed)
+            h_out.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e_val, _ = aggregate(cells * 3, t1 - t0, world)
+        res["e2e"] = {"value": e2e_val, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": 4 * mp.numel}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(wl)
+    return res
+
+
+# ---------------------------------------------------------------- oracle (CPU) arm
+def _oracle_sample(wl, steps_sample):
+    """Time the oracle on a bounded sample of the workload; returns (units/s, note, cores)."""
+    import oracle
+    cores = oracle.num_threads()
+    if isinstance(wl, inputs.CAWorkload):
+        g = oracle.ca_init(wl.m, wl.n, wl.seed, wl.threshold)
+        cells = oracle.count_cells(wl.m, wl.n)
+        t0 = time.perf_counter()
+        for _ in range(steps_sample):
+            g, _ = oracle.ca_step(wl.m, wl.n, wl.rule[0], wl.rule[1], g)
+        dt = time.perf_counter() - t0
+        note = f"{steps_sample} automaton step(s) of the full n={wl.n} grid ({cells} cells each)"
+        return cells * steps_sample / dt, note, cores, dt
+    cells = oracle.count_cells(wl.m, wl.n)
+    t0 = time.perf_counter()
+    for _ in range(steps_sample):
+        oracle.write(wl.m, wl.n, wl.seed)
+    dt = time.perf_counter() - t0
+    return cells * steps_sample / dt, f"{steps_sample} full write(s) of n={wl.n}", cores, dt
+
+
+def cpu_baseline(wl):
+    v, note, cores, dt = _oracle_sample(wl, 2 if isinstance(wl, inputs.CAWorkload) else 5)
+    return {"value": v, "unit": UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s", "cores": cores,
+            "kind": "oracle", "sample": note, "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl = _workload(args.workload)
+    unit = UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s"
+    for _ in range(args.warmup):
+        _oracle_sample(wl, 1)
+    vals, dts = [], []
+    cores, note = 1, ""
+    for _ in range(args.steps):
+        v, note, cores, dt = _oracle_sample(wl, 1)
+        vals.append(v)
+        dts.append(dt)
+    total = sum(dts)
+    value = len(vals) / sum(1.0 / v for v in vals)  # units over total time
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(dts) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8" if unit == UNIT else "u32",
+            "data": "synthetic", "config": {"workload": wl.name, "m": wl.m, "n": wl.n},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {note}"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank, world, local = _dist_init()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

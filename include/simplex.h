@@ -1,0 +1,228 @@
+/*
+ * simplex.h -- C ABI of libsimplex: the block-space map H of arXiv 2208.11617
+ * ("A Scalable and Energy Efficient GPU Thread Map for m-Simplex Domains"),
+ * fused into per-cell kernels on dense arrays that hold a discrete orthogonal
+ * m-simplex, for NVIDIA GB300 (sm_103a).
+ *
+ * Domain (Eq. 1, Sec. 1): Delta_n^m = { x in Z^m : x_i >= 0, x_1 + ... + x_m <= n },
+ * C(n+m, m) cells.  Arrays are dense, row-major with x_m fastest, `side` cells
+ * along every axis (side >= n + 1; element (x_1..x_m) at offset
+ * ((x_1*side + x_2)*side + ...)*side + x_m).  Only indices <= n are ever
+ * touched along the slow axes; along x_m a kernel may touch the rest of the
+ * 16-byte chunk that holds index n.
+ *
+ * Tiles: the array is cut into tiles of block^m cells; tile X (X in Z^m) covers
+ * cells block*X_i .. block*X_i + block - 1.  A CUDA block processes one tile.
+ * H (Sec. 4) sends a compact grid of CUDA blocks one-to-one onto the tiles
+ * that hold simplex cells; the bounding-box map f(x) = x (Sec. 2) launches all
+ * N^m tiles and lets the empty ones exit.
+ *
+ * Conventions for every call:
+ *   - return value: SIMPLEX_OK (0) or one of the error codes below; on error
+ *     simplex_last_error() gives a message (thread-local), nothing is aborted
+ *     and no device trap is ever raised.
+ *   - device pointers are plain CUDA device addresses owned by the caller (the
+ *     library never frees them); `stream` is a cudaStream_t passed as void*
+ *     (NULL = legacy default stream).  Calls that take a stream are
+ *     asynchronous on it unless stated otherwise.
+ *   - simplex_map_t objects are owned by the library: create/destroy them in
+ *     pairs.  A map is not safe for concurrent calls from several host
+ *     threads.
+ */
+#ifndef SIMPLEX_H
+#define SIMPLEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SIMPLEX_OK 0
+#define SIMPLEX_EINVAL 1       /* bad argument (message says which) */
+#define SIMPLEX_ENOMEM 2       /* host or device allocation failed */
+#define SIMPLEX_ECUDA 3        /* a CUDA runtime or driver call failed */
+#define SIMPLEX_ETIMEOUT 4     /* a bounded device-side wait gave up */
+#define SIMPLEX_EUNSUPPORTED 5 /* valid request this build does not implement */
+
+/* ---- map modes ----------------------------------------------------------- */
+#define SIMPLEX_MODE_H 0  /* block-space map H (Sec. 4)                         */
+#define SIMPLEX_MODE_BB 1 /* bounding box f(x) = x over N^m tiles (Sec. 2, Eq. 3) */
+
+/* ---- visit-count levels ---------------------------------------------------- */
+#define SIMPLEX_LEVEL_BLOCK 0
+#define SIMPLEX_LEVEL_CELL 1
+
+typedef struct simplex_map *simplex_map_t;
+
+typedef struct simplex_map_info {
+    int32_t m;              /* simplex dimension */
+    int32_t r_inv;          /* 1/r, scale factor of the self-similar set (Sec. 6) */
+    int32_t beta;           /* replication factor beta of the self-similar set (Sec. 6) */
+    int32_t block;          /* tile side rho in cells */
+    int64_t n;              /* simplex size: x_1 + ... + x_m <= n */
+    int64_t side;           /* array side in cells */
+    int32_t N;              /* tiles per axis of the block lattice (power of two) */
+    int32_t log2N;
+    uint64_t cells;         /* C(n+m, m), Eq. 1 */
+    uint64_t useful_blocks; /* tiles holding at least one cell: C(floor(n/rho)+m, m) */
+    uint64_t h_blocks;      /* CUDA blocks one H launch starts */
+    uint64_t bb_blocks;     /* CUDA blocks one bounding-box launch starts (N^m) */
+    uint64_t h_set_blocks;  /* blocks of the self-similar set S (Eq. generic-m) */
+} simplex_map_info_t;
+
+/*
+ * simplex_map_create -- plan H for Delta_n^m with tile side `block`, array
+ * side n + 1.
+ *   m      2, 3 or 4.
+ *   n      >= 0.
+ *   r_inv  1/r, the scale factor of the self-similar set (Sec. 6, Eq.
+ *          generic-m); only 2 (r = 1/2, the paper's value) is implemented.
+ *   beta   replication factor (Sec. 6).  m = 2: 2 (Eq. map2d, Thm. 1).
+ *          m = 3: 2 (the packed map with the hinge of Sec. 4.3) or 3 (every
+ *          corner recursed, no hinge).  m = 4: 4 (every corner recursed;
+ *          Lemma 5 shows beta = 2 does not cover the 4-simplex).
+ *   block  tile side rho in cells, a power of two in [4, 256].
+ *   out    receives the new map.
+ * Allocates host memory only.  The lattice side N is the power of two at or
+ * above ceil((n+1)/rho) ("approach n from above", Sec. 4.2); tiles past the
+ * domain exit at once.  Errors: SIMPLEX_EINVAL for a bad argument,
+ * SIMPLEX_EUNSUPPORTED for r_inv != 2 or a beta this build does not map,
+ * SIMPLEX_ENOMEM.
+ */
+int simplex_map_create(int m, int64_t n, int r_inv, int beta, int block, simplex_map_t *out);
+
+/* As simplex_map_create, with arrays of side `side` >= n + 1 (padding lets
+ * rows start on 16-byte boundaries for any n). */
+int simplex_map_create_padded(int m, int64_t n, int r_inv, int beta, int block,
+                              int64_t side, simplex_map_t *out);
+
+/* Frees the map, its cached CUDA graphs and its capture stream.  NULL is a no-op. */
+int simplex_map_destroy(simplex_map_t map);
+
+/* Fills *out with the plan's sizes and block counts (host only). */
+int simplex_map_info(simplex_map_t map, simplex_map_info_t *out);
+
+/*
+ * simplex_map_block -- host-side evaluation of the map for one CUDA block.
+ * Runs the same integer decode the kernels run (H: Eq. map2d and its 3-simplex
+ * and generic-m extensions; BB: f(x) = x) for linear CUDA block index `v` of a
+ * launch in `mode`, and writes the tile coordinate X[0..m-1] (X[m-1] fastest)
+ * to `coord`.  *valid = 1 iff that block processes a tile holding a simplex
+ * cell, 0 if it exits (packing waste, overhang, or a tile past the domain).
+ * v must be < h_blocks (mode H) or bb_blocks (mode BB), else SIMPLEX_EINVAL.
+ * No GPU needed.
+ */
+int simplex_map_block(simplex_map_t map, int mode, uint64_t v, int32_t *coord, int *valid);
+
+/*
+ * simplex_write -- coordinate-write test (Table 1 test 2 as a store-only
+ * kernel): for every cell x of the domain, out[x] = splitmix32(seed ^ lin(x)),
+ * lin(x) the row-major index on side n + 1 reduced mod 2^32; splitmix32 adds
+ * 0x9E3779B9 and applies the MurmurHash3 32-bit finaliser.  Cells outside the
+ * domain are not written.
+ *   out   device, uint32, side^m elements; 16-byte aligned rows (side % 4 == 0
+ *         and a 16-byte aligned base) take the 16-byte store path, anything
+ *         else the 4-byte path.
+ *   mode  SIMPLEX_MODE_H or SIMPLEX_MODE_BB (identical results).
+ */
+int simplex_write(simplex_map_t map, uint32_t *out, uint32_t seed, int mode, void *stream);
+
+/*
+ * simplex_ca_init -- seeded Bernoulli state for the automaton: cell x of the
+ * domain becomes 1 iff splitmix32(seed ^ lin(x)) < threshold, else 0 (p =
+ * threshold / 2^32).  Cells outside the domain that share a 16-byte chunk with
+ * a domain cell are written 0; others are not written.
+ *   grid   device, uint8, side^m elements, m = 2 or 3, side % 16 == 0,
+ *          16-byte aligned base; must be all zero outside the domain (e.g.
+ *          allocated zeroed).
+ *   live   device uint64 or NULL: when given, the number of live cells is
+ *          ADDED to *live.
+ * Uses H for its launch.  Errors: SIMPLEX_EINVAL (layout, m), SIMPLEX_ECUDA.
+ */
+int simplex_ca_init(simplex_map_t map, uint8_t *grid, uint32_t seed, uint32_t threshold,
+                    unsigned long long *live, void *stream);
+
+/*
+ * simplex_ca_step -- one synchronous step of a life-like automaton on the
+ * domain (Table 1 test 4): neighbours are the 3^m - 1 Moore offsets, a
+ * neighbour outside the domain is dead, a dead cell with k live neighbours is
+ * born iff bit k of `birth` is set, a live one survives iff bit k of
+ * `survive` is set.  Each CUDA block stages its tile plus a one-cell halo in
+ * shared memory with one TMA tiled load (out-of-range cells read as 0) and
+ * writes the tile of `out` with 16-byte stores.
+ *   in, out  device, uint8 (0/1), side^m elements, distinct buffers,
+ *            side % 16 == 0, 16-byte aligned; both must be zero outside the
+ *            domain (the step writes only 0 there).
+ *   birth, survive  rule masks, bits 0..3^m-1.  B3/S23: 0x8, 0xC.
+ *   live     device uint64 or NULL: the number of live cells after the step
+ *            is ADDED to *live.
+ *   mode     SIMPLEX_MODE_H or SIMPLEX_MODE_BB (identical results).
+ * m = 2 supports block 32, 64, 128; m = 3 supports block 16, 32.
+ * A device-side wait that exceeds its bound is reported by a later
+ * simplex_device_status() call (SIMPLEX_ETIMEOUT); the kernel never hangs.
+ */
+int simplex_ca_step(simplex_map_t map, const uint8_t *in, uint8_t *out, uint32_t birth,
+                    uint32_t survive, unsigned long long *live, int mode, void *stream);
+
+/*
+ * simplex_ca_run -- `steps` steps a -> b -> a -> ..., as repeated
+ * simplex_ca_step calls; the final state is in `a` when steps is even, in `b`
+ * when odd.
+ *   live       device uint64[steps + 1] or NULL.  When given, the run zeroes
+ *              it, stores the live count of the initial state in live[0]
+ *              and the count after step s in live[s].
+ *   use_graph  nonzero: the launches are captured once into a CUDA graph
+ *              (cached on the map per argument set) and replayed on `stream`.
+ */
+int simplex_ca_run(simplex_map_t map, uint8_t *a, uint8_t *b, int steps, uint32_t birth,
+                   uint32_t survive, unsigned long long *live, int use_graph, int mode,
+                   void *stream);
+
+/*
+ * simplex_ca_run_host -- end-to-end run from and to HOST memory: copies
+ * host_in (side^m uint8) into device buffer a, runs simplex_ca_run on the
+ * device buffers a and b, then copies the final grid into host_out and the
+ * live counts into host_live (uint64[steps + 1], may be NULL; needs dev_live
+ * when given).  Synchronises `stream` before returning.  Pinned host memory
+ * gives full copy bandwidth; pageable memory works but is slower.
+ *   b must be zero outside the domain; a is overwritten from host_in.
+ */
+int simplex_ca_run_host(simplex_map_t map, const uint8_t *host_in, uint8_t *host_out,
+                        uint8_t *a, uint8_t *b, int steps, uint32_t birth, uint32_t survive,
+                        unsigned long long *dev_live, unsigned long long *host_live,
+                        int use_graph, int mode, void *stream);
+
+/*
+ * simplex_visit_count -- coverage check of the map (Def. 1: every simplex
+ * block gets a unique CUDA block).  Launches the map in `mode` and
+ * increments, with atomics:
+ *   level SIMPLEX_LEVEL_BLOCK: counts[X] once per CUDA block that processes
+ *     tile X; counts is uint32, dense NB^m with NB = ceil((n+1)/block).
+ *   level SIMPLEX_LEVEL_CELL: counts[x] once per cell a thread processes;
+ *     counts is uint32, side^m.
+ * A correct map leaves 1 inside the domain and 0 outside.  counts must be
+ * zeroed by the caller.
+ */
+int simplex_visit_count(simplex_map_t map, uint32_t *counts, int level, int mode, void *stream);
+
+/*
+ * simplex_device_status -- reads and clears the library's device-side error
+ * word on the current device (synchronous).  *out receives 0 when no kernel
+ * gave up a bounded wait since the last call; the call returns
+ * SIMPLEX_ETIMEOUT if one did.
+ */
+int simplex_device_status(uint32_t *out);
+
+/* Message for the last failed call on this host thread ("" if none). */
+const char *simplex_last_error(void);
+
+/* Library version string. */
+const char *simplex_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMPLEX_H */

@@ -64,6 +64,8 @@ def _load():
         lib.oracle_ca_step.restype = u64
         lib.oracle_ca_run.argtypes = [i32, i64, i32, u32, u32, u8p, u8p, u64p]
         lib.oracle_ca_run.restype = None
+        lib.oracle_ca_cells.argtypes = [i32, i64, u32, u32, u8p, ctypes.POINTER(ctypes.c_int64), i64, u8p]
+        lib.oracle_ca_cells.restype = None
         lib.oracle_block_indicator.argtypes = [i32, i64, i32, u32p]
         lib.oracle_block_indicator.restype = None
         _lib = lib
@@ -124,6 +126,18 @@ def ca_run(m: int, n: int, steps: int, birth: int, survive: int, grid: np.ndarra
     _load().oracle_ca_run(m, n, steps, birth, survive, _ptr(a, ctypes.c_uint8),
                           _ptr(b, ctypes.c_uint8), _ptr(live, ctypes.c_uint64))
     return (a if steps % 2 == 0 else b), live
+
+
+def ca_cells(m: int, n: int, birth: int, survive: int, grid: np.ndarray, coords: np.ndarray) -> np.ndarray:
+    """Next state of the listed cells (coords: [k, m] int64), computed one by one."""
+    src = np.ascontiguousarray(grid, dtype=np.uint8)
+    assert src.shape == dense_shape(m, n)
+    c = np.ascontiguousarray(coords, dtype=np.int64)
+    assert c.ndim == 2 and c.shape[1] == m and (c.sum(1) <= n).all() and (c >= 0).all()
+    out = np.zeros(len(c), dtype=np.uint8)
+    _load().oracle_ca_cells(m, n, birth, survive, _ptr(src, ctypes.c_uint8),
+                            c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(c), _ptr(out, ctypes.c_uint8))
+    return out
 
 
 def block_indicator(m: int, n: int, rho: int) -> np.ndarray:

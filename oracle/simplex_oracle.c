@@ -256,3 +256,38 @@ void oracle_block_indicator(int m, int64_t n, int rho, uint32_t *ind)
                         ind[(((x1 / rho) * NB + x2 / rho) * NB + x3 / rho) * NB + x4 / rho] = 1;
     }
 }
+
+/* Next state of `count` listed cells of the domain, each given by m
+ * coordinates in `coords` (cell i at coords[i*m .. i*m + m - 1]), computed one
+ * by one from grid `in` (dense D^m) exactly as oracle_ca_step does; out[i]
+ * receives the state.  Lets a test check sampled cells of a grid too large to
+ * step on the CPU as a whole. */
+void oracle_ca_cells(int m, int64_t n, uint32_t birth, uint32_t survive, const uint8_t *in,
+                     const int64_t *coords, int64_t count, uint8_t *out)
+{
+    const int64_t D = n + 1;
+    for (int64_t i = 0; i < count; i++) {
+        const int64_t *x = coords + i * m;
+        int k = 0;
+        uint8_t alive = 0;
+        if (m == 2) {
+            for (int d1 = -1; d1 <= 1; d1++)
+                for (int d2 = -1; d2 <= 1; d2++) {
+                    if (d1 == 0 && d2 == 0) continue;
+                    int64_t y1 = x[0] + d1, y2 = x[1] + d2;
+                    if (in_domain2(y1, y2, n)) k += in[y1 * D + y2];
+                }
+            alive = in[x[0] * D + x[1]];
+        } else if (m == 3) {
+            for (int d1 = -1; d1 <= 1; d1++)
+                for (int d2 = -1; d2 <= 1; d2++)
+                    for (int d3 = -1; d3 <= 1; d3++) {
+                        if (d1 == 0 && d2 == 0 && d3 == 0) continue;
+                        int64_t y1 = x[0] + d1, y2 = x[1] + d2, y3 = x[2] + d3;
+                        if (in_domain3(y1, y2, y3, n)) k += in[(y1 * D + y2) * D + y3];
+                    }
+            alive = in[(x[0] * D + x[1]) * D + x[2]];
+        }
+        out[i] = alive ? (uint8_t)((survive >> k) & 1u) : (uint8_t)((birth >> k) & 1u);
+    }
+}

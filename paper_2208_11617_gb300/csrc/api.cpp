@@ -1,0 +1,500 @@
+// api.cpp -- the C ABI of libsimplex (include/simplex.h): argument checks, the
+// host-side launch plan, TMA tensor maps, CUDA-graph capture of automaton
+// runs, and the error model (status codes + thread-local message; nothing
+// aborts, no device trap).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/simplex.h"
+#include "hmap.cuh"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SIMPLEX_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+int ilog2_i64(int64_t x)
+{
+    int l = 0;
+    while ((int64_t(1) << (l + 1)) <= x) ++l;
+    return l;
+}
+
+uint64_t ipow(uint64_t b, int e)
+{
+    uint64_t r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+uint64_t binom(uint64_t n, int k)
+{
+    // C(n, k) for small k, exact in 128-bit intermediate
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return (uint64_t)r;
+}
+
+struct GraphEntry {
+    uint8_t *a, *b;
+    int steps;
+    uint32_t birth, survive;
+    unsigned long long *live;
+    int mode;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct simplex_map {
+    sx::Plan plan;
+    int r_inv;
+    int device = -1;
+    cudaStream_t capture = nullptr;
+    std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, sx::Plan *p)
+{
+    if (m < 2 || m > 4) return fail(SIMPLEX_EINVAL, "m must be 2, 3 or 4 (got %d)", m);
+    if (n < 0) return fail(SIMPLEX_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
+    if (r_inv != 2)
+        return fail(SIMPLEX_EUNSUPPORTED, "only r = 1/2 (r_inv = 2) is implemented (got r_inv = %d)", r_inv);
+    const bool beta_ok = (m == 2 && beta == 2) || (m == 3 && (beta == 2 || beta == 3)) || (m == 4 && beta == 4);
+    if (!beta_ok)
+        return fail(SIMPLEX_EUNSUPPORTED,
+                    "beta = %d does not give a covering map for m = %d (m=2: 2; m=3: 2 or 3; m=4: 4)", beta, m);
+    if (!is_pow2(block) || block < 4 || block > 256)
+        return fail(SIMPLEX_EINVAL, "block must be a power of two in [4, 256] (got %d)", block);
+    if (side < n + 1) return fail(SIMPLEX_EINVAL, "side (%lld) must be >= n + 1", (long long)side);
+    const int64_t nb = (n + block) / block;  // ceil((n+1)/rho)
+    int64_t N = 1;
+    int logN = 0;
+    while (N < nb) {
+        N <<= 1;
+        ++logN;
+    }
+    if (logN > 15) return fail(SIMPLEX_EINVAL, "n / block too large: %lld tiles per axis (max 32768)", (long long)nb);
+    // array size in elements must fit comfortably in 63 bits
+    {
+        long double tot = 1;
+        for (int i = 0; i < m; ++i) tot *= (long double)side;
+        if (tot > 4.0e18L) return fail(SIMPLEX_EINVAL, "side^m too large");
+    }
+
+    std::memset(p, 0, sizeof *p);
+    p->m = m;
+    p->rho = block;
+    p->log_rho = ilog2_i64(block);
+    p->N = (int32_t)N;
+    p->logN = logN;
+    p->beta = beta;
+    p->n = n;
+    p->side = side;
+    p->bb_blocks = ipow((uint64_t)N, m);
+    const uint64_t h2 = sx::h2_cover_blocks((int32_t)N);
+    if (m == 2) {
+        p->h_blocks = h2;
+    } else if (m == 3 && beta == 2) {
+        const uint64_t half = (uint64_t)N / 2;
+        p->h3_cube = half * half * half;
+        p->h3_layer = N >= 4 ? half * ((uint64_t)N / 4) * (half - 1) : 0;
+        p->h_blocks = p->h3_cube + p->h3_layer + h2;
+    } else {
+        uint64_t total = h2;
+        for (int d = 3; d <= m; ++d) {
+            uint64_t acc = 0;
+            p->level_end[d][0] = 0;
+            for (int k = 1; k <= logN; ++k) {
+                acc += ipow((uint64_t)d, k - 1) * ipow((uint64_t)(N >> k), d);
+                p->level_end[d][k] = acc;
+            }
+            p->cube_total[d] = acc;
+            total += acc;
+        }
+        p->h_blocks = total;
+    }
+    return SIMPLEX_OK;
+}
+
+sx::Rule make_rule(int m, uint32_t birth, uint32_t survive)
+{
+    sx::Rule r;
+    std::memset(&r, 0, sizeof r);
+    const int kmax = m == 2 ? 9 : 27;  // largest neighbourhood sum including the cell
+    for (int s = 0; s <= kmax; ++s) {
+        const bool b = s <= kmax - 1 && ((birth >> s) & 1u);
+        const bool sv = s >= 1 && ((survive >> (s - 1)) & 1u);
+        if (!b && !sv) continue;
+        r.kbytes[r.nk] = 0x01010101u * (uint32_t)s;
+        r.bsel[r.nk] = b ? 0xffffffffu : 0u;
+        r.ssel[r.nk] = sv ? 0xffffffffu : 0u;
+        ++r.nk;
+    }
+    return r;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
+}
+
+// Tensor map over a uint8 grid: extent n + 1 along every axis (cells past the
+// domain's bounding box read as zero), row pitch `side`, box of the tile plus
+// its halo: (rho + 32) x (rho + 2) [x (rho + 2)].
+int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3], estr[3] = {1, 1, 1};
+    for (int i = 0; i < p.m; ++i) dims[i] = (cuuint64_t)(p.n + 1);
+    strides[0] = (cuuint64_t)p.side;
+    if (p.m == 3) strides[1] = (cuuint64_t)(p.side * p.side);
+    box[0] = (cuuint32_t)(p.rho + 32);
+    box[1] = (cuuint32_t)(p.rho + 2);
+    box[2] = (cuuint32_t)(p.rho + 2);
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, (cuuint32_t)p.m, const_cast<void *>(base), dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return SIMPLEX_OK;
+}
+
+bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+int check_map(simplex_map_t map)
+{
+    if (!map) return fail(SIMPLEX_EINVAL, "map is NULL");
+    return SIMPLEX_OK;
+}
+
+int check_mode(int mode)
+{
+    if (mode != SIMPLEX_MODE_H && mode != SIMPLEX_MODE_BB)
+        return fail(SIMPLEX_EINVAL, "mode must be SIMPLEX_MODE_H or SIMPLEX_MODE_BB (got %d)", mode);
+    return SIMPLEX_OK;
+}
+
+int check_ca_layout(const sx::Plan &p, const void *grid, const char *name)
+{
+    if (p.m != 2 && p.m != 3) return fail(SIMPLEX_EINVAL, "the automaton is implemented for m = 2 and 3 (map has m = %d)", p.m);
+    if (!grid) return fail(SIMPLEX_EINVAL, "%s is NULL", name);
+    if (!aligned16(grid)) return fail(SIMPLEX_EINVAL, "%s must be 16-byte aligned", name);
+    if (p.side % 16 != 0) return fail(SIMPLEX_EINVAL, "the automaton needs side %% 16 == 0 (side = %lld)", (long long)p.side);
+    if (p.rho < 16) return fail(SIMPLEX_EINVAL, "the automaton needs block >= 16 (block = %d)", p.rho);
+    return SIMPLEX_OK;
+}
+
+int step_once(simplex_map_t map, const uint8_t *in, uint8_t *out, const sx::Rule &rule,
+              unsigned long long *live, int mode, cudaStream_t st)
+{
+    const sx::Plan &p = map->plan;
+    CUtensorMap tm;
+    int rc = make_tensor_map(p, in, &tm);
+    if (rc) return rc;
+    cudaError_t e = p.m == 2 ? sx::launch_ca2_step(p, tm, out, rule, mode, live, st)
+                             : sx::launch_ca3_step(p, tm, out, rule, mode, live, st);
+    if (e != cudaSuccess) return cuda_fail(e, "automaton step launch");
+    return SIMPLEX_OK;
+}
+
+int check_step_args(simplex_map_t map, const uint8_t *in, const uint8_t *out, int mode)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    const sx::Plan &p = map->plan;
+    if ((rc = check_ca_layout(p, in, "in")) || (rc = check_ca_layout(p, out, "out"))) return rc;
+    if (in == out) return fail(SIMPLEX_EINVAL, "in and out must be distinct buffers");
+    const bool ok = p.m == 2 ? sx::ca2_supports(p.rho) : sx::ca3_supports(p.rho);
+    if (!ok)
+        return fail(SIMPLEX_EUNSUPPORTED, "automaton step for m = %d supports block %s (got %d)", p.m,
+                    p.m == 2 ? "32, 64, 128" : "16, 32", p.rho);
+    return SIMPLEX_OK;
+}
+
+// The whole run as stream work: zero live, count live[0], then the steps.
+int enqueue_run(simplex_map_t map, uint8_t *a, uint8_t *b, int steps, const sx::Rule &rule,
+                unsigned long long *live, int mode, cudaStream_t st)
+{
+    if (live) {
+        cudaError_t e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * (size_t)(steps + 1), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(live)");
+        e = sx::launch_ca_count(map->plan, a, live, st);
+        if (e != cudaSuccess) return cuda_fail(e, "live count launch");
+    }
+    for (int s = 1; s <= steps; ++s) {
+        const uint8_t *src = (s & 1) ? a : b;
+        uint8_t *dst = (s & 1) ? b : a;
+        int rc = step_once(map, src, dst, rule, live ? live + s : nullptr, mode, st);
+        if (rc) return rc;
+    }
+    return SIMPLEX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int simplex_map_create_padded(int m, int64_t n, int r_inv, int beta, int block, int64_t side, simplex_map_t *out)
+{
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    *out = nullptr;
+    sx::Plan p;
+    int rc = build_plan(m, n, r_inv, beta, block, side, &p);
+    if (rc) return rc;
+    simplex_map *map = new (std::nothrow) simplex_map();
+    if (!map) return fail(SIMPLEX_ENOMEM, "host allocation failed");
+    map->plan = p;
+    map->r_inv = r_inv;
+    *out = map;
+    return SIMPLEX_OK;
+}
+
+int simplex_map_create(int m, int64_t n, int r_inv, int beta, int block, simplex_map_t *out)
+{
+    return simplex_map_create_padded(m, n, r_inv, beta, block, n + 1, out);
+}
+
+int simplex_map_destroy(simplex_map_t map)
+{
+    if (!map) return SIMPLEX_OK;
+    for (auto &g : map->graphs) cudaGraphExecDestroy(g.exec);
+    if (map->capture) cudaStreamDestroy(map->capture);
+    delete map;
+    return SIMPLEX_OK;
+}
+
+int simplex_map_info(simplex_map_t map, simplex_map_info_t *out)
+{
+    int rc;
+    if ((rc = check_map(map))) return rc;
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    const sx::Plan &p = map->plan;
+    std::memset(out, 0, sizeof *out);
+    out->m = p.m;
+    out->r_inv = map->r_inv;
+    out->beta = p.beta;
+    out->block = p.rho;
+    out->n = p.n;
+    out->side = p.side;
+    out->N = p.N;
+    out->log2N = p.logN;
+    out->cells = binom((uint64_t)p.n + (uint64_t)p.m, p.m);
+    out->useful_blocks = binom((uint64_t)(p.n / p.rho) + (uint64_t)p.m, p.m);
+    out->h_blocks = p.h_blocks;
+    out->bb_blocks = p.bb_blocks;
+    // Eq. generic-m with r = 1/2: (N^m - beta^log2 N) / (2^m - beta)
+    out->h_set_blocks = (ipow((uint64_t)p.N, p.m) - ipow((uint64_t)p.beta, p.logN)) /
+                        ((uint64_t(1) << p.m) - (uint64_t)p.beta);
+    return SIMPLEX_OK;
+}
+
+int simplex_map_block(simplex_map_t map, int mode, uint64_t v, int32_t *coord, int *valid)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    if (!coord || !valid) return fail(SIMPLEX_EINVAL, "coord and valid must not be NULL");
+    const sx::Plan &p = map->plan;
+    const uint64_t nb = mode == SIMPLEX_MODE_BB ? p.bb_blocks : p.h_blocks;
+    if (v >= nb) return fail(SIMPLEX_EINVAL, "block index %llu out of range (%llu blocks)",
+                             (unsigned long long)v, (unsigned long long)nb);
+    int32_t X[sx::kMaxM] = {0, 0, 0, 0};
+    bool ok = false;
+    switch (p.m) {
+    case 2: ok = sx::decode<2>(p, mode, v, X); break;
+    case 3: ok = sx::decode<3>(p, mode, v, X); break;
+    case 4: ok = sx::decode<4>(p, mode, v, X); break;
+    }
+    for (int i = 0; i < p.m; ++i) coord[i] = X[i];
+    if (ok) {
+        int64_t s = 0;
+        for (int i = 0; i < p.m; ++i) s += X[i];
+        ok = s * p.rho <= p.n;
+    }
+    *valid = ok ? 1 : 0;
+    return SIMPLEX_OK;
+}
+
+int simplex_write(simplex_map_t map, uint32_t *out, uint32_t seed, int mode, void *stream)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    if ((reinterpret_cast<uintptr_t>(out) & 3u) != 0) return fail(SIMPLEX_EINVAL, "out must be 4-byte aligned");
+    const sx::Plan &p = map->plan;
+    const bool vec = aligned16(out) && (p.side % 4 == 0);
+    cudaError_t e = sx::launch_write(p, out, seed, mode, vec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "write launch");
+    return SIMPLEX_OK;
+}
+
+int simplex_ca_init(simplex_map_t map, uint8_t *grid, uint32_t seed, uint32_t threshold,
+                    unsigned long long *live, void *stream)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_ca_layout(map->plan, grid, "grid"))) return rc;
+    cudaError_t e = sx::launch_ca_init(map->plan, grid, seed, threshold, live, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    return SIMPLEX_OK;
+}
+
+int simplex_ca_step(simplex_map_t map, const uint8_t *in, uint8_t *out, uint32_t birth, uint32_t survive,
+                    unsigned long long *live, int mode, void *stream)
+{
+    int rc = check_step_args(map, in, out, mode);
+    if (rc) return rc;
+    const sx::Rule rule = make_rule(map->plan.m, birth, survive);
+    return step_once(map, in, out, rule, live, mode, static_cast<cudaStream_t>(stream));
+}
+
+int simplex_ca_run(simplex_map_t map, uint8_t *a, uint8_t *b, int steps, uint32_t birth, uint32_t survive,
+                   unsigned long long *live, int use_graph, int mode, void *stream)
+{
+    int rc = check_step_args(map, a, b, mode);
+    if (rc) return rc;
+    if (steps < 0) return fail(SIMPLEX_EINVAL, "steps must be >= 0 (got %d)", steps);
+    const sx::Rule rule = make_rule(map->plan.m, birth, survive);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!use_graph) return enqueue_run(map, a, b, steps, rule, live, mode, st);
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (map->device >= 0 && map->device != dev)
+        return fail(SIMPLEX_EINVAL, "map was first used with graphs on device %d, now %d", map->device, dev);
+    if (!map->capture) {
+        e = cudaStreamCreateWithFlags(&map->capture, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+        map->device = dev;
+    }
+    e = map->plan.m == 2 ? sx::ca2_prepare(map->plan.rho) : sx::ca3_prepare(map->plan.rho);
+    if (e != cudaSuccess) return cuda_fail(e, "setting the kernel shared-memory limit");
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : map->graphs)
+        if (g.a == a && g.b == b && g.steps == steps && g.birth == birth && g.survive == survive && g.live == live &&
+            g.mode == mode)
+            exec = g.exec;
+    if (!exec) {
+        e = cudaStreamBeginCapture(map->capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        rc = enqueue_run(map, a, b, steps, rule, live, mode, map->capture);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(map->capture, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (map->graphs.size() >= 8) {
+            cudaGraphExecDestroy(map->graphs.front().exec);
+            map->graphs.erase(map->graphs.begin());
+        }
+        map->graphs.push_back(GraphEntry{a, b, steps, birth, survive, live, mode, exec});
+    }
+    e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return SIMPLEX_OK;
+}
+
+int simplex_ca_run_host(simplex_map_t map, const uint8_t *host_in, uint8_t *host_out, uint8_t *a, uint8_t *b,
+                        int steps, uint32_t birth, uint32_t survive, unsigned long long *dev_live,
+                        unsigned long long *host_live, int use_graph, int mode, void *stream)
+{
+    int rc;
+    if ((rc = check_map(map))) return rc;
+    if (!host_in || !host_out) return fail(SIMPLEX_EINVAL, "host_in and host_out must not be NULL");
+    if (host_live && !dev_live) return fail(SIMPLEX_EINVAL, "host_live needs dev_live");
+    const sx::Plan &p = map->plan;
+    size_t bytes = 1;
+    for (int i = 0; i < p.m; ++i) bytes *= (size_t)p.side;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(a, host_in, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(host_in -> a)");
+    rc = simplex_ca_run(map, a, b, steps, birth, survive, dev_live, use_graph, mode, stream);
+    if (rc) return rc;
+    const uint8_t *fin = (steps % 2 == 0) ? a : b;
+    e = cudaMemcpyAsync(host_out, fin, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(final -> host_out)");
+    if (host_live) {
+        e = cudaMemcpyAsync(host_live, dev_live, sizeof(unsigned long long) * (size_t)(steps + 1),
+                            cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(live -> host_live)");
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return SIMPLEX_OK;
+}
+
+int simplex_visit_count(simplex_map_t map, uint32_t *counts, int level, int mode, void *stream)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    if (!counts) return fail(SIMPLEX_EINVAL, "counts is NULL");
+    if (level != SIMPLEX_LEVEL_BLOCK && level != SIMPLEX_LEVEL_CELL)
+        return fail(SIMPLEX_EINVAL, "level must be SIMPLEX_LEVEL_BLOCK or SIMPLEX_LEVEL_CELL (got %d)", level);
+    cudaError_t e = sx::launch_visit(map->plan, counts, level, mode, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "visit-count launch");
+    return SIMPLEX_OK;
+}
+
+int simplex_device_status(uint32_t *out)
+{
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    uint32_t s2 = 0, s3 = 0;
+    cudaError_t e = sx::ca2_read_status(&s2);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+    e = sx::ca3_read_status(&s3);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+    *out = s2 | s3;
+    if (*out) return fail(SIMPLEX_ETIMEOUT, "a kernel gave up a bounded wait for its TMA load (status 0x%x)", *out);
+    return SIMPLEX_OK;
+}
+
+const char *simplex_last_error(void) { return g_last_error.c_str(); }
+
+const char *simplex_version(void) { return "libsimplex 0.1 (sm_103a)"; }
+
+}  // extern "C"

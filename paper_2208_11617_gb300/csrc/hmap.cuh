@@ -1,0 +1,246 @@
+// hmap.cuh -- the launch plan and the block-space maps of arXiv 2208.11617.
+//
+// Everything here is integer-only and shared by the kernels (device) and by the
+// host-side map evaluation (simplex_map_block), so the host tests exercise the
+// exact code the GPU runs.
+//
+// Frames.  Tiles have side rho cells; the block lattice has N tiles per axis,
+// N a power of two with N*rho >= n + 1.  Block coordinates X = (X_1..X_m)
+// with the orthogonal corner at the origin and X_m the fastest (memory) axis.
+// Every tile holding a simplex cell satisfies X_1 + ... + X_m <= N - 1; the
+// maps below cover that block simplex exactly once (tiles of it past the
+// domain, rho * sum(X) > n, exit in the kernels).
+//
+// Map summary (one linear CUDA block index v per launch):
+//   m = 2  H2 (Sec. 4.1, Thm. 1, Eq. map2d) on the N/2 x (N-1) grid covers the
+//          blocks with sum <= N-2; a row of N blocks covers the diagonal
+//          sum = N-1 ("extra threads at the diagonal", Sec. 4.1).
+//   m = 3  beta = 2: H3 (Sec. 4.3): the big cube (N/2)^3 at the corner, a layer
+//          of height N/4 holding the smaller cubes laid out by the 2-D levels
+//          b, q of Thm. 1, and the hinge that reflects each cube's overhang
+//          onto the third corner; the plane sum = N-1 is a 2-simplex of blocks
+//          mapped by H2 plus its diagonal.
+//          beta = 3: the generic construction below.
+//   m >= 3 generic, r = 1/2, beta = m (Sec. 6, Eq. generic-m): level k holds
+//          m^(k-1) cubes of side b = N / 2^k; a cube is named by k-1 base-m
+//          digits, each digit choosing the corner axis of one recursion step;
+//          blocks of a cube's overhang (local sum > 2b-2) exit.  The plane
+//          sum = N-1 is the (m-1)-dimensional cover of the same kind.
+#pragma once
+
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define SX_HD __host__ __device__ __forceinline__
+#else
+#define SX_HD inline
+#endif
+
+namespace sx {
+
+constexpr int kMaxM = 4;
+constexpr int kMaxLevels = 24;  // log2 N <= 15 keeps every count well inside 64 bits
+
+enum MapKind : int { kMapH = 0, kMapBB = 1 };
+
+// Launch plan, passed by value to every kernel.
+struct Plan {
+    int32_t m;
+    int32_t rho, log_rho;
+    int32_t N, logN;
+    int32_t beta;
+    int64_t n;
+    int64_t side;
+    uint64_t h_blocks;   // CUDA blocks of one H launch
+    uint64_t bb_blocks;  // N^m
+    // H3 (beta = 2): region sizes
+    uint64_t h3_cube, h3_layer;
+    // generic cubes of dimension d (3..kMaxM): level_end[d][k] = number of
+    // blocks in levels 1..k; cube_total[d] = level_end[d][logN]
+    uint64_t level_end[kMaxM + 1][kMaxLevels + 1];
+    uint64_t cube_total[kMaxM + 1];
+};
+
+// floor(log2 x) for x >= 1 from the count of leading zeros (Sec. 4.1: the
+// paper's "bits - clz" read with bits = 31 for a 32-bit word).
+SX_HD int ilog2_u32(uint32_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return 31 - __clz(x);
+#else
+    return 31 - __builtin_clz(x);
+#endif
+}
+
+// Eq. map2d of Thm. 1.  (wx, wy) in [0, N/2) x [0, N-1) -> the paper's
+// (H_x, H_y) = (wx + q b, wy + 2 q b + 1) with b = 2^floor(log2(wy + 1)),
+// q = floor(wx / b); H_x < H_y.  Returned in the corner frame:
+// X1 = N - 1 - H_y, X2 = H_x, so X1 + X2 <= N - 2.  b and q are returned too.
+SX_HD void h2_map(int32_t wx, int32_t wy, int32_t N, int32_t &X1, int32_t &X2, int32_t &b,
+                  int32_t &q)
+{
+    const int lb = ilog2_u32((uint32_t)wy + 1u);
+    b = 1 << lb;
+    q = wx >> lb;
+    const int32_t hx = wx + q * b;
+    const int32_t hy = wy + 2 * q * b + 1;
+    X1 = N - 1 - hy;
+    X2 = hx;
+}
+
+// Blocks of the 2-simplex sum <= N-1: H2 grid, then the diagonal row.
+SX_HD uint64_t h2_cover_blocks(int32_t N) { return (uint64_t)(N >> 1) * (uint64_t)(N - 1) + (uint64_t)N; }
+
+SX_HD bool h2_cover(uint64_t v, int32_t N, int32_t logN, int32_t *X)
+{
+    const uint64_t grid = (uint64_t)(N >> 1) * (uint64_t)(N - 1);
+    if (v < grid) {
+        const int32_t wx = (int32_t)(v & (uint64_t)((N >> 1) - 1));
+        const int32_t wy = (int32_t)(v >> (logN - 1));
+        int32_t b, q;
+        h2_map(wx, wy, N, X[0], X[1], b, q);
+        return true;
+    }
+    const int32_t d = (int32_t)(v - grid);
+    X[0] = d;
+    X[1] = N - 1 - d;
+    return true;
+}
+
+// Hinge of Sec. 4.3: a cube of side b with corner (c1, c2, 0) and local
+// offset l; if l falls past the tetrahedron (l1 + l2 + l3 >= 2b - 1), it is
+// reflected in x, y and complemented in z onto the cube's third corner
+// (c1, c2, b) + ... which that overhang fills exactly.
+SX_HD void h3_place(int32_t c1, int32_t c2, int32_t b, int32_t l1, int32_t l2, int32_t l3, int32_t *X)
+{
+    if (l1 + l2 + l3 >= 2 * b - 1) {
+        X[0] = c1 + b - 1 - l1;
+        X[1] = c2 + b - 1 - l2;
+        X[2] = 2 * b - 1 - l3;
+    } else {
+        X[0] = c1 + l1;
+        X[1] = c2 + l2;
+        X[2] = l3;
+    }
+}
+
+SX_HD bool h3_cover(const Plan &p, uint64_t v, int32_t *X)
+{
+    const int32_t N = p.N, logN = p.logN, half = N >> 1;
+    if (v < p.h3_cube) {
+        // the big cube (N/2)^3 at the orthogonal corner
+        const int lh = logN - 1;
+        const int32_t l3 = (int32_t)(v & (uint64_t)(half - 1));
+        const int32_t l2 = (int32_t)((v >> lh) & (uint64_t)(half - 1));
+        const int32_t l1 = (int32_t)(v >> (2 * lh));
+        h3_place(0, 0, half, l1, l2, l3, X);
+        return true;
+    }
+    v -= p.h3_cube;
+    if (v < p.h3_layer) {
+        // layer of height N/4: cubes of side b <= N/4 stacked by the 2-D levels
+        const int32_t wx = (int32_t)(v & (uint64_t)(half - 1));
+        const uint64_t t = v >> (logN - 1);
+        const int32_t lz = (int32_t)(t & (uint64_t)((N >> 2) - 1));
+        const int32_t wy = (int32_t)(t >> (logN - 2));
+        int32_t X1, X2, b, q;
+        h2_map(wx, wy, N, X1, X2, b, q);
+        if (lz >= b) return false;  // packing waste of the layer (Lemma 4)
+        const int32_t c1 = N - 2 * b - 2 * q * b, c2 = 2 * q * b;
+        h3_place(c1, c2, b, X1 - c1, X2 - c2, lz, X);
+        return true;
+    }
+    v -= p.h3_layer;
+    // diagonal plane X1 + X2 + X3 = N - 1 (Sec. 4.3 leaves it aside): a
+    // 2-simplex of blocks mapped by H2 plus its diagonal
+    int32_t Y[2];
+    h2_cover(v, N, logN, Y);
+    X[0] = Y[0];
+    X[1] = Y[1];
+    X[2] = N - 1 - Y[0] - Y[1];
+    return true;
+}
+
+// Generic self-similar cubes of dimension D (r = 1/2, beta = D), covering the
+// blocks with sum <= N - 2.
+template <int D>
+SX_HD bool cubes_generic(const Plan &p, uint64_t v, int32_t *X)
+{
+    const int32_t N = p.N, logN = p.logN;
+    int k = 1;
+    while (k < logN && v >= p.level_end[D][k]) ++k;
+    const int lb = logN - k;
+    const int32_t b = 1 << lb;
+    const uint64_t local = v - p.level_end[D][k - 1];
+    uint64_t c = local >> (D * lb);
+    const uint64_t l = local & ((1ull << (D * lb)) - 1ull);
+    int32_t corner[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) corner[i] = 0;
+    for (int j = k - 1; j >= 1; --j) {
+        const int dig = (int)(c % (uint64_t)D);
+        c /= (uint64_t)D;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+            if (i == dig) corner[i] += N >> j;
+    }
+    int32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const int32_t li = (int32_t)((l >> ((D - 1 - i) * lb)) & (uint64_t)(b - 1));
+        X[i] = corner[i] + li;
+        s += li;
+    }
+    return s <= 2 * b - 2;  // blocks of the cube's overhang exit
+}
+
+// Cover of {X in [0,N)^D : sum X <= N - 1}: the cubes, then the plane
+// sum = N - 1 as a (D-1)-dimensional cover.
+template <int D>
+struct Cover {
+    static SX_HD bool run(const Plan &p, uint64_t v, int32_t *X)
+    {
+        if (v < p.cube_total[D]) return cubes_generic<D>(p, v, X);
+        v -= p.cube_total[D];
+        const bool ok = Cover<D - 1>::run(p, v, X);
+        int32_t s = 0;
+#pragma unroll
+        for (int i = 0; i < D - 1; ++i) s += X[i];
+        X[D - 1] = p.N - 1 - s;
+        return ok;
+    }
+};
+
+template <>
+struct Cover<2> {
+    static SX_HD bool run(const Plan &p, uint64_t v, int32_t *X) { return h2_cover(v, p.N, p.logN, X); }
+};
+
+// The map of one launch: linear CUDA block index v -> tile X.  Returns false
+// when the block has no tile (packing waste or overhang).
+template <int M>
+SX_HD bool decode(const Plan &p, int kind, uint64_t v, int32_t *X)
+{
+    if (kind == kMapBB) {
+        // bounding box, f(x) = x (Eq. 3), on the N^m lattice linearised to 1-D
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            X[M - 1 - i] = (int32_t)((v >> (i * p.logN)) & (uint64_t)(p.N - 1));
+        return true;
+    }
+    if (M == 2) return h2_cover(v, p.N, p.logN, X);
+    if (M == 3 && p.beta == 2) return h3_cover(p, v, X);
+    return Cover<M>::run(p, v, X);
+}
+
+// rho * sum(X): first cell-coordinate sum of the tile.
+template <int M>
+SX_HD int64_t tile_base_sum(const Plan &p, const int32_t *X)
+{
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) s += X[i];
+    return s * p.rho;
+}
+
+}  // namespace sx

@@ -1,0 +1,180 @@
+// k_ca3.cu -- one step of a life-like automaton on the 3-simplex, fused with
+// the map (Table 1 test 4 on the tetrahedron, fixed-dead boundary, Sec. 5.1).
+//
+// One CUDA block per tile of RHO^3 uint8 cells (axes x1 slow .. x3 fast).  The
+// block decodes its tile with H (Sec. 4.3 packing with the hinge, or the
+// generic beta = 3 cubes) or the bounding box, stages the tile plus a one-cell
+// halo with a single 3-D TMA tiled load of (RHO + 32) x (RHO + 2) x (RHO + 2)
+// bytes, and each thread walks RZ planes along x1 for one (x2, 16-byte x3
+// chunk) column: per plane it forms the 3 x 3 sums P = h(x2-1) + h(x2) +
+// h(x2+1) of horizontal 3-sums, and the Moore-26 sum of three consecutive
+// planes, all byte-parallel in 32-bit registers.
+#include "common.cuh"
+#include "hmap.cuh"
+#include "kernels.h"
+
+namespace sx {
+
+static __device__ uint32_t g_ca3_status;
+
+template <int RHO, int RZ>
+__global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ))
+    ca3_step_kernel(const __grid_constant__ CUtensorMap tin, uint8_t *__restrict__ out, const Plan p,
+                    const Rule rule, int kind, uint64_t nblocks, unsigned long long *__restrict__ live)
+{
+    constexpr int TX = RHO / 16;
+    constexpr int BW = RHO + 32, BH = RHO + 2, BD = RHO + 2;
+    constexpr uint32_t kBoxBytes = BW * BH * BD;
+    extern __shared__ uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t red[32];
+    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX;
+    const int ty = (tid / TX) % RHO;         // x2 within the tile
+    const int tz = tid / (TX * RHO);         // plane segment along x1
+    uint32_t phase = 0, my_live = 0;
+    if (tid == 0) {
+        prefetch_tmap(&tin);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
+        int32_t X[3];
+        if (!decode<3>(p, kind, v, X)) continue;
+        const int64_t z0 = (int64_t)X[0] * RHO, y0 = (int64_t)X[1] * RHO, x0 = (int64_t)X[2] * RHO;
+        if (z0 + y0 + x0 > p.n) continue;
+        const bool partial = z0 + y0 + x0 + 3 * (RHO - 1) > p.n;
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar, kBoxBytes);
+            tma_load_3d(tile, &tin, (int32_t)(x0 - 16), (int32_t)(y0 - 1), (int32_t)(z0 - 1), &bar);
+        }
+        const bool ok = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&g_ca3_status, 1u);
+                mbar_wait_bounded(&bar, phase ^ 1u, kWaitLimitNs);
+            }
+            return;
+        }
+
+        // staged row (x2 = y0 + yy - 1, x1 = z0 + zz - 1) starts at (zz * BH + yy) * BW
+        const uint8_t *col = tile + 16 + 16 * tx;
+        const int64_t xc = x0 + 16 * tx;
+        const int64_t x2 = y0 + ty;
+        const int zb = tz * RZ;  // first output plane of this thread
+        uint32_t pp[4], pc[4], ac[4];
+        {
+            uint32_t h0[4], h1[4], h2[4], c[4];
+            const uint8_t *pl = col + (zb * BH + ty) * BW;
+            hsum_row(pl, h0, c);
+            hsum_row(pl + BW, h1, c);
+            hsum_row(pl + 2 * BW, h2, c);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) pp[w] = h0[w] + h1[w] + h2[w];
+            pl += BH * BW;
+            hsum_row(pl, h0, c);
+            hsum_row(pl + BW, h1, ac);
+            hsum_row(pl + 2 * BW, h2, c);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) pc[w] = h0[w] + h1[w] + h2[w];
+        }
+#pragma unroll
+        for (int i = 0; i < RZ; ++i) {
+            uint32_t h0[4], h1[4], h2[4], c[4], an[4], pn[4], s[4], nw[4];
+            const uint8_t *pl = col + ((zb + i + 2) * BH + ty) * BW;
+            hsum_row(pl, h0, c);
+            hsum_row(pl + BW, h1, an);
+            hsum_row(pl + 2 * BW, h2, c);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                pn[w] = h0[w] + h1[w] + h2[w];
+                s[w] = pp[w] + pc[w] + pn[w];
+            }
+            apply_rule4(s, ac, rule, nw);
+            const int64_t x1 = z0 + zb + i;
+            bool store = true;
+            if (partial) {
+                const int64_t c64 = p.n - x1 - x2 - xc + 1;
+                const int cnt = (int)(c64 < 0 ? 0 : (c64 > 16 ? 16 : c64));
+#pragma unroll
+                for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(cnt, w);
+                store = cnt > 0;
+            }
+            if (store) store16(out + (x1 * p.side + x2) * p.side + xc, nw);
+            my_live += __popc(nw[0]) + __popc(nw[1]) + __popc(nw[2]) + __popc(nw[3]);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                pp[w] = pc[w];
+                pc[w] = pn[w];
+                ac[w] = an[w];
+            }
+        }
+        __syncthreads();
+    }
+    if (live) block_add_u64(live, my_live, red);
+}
+
+bool ca3_supports(int rho) { return rho == 16 || rho == 32; }
+
+template <int RHO, int RZ>
+static cudaError_t prepare_t()
+{
+    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 128;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(ca3_step_kernel<RHO, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
+    return e;
+}
+
+template <int RHO, int RZ>
+static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
+                            unsigned long long *live, cudaStream_t st)
+{
+    constexpr int T = (RHO / 16) * RHO * (RHO / RZ);
+    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 128;
+    cudaError_t e = prepare_t<RHO, RZ>();
+    if (e != cudaSuccess) return e;
+    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const unsigned g = (unsigned)(nb < 0x7fffffffull ? (nb ? nb : 1) : 0x7fffffffull);
+    ca3_step_kernel<RHO, RZ><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
+                            unsigned long long *live, cudaStream_t st)
+{
+    switch (p.rho) {
+    case 16: return launch_t<16, 4>(p, tin, out, rule, kind, live, st);
+    case 32: return launch_t<32, 8>(p, tin, out, rule, kind, live, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t ca3_prepare(int rho)
+{
+    switch (rho) {
+    case 16: return prepare_t<16, 4>();
+    case 32: return prepare_t<32, 8>();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t ca3_read_status(uint32_t *out)
+{
+    uint32_t zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_ca3_status, sizeof(uint32_t));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(g_ca3_status, &zero, sizeof(uint32_t));
+}
+
+}  // namespace sx

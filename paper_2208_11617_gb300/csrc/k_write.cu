@@ -1,0 +1,119 @@
+// k_write.cu -- the coordinate-write test fused with the map (Table 1 test 2
+// as a store-only kernel) and the coverage (visit-count) kernels.
+//
+// One CUDA block per tile: the block decodes its tile with H (or the bounding
+// box), and its threads write the tile's cells in chunks of 4 consecutive
+// cells along x_m with one 16-byte store each.  Tiles that lie wholly inside
+// the domain (rho * sum(X) + m (rho - 1) <= n) take the predicate-free path;
+// only tiles on the diagonal band test each cell (Sec. 4.1: extra threads only
+// at the diagonal).
+#include "common.cuh"
+#include "hmap.cuh"
+#include "kernels.h"
+#include "tile.cuh"
+
+namespace sx {
+
+template <int M>
+__global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__restrict__ out, uint32_t seed,
+                                                    int kind, uint64_t nblocks, int vec)
+{
+    const uint32_t nchunks = 1u << (M * p.log_rho - 2);
+    for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
+        int32_t X[M];
+        if (!decode<M>(p, kind, v, X)) continue;
+        const int64_t s0 = tile_base_sum<M>(p, X);
+        if (s0 > p.n) continue;  // tile past the domain
+        const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
+        for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+            const ChunkPos<M> q = chunk_pos<M>(p, X, c, 2);
+            const uint32_t l0 = (uint32_t)q.lin;
+            if (!partial) {
+                const uint32_t h0 = splitmix32(seed ^ l0), h1 = splitmix32(seed ^ (l0 + 1u));
+                const uint32_t h2 = splitmix32(seed ^ (l0 + 2u)), h3 = splitmix32(seed ^ (l0 + 3u));
+                if (vec) {
+                    *reinterpret_cast<uint4 *>(out + q.addr) = make_uint4(h0, h1, h2, h3);
+                } else {
+                    out[q.addr] = h0;
+                    out[q.addr + 1] = h1;
+                    out[q.addr + 2] = h2;
+                    out[q.addr + 3] = h3;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (q.sum + j <= p.n) out[q.addr + j] = splitmix32(seed ^ (l0 + (uint32_t)j));
+            }
+        }
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) visit_kernel(const Plan p, uint32_t *__restrict__ counts, int level,
+                                                    int kind, uint64_t nblocks)
+{
+    const uint32_t nchunks = 1u << (M * p.log_rho - 2);
+    const int64_t nb = (p.n + p.rho) / p.rho;
+    for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
+        int32_t X[M];
+        if (!decode<M>(p, kind, v, X)) continue;
+        const int64_t s0 = tile_base_sum<M>(p, X);
+        if (s0 > p.n) continue;
+        if (level == 0) {
+            if (threadIdx.x == 0) {
+                int64_t b = 0;
+#pragma unroll
+                for (int i = 0; i < M; ++i) b = b * nb + X[i];
+                atomicAdd(counts + b, 1u);
+            }
+            continue;
+        }
+        const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
+        for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+            const ChunkPos<M> q = chunk_pos<M>(p, X, c, 2);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (!partial || q.sum + j <= p.n) atomicAdd(counts + q.addr + j, 1u);
+        }
+    }
+}
+
+static unsigned grid_for(uint64_t nblocks)
+{
+    const uint64_t cap = 0x7fffffffull;
+    return (unsigned)(nblocks < cap ? (nblocks ? nblocks : 1) : cap);
+}
+
+static unsigned threads_for(const Plan &p, int lw)
+{
+    const uint64_t nchunks = 1ull << (p.m * p.log_rho - lw);
+    return (unsigned)(nchunks < 256 ? nchunks : 256);
+}
+
+cudaError_t launch_write(const Plan &p, uint32_t *out, uint32_t seed, int kind, bool vec, cudaStream_t st)
+{
+    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const unsigned g = grid_for(nb), t = threads_for(p, 2);
+    switch (p.m) {
+    case 2: write_kernel<2><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
+    case 3: write_kernel<3><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
+    case 4: write_kernel<4><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_visit(const Plan &p, uint32_t *counts, int level, int kind, cudaStream_t st)
+{
+    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const unsigned g = grid_for(nb), t = threads_for(p, 2);
+    switch (p.m) {
+    case 2: visit_kernel<2><<<g, t, 0, st>>>(p, counts, level, kind, nb); break;
+    case 3: visit_kernel<3><<<g, t, 0, st>>>(p, counts, level, kind, nb); break;
+    case 4: visit_kernel<4><<<g, t, 0, st>>>(p, counts, level, kind, nb); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sx

@@ -1,0 +1,42 @@
+// kernels.h -- host-side launchers of the CUDA kernels (one per .cu file).
+// Each returns a cudaError_t from the launch; arguments are validated by the
+// C ABI layer before they get here.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmap.cuh"
+#include "rule.h"
+
+namespace sx {
+
+cudaError_t launch_write(const Plan &p, uint32_t *out, uint32_t seed, int kind, bool vec, cudaStream_t st);
+
+cudaError_t launch_visit(const Plan &p, uint32_t *counts, int level, int kind, cudaStream_t st);
+
+cudaError_t launch_ca_init(const Plan &p, uint8_t *grid, uint32_t seed, uint32_t threshold,
+                           unsigned long long *live, cudaStream_t st);
+
+cudaError_t launch_ca_count(const Plan &p, const uint8_t *grid, unsigned long long *live, cudaStream_t st);
+
+// TMA-staged automaton steps; `tin` maps the input grid (see make_tensor_map).
+bool ca2_supports(int rho);
+bool ca3_supports(int rho);
+cudaError_t launch_ca2_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
+                            int kind, unsigned long long *live, cudaStream_t st);
+cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
+                            int kind, unsigned long long *live, cudaStream_t st);
+
+// Sets the kernels' shared-memory limits for the current device (before any
+// stream capture).
+cudaError_t ca2_prepare(int rho);
+cudaError_t ca3_prepare(int rho);
+
+// Device error words of the TMA kernels (bounded waits that gave up).
+// Reads and clears; synchronous.
+cudaError_t ca2_read_status(uint32_t *out);
+cudaError_t ca3_read_status(uint32_t *out);
+
+}  // namespace sx

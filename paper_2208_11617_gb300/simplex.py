@@ -1,0 +1,257 @@
+"""Python binding of libsimplex (include/simplex.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes torch
+tensors (or host numpy arrays where the C call takes host memory); the work
+itself runs in the CUDA kernels of ``libsimplex.so``.  Importing this module
+fails loudly when the library has not been built -- there is no fallback.
+
+The stream of every call is torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsimplex.so")
+
+SIMPLEX_OK = 0
+SIMPLEX_EINVAL = 1
+SIMPLEX_ENOMEM = 2
+SIMPLEX_ECUDA = 3
+SIMPLEX_ETIMEOUT = 4
+SIMPLEX_EUNSUPPORTED = 5
+
+SIMPLEX_MODE_H = 0
+SIMPLEX_MODE_BB = 1
+SIMPLEX_LEVEL_BLOCK = 0
+SIMPLEX_LEVEL_CELL = 1
+
+EXPORTED = (
+    "simplex_map_create", "simplex_map_create_padded", "simplex_map_destroy", "simplex_map_info",
+    "simplex_map_block", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
+    "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
+    "simplex_version",
+)
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2208_11617_gb300.build` "
+                      "(the CUDA library is required; there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_i32, _i64, _u32, _u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+
+
+class SimplexMapInfo(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("r_inv", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("n", ctypes.c_int64), ("side", ctypes.c_int64),
+                ("N", ctypes.c_int32), ("log2N", ctypes.c_int32), ("cells", ctypes.c_uint64),
+                ("useful_blocks", ctypes.c_uint64), ("h_blocks", ctypes.c_uint64),
+                ("bb_blocks", ctypes.c_uint64), ("h_set_blocks", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _sig(name, args):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = _i32
+    return f
+
+
+_sig("simplex_map_create", [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(_vp)])
+_sig("simplex_map_create_padded", [_i32, _i64, _i32, _i32, _i32, _i64, ctypes.POINTER(_vp)])
+_sig("simplex_map_destroy", [_vp])
+_sig("simplex_map_info", [_vp, ctypes.POINTER(SimplexMapInfo)])
+_sig("simplex_map_block", [_vp, _i32, _u64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i32)])
+_sig("simplex_write", [_vp, _vp, _u32, _i32, _vp])
+_sig("simplex_ca_init", [_vp, _vp, _u32, _u32, _vp, _vp])
+_sig("simplex_ca_step", [_vp, _vp, _vp, _u32, _u32, _vp, _i32, _vp])
+_sig("simplex_ca_run", [_vp, _vp, _vp, _i32, _u32, _u32, _vp, _i32, _i32, _vp])
+_sig("simplex_ca_run_host", [_vp, _vp, _vp, _vp, _vp, _i32, _u32, _u32, _vp, _vp, _i32, _i32, _vp])
+_sig("simplex_visit_count", [_vp, _vp, _i32, _i32, _vp])
+_sig("simplex_device_status", [ctypes.POINTER(_u32)])
+_lib.simplex_last_error.argtypes = []
+_lib.simplex_last_error.restype = ctypes.c_char_p
+_lib.simplex_version.argtypes = []
+_lib.simplex_version.restype = ctypes.c_char_p
+
+
+class SimplexError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.simplex_last_error().decode()
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, where: str):
+    if rc != SIMPLEX_OK:
+        raise SimplexError(rc, where)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dptr(t: torch.Tensor | None, dtype, name: str, numel: int | None = None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements, has {t.numel()}")
+    return t.data_ptr()
+
+
+@dataclass
+class SimplexMap:
+    """A planned map (owns the C handle)."""
+    handle: int
+    info: SimplexMapInfo
+
+    @property
+    def m(self) -> int:
+        return self.info.m
+
+    @property
+    def n(self) -> int:
+        return self.info.n
+
+    @property
+    def side(self) -> int:
+        return self.info.side
+
+    @property
+    def numel(self) -> int:
+        return self.info.side ** self.info.m
+
+    @property
+    def shape(self) -> tuple:
+        return (self.info.side,) * self.info.m
+
+    def close(self):
+        if self.handle:
+            _lib.simplex_map_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, block: int = 16,
+                       side: int | None = None) -> SimplexMap:
+    """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4)."""
+    if beta is None:
+        beta = 2 if m <= 3 else m
+    h = _vp()
+    if side is None:
+        _check(_lib.simplex_map_create(m, n, r_inv, beta, block, ctypes.byref(h)), "simplex_map_create")
+    else:
+        _check(_lib.simplex_map_create_padded(m, n, r_inv, beta, block, side, ctypes.byref(h)),
+               "simplex_map_create_padded")
+    info = SimplexMapInfo()
+    _check(_lib.simplex_map_info(h, ctypes.byref(info)), "simplex_map_info")
+    return SimplexMap(h.value, info)
+
+
+def simplex_map_info(mp: SimplexMap) -> dict:
+    info = SimplexMapInfo()
+    _check(_lib.simplex_map_info(mp.handle, ctypes.byref(info)), "simplex_map_info")
+    return info.as_dict()
+
+
+def simplex_map_block(mp: SimplexMap, mode: int, v: int):
+    """Host evaluation of the map for CUDA block v: (tile coordinate tuple, valid)."""
+    coord = (ctypes.c_int32 * 4)()
+    valid = _i32()
+    _check(_lib.simplex_map_block(mp.handle, mode, v, coord, ctypes.byref(valid)), "simplex_map_block")
+    return tuple(coord[: mp.m]), bool(valid.value)
+
+
+def simplex_write(mp: SimplexMap, out: torch.Tensor, seed: int, mode: int = SIMPLEX_MODE_H):
+    p = _dptr(out, torch.int32, "out", mp.numel) if out.dtype == torch.int32 else \
+        _dptr(out, torch.uint32, "out", mp.numel)
+    _check(_lib.simplex_write(mp.handle, p, seed & 0xFFFFFFFF, mode, _stream()), "simplex_write")
+
+
+def simplex_ca_init(mp: SimplexMap, grid: torch.Tensor, seed: int, threshold: int,
+                    live: torch.Tensor | None = None):
+    _check(_lib.simplex_ca_init(mp.handle, _dptr(grid, torch.uint8, "grid", mp.numel), seed & 0xFFFFFFFF,
+                                threshold & 0xFFFFFFFF, _dptr(live, torch.int64, "live", 1), _stream()),
+           "simplex_ca_init")
+
+
+def simplex_ca_step(mp: SimplexMap, src: torch.Tensor, dst: torch.Tensor, birth: int, survive: int,
+                    live: torch.Tensor | None = None, mode: int = SIMPLEX_MODE_H):
+    _check(_lib.simplex_ca_step(mp.handle, _dptr(src, torch.uint8, "in", mp.numel),
+                                _dptr(dst, torch.uint8, "out", mp.numel), birth, survive,
+                                _dptr(live, torch.int64, "live", 1), mode, _stream()), "simplex_ca_step")
+
+
+def simplex_ca_run(mp: SimplexMap, a: torch.Tensor, b: torch.Tensor, steps: int, birth: int, survive: int,
+                   live: torch.Tensor | None = None, use_graph: bool = True, mode: int = SIMPLEX_MODE_H):
+    """steps a -> b -> a ...; returns the tensor holding the final state."""
+    _check(_lib.simplex_ca_run(mp.handle, _dptr(a, torch.uint8, "a", mp.numel), _dptr(b, torch.uint8, "b", mp.numel),
+                               steps, birth, survive, _dptr(live, torch.int64, "live", steps + 1),
+                               1 if use_graph else 0, mode, _stream()), "simplex_ca_run")
+    return a if steps % 2 == 0 else b
+
+
+def simplex_ca_run_host(mp: SimplexMap, host_in: torch.Tensor, host_out: torch.Tensor, a: torch.Tensor,
+                        b: torch.Tensor, steps: int, birth: int, survive: int,
+                        dev_live: torch.Tensor | None = None, host_live: torch.Tensor | None = None,
+                        use_graph: bool = True, mode: int = SIMPLEX_MODE_H):
+    """End-to-end run from and to host (CPU, ideally pinned) tensors; synchronous."""
+    for t, nm in ((host_in, "host_in"), (host_out, "host_out")):
+        if t.is_cuda or t.dtype != torch.uint8 or not t.is_contiguous() or t.numel() < mp.numel:
+            raise ValueError(f"{nm} must be a contiguous CPU uint8 tensor of {mp.numel} elements")
+    if host_live is not None and (host_live.is_cuda or host_live.dtype != torch.int64 or host_live.numel() < steps + 1):
+        raise ValueError("host_live must be a CPU int64 tensor of steps + 1 elements")
+    _check(_lib.simplex_ca_run_host(mp.handle, host_in.data_ptr(), host_out.data_ptr(),
+                                    _dptr(a, torch.uint8, "a", mp.numel), _dptr(b, torch.uint8, "b", mp.numel),
+                                    steps, birth, survive, _dptr(dev_live, torch.int64, "dev_live", steps + 1),
+                                    None if host_live is None else host_live.data_ptr(), 1 if use_graph else 0,
+                                    mode, _stream()), "simplex_ca_run_host")
+
+
+def simplex_visit_count(mp: SimplexMap, counts: torch.Tensor, level: int, mode: int = SIMPLEX_MODE_H):
+    if level == SIMPLEX_LEVEL_BLOCK:
+        nb = (mp.n + mp.info.block) // mp.info.block
+        need = nb ** mp.m
+    else:
+        need = mp.numel
+    _check(_lib.simplex_visit_count(mp.handle, _dptr(counts, torch.int32, "counts", need), level, mode,
+                                    _stream()), "simplex_visit_count")
+
+
+def simplex_device_status() -> int:
+    out = _u32()
+    rc = _lib.simplex_device_status(ctypes.byref(out))
+    if rc not in (SIMPLEX_OK, SIMPLEX_ETIMEOUT):
+        _check(rc, "simplex_device_status")
+    return int(out.value)
+
+
+def simplex_last_error() -> str:
+    return _lib.simplex_last_error().decode()
+
+
+def simplex_version() -> str:
+    return _lib.simplex_version().decode()
+
+
+def library_path() -> str:
+    return LIB_PATH

@@ -1,0 +1,318 @@
+"""GPU parity: every CUDA result against the CPU oracle, bit for bit.
+
+All work here is integer, so the bar is exact equality (no tolerance).  Cases
+span several tiles with ragged tails (n + 1 not a multiple of the tile side),
+padded and unaligned array sides, degenerate sizes (n = 0), both maps (H and
+the bounding box) and, at the full workload sizes, the launch configuration
+the benchmark times, checked on whole grids where the oracle finishes in
+seconds and on sampled cells or map-independent properties beyond that.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2208_11617_gb300 import inputs
+from paper_2208_11617_gb300 import simplex as sx
+
+pytestmark = pytest.mark.gpu
+
+MODES = [sx.SIMPLEX_MODE_H, sx.SIMPLEX_MODE_BB]
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    torch.cuda.init()
+    yield
+    assert sx.simplex_device_status() == 0
+
+
+def _logical(t: torch.Tensor, mp, n):
+    """View of the logical (n+1)^m block of a side^m device array, and the rest."""
+    a = t.view(mp.shape).cpu().numpy()
+    sl = tuple(slice(0, n + 1) for _ in range(mp.m))
+    rest = a.copy()
+    rest[sl] = 0
+    return a[sl], rest
+
+
+def _beta(m):
+    return 2 if m <= 3 else m
+
+
+# ---------------------------------------------------------------- write test
+WRITE_CASES = [
+    (2, 1023, 16, None, 2),        # 1024^2, 16 x 16 tiles, the write workload
+    (2, 1000, 16, None, 2),        # ragged: 1001 not a multiple of 16, side not a multiple of 4
+    (2, 1000, 16, 1004, 2),        # padded side, 16-byte rows
+    (2, 0, 16, None, 2),
+    (2, 5, 4, None, 2),
+    (2, 4095, 32, None, 2),
+    (3, 63, 4, None, 2),
+    (3, 100, 8, None, 2),
+    (3, 100, 8, None, 3),
+    (3, 64, 16, 68, 2),
+    (4, 31, 4, None, 4),
+    (4, 127, 8, None, 4),          # 128^4, the m = 4 write workload
+    (4, 127, 4, None, 4),
+    (4, 40, 4, 44, 4),
+]
+
+
+@pytest.mark.parametrize("case", WRITE_CASES)
+@pytest.mark.parametrize("mode", MODES)
+def test_write_matches_oracle(case, mode):
+    m, n, block, side, beta = case
+    mp = sx.simplex_map_create(m, n, 2, beta, block, side=side)
+    seed = inputs.DEFAULT_SEED ^ (n * 7919)
+    out = torch.zeros(mp.numel, dtype=torch.int32, device=DEV)
+    sx.simplex_write(mp, out, seed, mode)
+    torch.cuda.synchronize()
+    got, rest = _logical(out, mp, n)
+    ref = oracle.write(m, n, seed)
+    np.testing.assert_array_equal(got.view(np.uint32), ref)
+    assert not rest.any()
+
+
+def test_write_leaves_outside_untouched():
+    mp = sx.simplex_map_create(2, 500, 2, 2, 16, side=512)
+    out = torch.full((mp.numel,), -7, dtype=torch.int32, device=DEV)
+    sx.simplex_write(mp, out, 3)
+    a = out.view(mp.shape).cpu().numpy()
+    idx = np.indices(a.shape).sum(0)
+    ref = oracle.write(2, 500, 3)
+    np.testing.assert_array_equal(a[:501, :501][idx[:501, :501] <= 500].view(np.uint32),
+                                  ref[idx[:501, :501] <= 500])
+    assert (a[idx > 500] == -7).all()
+
+
+# ---------------------------------------------------------------- coverage
+VISIT_CASES = [(2, 1023, 16, 2), (2, 1000, 16, 2), (2, 77, 4, 2), (3, 100, 8, 2), (3, 63, 4, 2),
+               (3, 100, 8, 3), (3, 255, 16, 2), (4, 31, 4, 4), (4, 63, 8, 4), (2, 0, 16, 2), (3, 0, 4, 2)]
+
+
+@pytest.mark.parametrize("case", VISIT_CASES)
+@pytest.mark.parametrize("mode", MODES)
+def test_visit_counts_block_and_cell(case, mode):
+    m, n, block, beta = case
+    mp = sx.simplex_map_create(m, n, 2, beta, block)
+    nb = (n + block) // block
+    blk = torch.zeros(nb ** m, dtype=torch.int32, device=DEV)
+    sx.simplex_visit_count(mp, blk, sx.SIMPLEX_LEVEL_BLOCK, mode)
+    ref = oracle.block_indicator(m, n, block)
+    np.testing.assert_array_equal(blk.view((nb,) * m).cpu().numpy().astype(np.uint32), ref)
+    cell = torch.zeros(mp.numel, dtype=torch.int32, device=DEV)
+    sx.simplex_visit_count(mp, cell, sx.SIMPLEX_LEVEL_CELL, mode)
+    c = cell.view(mp.shape).cpu().numpy()
+    inside = (np.indices(c.shape).sum(0) <= n).astype(np.int32)
+    np.testing.assert_array_equal(c, inside)
+
+
+# ---------------------------------------------------------------- automaton init
+INIT_CASES = [(2, 4095, 128, None), (2, 1000, 32, 1008), (2, 1000, 64, 1008), (2, 0, 32, 16), (2, 17, 16, 32),
+              (3, 255, 16, None), (3, 255, 32, None), (3, 200, 16, 208), (3, 0, 16, 16)]
+
+
+@pytest.mark.parametrize("case", INIT_CASES)
+def test_ca_init_matches_oracle(case):
+    m, n, block, side = case
+    mp = sx.simplex_map_create(m, n, 2, 2, block, side=side)
+    thr = inputs.bernoulli_threshold(0.5 if m == 2 else 0.3)
+    g = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    live = torch.zeros(1, dtype=torch.int64, device=DEV)
+    sx.simplex_ca_init(mp, g, 1234, thr, live)
+    got, rest = _logical(g, mp, n)
+    ref = oracle.ca_init(m, n, 1234, thr)
+    np.testing.assert_array_equal(got, ref)
+    assert not rest.any()
+    assert int(live.item()) == int(ref.sum())
+
+
+# ---------------------------------------------------------------- automaton runs
+def _gpu_run(mp, n, steps, rule, seed, thr, mode, use_graph=True):
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    b = torch.zeros_like(a)
+    sx.simplex_ca_init(mp, a, seed, thr)
+    live = torch.zeros(steps + 1, dtype=torch.int64, device=DEV)
+    fin = sx.simplex_ca_run(mp, a, b, steps, rule[0], rule[1], live, use_graph, mode)
+    torch.cuda.synchronize()
+    return fin, live.cpu().numpy().astype(np.uint64)
+
+
+RUN_CASES = [
+    # m, n, block, side, steps, rule, p, beta
+    (2, 4095, 128, None, 100, inputs.B3S23, 0.5, 2),     # the m = 2 automaton at the oracle's size
+    (2, 1000, 32, 1008, 30, inputs.B3S23, 0.5, 2),
+    (2, 1000, 64, 1008, 30, inputs.B3S23, 0.5, 2),
+    (2, 1000, 128, 1008, 30, inputs.B3S23, 0.5, 2),
+    (2, 300, 32, 304, 20, (1 << 3 | 1 << 6, 1 << 2 | 1 << 3), 0.4, 2),   # B36/S23
+    (2, 300, 64, 304, 5, (1, 0), 0.3, 2),                                  # birth on 0: tests the edge mask
+    (2, 300, 128, 304, 5, (0x1FF, 0x1FF), 0.3, 2),
+    (2, 0, 32, 16, 3, (1, 1), 0.5, 2),
+    (2, 15, 32, 16, 5, inputs.B3S23, 0.5, 2),
+    (2, 16, 32, 32, 5, inputs.B3S23, 0.5, 2),
+    (3, 255, 16, None, 20, inputs.B5S45, 0.3, 2),
+    (3, 255, 32, None, 20, inputs.B5S45, 0.3, 2),
+    (3, 255, 16, None, 10, inputs.B5S45, 0.3, 3),
+    (3, 200, 16, 208, 10, inputs.B5S45, 0.3, 2),
+    (3, 200, 32, 208, 10, (1 << 4, 1 << 2 | 1 << 3 | 1 << 4), 0.4, 2),
+    (3, 100, 16, 112, 4, (1, 0), 0.3, 2),
+    (3, 0, 16, 16, 3, (1, 1), 0.5, 2),
+    (3, 20, 16, 32, 6, inputs.B5S45, 0.5, 2),
+]
+
+
+@pytest.mark.parametrize("case", RUN_CASES)
+@pytest.mark.parametrize("mode", MODES)
+def test_ca_run_matches_oracle(case, mode):
+    m, n, block, side, steps, rule, p, beta = case
+    mp = sx.simplex_map_create(m, n, 2, beta, block, side=side)
+    thr = inputs.bernoulli_threshold(p)
+    seed = 99 + n
+    fin, live = _gpu_run(mp, n, steps, rule, seed, thr, mode)
+    got, rest = _logical(fin, mp, n)
+    ref0 = oracle.ca_init(m, n, seed, thr)
+    ref, ref_live = oracle.ca_run(m, n, steps, rule[0], rule[1], ref0)
+    np.testing.assert_array_equal(got, ref)
+    assert not rest.any()
+    np.testing.assert_array_equal(live, ref_live)
+
+
+def test_ca_step_by_step_equals_graph_run():
+    mp = sx.simplex_map_create(2, 2047, 2, 2, 64)
+    thr = inputs.bernoulli_threshold(0.5)
+    fin_g, live_g = _gpu_run(mp, 2047, 9, inputs.B3S23, 5, thr, sx.SIMPLEX_MODE_H, use_graph=True)
+    fin_s, live_s = _gpu_run(mp, 2047, 9, inputs.B3S23, 5, thr, sx.SIMPLEX_MODE_H, use_graph=False)
+    assert torch.equal(fin_g, fin_s)
+    np.testing.assert_array_equal(live_g, live_s)
+    # replaying the cached graph gives the same answer again
+    fin_g2, live_g2 = _gpu_run(mp, 2047, 9, inputs.B3S23, 5, thr, sx.SIMPLEX_MODE_H, use_graph=True)
+    assert torch.equal(fin_g, fin_g2)
+
+
+def test_ca_step_api_single_steps():
+    m, n = 2, 777
+    mp = sx.simplex_map_create(m, n, 2, 2, 32, side=784)
+    thr = inputs.bernoulli_threshold(0.5)
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    b = torch.zeros_like(a)
+    sx.simplex_ca_init(mp, a, 42, thr)
+    ref = oracle.ca_init(m, n, 42, thr)
+    for _ in range(4):
+        live = torch.zeros(1, dtype=torch.int64, device=DEV)
+        sx.simplex_ca_step(mp, a, b, *inputs.B3S23, live)
+        ref, ref_live = oracle.ca_step(m, n, *inputs.B3S23, ref)
+        got, _ = _logical(b, mp, n)
+        np.testing.assert_array_equal(got, ref)
+        assert int(live.item()) == ref_live
+        a, b = b, a
+
+
+def test_ca_run_host_end_to_end():
+    m, n, steps = 2, 1023, 12
+    mp = sx.simplex_map_create(m, n, 2, 2, 128)
+    thr = inputs.bernoulli_threshold(0.5)
+    init = oracle.ca_init(m, n, 7, thr)
+    h_in = torch.from_numpy(init.reshape(-1).copy()).pin_memory()
+    h_out = torch.zeros(mp.numel, dtype=torch.uint8).pin_memory()
+    h_live = torch.zeros(steps + 1, dtype=torch.int64)
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    b = torch.zeros_like(a)
+    d_live = torch.zeros(steps + 1, dtype=torch.int64, device=DEV)
+    sx.simplex_ca_run_host(mp, h_in, h_out, a, b, steps, *inputs.B3S23, d_live, h_live)
+    ref, ref_live = oracle.ca_run(m, n, steps, *inputs.B3S23, init)
+    np.testing.assert_array_equal(h_out.numpy().reshape(mp.shape), ref)
+    np.testing.assert_array_equal(h_live.numpy().astype(np.uint64), ref_live)
+
+
+def test_ca_rejects_bad_layouts():
+    mp = sx.simplex_map_create(2, 1000, 2, 2, 32)   # side 1001: rows not 16-byte aligned
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_ca_step(mp, a, a.clone(), *inputs.B3S23)
+    assert ei.value.code == sx.SIMPLEX_EINVAL
+    mp = sx.simplex_map_create(2, 1023, 2, 2, 16)   # block 16 has no m = 2 step kernel
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_ca_step(mp, a, a.clone(), *inputs.B3S23)
+    assert ei.value.code == sx.SIMPLEX_EUNSUPPORTED
+    mp = sx.simplex_map_create(2, 1023, 2, 2, 64)
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_ca_step(mp, a, a, *inputs.B3S23)     # in == out
+    mp4 = sx.simplex_map_create(4, 31, 2, 4, 16)
+    a = torch.zeros(mp4.numel, dtype=torch.uint8, device=DEV)
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_ca_step(mp4, a, a.clone(), *inputs.B3S23)
+
+
+# ---------------------------------------------------------------- full workload sizes
+def test_ca_m3_full_size_steps_match_oracle():
+    """m = 3, n = 1023, B5/S45, Bernoulli(0.3): first steps whole-grid against the
+    oracle, then H and BB agree over all 50 steps."""
+    w = inputs.CA_M3
+    mp = sx.simplex_map_create(w.m, w.n, 2, 2, w.block)
+    first = 3
+    fin, live = _gpu_run(mp, w.n, first, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+    ref0 = oracle.ca_init(w.m, w.n, w.seed, w.threshold)
+    ref, ref_live = oracle.ca_run(w.m, w.n, first, w.rule[0], w.rule[1], ref0)
+    got, _ = _logical(fin, mp, w.n)
+    np.testing.assert_array_equal(got, ref)
+    np.testing.assert_array_equal(live, ref_live)
+    del fin, got, ref, ref0
+    fin_h, live_h = _gpu_run(mp, w.n, w.steps, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+    fin_b, live_b = _gpu_run(mp, w.n, w.steps, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_BB)
+    assert torch.equal(fin_h, fin_b)
+    np.testing.assert_array_equal(live_h, live_b)
+    assert live_h[-1] > 0
+
+
+def test_ca_m2_full_size_matches_oracle():
+    """m = 2, n = 32767, B3/S23, Bernoulli(0.5) in the benchmark's launch
+    configuration (128 x 128 tiles, graph-captured): two whole steps against
+    the oracle, H == BB over the 100 steps, and 4096 sampled cells of the last
+    step recomputed one by one by the oracle."""
+    w = inputs.CA_M2
+    mp = sx.simplex_map_create(w.m, w.n, 2, 2, w.block)
+    fin, live = _gpu_run(mp, w.n, 2, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+    ref0 = oracle.ca_init(w.m, w.n, w.seed, w.threshold)
+    ref, ref_live = oracle.ca_run(w.m, w.n, 2, w.rule[0], w.rule[1], ref0)
+    np.testing.assert_array_equal(fin.view(mp.shape).cpu().numpy(), ref)
+    np.testing.assert_array_equal(live, ref_live)
+    del fin, ref, ref0
+    # 99 steps, then one more: compare sampled cells of step 100 with the oracle
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    b = torch.zeros_like(a)
+    sx.simplex_ca_init(mp, a, w.seed, w.threshold)
+    live_h = torch.zeros(w.steps + 1, dtype=torch.int64, device=DEV)
+    prev = sx.simplex_ca_run(mp, a, b, w.steps - 1, w.rule[0], w.rule[1], live_h[: w.steps])
+    nxt = b if prev is a else a
+    step_live = torch.zeros(1, dtype=torch.int64, device=DEV)
+    sx.simplex_ca_step(mp, prev, nxt, w.rule[0], w.rule[1], step_live)
+    torch.cuda.synchronize()
+    prev_host = prev.view(mp.shape).cpu().numpy()
+    last = nxt.view(mp.shape)
+    rng = np.random.default_rng(2208)
+    pts = []
+    while len(pts) < 4096:
+        x1, x2 = rng.integers(0, w.n + 1, size=2)
+        if x1 + x2 <= w.n:
+            pts.append((x1, x2))
+    pts += [(0, 0), (0, w.n), (w.n, 0), (w.n // 2, w.n - w.n // 2), (127, 128), (128, 127)]
+    coords = np.array(pts, dtype=np.int64)
+    want = oracle.ca_cells(w.m, w.n, w.rule[0], w.rule[1], prev_host, coords)
+    idx = torch.from_numpy(coords).to(DEV)
+    got = last[idx[:, 0], idx[:, 1]].cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    # the bounding-box map computes the same 100 steps
+    fin_b, live_b = _gpu_run(mp, w.n, w.steps, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_BB)
+    assert torch.equal(fin_b, nxt)
+    live_all = live_h.cpu().numpy().astype(np.uint64)
+    live_all[w.steps] = int(step_live.item())
+    np.testing.assert_array_equal(live_b, live_all)
+    assert int(fin_b.sum(dtype=torch.int64).item()) == int(live_b[-1])

@@ -1,0 +1,174 @@
+"""Host-side tests of libsimplex: exported symbols, the launch plan and the maps.
+
+These run without a GPU: simplex_map_create / simplex_map_info /
+simplex_map_block only touch host memory, and simplex_map_block evaluates the
+same integer decode the kernels run, so the coverage of H is checked
+exhaustively here (Def. 1: every block of the simplex gets exactly one CUDA
+block).
+"""
+import collections
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_11617_gb300 import simplex as sx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "simplex.h")).read()
+    declared = set(re.findall(r"^(?:int|const char \*)\s*(simplex_\w+)\s*\(", hdr, flags=re.M))
+    assert declared, "no declarations parsed"
+    assert declared == set(sx.EXPORTED)
+    for name in declared:
+        assert hasattr(sx._lib, name), name
+    assert "sm_103a" in sx.simplex_version()
+
+
+# ------------------------------------------------------------------ plan sizes
+@pytest.mark.parametrize("m,n,block", [(2, 1023, 16), (2, 32767, 128), (2, 4095, 128), (3, 1023, 32),
+                                       (3, 1023, 16), (4, 127, 4), (4, 127, 8), (2, 1000, 16), (3, 200, 16),
+                                       (2, 0, 16), (3, 5, 4)])
+def test_info_counts(m, n, block):
+    beta = 2 if m <= 3 else 4
+    mp = sx.simplex_map_create(m, n, 2, beta, block)
+    info = sx.simplex_map_info(mp)
+    nb = (n + block) // block
+    N = 1 << max(0, (nb - 1).bit_length())
+    assert info["N"] == N
+    assert info["cells"] == math.comb(n + m, m)
+    assert info["useful_blocks"] == math.comb(n // block + m, m)
+    assert info["bb_blocks"] == N ** m
+    logN = N.bit_length() - 1
+    # Eq. generic-m with r = 1/2 (reduces to Eq. m2 / Eq. m3 for beta = 2)
+    assert info["h_set_blocks"] == (N ** m - beta ** logN) // (2 ** m - beta)
+    if m == 2:
+        assert info["h_set_blocks"] == N * (N - 1) // 2          # Eq. m2 (Lemma 1)
+        assert info["h_blocks"] == N * (N - 1) // 2 + N
+    if m == 3:
+        assert info["h_set_blocks"] == (N ** 3 - N) // 6          # Eq. m3 (Lemma 3)
+
+
+def test_h3_packing_waste_tends_to_one_eighth():
+    # Sec. 4.3: the single-grid packing adds 1/8 of V(Delta) in the limit
+    mp = sx.simplex_map_create(3, 32767, 2, 2, 4)   # N = 8192
+    info = sx.simplex_map_info(mp)
+    N = info["N"]
+    plane = (N // 2) * (N - 1) + N
+    packed = info["h_blocks"] - plane
+    tet = (N ** 3 - N) // 6
+    assert abs(packed / tet - 1 - 0.125) < 0.002
+
+
+def test_m4_overhang_fraction_matches_lemma_5_scaling():
+    # beta = m = 4 cubes: V = (N^4 - N^2)/12 against V(Delta) ~ N^4/24
+    mp = sx.simplex_map_create(4, 2 ** 12 - 1, 2, 4, 4)
+    info = sx.simplex_map_info(mp)
+    N = info["N"]
+    assert info["h_set_blocks"] == (N ** 4 - N ** 2) // 12
+
+
+# ------------------------------------------------------------------ errors
+@pytest.mark.parametrize("args,code", [((1, 10, 2, 2, 16), sx.SIMPLEX_EINVAL), ((5, 10, 2, 2, 16), sx.SIMPLEX_EINVAL),
+                                       ((2, -1, 2, 2, 16), sx.SIMPLEX_EINVAL), ((2, 10, 3, 2, 16), sx.SIMPLEX_EUNSUPPORTED),
+                                       ((2, 10, 2, 3, 16), sx.SIMPLEX_EUNSUPPORTED), ((4, 10, 2, 2, 4), sx.SIMPLEX_EUNSUPPORTED),
+                                       ((2, 10, 2, 2, 12), sx.SIMPLEX_EINVAL), ((2, 10, 2, 2, 2), sx.SIMPLEX_EINVAL),
+                                       ((2, 10, 2, 2, 512), sx.SIMPLEX_EINVAL), ((2, 2 ** 40, 2, 2, 16), sx.SIMPLEX_EINVAL)])
+def test_create_rejects_bad_arguments(args, code):
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_map_create(*args)
+    assert ei.value.code == code
+    assert sx.simplex_last_error()
+
+
+def test_padded_side_must_hold_the_domain():
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_map_create(2, 100, 2, 2, 16, side=100)
+    assert ei.value.code == sx.SIMPLEX_EINVAL
+    mp = sx.simplex_map_create(2, 100, 2, 2, 16, side=112)
+    assert mp.side == 112
+
+
+def test_map_block_rejects_out_of_range():
+    mp = sx.simplex_map_create(2, 63, 2, 2, 16)
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, mp.info.h_blocks)
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_block(mp, 7, 0)
+
+
+# ------------------------------------------------------------------ Eq. map2d as printed
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 32, 64, 128, 256])
+def test_h2_grid_is_eq_map2d(N):
+    rho = 4
+    mp = sx.simplex_map_create(2, N * rho - 1, 2, 2, rho)
+    assert mp.info.N == N
+    seen = set()
+    for v in range((N // 2) * (N - 1)):
+        wx, wy = v % (N // 2), v // (N // 2)
+        b = 1 << (wy + 1).bit_length() - 1
+        q = wx // b
+        hx, hy = wx + q * b, wy + 2 * q * b + 1          # Thm. 1
+        (X1, X2), valid = sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)
+        assert valid
+        assert (X2, N - 1 - X1) == (hx, hy)
+        assert hx < hy <= N - 1
+        seen.add((hx, hy))
+    # a bijection onto the blocks strictly below the diagonal (Lemma 1, Lemma 2)
+    assert len(seen) == N * (N - 1) // 2
+
+
+# ------------------------------------------------------------------ exhaustive coverage
+def _covered(mp, mode):
+    nblocks = mp.info.h_blocks if mode == sx.SIMPLEX_MODE_H else mp.info.bb_blocks
+    cnt = collections.Counter()
+    for v in range(nblocks):
+        X, valid = sx.simplex_map_block(mp, mode, v)
+        if valid:
+            cnt[X] += 1
+    return cnt
+
+
+COVER_CASES = [(2, n, 4) for n in (0, 1, 3, 4, 7, 8, 15, 16, 17, 31, 63, 100, 127, 255, 1000, 1023)] + \
+    [(3, n, 4, 2) for n in (0, 3, 4, 7, 8, 15, 31, 63, 100, 127, 255)] + \
+    [(3, n, 4, 3) for n in (0, 7, 15, 31, 63, 100, 127)] + \
+    [(4, n, 4, 4) for n in (0, 3, 7, 15, 31, 50, 63)]
+
+
+@pytest.mark.parametrize("case", COVER_CASES)
+def test_h_covers_each_simplex_block_exactly_once(case):
+    m, n, rho = case[:3]
+    beta = case[3] if len(case) > 3 else 2
+    mp = sx.simplex_map_create(m, n, 2, beta, rho)
+    got = _covered(mp, sx.SIMPLEX_MODE_H)
+    ind = oracle.block_indicator(m, n, rho)
+    want = {tuple(int(i) for i in x) for x in np.argwhere(ind)}
+    assert set(got) == want
+    assert all(c == 1 for c in got.values())
+
+
+@pytest.mark.parametrize("case", [(2, 63, 4), (2, 100, 8), (3, 63, 4), (3, 50, 8), (4, 31, 4)])
+def test_bb_covers_each_simplex_block_exactly_once(case):
+    m, n, rho = case
+    mp = sx.simplex_map_create(m, n, 2, 2 if m <= 3 else 4, rho)
+    got = _covered(mp, sx.SIMPLEX_MODE_BB)
+    ind = oracle.block_indicator(m, n, rho)
+    want = {tuple(int(i) for i in x) for x in np.argwhere(ind)}
+    assert set(got) == want and all(c == 1 for c in got.values())
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 64])
+def test_h3_hinge_valid_blocks_equal_eq_m3(N):
+    # blocks mapped by the cube + layer regions (before the diagonal plane):
+    # exactly the (N^3 - N)/6 blocks of Delta_{N-1} below the plane (Lemma 3)
+    rho = 4
+    mp = sx.simplex_map_create(3, N * rho - 1, 2, 2, rho)
+    plane = (N // 2) * (N - 1) + N
+    main = mp.info.h_blocks - plane
+    valid = sum(1 for v in range(main) if sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)[1])
+    assert valid == (N ** 3 - N) // 6

@@ -303,3 +303,14 @@ def test_block_indicator_closed_form(m, n, rho):
     X = np.indices(ind.shape).sum(0)
     np.testing.assert_array_equal(ind, (rho * X <= n).astype(np.uint32))
     assert int(ind.sum()) == math.comb(n // rho + m, m)
+
+
+def test_ca_cells_agrees_with_whole_step():
+    for m, n, rule in ((2, 30, inputs.B3S23), (3, 12, inputs.B5S45)):
+        rng = np.random.default_rng(m)
+        g = rng.integers(0, 2, size=(n + 1,) * m, dtype=np.uint8)
+        g = np.where(np.indices(g.shape).sum(0) <= n, g, 0).astype(np.uint8)
+        ref = _shift_sum_step(g, n, *rule)
+        coords = np.argwhere(np.indices(g.shape).sum(0) <= n)
+        got = oracle.ca_cells(m, n, rule[0], rule[1], g, coords)
+        np.testing.assert_array_equal(got, ref[tuple(coords.T)])
