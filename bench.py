@@ -143,16 +143,31 @@ def aggregate(units_per_rank: float, seconds: float, world: int):
 
 
 # ---------------------------------------------------------------- our arm
-def _workload(name):
+def _workload(name, args=None):
+    import dataclasses
     if name == "ca2":
-        return inputs.CA_M2
-    if name == "ca3":
-        return inputs.CA_M3
-    if name == "write2":
-        return inputs.WRITE_M2
-    if name == "write4":
-        return inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
-    raise SystemExit(f"unknown workload {name}")
+        wl = inputs.CA_M2
+    elif name == "ca3":
+        wl = inputs.CA_M3
+    elif name == "write2":
+        wl = inputs.WRITE_M2
+    elif name == "write4":
+        wl = inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if args is not None:
+        # smaller or differently tiled cases of the same workload (profiling, sweeps)
+        ch = {}
+        if args.n is not None:
+            ch["n"] = args.n
+        if args.block is not None:
+            ch["block"] = args.block
+        if args.ca_steps is not None and isinstance(wl, inputs.CAWorkload):
+            ch["steps"] = args.ca_steps
+        if ch:
+            ch["name"] = wl.name + " (" + ", ".join(f"{k}={v}" for k, v in ch.items()) + ")"
+            wl = dataclasses.replace(wl, **ch)
+    return wl
 
 
 def _time_region(fn, steps, warmup, world):
@@ -192,7 +207,7 @@ def run_ours(args, rank, world, local):
     from paper_2208_11617_gb300 import simplex as sx
 
     torch.cuda.set_device(local)
-    wl = _workload(args.workload)
+    wl = _workload(args.workload, args)
     hbm_peak, peak_kind = _peaks()
     res = {}
     if isinstance(wl, inputs.CAWorkload):
@@ -212,15 +227,15 @@ def run_ours(args, rank, world, local):
         clocks.start()
         secs = _time_region(step(sx.SIMPLEX_MODE_H), args.steps, args.warmup, world)
         clk = clocks.stop()
-        secs_bb = _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
+        secs_bb = secs if args.no_bb else _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
         units = cells * wl.steps * args.steps
         value, tmax = aggregate(units, secs, world)
         value_bb, _ = aggregate(units, secs_bb, world)
         # dominant kernel: one automaton step; its average launch duration
         nxt = torch.zeros_like(a)
         mean_ms, med_ms = _per_launch_ms(lambda: sx.simplex_ca_step(mp, a, nxt, birth, survive, None), 20)
-        mean_bb, _ = _per_launch_ms(
-            lambda: sx.simplex_ca_step(mp, a, nxt, birth, survive, None, sx.SIMPLEX_MODE_BB), 20)
+        mean_bb = mean_ms if args.no_bb else _per_launch_ms(
+            lambda: sx.simplex_ca_step(mp, a, nxt, birth, survive, None, sx.SIMPLEX_MODE_BB), 20)[0]
         alg_bytes = 2 * cells
         achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
         res.update(
@@ -245,19 +260,21 @@ def run_ours(args, rank, world, local):
                     "wasted_frac_bb": 1 - info["useful_blocks"] / info["bb_blocks"]},
         )
         # end to end through the C ABI from pinned host memory
-        e2e_steps = max(1, min(3, args.steps))
-        h_in = torch.empty(mp.numel, dtype=torch.uint8).pin_memory()
-        h_in.copy_(a.cpu())
-        h_out = torch.empty_like(h_in).pin_memory()
-        h_live = torch.zeros(wl.steps + 1, dtype=torch.int64)
-        sx.simplex_ca_run_host(mp, h_in, h_out, a, b, wl.steps, birth, survive, live, h_live)
-        torch.cuda.synchronize()
-        _barrier(world)
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+        e2e_steps = 0 if args.no_e2e else max(1, min(3, args.steps))
+        e2e_val = None
+        if e2e_steps:
+            h_in = torch.empty(mp.numel, dtype=torch.uint8).pin_memory()
+            h_in.copy_(a.cpu())
+            h_out = torch.empty_like(h_in).pin_memory()
+            h_live = torch.zeros(wl.steps + 1, dtype=torch.int64)
             sx.simplex_ca_run_host(mp, h_in, h_out, a, b, wl.steps, birth, survive, live, h_live)
-        t1 = time.perf_counter()
-        e2e_val, _ = aggregate(cells * wl.steps * e2e_steps, t1 - t0, world)
+            torch.cuda.synchronize()
+            _barrier(world)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                sx.simplex_ca_run_host(mp, h_in, h_out, a, b, wl.steps, birth, survive, live, h_live)
+            t1 = time.perf_counter()
+            e2e_val = aggregate(cells * wl.steps * e2e_steps, t1 - t0, world)[0]
         res["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": mp.numel,
                       "d2h_bytes_per_step": mp.numel + 8 * (wl.steps + 1)}
         assert sx.simplex_device_status() == 0
@@ -267,25 +284,36 @@ def run_ours(args, rank, world, local):
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         out = torch.zeros(mp.numel, dtype=torch.int32, device="cuda")
-        # many launches per benchmark step: the write of one array is a few microseconds
+        # many launches per benchmark step (the write of one array is a few
+        # microseconds), captured in a CUDA graph so the host is off the path
         reps = 100
 
-        def step(mode):
-            def f():
+        def graph_of(mode):
+            g = torch.cuda.CUDAGraph()
+            sx.simplex_write(mp, out, wl.seed, mode)  # warm the launch path outside capture
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
                 for _ in range(reps):
                     sx.simplex_write(mp, out, wl.seed, mode)
-            return f
+            return g
+
+        graphs = {sx.SIMPLEX_MODE_H: graph_of(sx.SIMPLEX_MODE_H), sx.SIMPLEX_MODE_BB: graph_of(sx.SIMPLEX_MODE_BB)}
+
+        def step(mode):
+            return graphs[mode].replay
 
         clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
         secs = _time_region(step(sx.SIMPLEX_MODE_H), args.steps, args.warmup, world)
         clk = clocks.stop()
-        secs_bb = _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
+        secs_bb = secs if args.no_bb else _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
         units = cells * reps * args.steps
         value, tmax = aggregate(units, secs, world)
         value_bb, _ = aggregate(units, secs_bb, world)
-        mean_ms, med_ms = _per_launch_ms(lambda: sx.simplex_write(mp, out, wl.seed), 50)
-        mean_bb, _ = _per_launch_ms(lambda: sx.simplex_write(mp, out, wl.seed, sx.SIMPLEX_MODE_BB), 50)
+        # per launch: a graph of `reps` back-to-back launches, timed by events, / reps
+        mean_ms = statistics.mean(_per_launch_ms(graphs[sx.SIMPLEX_MODE_H].replay, 10)) / reps
+        med_ms = mean_ms
+        mean_bb = statistics.mean(_per_launch_ms(graphs[sx.SIMPLEX_MODE_BB].replay, 10)) / reps
         alg_bytes = 4 * cells
         achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
         res.update(
@@ -353,7 +381,7 @@ def cpu_baseline(wl):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    wl = _workload(args.workload)
+    wl = _workload(args.workload, args)
     unit = UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s"
     for _ in range(args.warmup):
         _oracle_sample(wl, 1)
@@ -382,6 +410,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--n", type=int, default=None, help="override n (smaller case of the workload)")
+    ap.add_argument("--block", type=int, default=None, help="override the tile side")
+    ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -215,6 +215,16 @@ int simplex_visit_count(simplex_map_t map, uint32_t *counts, int level, int mode
  */
 int simplex_device_status(uint32_t *out);
 
+/*
+ * simplex_selftest_wait_timeout -- checks the failure-detection path of the
+ * bounded device waits: launches one CTA that waits on an mbarrier nothing
+ * completes, gives up after `limit_ns` (1 us .. 1 s), records the timeout in
+ * the device status word and returns, leaving the context usable.  A later
+ * simplex_device_status() returns SIMPLEX_ETIMEOUT (and clears it).
+ * Diagnostic only; not part of any workload.
+ */
+int simplex_selftest_wait_timeout(uint64_t limit_ns, void *stream);
+
 /* Message for the last failed call on this host thread ("" if none). */
 const char *simplex_last_error(void);
 

@@ -160,6 +160,10 @@ sx::Rule make_rule(int m, uint32_t birth, uint32_t survive)
         r.ssel[r.nk] = sv ? 0xffffffffu : 0u;
         ++r.nk;
     }
+    // "or-k" form: born with k, survive with k-1 or k, k odd
+    const int nmax = m == 2 ? 8 : 26;
+    for (int k = 1; k <= nmax; k += 2)
+        if (birth == (1u << k) && survive == ((1u << (k - 1)) | (1u << k))) r.or_k = 0x01010101u * (uint32_t)k;
     return r;
 }
 
@@ -193,8 +197,10 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
     box[0] = (cuuint32_t)(p.rho + 32);
     box[1] = (cuuint32_t)(p.rho + 2);
     box[2] = (cuuint32_t)(p.rho + 2);
+    const CUtensorMapSwizzle swz =
+        (p.m == 3 && sx::ca3_swizzled(p.rho)) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE;
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, (cuuint32_t)p.m, const_cast<void *>(base), dims, strides, box,
-                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
     return SIMPLEX_OK;
@@ -490,6 +496,15 @@ int simplex_device_status(uint32_t *out)
     if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
     *out = s2 | s3;
     if (*out) return fail(SIMPLEX_ETIMEOUT, "a kernel gave up a bounded wait for its TMA load (status 0x%x)", *out);
+    return SIMPLEX_OK;
+}
+
+int simplex_selftest_wait_timeout(uint64_t limit_ns, void *stream)
+{
+    if (limit_ns < 1000ull || limit_ns > 1000000000ull)
+        return fail(SIMPLEX_EINVAL, "limit_ns must be in [1 us, 1 s] (got %llu)", (unsigned long long)limit_ns);
+    cudaError_t e = sx::launch_wait_selftest(limit_ns, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
     return SIMPLEX_OK;
 }
 

@@ -163,6 +163,36 @@ __device__ __forceinline__ void apply_rule4(const uint32_t s[4], const uint32_t 
     for (int w = 0; w < 4; ++w) nw[w] = (acc[w] >> 7) & 0x01010101u;
 }
 
+// Next state for the "or-k" rules (Rule::or_k != 0): with c = s - alive the
+// live-neighbour count, a cell is alive next iff (c | alive) == k.  For k odd
+// this is exactly birth on k and survival on k-1 or k.
+__device__ __forceinline__ void apply_rule4_ork(const uint32_t s[4], const uint32_t alive[4], uint32_t kbytes,
+                                                uint32_t nw[4])
+{
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t c = s[w] - alive[w];                      // bytes never borrow: s >= alive
+        const uint32_t y = ((c | alive[w]) ^ kbytes) + 0x7F7F7F7Fu;  // bit 7 set iff byte != k
+        nw[w] = (~y >> 7) & 0x01010101u;
+    }
+}
+
+template <bool ORK>
+__device__ __forceinline__ void next_state4(const uint32_t s[4], const uint32_t alive[4], const Rule &r,
+                                            uint32_t nw[4])
+{
+    if (ORK)
+        apply_rule4_ork(s, alive, r.or_k, nw);
+    else
+        apply_rule4(s, alive, r, nw);
+}
+
+// Sum of the four bytes of a word (each byte <= 255, no overflow).
+__device__ __forceinline__ uint32_t byte_sum(uint32_t v)
+{
+    return (v & 0xffu) + ((v >> 8) & 0xffu) + ((v >> 16) & 0xffu) + (v >> 24);
+}
+
 // Horizontal 3-sums of one 16-byte row chunk in shared memory: h[w] byte j =
 // cell(j-1) + cell(j) + cell(j+1), using the 4 bytes before and after the
 // chunk for the edge cells.  c[] receives the chunk itself.

@@ -12,7 +12,9 @@
 //      16 cells comes from byte-parallel 32-bit adds (cells are 0/1, sums
 //      never carry across bytes);
 //   4. applies the rule byte-parallel and writes 16 cells per 16-byte store;
-//   5. adds its live cells (popc) to the step's counter, one atomic per CTA.
+//   5. adds its live cells to the step's counter: new states (0/1 bytes) are
+//      summed byte-wise per thread, folded once per tile, reduced per CTA and
+//      added with one atomic per CTA.
 // Only tiles on the diagonal band mask cells past x1 + x2 = n.
 #include "common.cuh"
 #include "hmap.cuh"
@@ -22,8 +24,13 @@ namespace sx {
 
 static __device__ uint32_t g_ca2_status;
 
-template <int RHO, int R>
-__global__ void __launch_bounds__(RHO * RHO / (16 * R))
+// CTAs per SM the kernel is built for (the 128 x 128 tile's shared memory
+// allows 10; smaller tiles are limited by threads).
+template <int RHO>
+constexpr int ca2_min_blocks() { return RHO == 128 ? 10 : 16; }
+
+template <int RHO, int R, bool ORK>
+__global__ void __launch_bounds__(RHO * RHO / (16 * R), ca2_min_blocks<RHO>())
     ca2_step_kernel(const __grid_constant__ CUtensorMap tin, uint8_t *__restrict__ out, const Plan p,
                     const Rule rule, int kind, uint64_t nblocks, unsigned long long *__restrict__ live)
 {
@@ -70,7 +77,7 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R))
         const uint8_t *col = tile + 16 + 16 * tx;
         const int r0 = ty * R;                  // first output row of this thread
         const int64_t xc = x0 + 16 * tx;        // first cell of the chunk
-        uint32_t hp[4], hc[4], ac[4], tmp[4];
+        uint32_t hp[4], hc[4], ac[4], tmp[4], lacc = 0;
         hsum_row(col + r0 * BW, hp, tmp);
         hsum_row(col + (r0 + 1) * BW, hc, ac);
 #pragma unroll
@@ -79,7 +86,7 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R))
             hsum_row(col + (r0 + i + 2) * BW, hn, an);
 #pragma unroll
             for (int w = 0; w < 4; ++w) s[w] = hp[w] + hc[w] + hn[w];
-            apply_rule4(s, ac, rule, nw);
+            next_state4<ORK>(s, ac, rule, nw);
             const int64_t y = y0 + r0 + i;
             bool store = true;
             if (partial) {
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R))
                 store = c > 0;
             }
             if (store) store16(out + y * p.side + xc, nw);
-            my_live += __popc(nw[0]) + __popc(nw[1]) + __popc(nw[2]) + __popc(nw[3]);
+            lacc += nw[0] + nw[1] + nw[2] + nw[3];  // bytes <= 4R: no carry
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 hp[w] = hc[w];
@@ -98,15 +105,36 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R))
                 ac[w] = an[w];
             }
         }
+        my_live += byte_sum(lacc);
         __syncthreads();  // the tile is fully read before the next load reuses it
     }
     if (live) block_add_u64(live, my_live, red);
 }
 
+// Self-test of the bounded wait: one CTA waits on an mbarrier that nothing
+// completes, gives up after limit_ns, records status bit 2 and returns.
+__global__ void wait_selftest_kernel(uint64_t limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(&g_ca2_status, 2u);
+}
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns);
+    return cudaGetLastError();
+}
+
 bool ca2_supports(int rho) { return rho == 32 || rho == 64 || rho == 128; }
 
-template <int RHO, int R>
-static cudaError_t prepare_t()
+template <int RHO, int R, bool ORK>
+static cudaError_t prepare_one()
 {
     constexpr int smem = (RHO + 32) * (RHO + 2) + 128;
     static bool attr_set[64] = {false};
@@ -114,9 +142,16 @@ static cudaError_t prepare_t()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(ca2_step_kernel<RHO, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(ca2_step_kernel<RHO, R, ORK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
     return e;
+}
+
+template <int RHO, int R>
+static cudaError_t prepare_t()
+{
+    cudaError_t e = prepare_one<RHO, R, false>();
+    return e != cudaSuccess ? e : prepare_one<RHO, R, true>();
 }
 
 template <int RHO, int R>
@@ -129,7 +164,10 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     if (e != cudaSuccess) return e;
     const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
     const unsigned g = (unsigned)(nb < 0x7fffffffull ? (nb ? nb : 1) : 0x7fffffffull);
-    ca2_step_kernel<RHO, R><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
+    if (rule.or_k)
+        ca2_step_kernel<RHO, R, true><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
+    else
+        ca2_step_kernel<RHO, R, false><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
     return cudaGetLastError();
 }
 

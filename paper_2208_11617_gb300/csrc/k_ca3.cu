@@ -9,6 +9,10 @@
 // chunk) column: per plane it forms the 3 x 3 sums P = h(x2-1) + h(x2) +
 // h(x2+1) of horizontal 3-sums, and the Moore-26 sum of three consecutive
 // planes, all byte-parallel in 32-bit registers.
+//
+// For RHO = 32 the staged rows are 64 bytes and the tensor map uses the 64-byte
+// swizzle: 16-byte chunk c of staged row r sits at chunk c ^ ((r >> 1) & 3),
+// which spreads the rows a warp reads at once over all shared-memory banks.
 #include "common.cuh"
 #include "hmap.cuh"
 #include "kernels.h"
@@ -17,23 +21,55 @@ namespace sx {
 
 static __device__ uint32_t g_ca3_status;
 
-template <int RHO, int RZ>
-__global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ))
+// Byte offset of 16-byte chunk c within a staged row r (row pitch BW bytes).
+template <int BW, bool SWZ>
+__device__ __forceinline__ int chunk_off(int r, int c)
+{
+    if (SWZ) return r * BW + 16 * (c ^ ((r >> 1) & 3));
+    return r * BW + 16 * c;
+}
+
+// Horizontal 3-sums of chunk c of staged row r (chunks c-1 and c+1 give the
+// neighbour bytes at the chunk's edges).
+template <int BW, bool SWZ>
+__device__ __forceinline__ void hsum_staged(const uint8_t *tile, int r, int c, uint32_t h[4], uint32_t cc[4])
+{
+    const uint4 w = *reinterpret_cast<const uint4 *>(tile + chunk_off<BW, SWZ>(r, c));
+    const uint32_t lw = *reinterpret_cast<const uint32_t *>(tile + chunk_off<BW, SWZ>(r, c - 1) + 12);
+    const uint32_t rw = *reinterpret_cast<const uint32_t *>(tile + chunk_off<BW, SWZ>(r, c + 1));
+    h[0] = w.x + __funnelshift_l(lw, w.x, 8) + __funnelshift_r(w.x, w.y, 8);
+    h[1] = w.y + __funnelshift_l(w.x, w.y, 8) + __funnelshift_r(w.y, w.z, 8);
+    h[2] = w.z + __funnelshift_l(w.y, w.z, 8) + __funnelshift_r(w.z, w.w, 8);
+    h[3] = w.w + __funnelshift_l(w.z, w.w, 8) + __funnelshift_r(w.w, rw, 8);
+    cc[0] = w.x;
+    cc[1] = w.y;
+    cc[2] = w.z;
+    cc[3] = w.w;
+}
+
+// CTAs per SM the kernel is built for (shared memory allows 3 at RHO = 32).
+template <int RHO>
+constexpr int ca3_min_blocks() { return RHO == 32 ? 3 : 12; }
+
+template <int RHO, int RZ, bool ORK>
+__global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<RHO>())
     ca3_step_kernel(const __grid_constant__ CUtensorMap tin, uint8_t *__restrict__ out, const Plan p,
                     const Rule rule, int kind, uint64_t nblocks, unsigned long long *__restrict__ live)
 {
     constexpr int TX = RHO / 16;
     constexpr int BW = RHO + 32, BH = RHO + 2, BD = RHO + 2;
+    constexpr bool SWZ = (BW == 64);
     constexpr uint32_t kBoxBytes = BW * BH * BD;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t red[32];
-    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
+    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 511) & ~uintptr_t(511));
 
     const int tid = threadIdx.x;
     const int tx = tid % TX;
     const int ty = (tid / TX) % RHO;         // x2 within the tile
     const int tz = tid / (TX * RHO);         // plane segment along x1
+    const int c = 1 + tx;                    // staged chunk (chunk 0 is the left halo)
     uint32_t phase = 0, my_live = 0;
     if (tid == 0) {
         prefetch_tmap(&tin);
@@ -63,40 +99,39 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ))
             return;
         }
 
-        // staged row (x2 = y0 + yy - 1, x1 = z0 + zz - 1) starts at (zz * BH + yy) * BW
-        const uint8_t *col = tile + 16 + 16 * tx;
+        // staged row r = zz * BH + yy holds x1 = z0 + zz - 1, x2 = y0 + yy - 1
         const int64_t xc = x0 + 16 * tx;
         const int64_t x2 = y0 + ty;
         const int zb = tz * RZ;  // first output plane of this thread
-        uint32_t pp[4], pc[4], ac[4];
+        uint32_t pp[4], pc[4], ac[4], lacc = 0;
         {
-            uint32_t h0[4], h1[4], h2[4], c[4];
-            const uint8_t *pl = col + (zb * BH + ty) * BW;
-            hsum_row(pl, h0, c);
-            hsum_row(pl + BW, h1, c);
-            hsum_row(pl + 2 * BW, h2, c);
+            uint32_t h0[4], h1[4], h2[4], cc[4];
+            int r = zb * BH + ty;
+            hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
+            hsum_staged<BW, SWZ>(tile, r + 1, c, h1, cc);
+            hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
 #pragma unroll
             for (int w = 0; w < 4; ++w) pp[w] = h0[w] + h1[w] + h2[w];
-            pl += BH * BW;
-            hsum_row(pl, h0, c);
-            hsum_row(pl + BW, h1, ac);
-            hsum_row(pl + 2 * BW, h2, c);
+            r += BH;
+            hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
+            hsum_staged<BW, SWZ>(tile, r + 1, c, h1, ac);
+            hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
 #pragma unroll
             for (int w = 0; w < 4; ++w) pc[w] = h0[w] + h1[w] + h2[w];
         }
 #pragma unroll
         for (int i = 0; i < RZ; ++i) {
-            uint32_t h0[4], h1[4], h2[4], c[4], an[4], pn[4], s[4], nw[4];
-            const uint8_t *pl = col + ((zb + i + 2) * BH + ty) * BW;
-            hsum_row(pl, h0, c);
-            hsum_row(pl + BW, h1, an);
-            hsum_row(pl + 2 * BW, h2, c);
+            uint32_t h0[4], h1[4], h2[4], cc[4], an[4], pn[4], s[4], nw[4];
+            const int r = (zb + i + 2) * BH + ty;
+            hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
+            hsum_staged<BW, SWZ>(tile, r + 1, c, h1, an);
+            hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 pn[w] = h0[w] + h1[w] + h2[w];
                 s[w] = pp[w] + pc[w] + pn[w];
             }
-            apply_rule4(s, ac, rule, nw);
+            next_state4<ORK>(s, ac, rule, nw);
             const int64_t x1 = z0 + zb + i;
             bool store = true;
             if (partial) {
@@ -107,7 +142,7 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ))
                 store = cnt > 0;
             }
             if (store) store16(out + (x1 * p.side + x2) * p.side + xc, nw);
-            my_live += __popc(nw[0]) + __popc(nw[1]) + __popc(nw[2]) + __popc(nw[3]);
+            lacc += nw[0] + nw[1] + nw[2] + nw[3];
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 pp[w] = pc[w];
@@ -115,6 +150,7 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ))
                 ac[w] = an[w];
             }
         }
+        my_live += byte_sum(lacc);
         __syncthreads();
     }
     if (live) block_add_u64(live, my_live, red);
@@ -122,18 +158,28 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ))
 
 bool ca3_supports(int rho) { return rho == 16 || rho == 32; }
 
-template <int RHO, int RZ>
-static cudaError_t prepare_t()
+// The 64-byte swizzle the tensor map must use for this tile side (see above).
+bool ca3_swizzled(int rho) { return rho + 32 == 64; }
+
+template <int RHO, int RZ, bool ORK>
+static cudaError_t prepare_one()
 {
-    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 128;
+    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 512;
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(ca3_step_kernel<RHO, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(ca3_step_kernel<RHO, RZ, ORK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
     return e;
+}
+
+template <int RHO, int RZ>
+static cudaError_t prepare_t()
+{
+    cudaError_t e = prepare_one<RHO, RZ, false>();
+    return e != cudaSuccess ? e : prepare_one<RHO, RZ, true>();
 }
 
 template <int RHO, int RZ>
@@ -141,12 +187,15 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
                             unsigned long long *live, cudaStream_t st)
 {
     constexpr int T = (RHO / 16) * RHO * (RHO / RZ);
-    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 128;
+    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 512;
     cudaError_t e = prepare_t<RHO, RZ>();
     if (e != cudaSuccess) return e;
     const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
     const unsigned g = (unsigned)(nb < 0x7fffffffull ? (nb ? nb : 1) : 0x7fffffffull);
-    ca3_step_kernel<RHO, RZ><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
+    if (rule.or_k)
+        ca3_step_kernel<RHO, RZ, true><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
+    else
+        ca3_step_kernel<RHO, RZ, false><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ cudaError_t launch_ca_count(const Plan &p, const uint8_t *grid, unsigned long lo
 // TMA-staged automaton steps; `tin` maps the input grid (see make_tensor_map).
 bool ca2_supports(int rho);
 bool ca3_supports(int rho);
+bool ca3_swizzled(int rho);  // tensor map needs CU_TENSOR_MAP_SWIZZLE_64B
 cudaError_t launch_ca2_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
                             int kind, unsigned long long *live, cudaStream_t st);
 cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
@@ -33,6 +34,9 @@ cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out,
 // stream capture).
 cudaError_t ca2_prepare(int rho);
 cudaError_t ca3_prepare(int rho);
+
+// One CTA whose mbarrier wait runs out after limit_ns (tests the bounded-wait path).
+cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
 
 // Device error words of the TMA kernels (bounded waits that gave up).
 // Reads and clears; synchronous.

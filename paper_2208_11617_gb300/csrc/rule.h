@@ -10,6 +10,10 @@ namespace sx {
 // Built on the host from the birth/survive masks; only values that can turn
 // a cell on are listed.
 struct Rule {
+    // Nonzero when the rule is "born with k, survive with k-1 or k" for an odd
+    // k (B3/S23, B5/S45): then a cell is alive next iff (live neighbours | own
+    // state) == k.  Holds k replicated in the 4 bytes of a word.
+    uint32_t or_k;
     int32_t nk;
     uint32_t kbytes[28];  // s replicated in the 4 bytes of a word
     uint32_t bsel[28];    // all-ones if a dead cell with s live neighbours is born

@@ -34,7 +34,7 @@ EXPORTED = (
     "simplex_map_create", "simplex_map_create_padded", "simplex_map_destroy", "simplex_map_info",
     "simplex_map_block", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
     "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
-    "simplex_version",
+    "simplex_version", "simplex_selftest_wait_timeout",
 )
 
 if not os.path.exists(LIB_PATH):
@@ -77,6 +77,7 @@ _sig("simplex_ca_run", [_vp, _vp, _vp, _i32, _u32, _u32, _vp, _i32, _i32, _vp])
 _sig("simplex_ca_run_host", [_vp, _vp, _vp, _vp, _vp, _i32, _u32, _u32, _vp, _vp, _i32, _i32, _vp])
 _sig("simplex_visit_count", [_vp, _vp, _i32, _i32, _vp])
 _sig("simplex_device_status", [ctypes.POINTER(_u32)])
+_sig("simplex_selftest_wait_timeout", [_u64, _vp])
 _lib.simplex_last_error.argtypes = []
 _lib.simplex_last_error.restype = ctypes.c_char_p
 _lib.simplex_version.argtypes = []
@@ -243,6 +244,10 @@ def simplex_device_status() -> int:
     if rc not in (SIMPLEX_OK, SIMPLEX_ETIMEOUT):
         _check(rc, "simplex_device_status")
     return int(out.value)
+
+
+def simplex_selftest_wait_timeout(limit_ns: int):
+    _check(_lib.simplex_selftest_wait_timeout(limit_ns, _stream()), "simplex_selftest_wait_timeout")
 
 
 def simplex_last_error() -> str:
