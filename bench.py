@@ -311,9 +311,9 @@ def run_ours(args, rank, world, local):
         value, tmax = aggregate(units, secs, world)
         value_bb, _ = aggregate(units, secs_bb, world)
         # per launch: a graph of `reps` back-to-back launches, timed by events, / reps
-        mean_ms = statistics.mean(_per_launch_ms(graphs[sx.SIMPLEX_MODE_H].replay, 10)) / reps
+        mean_ms = _per_launch_ms(graphs[sx.SIMPLEX_MODE_H].replay, 10)[0] / reps
         med_ms = mean_ms
-        mean_bb = statistics.mean(_per_launch_ms(graphs[sx.SIMPLEX_MODE_BB].replay, 10)) / reps
+        mean_bb = _per_launch_ms(graphs[sx.SIMPLEX_MODE_BB].replay, 10)[0] / reps
         alg_bytes = 4 * cells
         achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
         res.update(
