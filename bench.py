@@ -170,6 +170,14 @@ def _workload(name, args=None):
     return wl
 
 
+def _map_name(info):
+    if info["m"] == 2 and info["band"]:
+        return f"H, trapezoid bands of {info['band']} tile rows (r=1/2, beta=2)"
+    if info["m"] == 2:
+        return "H, single Eq. map2d grid (r=1/2, beta=2)"
+    return f"H (r=1/{info['r_inv']}, beta={info['beta']})"
+
+
 def _time_region(fn, steps, warmup, world):
     import torch
     for _ in range(warmup):
@@ -211,7 +219,7 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_kind = _peaks()
     res = {}
     if isinstance(wl, inputs.CAWorkload):
-        mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block)
+        mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, band=args.band if wl.m == 2 else None)
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
@@ -244,7 +252,7 @@ def run_ours(args, rank, world, local):
             dtype="u8", data="synthetic",
             config={"workload": wl.name, "m": wl.m, "n": wl.n, "array": f"{mp.side}^{wl.m} uint8",
                     "tile": f"{wl.block}^{wl.m}", "ca_steps_per_step": wl.steps, "p": wl.p,
-                    "rule": "B3/S23" if wl.m == 2 else "B5/S45", "map": "H (r=1/2, beta=2)",
+                    "rule": "B3/S23" if wl.m == 2 else "B5/S45", "map": _map_name(info),
                     "cells": cells, "parallelism": "replicas" if world > 1 else "single",
                     "l2": "inputs 1 GiB per grid >> 129 MB L2, no flush"},
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -280,7 +288,7 @@ def run_ours(args, rank, world, local):
         assert sx.simplex_device_status() == 0
     else:
         beta = 2 if wl.m <= 3 else wl.m
-        mp = sx.simplex_map_create(wl.m, wl.n, 2, beta, wl.block)
+        mp = sx.simplex_map_create(wl.m, wl.n, 2, beta, wl.block, band=args.band if wl.m == 2 else None)
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         out = torch.zeros(mp.numel, dtype=torch.int32, device="cuda")
@@ -321,7 +329,7 @@ def run_ours(args, rank, world, local):
             ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="u32", data="synthetic",
             config={"workload": wl.name, "m": wl.m, "n": wl.n, "array": f"{mp.side}^{wl.m} uint32",
-                    "tile": f"{wl.block}^{wl.m}", "writes_per_step": reps, "cells": cells,
+                    "tile": f"{wl.block}^{wl.m}", "writes_per_step": reps, "cells": cells, "map": _map_name(info),
                     "parallelism": "replicas" if world > 1 else "single",
                     "l2": "array re-written back to back (L2-resident when it fits)"},
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -414,6 +422,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller case of the workload)")
     ap.add_argument("--block", type=int, default=None, help="override the tile side")
+    ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
     ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -65,6 +65,8 @@ typedef struct simplex_map_info {
     int64_t side;           /* array side in cells */
     int32_t N;              /* tiles per axis of the block lattice (power of two) */
     int32_t log2N;
+    int32_t band;           /* m = 2 trapezoid band height in tiles; 0 = single H2 grid */
+    int32_t Ne;             /* m = 2 trapezoid form: block-triangle side (multiple of band) */
     uint64_t cells;         /* C(n+m, m), Eq. 1 */
     uint64_t useful_blocks; /* tiles holding at least one cell: C(floor(n/rho)+m, m) */
     uint64_t h_blocks;      /* CUDA blocks one H launch starts */
@@ -97,6 +99,31 @@ int simplex_map_create(int m, int64_t n, int r_inv, int beta, int block, simplex
  * rows start on 16-byte boundaries for any n). */
 int simplex_map_create_padded(int m, int64_t n, int r_inv, int beta, int block,
                               int64_t side, simplex_map_t *out);
+
+typedef struct simplex_map_params {
+    int32_t m, r_inv, beta, block; /* as simplex_map_create */
+    int64_t n;
+    int64_t side;                  /* array side, >= n + 1; 0 means n + 1 */
+    int32_t band;                  /* m = 2 only, see below; must be 0 or -1 for m > 2 */
+    int32_t reserved;              /* must be 0 */
+} simplex_map_params_t;
+
+/*
+ * simplex_map_create_ex -- as simplex_map_create with every planning choice
+ * explicit.  For m = 2, `band` selects the form of H:
+ *   band > 0 (a power of two): the trapezoid form of Sec. 4.2 (Eq. trapezoids,
+ *     concurrent trapezoids), all in one launch.  The block triangle of side
+ *     Ne = ceil(ceil((n+1)/block) / band) * band is cut into bands of `band`
+ *     tile rows; band k is a trapezoid: a rectangle of band x (Ne - (k+1) band)
+ *     tiles taken row by row, then a triangle of side `band` mapped by Eq.
+ *     map2d plus its diagonal.  Ne needs no power of two, and consecutive
+ *     CUDA blocks walk whole rows of tiles, which keeps stencil halos in L2.
+ *   band = 0: automatic (currently 8).
+ *   band = -1: the single grid of Eq. map2d (Thm. 1) on the power-of-two side
+ *     N, with the diagonal row appended.
+ * simplex_map_create and simplex_map_create_padded use band = 0.
+ */
+int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out);
 
 /* Frees the map, its cached CUDA graphs and its capture stream.  NULL is a no-op. */
 int simplex_map_destroy(simplex_map_t map);

@@ -62,6 +62,9 @@ uint64_t binom(uint64_t n, int k)
     return (uint64_t)r;
 }
 
+// Trapezoid band height (tiles) the automatic plan uses for m = 2.
+constexpr int kDefaultBand = 8;
+
 struct GraphEntry {
     uint8_t *a, *b;
     int steps;
@@ -83,7 +86,7 @@ struct simplex_map {
 
 namespace {
 
-int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, sx::Plan *p)
+int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, int band, sx::Plan *p)
 {
     if (m < 2 || m > 4) return fail(SIMPLEX_EINVAL, "m must be 2, 3 or 4 (got %d)", m);
     if (n < 0) return fail(SIMPLEX_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
@@ -122,7 +125,18 @@ int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, s
     p->side = side;
     p->bb_blocks = ipow((uint64_t)N, m);
     const uint64_t h2 = sx::h2_cover_blocks((int32_t)N);
-    if (m == 2) {
+    if (m != 2 && band > 0)
+        return fail(SIMPLEX_EINVAL, "band (trapezoid height) applies to m = 2 only (got %d for m = %d)", band, m);
+    if (m == 2 && band > 0) {
+        if (!is_pow2(band) || band > 32768)
+            return fail(SIMPLEX_EINVAL, "band must be a power of two <= 32768 (got %d)", band);
+        const int64_t Ne = (nb + band - 1) / band * band;
+        p->band = band;
+        p->log_band = ilog2_i64(band);
+        p->Ne = (int32_t)Ne;
+        p->nbands = (int32_t)(Ne / band);
+        p->h_blocks = (uint64_t)Ne * (uint64_t)(Ne + 1) / 2;
+    } else if (m == 2) {
         p->h_blocks = h2;
     } else if (m == 3 && beta == 2) {
         const uint64_t half = (uint64_t)N / 2;
@@ -281,19 +295,30 @@ int enqueue_run(simplex_map_t map, uint8_t *a, uint8_t *b, int steps, const sx::
 
 extern "C" {
 
-int simplex_map_create_padded(int m, int64_t n, int r_inv, int beta, int block, int64_t side, simplex_map_t *out)
+int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out)
 {
-    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    if (!params || !out) return fail(SIMPLEX_EINVAL, "params and out must not be NULL");
     *out = nullptr;
+    if (params->reserved != 0) return fail(SIMPLEX_EINVAL, "params->reserved must be 0");
+    const int64_t side = params->side ? params->side : params->n + 1;
+    int band = params->band;
+    if (band == 0) band = params->m == 2 ? kDefaultBand : 0;  // automatic
+    if (band < 0) band = 0;                                   // single H2 grid
     sx::Plan p;
-    int rc = build_plan(m, n, r_inv, beta, block, side, &p);
+    int rc = build_plan(params->m, params->n, params->r_inv, params->beta, params->block, side, band, &p);
     if (rc) return rc;
     simplex_map *map = new (std::nothrow) simplex_map();
     if (!map) return fail(SIMPLEX_ENOMEM, "host allocation failed");
     map->plan = p;
-    map->r_inv = r_inv;
+    map->r_inv = params->r_inv;
     *out = map;
     return SIMPLEX_OK;
+}
+
+int simplex_map_create_padded(int m, int64_t n, int r_inv, int beta, int block, int64_t side, simplex_map_t *out)
+{
+    const simplex_map_params_t prm = {m, r_inv, beta, block, n, side, 0, 0};
+    return simplex_map_create_ex(&prm, out);
 }
 
 int simplex_map_create(int m, int64_t n, int r_inv, int beta, int block, simplex_map_t *out)
@@ -325,6 +350,8 @@ int simplex_map_info(simplex_map_t map, simplex_map_info_t *out)
     out->side = p.side;
     out->N = p.N;
     out->log2N = p.logN;
+    out->band = p.band;
+    out->Ne = p.Ne;
     out->cells = binom((uint64_t)p.n + (uint64_t)p.m, p.m);
     out->useful_blocks = binom((uint64_t)(p.n / p.rho) + (uint64_t)p.m, p.m);
     out->h_blocks = p.h_blocks;

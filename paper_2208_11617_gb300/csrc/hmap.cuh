@@ -15,6 +15,12 @@
 //   m = 2  H2 (Sec. 4.1, Thm. 1, Eq. map2d) on the N/2 x (N-1) grid covers the
 //          blocks with sum <= N-2; a row of N blocks covers the diagonal
 //          sum = N-1 ("extra threads at the diagonal", Sec. 4.1).
+//          Trapezoid form (Sec. 4.2, concurrent trapezoids, in one launch):
+//          the block triangle of side Ne (any multiple of the band height h)
+//          is cut into bands of h tile rows; band k is a trapezoid made of a
+//          rectangle h x (Ne - (k+1) h) (identity map) and a triangle of side
+//          h mapped by H2 + diagonal.  Bands run in order, so the blocks in
+//          flight stream whole memory rows.
 //   m = 3  beta = 2: H3 (Sec. 4.3): the big cube (N/2)^3 at the corner, a layer
 //          of height N/4 holding the smaller cubes laid out by the 2-D levels
 //          b, q of Thm. 1, and the hinge that reflects each cube's overhang
@@ -51,6 +57,11 @@ struct Plan {
     int32_t beta;
     int64_t n;
     int64_t side;
+    // m = 2 trapezoid form: band height h (power of two) and triangle side Ne
+    // (a multiple of h, >= ceil((n+1)/rho)); band = 0 selects the single H2
+    // grid on the power-of-two side N
+    int32_t band, log_band;
+    int32_t Ne, nbands;
     uint64_t h_blocks;   // CUDA blocks of one H launch
     uint64_t bb_blocks;  // N^m
     // H3 (beta = 2): region sizes
@@ -104,6 +115,36 @@ SX_HD bool h2_cover(uint64_t v, int32_t N, int32_t logN, int32_t *X)
     const int32_t d = (int32_t)(v - grid);
     X[0] = d;
     X[1] = N - 1 - d;
+    return true;
+}
+
+// Blocks before band k of the trapezoid form: sum over j < k of
+// h (Ne - (j+1) h) + h (h+1) / 2 = k h (2 Ne - k h + 1) / 2.
+SX_HD uint64_t trapezoid_prefix(int64_t k, int64_t h, int64_t Ne) { return (uint64_t)(k * h * (2 * Ne - k * h + 1) / 2); }
+
+SX_HD bool h2_trapezoids(const Plan &p, uint64_t v, int32_t *X)
+{
+    const int64_t h = p.band, Ne = p.Ne;
+    // band k: the largest k with prefix(k) <= v (binary search, uniform per block)
+    int32_t lo = 0, hi = p.nbands - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (trapezoid_prefix(mid, h, Ne) <= v) lo = mid; else hi = mid - 1;
+    }
+    const int32_t k = lo;
+    uint64_t u = v - trapezoid_prefix(k, h, Ne);
+    const int32_t W = (int32_t)(Ne - (int64_t)(k + 1) * h);  // rectangle width
+    const uint64_t rect = (uint64_t)h * (uint64_t)W;
+    if (u < rect) {
+        const uint32_t i = (uint32_t)u / (uint32_t)W;  // rectangle row-major
+        X[0] = (int32_t)(k * h) + (int32_t)i;
+        X[1] = (int32_t)((uint32_t)u - i * (uint32_t)W);
+        return true;
+    }
+    int32_t Y[2];
+    h2_cover(u - rect, (int32_t)h, p.log_band, Y);  // triangle of side h
+    X[0] = (int32_t)(k * h) + Y[0];
+    X[1] = W + Y[1];
     return true;
 }
 
@@ -228,7 +269,7 @@ SX_HD bool decode(const Plan &p, int kind, uint64_t v, int32_t *X)
             X[M - 1 - i] = (int32_t)((v >> (i * p.logN)) & (uint64_t)(p.N - 1));
         return true;
     }
-    if (M == 2) return h2_cover(v, p.N, p.logN, X);
+    if (M == 2) return p.band ? h2_trapezoids(p, v, X) : h2_cover(v, p.N, p.logN, X);
     if (M == 3 && p.beta == 2) return h3_cover(p, v, X);
     return Cover<M>::run(p, v, X);
 }

@@ -31,7 +31,7 @@ SIMPLEX_LEVEL_BLOCK = 0
 SIMPLEX_LEVEL_CELL = 1
 
 EXPORTED = (
-    "simplex_map_create", "simplex_map_create_padded", "simplex_map_destroy", "simplex_map_info",
+    "simplex_map_create", "simplex_map_create_padded", "simplex_map_create_ex", "simplex_map_destroy", "simplex_map_info",
     "simplex_map_block", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
     "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
     "simplex_version", "simplex_selftest_wait_timeout",
@@ -50,12 +50,19 @@ _i32, _i64, _u32, _u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c
 class SimplexMapInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("r_inv", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("n", ctypes.c_int64), ("side", ctypes.c_int64),
-                ("N", ctypes.c_int32), ("log2N", ctypes.c_int32), ("cells", ctypes.c_uint64),
+                ("N", ctypes.c_int32), ("log2N", ctypes.c_int32), ("band", ctypes.c_int32),
+                ("Ne", ctypes.c_int32), ("cells", ctypes.c_uint64),
                 ("useful_blocks", ctypes.c_uint64), ("h_blocks", ctypes.c_uint64),
                 ("bb_blocks", ctypes.c_uint64), ("h_set_blocks", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SimplexMapParams(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("r_inv", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("n", ctypes.c_int64), ("side", ctypes.c_int64),
+                ("band", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _sig(name, args):
@@ -67,6 +74,7 @@ def _sig(name, args):
 
 _sig("simplex_map_create", [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(_vp)])
 _sig("simplex_map_create_padded", [_i32, _i64, _i32, _i32, _i32, _i64, ctypes.POINTER(_vp)])
+_sig("simplex_map_create_ex", [ctypes.POINTER(SimplexMapParams), ctypes.POINTER(_vp)])
 _sig("simplex_map_destroy", [_vp])
 _sig("simplex_map_info", [_vp, ctypes.POINTER(SimplexMapInfo)])
 _sig("simplex_map_block", [_vp, _i32, _u64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i32)])
@@ -153,12 +161,18 @@ class SimplexMap:
 
 
 def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, block: int = 16,
-                       side: int | None = None) -> SimplexMap:
-    """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4)."""
+                       side: int | None = None, band: int | None = None) -> SimplexMap:
+    """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4).
+
+    band (m = 2): None/0 automatic trapezoid bands, > 0 band height, -1 the
+    single grid of Eq. map2d."""
     if beta is None:
         beta = 2 if m <= 3 else m
     h = _vp()
-    if side is None:
+    if band is not None:
+        prm = SimplexMapParams(m, r_inv, beta, block, n, side or 0, band, 0)
+        _check(_lib.simplex_map_create_ex(ctypes.byref(prm), ctypes.byref(h)), "simplex_map_create_ex")
+    elif side is None:
         _check(_lib.simplex_map_create(m, n, r_inv, beta, block, ctypes.byref(h)), "simplex_map_create")
     else:
         _check(_lib.simplex_map_create_padded(m, n, r_inv, beta, block, side, ctypes.byref(h)),

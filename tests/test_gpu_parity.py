@@ -183,6 +183,29 @@ def test_ca_run_matches_oracle(case, mode):
     np.testing.assert_array_equal(live, ref_live)
 
 
+@pytest.mark.parametrize("band", [-1, 2, 32])
+@pytest.mark.parametrize("n,block,side", [(4095, 128, None), (1000, 32, 1008), (2047, 64, None)])
+def test_ca_run_h2_forms_match_oracle(band, n, block, side):
+    """Both forms of H for m = 2 (the single Eq. map2d grid, band = -1, and
+    trapezoid bands) give the oracle's grid."""
+    mp = sx.simplex_map_create(2, n, 2, 2, block, side=side, band=band)
+    thr = inputs.bernoulli_threshold(0.5)
+    fin, live = _gpu_run(mp, n, 12, inputs.B3S23, 31, thr, sx.SIMPLEX_MODE_H)
+    got, rest = _logical(fin, mp, n)
+    ref, ref_live = oracle.ca_run(2, n, 12, *inputs.B3S23, oracle.ca_init(2, n, 31, thr))
+    np.testing.assert_array_equal(got, ref)
+    assert not rest.any()
+    np.testing.assert_array_equal(live, ref_live)
+
+
+@pytest.mark.parametrize("band", [-1, 4])
+def test_write_h2_forms_match_oracle(band):
+    mp = sx.simplex_map_create(2, 1023, 2, 2, 16, band=band)
+    out = torch.zeros(mp.numel, dtype=torch.int32, device=DEV)
+    sx.simplex_write(mp, out, 77)
+    np.testing.assert_array_equal(out.view(mp.shape).cpu().numpy().view(np.uint32), oracle.write(2, 1023, 77))
+
+
 def test_ca_step_by_step_equals_graph_run():
     mp = sx.simplex_map_create(2, 2047, 2, 2, 64)
     thr = inputs.bernoulli_threshold(0.5)

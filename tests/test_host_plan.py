@@ -49,7 +49,12 @@ def test_info_counts(m, n, block):
     assert info["h_set_blocks"] == (N ** m - beta ** logN) // (2 ** m - beta)
     if m == 2:
         assert info["h_set_blocks"] == N * (N - 1) // 2          # Eq. m2 (Lemma 1)
-        assert info["h_blocks"] == N * (N - 1) // 2 + N
+        band = info["band"]
+        Ne = -(-nb // band) * band
+        assert info["Ne"] == Ne
+        assert info["h_blocks"] == Ne * (Ne + 1) // 2            # trapezoid bands
+        single = sx.simplex_map_info(sx.simplex_map_create(m, n, 2, beta, block, band=-1))
+        assert single["band"] == 0 and single["h_blocks"] == N * (N - 1) // 2 + N
     if m == 3:
         assert info["h_set_blocks"] == (N ** 3 - N) // 6          # Eq. m3 (Lemma 3)
 
@@ -106,7 +111,7 @@ def test_map_block_rejects_out_of_range():
 @pytest.mark.parametrize("N", [2, 4, 8, 16, 32, 64, 128, 256])
 def test_h2_grid_is_eq_map2d(N):
     rho = 4
-    mp = sx.simplex_map_create(2, N * rho - 1, 2, 2, rho)
+    mp = sx.simplex_map_create(2, N * rho - 1, 2, 2, rho, band=-1)
     assert mp.info.N == N
     seen = set()
     for v in range((N // 2) * (N - 1)):
@@ -138,6 +143,36 @@ COVER_CASES = [(2, n, 4) for n in (0, 1, 3, 4, 7, 8, 15, 16, 17, 31, 63, 100, 12
     [(3, n, 4, 2) for n in (0, 3, 4, 7, 8, 15, 31, 63, 100, 127, 255)] + \
     [(3, n, 4, 3) for n in (0, 7, 15, 31, 63, 100, 127)] + \
     [(4, n, 4, 4) for n in (0, 3, 7, 15, 31, 50, 63)]
+
+
+@pytest.mark.parametrize("band", [-1, 1, 2, 4, 8, 16, 64])
+@pytest.mark.parametrize("n,rho", [(0, 4), (3, 4), (4, 4), (31, 4), (63, 4), (100, 4), (101, 8), (255, 4),
+                                   (1000, 16), (1023, 4), (77, 4)])
+def test_h2_forms_cover_each_simplex_block_exactly_once(band, n, rho):
+    mp = sx.simplex_map_create(2, n, 2, 2, rho, band=band)
+    got = _covered(mp, sx.SIMPLEX_MODE_H)
+    ind = oracle.block_indicator(2, n, rho)
+    want = {tuple(int(i) for i in x) for x in np.argwhere(ind)}
+    assert set(got) == want
+    assert all(c == 1 for c in got.values())
+
+
+def test_h2_trapezoid_bands_walk_rows_in_order():
+    # consecutive blocks of a band's rectangle are consecutive tiles of a row
+    mp = sx.simplex_map_create(2, 64 * 16 - 1, 2, 2, 16, band=8)
+    Ne = mp.info.Ne
+    first = [sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)[0] for v in range(Ne - 8)]
+    assert first == [(0, j) for j in range(Ne - 8)]
+
+
+def test_band_rejected_for_m3_and_bad_values():
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_create(3, 63, 2, 2, 4, band=8)
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_create(2, 63, 2, 2, 4, band=6)
+    prm = sx.SimplexMapParams(2, 2, 2, 4, 63, 0, 0, 1)
+    h = sx._vp()
+    assert sx._lib.simplex_map_create_ex(sx.ctypes.byref(prm), sx.ctypes.byref(h)) == sx.SIMPLEX_EINVAL
 
 
 @pytest.mark.parametrize("case", COVER_CASES)
