@@ -219,7 +219,8 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_kind = _peaks()
     res = {}
     if isinstance(wl, inputs.CAWorkload):
-        mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, band=args.band if wl.m == 2 else None)
+        mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, band=args.band if wl.m == 2 else None,
+                                   launch=args.launch)
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
@@ -257,7 +258,8 @@ def run_ours(args, rank, world, local):
                     "l2": "inputs 1 GiB per grid >> 129 MB L2, no flush"},
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                       "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                      "kernel": f"ca{wl.m}_step_kernel<{wl.block}>", "alg_bytes_per_launch": alg_bytes,
+                      "kernel": (f"ca{wl.m}_step_persistent<{wl.block}>" if info["launch"] == 2
+                                 else f"ca{wl.m}_step_kernel<{wl.block}>"), "alg_bytes_per_launch": alg_bytes,
                       "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
             clocks=clk,
             gpu_launches=args.steps * (wl.steps + 1),
@@ -423,6 +425,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override n (smaller case of the workload)")
     ap.add_argument("--block", type=int, default=None, help="override the tile side")
     ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
+    ap.add_argument("--launch", type=int, default=0, help="automaton step form: 0 auto, 1 grid, 2 persistent")
     ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

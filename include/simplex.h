@@ -67,6 +67,8 @@ typedef struct simplex_map_info {
     int32_t log2N;
     int32_t band;           /* m = 2 trapezoid band height in tiles; 0 = single H2 grid */
     int32_t Ne;             /* m = 2 trapezoid form: block-triangle side (multiple of band) */
+    int32_t launch;         /* automaton step form: 1 grid, 2 persistent */
+    int32_t reserved;
     uint64_t cells;         /* C(n+m, m), Eq. 1 */
     uint64_t useful_blocks; /* tiles holding at least one cell: C(floor(n/rho)+m, m) */
     uint64_t h_blocks;      /* CUDA blocks one H launch starts */
@@ -105,7 +107,7 @@ typedef struct simplex_map_params {
     int64_t n;
     int64_t side;                  /* array side, >= n + 1; 0 means n + 1 */
     int32_t band;                  /* m = 2 only, see below; must be 0 or -1 for m > 2 */
-    int32_t reserved;              /* must be 0 */
+    int32_t launch;                /* automaton step: 0 automatic, 1 grid, 2 persistent (see below) */
 } simplex_map_params_t;
 
 /*
@@ -121,7 +123,14 @@ typedef struct simplex_map_params {
  *   band = 0: automatic (currently 8).
  *   band = -1: the single grid of Eq. map2d (Thm. 1) on the power-of-two side
  *     N, with the diagonal row appended.
- * simplex_map_create and simplex_map_create_padded use band = 0.
+ * `launch` selects how simplex_ca_step runs the map's blocks:
+ *   1 (grid): one CUDA block per block of the map, the paper's execution
+ *     model (Sec. 2): the grid of a launch is the map's parallel space;
+ *   2 (persistent): one CTA per SM walks the map's blocks in the same order
+ *     through a ring of shared-memory stages, with TMA loads for the next
+ *     tiles in flight while it computes the current one (m = 3, block 32);
+ *   0 (automatic): persistent where it exists, grid elsewhere.
+ * simplex_map_create and simplex_map_create_padded use band = 0, launch = 0.
  */
 int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out);
 

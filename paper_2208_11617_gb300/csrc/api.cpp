@@ -299,13 +299,22 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
 {
     if (!params || !out) return fail(SIMPLEX_EINVAL, "params and out must not be NULL");
     *out = nullptr;
-    if (params->reserved != 0) return fail(SIMPLEX_EINVAL, "params->reserved must be 0");
+    if (params->launch < 0 || params->launch > 2)
+        return fail(SIMPLEX_EINVAL, "params->launch must be 0 (automatic), 1 (grid) or 2 (persistent), got %d",
+                    params->launch);
     const int64_t side = params->side ? params->side : params->n + 1;
     int band = params->band;
     if (band == 0) band = params->m == 2 ? kDefaultBand : 0;  // automatic
     if (band < 0) band = 0;                                   // single H2 grid
     sx::Plan p;
     int rc = build_plan(params->m, params->n, params->r_inv, params->beta, params->block, side, band, &p);
+    if (rc == SIMPLEX_OK) {
+        // automatic: the persistent pipelined step where it is implemented (m = 3, block 32)
+        const bool can_persist = p.m == 3 && p.rho == 32;
+        if (params->launch == 2 && !can_persist)
+            return fail(SIMPLEX_EUNSUPPORTED, "the persistent automaton step exists for m = 3, block 32");
+        p.persistent = (params->launch == 2 || (params->launch == 0 && can_persist)) ? 1 : 0;
+    }
     if (rc) return rc;
     simplex_map *map = new (std::nothrow) simplex_map();
     if (!map) return fail(SIMPLEX_ENOMEM, "host allocation failed");
@@ -352,6 +361,7 @@ int simplex_map_info(simplex_map_t map, simplex_map_info_t *out)
     out->log2N = p.logN;
     out->band = p.band;
     out->Ne = p.Ne;
+    out->launch = p.persistent ? 2 : 1;
     out->cells = binom((uint64_t)p.n + (uint64_t)p.m, p.m);
     out->useful_blocks = binom((uint64_t)(p.n / p.rho) + (uint64_t)p.m, p.m);
     out->h_blocks = p.h_blocks;

@@ -62,6 +62,9 @@ struct Plan {
     // grid on the power-of-two side N
     int32_t band, log_band;
     int32_t Ne, nbands;
+    // automaton launch form: 0 = one CTA per block of the map (the paper's
+    // execution model), 1 = persistent CTAs walking the map's blocks
+    int32_t persistent, pad_;
     uint64_t h_blocks;   // CUDA blocks of one H launch
     uint64_t bb_blocks;  // N^m
     // H3 (beta = 2): region sizes

@@ -51,6 +51,71 @@ __device__ __forceinline__ void hsum_staged(const uint8_t *tile, int r, int c, u
 template <int RHO>
 constexpr int ca3_min_blocks() { return RHO == 32 ? 3 : 12; }
 
+// One tile's step from its staged box: thread (tx, ty, tz) owns the 16-byte
+// chunk tx of row x2 = y0 + ty and walks RZ planes x1 = z0 + tz*RZ ... along
+// x1.  Returns the live cells it wrote.
+template <int RHO, int RZ, bool ORK>
+__device__ __forceinline__ uint32_t ca3_tile(const uint8_t *tile, const Plan &p, const Rule &rule,
+                                             uint8_t *__restrict__ out, int64_t x0, int64_t y0, int64_t z0,
+                                             bool partial, int tx, int ty, int tz)
+{
+    constexpr int BW = RHO + 32, BH = RHO + 2;
+    constexpr bool SWZ = (BW == 64);
+    const int c = 1 + tx;  // staged chunk (chunk 0 is the left halo)
+    // staged row r = zz * BH + yy holds x1 = z0 + zz - 1, x2 = y0 + yy - 1
+    const int64_t xc = x0 + 16 * tx;
+    const int64_t x2 = y0 + ty;
+    const int zb = tz * RZ;  // first output plane of this thread
+    uint32_t pp[4], pc[4], ac[4], lacc = 0;
+    {
+        uint32_t h0[4], h1[4], h2[4], cc[4];
+        int r = zb * BH + ty;
+        hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
+        hsum_staged<BW, SWZ>(tile, r + 1, c, h1, cc);
+        hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) pp[w] = h0[w] + h1[w] + h2[w];
+        r += BH;
+        hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
+        hsum_staged<BW, SWZ>(tile, r + 1, c, h1, ac);
+        hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) pc[w] = h0[w] + h1[w] + h2[w];
+    }
+#pragma unroll
+    for (int i = 0; i < RZ; ++i) {
+        uint32_t h0[4], h1[4], h2[4], cc[4], an[4], pn[4], s[4], nw[4];
+        const int r = (zb + i + 2) * BH + ty;
+        hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
+        hsum_staged<BW, SWZ>(tile, r + 1, c, h1, an);
+        hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            pn[w] = h0[w] + h1[w] + h2[w];
+            s[w] = pp[w] + pc[w] + pn[w];
+        }
+        next_state4<ORK>(s, ac, rule, nw);
+        const int64_t x1 = z0 + zb + i;
+        bool store = true;
+        if (partial) {
+            const int64_t c64 = p.n - x1 - x2 - xc + 1;
+            const int cnt = (int)(c64 < 0 ? 0 : (c64 > 16 ? 16 : c64));
+#pragma unroll
+            for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(cnt, w);
+            store = cnt > 0;
+        }
+        if (store) store16(out + (x1 * p.side + x2) * p.side + xc, nw);
+        lacc += nw[0] + nw[1] + nw[2] + nw[3];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            pp[w] = pc[w];
+            pc[w] = pn[w];
+            ac[w] = an[w];
+        }
+    }
+    return byte_sum(lacc);
+}
+
 template <int RHO, int RZ, bool ORK>
 __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<RHO>())
     ca3_step_kernel(const __grid_constant__ CUtensorMap tin, uint8_t *__restrict__ out, const Plan p,
@@ -69,7 +134,6 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<
     const int tx = tid % TX;
     const int ty = (tid / TX) % RHO;         // x2 within the tile
     const int tz = tid / (TX * RHO);         // plane segment along x1
-    const int c = 1 + tx;                    // staged chunk (chunk 0 is the left halo)
     uint32_t phase = 0, my_live = 0;
     if (tid == 0) {
         prefetch_tmap(&tin);
@@ -99,59 +163,93 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<
             return;
         }
 
-        // staged row r = zz * BH + yy holds x1 = z0 + zz - 1, x2 = y0 + yy - 1
-        const int64_t xc = x0 + 16 * tx;
-        const int64_t x2 = y0 + ty;
-        const int zb = tz * RZ;  // first output plane of this thread
-        uint32_t pp[4], pc[4], ac[4], lacc = 0;
-        {
-            uint32_t h0[4], h1[4], h2[4], cc[4];
-            int r = zb * BH + ty;
-            hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
-            hsum_staged<BW, SWZ>(tile, r + 1, c, h1, cc);
-            hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) pp[w] = h0[w] + h1[w] + h2[w];
-            r += BH;
-            hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
-            hsum_staged<BW, SWZ>(tile, r + 1, c, h1, ac);
-            hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) pc[w] = h0[w] + h1[w] + h2[w];
-        }
-#pragma unroll
-        for (int i = 0; i < RZ; ++i) {
-            uint32_t h0[4], h1[4], h2[4], cc[4], an[4], pn[4], s[4], nw[4];
-            const int r = (zb + i + 2) * BH + ty;
-            hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
-            hsum_staged<BW, SWZ>(tile, r + 1, c, h1, an);
-            hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                pn[w] = h0[w] + h1[w] + h2[w];
-                s[w] = pp[w] + pc[w] + pn[w];
-            }
-            next_state4<ORK>(s, ac, rule, nw);
-            const int64_t x1 = z0 + zb + i;
-            bool store = true;
-            if (partial) {
-                const int64_t c64 = p.n - x1 - x2 - xc + 1;
-                const int cnt = (int)(c64 < 0 ? 0 : (c64 > 16 ? 16 : c64));
-#pragma unroll
-                for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(cnt, w);
-                store = cnt > 0;
-            }
-            if (store) store16(out + (x1 * p.side + x2) * p.side + xc, nw);
-            lacc += nw[0] + nw[1] + nw[2] + nw[3];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                pp[w] = pc[w];
-                pc[w] = pn[w];
-                ac[w] = an[w];
-            }
-        }
-        my_live += byte_sum(lacc);
+        my_live += ca3_tile<RHO, RZ, ORK>(tile, p, rule, out, x0, y0, z0, partial, tx, ty, tz);
         __syncthreads();
+    }
+    if (live) block_add_u64(live, my_live, red);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form: one CTA per SM walks the map's blocks v = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (the same H or bounding-box decode) through a
+// ring of S shared-memory stages.  Thread 0 keeps S - 1 TMA loads in flight
+// ahead of the tile the CTA is computing, so loads and compute overlap
+// instead of every CTA waiting for its own load.
+template <int RHO, int T>
+struct Ca3Persist {
+    static constexpr int TX = RHO / 16;
+    static constexpr int ZS = T / (TX * RHO);  // plane segments per tile
+    static constexpr int RZ = RHO / ZS;
+    static constexpr uint32_t kBox = (RHO + 32) * (RHO + 2) * (RHO + 2);
+    static constexpr uint32_t kStage = (kBox + 511u) & ~511u;
+    static constexpr int S = (3 * kStage + 512 <= 227 * 1024) ? 3 : 2;
+    static constexpr int kSmem = S * kStage + 512;
+};
+
+template <int RHO, int T, bool ORK>
+__global__ void __launch_bounds__(T, 1)
+    ca3_step_persistent(const __grid_constant__ CUtensorMap tin, uint8_t *__restrict__ out, const Plan p,
+                        const Rule rule, int kind, uint64_t nblocks, unsigned long long *__restrict__ live)
+{
+    using C = Ca3Persist<RHO, T>;
+    constexpr int S = C::S;
+    extern __shared__ uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ int4 info[S];  // x0, y0, z0 of the staged tile; w: 1 = valid, 2 = partial
+    __shared__ uint32_t red[32];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 511) & ~uintptr_t(511));
+    const int tid = threadIdx.x;
+    const int tx = tid % C::TX, ty = (tid / C::TX) % RHO, tz = tid / (C::TX * RHO);
+    uint64_t vnext = blockIdx.x;  // producer state (thread 0)
+    uint32_t my_live = 0;
+
+    // thread 0: find the next block with a tile and start its load into stage s
+    auto produce = [&](int s) {
+        while (vnext < nblocks) {
+            const uint64_t v = vnext;
+            vnext += gridDim.x;
+            int32_t X[3];
+            if (!decode<3>(p, kind, v, X)) continue;
+            const int64_t z0 = (int64_t)X[0] * RHO, y0 = (int64_t)X[1] * RHO, x0 = (int64_t)X[2] * RHO;
+            if (z0 + y0 + x0 > p.n) continue;
+            const bool partial = z0 + y0 + x0 + 3 * (RHO - 1) > p.n;
+            info[s] = make_int4((int)x0, (int)y0, (int)z0, 1 | (partial ? 2 : 0));
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[s], C::kBox);
+            tma_load_3d(base + s * C::kStage, &tin, (int32_t)(x0 - 16), (int32_t)(y0 - 1), (int32_t)(z0 - 1),
+                        &full[s]);
+            return;
+        }
+        info[s] = make_int4(0, 0, 0, 0);
+    };
+
+    if (tid == 0) {
+        prefetch_tmap(&tin);
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+        for (int s = 0; s < S; ++s) produce(s);
+    }
+    __syncthreads();
+
+    for (int k = 0;; ++k) {
+        const int s = k % S;
+        const int4 inf = info[s];
+        if (!(inf.w & 1)) break;  // the producer ran out of tiles (uniform)
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1), kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&g_ca3_status, 1u);
+                // wait (bounded) for every load still in flight before leaving
+                for (int j = 0; j < S; ++j)
+                    if (info[(k + j) % S].w & 1)
+                        mbar_wait_bounded(&full[(k + j) % S], (uint32_t)(((k + j) / S) & 1), kWaitLimitNs);
+            }
+            return;
+        }
+        my_live += ca3_tile<RHO, C::RZ, ORK>(base + s * C::kStage, p, rule, out, inf.x, inf.y, inf.z,
+                                              (inf.w & 2) != 0, tx, ty, tz);
+        __syncthreads();  // stage s fully read
+        if (tid == 0) produce(s);
     }
     if (live) block_add_u64(live, my_live, red);
 }
@@ -199,9 +297,48 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     return cudaGetLastError();
 }
 
+constexpr int kCa3PersistThreads = 512;
+
+template <bool ORK>
+static cudaError_t prepare_persist_one()
+{
+    using C = Ca3Persist<32, kCa3PersistThreads>;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(ca3_step_persistent<32, kCa3PersistThreads, ORK>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
+    return e;
+}
+
+static cudaError_t launch_persist(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
+                                  unsigned long long *live, cudaStream_t st)
+{
+    using C = Ca3Persist<32, kCa3PersistThreads>;
+    cudaError_t e = prepare_persist_one<false>();
+    if (e == cudaSuccess) e = prepare_persist_one<true>();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const uint64_t g = nb < (uint64_t)sms ? (nb ? nb : 1) : (uint64_t)sms;  // one CTA per SM
+    if (rule.or_k)
+        ca3_step_persistent<32, kCa3PersistThreads, true><<<(unsigned)g, kCa3PersistThreads, C::kSmem, st>>>(
+            tin, out, p, rule, kind, nb, live);
+    else
+        ca3_step_persistent<32, kCa3PersistThreads, false><<<(unsigned)g, kCa3PersistThreads, C::kSmem, st>>>(
+            tin, out, p, rule, kind, nb, live);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
                             unsigned long long *live, cudaStream_t st)
 {
+    if (p.persistent && p.rho == 32) return launch_persist(p, tin, out, rule, kind, live, st);
     switch (p.rho) {
     case 16: return launch_t<16, 4>(p, tin, out, rule, kind, live, st);
     case 32: return launch_t<32, 8>(p, tin, out, rule, kind, live, st);
@@ -211,6 +348,11 @@ cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out,
 
 cudaError_t ca3_prepare(int rho)
 {
+    if (rho == 32) {
+        cudaError_t e = prepare_persist_one<false>();
+        if (e == cudaSuccess) e = prepare_persist_one<true>();
+        if (e != cudaSuccess) return e;
+    }
     switch (rho) {
     case 16: return prepare_t<16, 4>();
     case 32: return prepare_t<32, 8>();

@@ -51,7 +51,8 @@ class SimplexMapInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("r_inv", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("n", ctypes.c_int64), ("side", ctypes.c_int64),
                 ("N", ctypes.c_int32), ("log2N", ctypes.c_int32), ("band", ctypes.c_int32),
-                ("Ne", ctypes.c_int32), ("cells", ctypes.c_uint64),
+                ("Ne", ctypes.c_int32), ("launch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cells", ctypes.c_uint64),
                 ("useful_blocks", ctypes.c_uint64), ("h_blocks", ctypes.c_uint64),
                 ("bb_blocks", ctypes.c_uint64), ("h_set_blocks", ctypes.c_uint64)]
 
@@ -62,7 +63,7 @@ class SimplexMapInfo(ctypes.Structure):
 class SimplexMapParams(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("r_inv", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("n", ctypes.c_int64), ("side", ctypes.c_int64),
-                ("band", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("band", ctypes.c_int32), ("launch", ctypes.c_int32)]
 
 
 def _sig(name, args):
@@ -161,16 +162,17 @@ class SimplexMap:
 
 
 def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, block: int = 16,
-                       side: int | None = None, band: int | None = None) -> SimplexMap:
+                       side: int | None = None, band: int | None = None, launch: int = 0) -> SimplexMap:
     """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4).
 
     band (m = 2): None/0 automatic trapezoid bands, > 0 band height, -1 the
-    single grid of Eq. map2d."""
+    single grid of Eq. map2d.  launch: 0 automatic, 1 grid, 2 persistent
+    automaton step."""
     if beta is None:
         beta = 2 if m <= 3 else m
     h = _vp()
-    if band is not None:
-        prm = SimplexMapParams(m, r_inv, beta, block, n, side or 0, band, 0)
+    if band is not None or launch:
+        prm = SimplexMapParams(m, r_inv, beta, block, n, side or 0, band or 0, launch)
         _check(_lib.simplex_map_create_ex(ctypes.byref(prm), ctypes.byref(h)), "simplex_map_create_ex")
     elif side is None:
         _check(_lib.simplex_map_create(m, n, r_inv, beta, block, ctypes.byref(h)), "simplex_map_create")

@@ -206,6 +206,23 @@ def test_write_h2_forms_match_oracle(band):
     np.testing.assert_array_equal(out.view(mp.shape).cpu().numpy().view(np.uint32), oracle.write(2, 1023, 77))
 
 
+@pytest.mark.parametrize("launch", [1, 2])
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,side,beta", [(255, None, 2), (200, 208, 2), (255, None, 3), (31, 32, 2), (1, 16, 2)])
+def test_ca3_grid_and_persistent_forms_match_oracle(launch, mode, n, side, beta):
+    """The m = 3 step in both launch forms (one CTA per block of the map, and
+    persistent CTAs with a TMA stage ring) gives the oracle's grid."""
+    mp = sx.simplex_map_create(3, n, 2, beta, 32, side=side, launch=launch)
+    assert mp.info.launch == launch
+    thr = inputs.bernoulli_threshold(0.3)
+    fin, live = _gpu_run(mp, n, 7, inputs.B5S45, 17, thr, mode)
+    got, rest = _logical(fin, mp, n)
+    ref, ref_live = oracle.ca_run(3, n, 7, *inputs.B5S45, oracle.ca_init(3, n, 17, thr))
+    np.testing.assert_array_equal(got, ref)
+    assert not rest.any()
+    np.testing.assert_array_equal(live, ref_live)
+
+
 def test_ca_step_by_step_equals_graph_run():
     mp = sx.simplex_map_create(2, 2047, 2, 2, 64)
     thr = inputs.bernoulli_threshold(0.5)

@@ -170,7 +170,7 @@ def test_band_rejected_for_m3_and_bad_values():
         sx.simplex_map_create(3, 63, 2, 2, 4, band=8)
     with pytest.raises(sx.SimplexError):
         sx.simplex_map_create(2, 63, 2, 2, 4, band=6)
-    prm = sx.SimplexMapParams(2, 2, 2, 4, 63, 0, 0, 1)
+    prm = sx.SimplexMapParams(2, 2, 2, 4, 63, 0, 0, 7)
     h = sx._vp()
     assert sx._lib.simplex_map_create_ex(sx.ctypes.byref(prm), sx.ctypes.byref(h)) == sx.SIMPLEX_EINVAL
 
@@ -207,3 +207,13 @@ def test_h3_hinge_valid_blocks_equal_eq_m3(N):
     main = mp.info.h_blocks - plane
     valid = sum(1 for v in range(main) if sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)[1])
     assert valid == (N ** 3 - N) // 6
+
+
+def test_launch_form_choice():
+    assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 32))["launch"] == 2
+    assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 32, launch=1))["launch"] == 1
+    assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 16))["launch"] == 1
+    assert sx.simplex_map_info(sx.simplex_map_create(2, 1023, 2, 2, 128))["launch"] == 1
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_map_create(2, 1023, 2, 2, 128, launch=2)
+    assert ei.value.code == sx.SIMPLEX_EUNSUPPORTED
