@@ -129,7 +129,8 @@ typedef struct simplex_map_params {
  *   2 (persistent): one CTA per SM walks the map's blocks in the same order
  *     through a ring of shared-memory stages, with TMA loads for the next
  *     tiles in flight while it computes the current one (m = 3, block 32);
- *   0 (automatic): persistent where it exists, grid elsewhere.
+ *   0 (automatic): grid (the faster form on GB300 for every tile size
+ *     implemented so far).
  * simplex_map_create and simplex_map_create_padded use band = 0, launch = 0.
  */
 int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out);

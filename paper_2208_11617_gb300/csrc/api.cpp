@@ -309,11 +309,12 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
     sx::Plan p;
     int rc = build_plan(params->m, params->n, params->r_inv, params->beta, params->block, side, band, &p);
     if (rc == SIMPLEX_OK) {
-        // automatic: the persistent pipelined step where it is implemented (m = 3, block 32)
+        // automatic: the grid form (measured faster on GB300 for every tile
+        // size implemented); the persistent form on request (m = 3, block 32)
         const bool can_persist = p.m == 3 && p.rho == 32;
         if (params->launch == 2 && !can_persist)
             return fail(SIMPLEX_EUNSUPPORTED, "the persistent automaton step exists for m = 3, block 32");
-        p.persistent = (params->launch == 2 || (params->launch == 0 && can_persist)) ? 1 : 0;
+        p.persistent = params->launch == 2 ? 1 : 0;
     }
     if (rc) return rc;
     simplex_map *map = new (std::nothrow) simplex_map();

@@ -210,7 +210,8 @@ def test_h3_hinge_valid_blocks_equal_eq_m3(N):
 
 
 def test_launch_form_choice():
-    assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 32))["launch"] == 2
+    assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 32))["launch"] == 1
+    assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 32, launch=2))["launch"] == 2
     assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 32, launch=1))["launch"] == 1
     assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 16))["launch"] == 1
     assert sx.simplex_map_info(sx.simplex_map_create(2, 1023, 2, 2, 128))["launch"] == 1
