@@ -244,6 +244,75 @@ int simplex_ca_run_host(simplex_map_t map, const uint8_t *host_in, uint8_t *host
  */
 int simplex_visit_count(simplex_map_t map, uint32_t *counts, int level, int mode, void *stream);
 
+/* ---- batched engine ------------------------------------------------------
+ *
+ * Many automaton instances of uneven m and n advance together: each step is
+ * ONE persistent launch over the CUDA blocks of every instance's map (H in the
+ * trapezoid form for m = 2, H3 with the hinge or the generic beta = 3 cubes for
+ * m = 3), cut into work items of up to 8 blocks of one instance and handed out
+ * by a device-side work queue (a global atomic counter); a run of `steps`
+ * steps can be captured once into a CUDA graph and replayed.  Every instance's
+ * two grids, map, rule and TMA descriptors live in one caller-provided arena
+ * of device memory.  Results are identical to running each instance alone
+ * with simplex_ca_run.  Not part of the paper: its batched form is the
+ * concurrent-kernel idea of Sec. 4.2/4.3 (several maps in flight at once)
+ * carried to many independent domains.
+ */
+typedef struct simplex_batch *simplex_batch_t;
+
+typedef struct simplex_instance {
+    int32_t m;          /* 2 or 3 */
+    int32_t block;      /* tile side: m = 2: 64 or 128; m = 3: 16 */
+    int32_t beta;       /* m = 3: 2 (hinge) or 3; m = 2: 2 */
+    int32_t band;       /* m = 2 trapezoid band (power of two); 0: automatic */
+    int64_t n;          /* simplex size, >= 0 */
+    uint32_t birth;     /* rule masks, bit k = k live neighbours */
+    uint32_t survive;
+    uint32_t seed;      /* initial state: Bernoulli(threshold / 2^32), as simplex_ca_init */
+    uint32_t threshold;
+} simplex_instance_t;
+
+typedef struct simplex_batch_info {
+    int32_t count;            /* instances */
+    int32_t parity;           /* which of each instance's two grids holds its state */
+    uint64_t items;           /* work items per step */
+    uint64_t blocks;          /* CUDA blocks (map blocks) per step, all instances */
+    uint64_t cells;           /* simplex cells, all instances */
+    uint64_t arena_bytes;     /* device memory simplex_batch_bind needs */
+} simplex_batch_info_t;
+
+/* Plans every instance (host memory only).  Each instance's grids have side
+ * round_up(n + 1, 16).  Errors: SIMPLEX_EINVAL (an instance's parameters; the
+ * message names it), SIMPLEX_ENOMEM. */
+int simplex_batch_create(const simplex_instance_t *instances, int count, simplex_batch_t *out);
+
+int simplex_batch_destroy(simplex_batch_t batch);
+
+int simplex_batch_info(simplex_batch_t batch, simplex_batch_info_t *out);
+
+/* Binds the batch to `arena` (device, 256-byte aligned, >= arena_bytes,
+ * owned by the caller, not shared with anything else while bound): uploads the
+ * descriptors and tensor maps and zeroes every grid.  Synchronous. */
+int simplex_batch_bind(simplex_batch_t batch, void *arena, uint64_t arena_bytes, void *stream);
+
+/* Writes every instance's initial state (its seed and threshold, as
+ * simplex_ca_init) into grid 0 and sets parity 0.  Asynchronous. */
+int simplex_batch_init(simplex_batch_t batch, void *stream);
+
+/*
+ * simplex_batch_run -- `steps` (1..4096) steps of every instance.
+ *   live  device uint64[count * (steps + 1)] or NULL: when given, it is
+ *         zeroed and live[i * (steps + 1) + s] receives instance i's live
+ *         cells after step s (s = 0: before the first step).
+ *   use_graph  nonzero: the launches are captured once per (steps, live,
+ *         parity) into a CUDA graph and replayed.
+ * The state then sits in grid (parity + steps) % 2 of each instance.
+ */
+int simplex_batch_run(simplex_batch_t batch, int steps, unsigned long long *live, int use_graph, void *stream);
+
+/* Device address and side of instance i's current grid (its state). */
+int simplex_batch_grid(simplex_batch_t batch, int i, uint8_t **grid, int64_t *side);
+
 /*
  * simplex_device_status -- reads and clears the library's device-side error
  * word on the current device (synchronous).  *out receives 0 when no kernel

@@ -1,0 +1,91 @@
+"""Autotuner for the batched engine: picks the tile side and (r, beta) per
+(m, n) size class by timing the candidates on the GPU.
+
+Size class of an instance: (m, floor(log2 n)).  Candidates (r = 1/2 is the
+only scale factor implemented):
+  m = 2: tile 64 or 128 (H in trapezoid form, band chosen by the plan);
+  m = 3: tile 16 with beta = 2 (H3 with the hinge) or beta = 3 (every corner
+         recursed).
+For each class the tuner builds a batch of that class's instances alone for
+every candidate, runs a few graph-captured steps, and keeps the candidate with
+the most cell-updates per second.  Results can be cached in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+CANDIDATES = {2: [dict(block=64, beta=2), dict(block=128, beta=2)],
+              3: [dict(block=16, beta=2), dict(block=16, beta=3)]}
+
+
+def size_class(m: int, n: int):
+    return (m, int(math.floor(math.log2(max(n, 1)))))
+
+
+def default_config(m: int, n: int) -> dict:
+    """Untuned choice: 128-cell tiles from n = 1024 up, else 64 (m = 2); 16^3, beta = 2 (m = 3)."""
+    if m == 2:
+        return dict(block=128 if n >= 1024 else 64, beta=2)
+    return dict(block=16, beta=2)
+
+
+def apply(instances, table=None):
+    """Instances with block/beta filled from the tuned table (or the defaults)."""
+    out = []
+    for d in instances:
+        cfg = (table or {}).get(size_class(d["m"], d["n"])) or default_config(d["m"], d["n"])
+        e = dict(d)
+        e.update(block=cfg["block"], beta=cfg["beta"], band=cfg.get("band", 0))
+        out.append(e)
+    return out
+
+
+def _time_batch(sx, torch, insts, steps: int, reps: int) -> float:
+    b = sx.simplex_batch_create(insts)
+    sx.simplex_batch_bind(b)
+    sx.simplex_batch_init(b)
+    sx.simplex_batch_run(b, steps)          # capture + warm up
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        sx.simplex_batch_run(b, steps)
+    e.record()
+    torch.cuda.synchronize()
+    cells = sx.simplex_batch_info(b)["cells"]
+    b.close()
+    return cells * steps * reps / (s.elapsed_time(e) * 1e-3)
+
+
+def tune(instances, steps: int = 4, reps: int = 3, max_per_class: int = 256, cache: str | None = None):
+    """Returns {size class: config}; reads/writes `cache` (JSON) when given."""
+    import torch
+    from . import simplex as sx
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            raw = json.load(f)
+        return {tuple(json.loads(k)): v for k, v in raw.items()}
+    classes = {}
+    for d in instances:
+        classes.setdefault(size_class(d["m"], d["n"]), []).append(d)
+    table = {}
+    t0 = time.perf_counter()
+    for cls, members in sorted(classes.items()):
+        members = members[:max_per_class]
+        best, best_rate = None, -1.0
+        for cand in CANDIDATES[cls[0]]:
+            insts = [dict(d, block=cand["block"], beta=cand["beta"], band=0) for d in members]
+            rate = _time_batch(sx, torch, insts, steps, reps)
+            if rate > best_rate:
+                best, best_rate = dict(cand, rate=rate), rate
+        table[cls] = best
+    table_meta = time.perf_counter() - t0
+    if cache:
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump({json.dumps(list(k)): v for k, v in table.items()}, f, indent=1)
+    tune.last_seconds = table_meta
+    return table

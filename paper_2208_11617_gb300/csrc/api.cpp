@@ -16,9 +16,10 @@
 
 #include "../../include/simplex.h"
 #include "hmap.cuh"
+#include "host.h"
 #include "kernels.h"
 
-namespace {
+namespace sxh {
 
 thread_local std::string g_last_error;
 
@@ -37,6 +38,12 @@ int cuda_fail(cudaError_t e, const char *what)
 {
     return fail(SIMPLEX_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+}  // namespace sxh
+
+using namespace sxh;
+
+namespace {
 
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 
@@ -84,7 +91,7 @@ struct simplex_map {
     std::vector<GraphEntry> graphs;
 };
 
-namespace {
+namespace sxh {
 
 int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, int band, sx::Plan *p)
 {
@@ -147,12 +154,12 @@ int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, i
         uint64_t total = h2;
         for (int d = 3; d <= m; ++d) {
             uint64_t acc = 0;
-            p->level_end[d][0] = 0;
+            p->level_end[d - 3][0] = 0;
             for (int k = 1; k <= logN; ++k) {
                 acc += ipow((uint64_t)d, k - 1) * ipow((uint64_t)(N >> k), d);
-                p->level_end[d][k] = acc;
+                p->level_end[d - 3][k] = acc;
             }
-            p->cube_total[d] = acc;
+            p->cube_total[d - 3] = acc;
             total += acc;
         }
         p->h_blocks = total;
@@ -181,7 +188,7 @@ sx::Rule make_rule(int m, uint32_t birth, uint32_t survive)
     return r;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -219,6 +226,10 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
     if (r != CUDA_SUCCESS) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
     return SIMPLEX_OK;
 }
+
+}  // namespace sxh
+
+namespace {
 
 bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 
@@ -532,7 +543,10 @@ int simplex_device_status(uint32_t *out)
     if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
     e = sx::ca3_read_status(&s3);
     if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
-    *out = s2 | s3;
+    uint32_t sb = 0;
+    e = sx::batch_read_status(&sb);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+    *out = s2 | s3 | sb;
     if (*out) return fail(SIMPLEX_ETIMEOUT, "a kernel gave up a bounded wait for its TMA load (status 0x%x)", *out);
     return SIMPLEX_OK;
 }

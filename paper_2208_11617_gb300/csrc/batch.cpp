@@ -1,0 +1,314 @@
+// batch.cpp -- C ABI of the batched engine (include/simplex.h): planning of
+// every instance, arena layout, descriptor upload, graph capture of runs.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/simplex.h"
+#include "batch.h"
+#include "host.h"
+#include "kernels.h"
+
+using namespace sxh;
+
+namespace {
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+uint64_t binom(uint64_t n, int k)
+{
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return (uint64_t)r;
+}
+
+struct RunGraph {
+    int steps;
+    unsigned long long *live;
+    int parity;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct simplex_batch {
+    std::vector<simplex_instance_t> spec;
+    std::vector<sx::BatchInst> insts;
+    std::vector<sx::BatchItem> items;
+    std::vector<uint64_t> grid_bytes;
+    uint64_t blocks = 0, cells = 0;
+    // arena layout (byte offsets)
+    uint64_t off_insts = 0, off_items = 0, off_tmaps = 0, off_queue = 0, off_grids = 0, bytes = 0;
+    uint8_t *arena = nullptr;
+    int device = -1;
+    int parity = 0;
+    cudaStream_t capture = nullptr;
+    std::vector<RunGraph> graphs;
+};
+
+namespace {
+
+int check_batch(simplex_batch_t b, bool bound)
+{
+    if (!b) return fail(SIMPLEX_EINVAL, "batch is NULL");
+    if (bound && !b->arena) return fail(SIMPLEX_EINVAL, "batch is not bound to an arena (simplex_batch_bind)");
+    return SIMPLEX_OK;
+}
+
+// The whole run as stream work on `st`.
+int enqueue_batch_run(simplex_batch_t b, int steps, unsigned long long *live, int parity, cudaStream_t st)
+{
+    const sx::BatchInst *insts = reinterpret_cast<const sx::BatchInst *>(b->arena + b->off_insts);
+    const sx::BatchItem *items = reinterpret_cast<const sx::BatchItem *>(b->arena + b->off_items);
+    const CUtensorMap *tmaps = reinterpret_cast<const CUtensorMap *>(b->arena + b->off_tmaps);
+    unsigned int *queue = reinterpret_cast<unsigned int *>(b->arena + b->off_queue);
+    const uint32_t nitems = (uint32_t)b->items.size();
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * (size_t)(steps + 1), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(queue)");
+    if (live) {
+        e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * b->insts.size() * (size_t)(steps + 1), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(live)");
+        e = sx::launch_batch_pass(insts, items, nitems, tmaps, b->arena, parity, queue, live, steps + 1, 0, true, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch count launch");
+    }
+    for (int s = 1; s <= steps; ++s) {
+        const int in = (parity + s - 1) & 1;
+        e = sx::launch_batch_pass(insts, items, nitems, tmaps, b->arena, in, queue + s, live, steps + 1, s, false,
+                                  st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
+    }
+    return SIMPLEX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int simplex_batch_create(const simplex_instance_t *instances, int count, simplex_batch_t *out)
+{
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!instances || count <= 0) return fail(SIMPLEX_EINVAL, "need at least one instance");
+    if (count > (1 << 24)) return fail(SIMPLEX_EINVAL, "too many instances (%d)", count);
+    simplex_batch *b = new (std::nothrow) simplex_batch();
+    if (!b) return fail(SIMPLEX_ENOMEM, "host allocation failed");
+    try {
+        b->spec.assign(instances, instances + count);
+        b->insts.resize(count);
+        b->grid_bytes.resize(count);
+    } catch (...) {
+        delete b;
+        return fail(SIMPLEX_ENOMEM, "host allocation failed");
+    }
+    uint64_t grid_off = 0;
+    for (int i = 0; i < count; ++i) {
+        const simplex_instance_t &in = instances[i];
+        sx::BatchInst &bi = b->insts[i];
+        std::memset(&bi, 0, sizeof bi);
+        int body = -1;
+        if (in.m == 2 && in.block == 64) body = sx::kBody2x64;
+        if (in.m == 2 && in.block == 128) body = sx::kBody2x128;
+        if (in.m == 3 && in.block == 16) body = sx::kBody3x16;
+        if (body < 0) {
+            delete b;
+            return fail(SIMPLEX_EINVAL, "instance %d: the batched engine runs m = 2 with block 64 or 128 and m = 3 "
+                                        "with block 16 (got m = %d, block = %d)", i, in.m, in.block);
+        }
+        const int64_t side = (in.n + 16) / 16 * 16;  // round_up(n + 1, 16)
+        int band = 0;
+        if (in.m == 2) {
+            band = in.band;
+            if (band <= 0) {  // automatic: 8 tile rows, fewer for small domains
+                const int64_t nb = (in.n + in.block) / in.block;
+                band = 1;
+                while (band < 8 && band * 2 <= nb) band *= 2;
+            }
+        }
+        int rc = build_plan(in.m, in.n, 2, in.beta, in.block, side, band, &bi.plan);
+        if (rc) {
+            std::string msg = g_last_error;
+            delete b;
+            return fail(rc, "instance %d: %s", i, msg.c_str());
+        }
+        bi.rule = make_rule(in.m, in.birth, in.survive);
+        bi.body = body;
+        bi.tmap = 2 * i;
+        uint64_t gb = 1;
+        for (int d = 0; d < in.m; ++d) gb *= (uint64_t)side;
+        b->grid_bytes[i] = gb;
+        bi.grid[0] = grid_off;
+        grid_off += align_up(gb, 256);
+        bi.grid[1] = grid_off;
+        grid_off += align_up(gb, 256);
+        b->blocks += bi.plan.h_blocks;
+        b->cells += binom((uint64_t)in.n + (uint64_t)in.m, in.m);
+        for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += sx::kBatchChunk) {
+            const uint64_t cnt = bi.plan.h_blocks - v0 < (uint64_t)sx::kBatchChunk ? bi.plan.h_blocks - v0
+                                                                                    : (uint64_t)sx::kBatchChunk;
+            b->items.push_back(sx::BatchItem{(uint32_t)i, (uint32_t)v0, (uint32_t)cnt, 0u});
+        }
+    }
+    if (b->items.size() >= 0xffffff00ull) {
+        delete b;
+        return fail(SIMPLEX_EINVAL, "too many work items (%zu)", b->items.size());
+    }
+    // arena layout
+    uint64_t off = 0;
+    b->off_insts = off;
+    off = align_up(off + sizeof(sx::BatchInst) * (uint64_t)count, 256);
+    b->off_items = off;
+    off = align_up(off + sizeof(sx::BatchItem) * b->items.size(), 256);
+    b->off_tmaps = off;
+    off = align_up(off + sizeof(CUtensorMap) * 2ull * (uint64_t)count, 256);
+    b->off_queue = off;
+    off = align_up(off + sizeof(unsigned int) * (uint64_t)(sx::kBatchMaxSteps + 1), 256);
+    b->off_grids = off;
+    for (auto &bi : b->insts) {
+        bi.grid[0] += off;
+        bi.grid[1] += off;
+    }
+    b->bytes = off + grid_off;
+    *out = b;
+    return SIMPLEX_OK;
+}
+
+int simplex_batch_destroy(simplex_batch_t b)
+{
+    if (!b) return SIMPLEX_OK;
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+    return SIMPLEX_OK;
+}
+
+int simplex_batch_info(simplex_batch_t b, simplex_batch_info_t *out)
+{
+    int rc;
+    if ((rc = check_batch(b, false))) return rc;
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof *out);
+    out->count = (int32_t)b->insts.size();
+    out->parity = b->parity;
+    out->items = b->items.size();
+    out->blocks = b->blocks;
+    out->cells = b->cells;
+    out->arena_bytes = b->bytes;
+    return SIMPLEX_OK;
+}
+
+int simplex_batch_bind(simplex_batch_t b, void *arena, uint64_t arena_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_batch(b, false))) return rc;
+    if (!arena) return fail(SIMPLEX_EINVAL, "arena is NULL");
+    if ((reinterpret_cast<uintptr_t>(arena) & 255u) != 0) return fail(SIMPLEX_EINVAL, "arena must be 256-byte aligned");
+    if (arena_bytes < b->bytes)
+        return fail(SIMPLEX_EINVAL, "arena too small: %llu bytes, need %llu", (unsigned long long)arena_bytes,
+                    (unsigned long long)b->bytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t *base = static_cast<uint8_t *>(arena);
+    std::vector<CUtensorMap> tmaps(2 * b->insts.size());
+    for (size_t i = 0; i < b->insts.size(); ++i)
+        for (int g = 0; g < 2; ++g) {
+            rc = make_tensor_map(b->insts[i].plan, base + b->insts[i].grid[g], &tmaps[2 * i + g]);
+            if (rc) return rc;
+        }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(base + b->off_insts, b->insts.data(), sizeof(sx::BatchInst) * b->insts.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(base + b->off_items, b->items.data(), sizeof(sx::BatchItem) * b->items.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(base + b->off_tmaps, tmaps.data(), sizeof(CUtensorMap) * tmaps.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(base + b->off_grids, 0, b->bytes - b->off_grids, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "binding the batch arena");
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    b->arena = base;
+    b->parity = 0;
+    return SIMPLEX_OK;
+}
+
+int simplex_batch_init(simplex_batch_t b, void *stream)
+{
+    int rc;
+    if ((rc = check_batch(b, true))) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < b->insts.size(); ++i) {
+        const simplex_instance_t &in = b->spec[i];
+        cudaError_t e = sx::launch_ca_init(b->insts[i].plan, b->arena + b->insts[i].grid[0], in.seed, in.threshold,
+                                           nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch init launch");
+    }
+    b->parity = 0;
+    return SIMPLEX_OK;
+}
+
+int simplex_batch_run(simplex_batch_t b, int steps, unsigned long long *live, int use_graph, void *stream)
+{
+    int rc;
+    if ((rc = check_batch(b, true))) return rc;
+    if (steps < 1 || steps > sx::kBatchMaxSteps)
+        return fail(SIMPLEX_EINVAL, "steps must be in [1, %d] (got %d)", sx::kBatchMaxSteps, steps);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = sx::batch_prepare();
+    if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared-memory limit");
+    if (!use_graph) {
+        rc = enqueue_batch_run(b, steps, live, b->parity, st);
+        if (rc) return rc;
+        b->parity = (b->parity + steps) & 1;
+        return SIMPLEX_OK;
+    }
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (b->device >= 0 && b->device != dev)
+        return fail(SIMPLEX_EINVAL, "batch was first run with graphs on device %d, now %d", b->device, dev);
+    if (!b->capture) {
+        if ((e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        b->device = dev;
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : b->graphs)
+        if (g.steps == steps && g.live == live && g.parity == b->parity) exec = g.exec;
+    if (!exec) {
+        if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamBeginCapture");
+        rc = enqueue_batch_run(b, steps, live, b->parity, b->capture);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b->capture, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (b->graphs.size() >= 8) {
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.erase(b->graphs.begin());
+        }
+        b->graphs.push_back(RunGraph{steps, live, b->parity, exec});
+    }
+    if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    b->parity = (b->parity + steps) & 1;
+    return SIMPLEX_OK;
+}
+
+int simplex_batch_grid(simplex_batch_t b, int i, uint8_t **grid, int64_t *side)
+{
+    int rc;
+    if ((rc = check_batch(b, true))) return rc;
+    if (i < 0 || i >= (int)b->insts.size()) return fail(SIMPLEX_EINVAL, "instance index %d out of range", i);
+    if (!grid || !side) return fail(SIMPLEX_EINVAL, "grid and side must not be NULL");
+    *grid = b->arena + b->insts[i].grid[b->parity];
+    *side = b->insts[i].plan.side;
+    return SIMPLEX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// batch.h -- device-resident description of a batch of automaton instances
+// (host and device).  The batched engine keeps, in one arena of device memory:
+//   BatchInst[count]        each instance's map, rule and grid offsets
+//   BatchItem[nitems]       the work items (runs of blocks of one instance)
+//   CUtensorMap[2 * count]  TMA maps of each instance's two grids
+//   queue[kBatchMaxSteps+1] work-queue counters, one per pass of a run
+//   grids                   two side^m uint8 grids per instance
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+#include "hmap.cuh"
+#include "rule.h"
+
+namespace sx {
+
+// Tile bodies the batched kernel implements (all with 128-thread CTAs).
+enum BatchBody : int32_t {
+    kBody2x64 = 0,   // m = 2, 64 x 64 tiles
+    kBody2x128 = 1,  // m = 2, 128 x 128 tiles
+    kBody3x16 = 2,   // m = 3, 16^3 tiles
+};
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchChunk = 8;         // CUDA blocks of one instance per work item
+constexpr int kBatchMaxSteps = 4096;   // steps per simplex_batch_run call
+
+// One work item of the device queue: up to kBatchChunk consecutive CUDA
+// blocks v0 .. v0 + cnt - 1 of instance `inst`'s map.
+struct BatchItem {
+    uint32_t inst, v0, cnt, pad;
+};
+
+struct BatchInst {
+    Plan plan;
+    Rule rule;
+    uint64_t grid[2];  // byte offsets of the two grids in the arena
+    int32_t body;      // BatchBody
+    int32_t tmap;      // index of the tensor map of grid 0 (grid 1 follows)
+};
+
+}  // namespace sx

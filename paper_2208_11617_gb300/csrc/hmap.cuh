@@ -45,7 +45,7 @@
 namespace sx {
 
 constexpr int kMaxM = 4;
-constexpr int kMaxLevels = 24;  // log2 N <= 15 keeps every count well inside 64 bits
+constexpr int kMaxLevels = 16;  // log2 N <= 15 keeps every count well inside 64 bits
 
 enum MapKind : int { kMapH = 0, kMapBB = 1 };
 
@@ -69,10 +69,10 @@ struct Plan {
     uint64_t bb_blocks;  // N^m
     // H3 (beta = 2): region sizes
     uint64_t h3_cube, h3_layer;
-    // generic cubes of dimension d (3..kMaxM): level_end[d][k] = number of
-    // blocks in levels 1..k; cube_total[d] = level_end[d][logN]
-    uint64_t level_end[kMaxM + 1][kMaxLevels + 1];
-    uint64_t cube_total[kMaxM + 1];
+    // generic cubes of dimension d (3..kMaxM): level_end[d-3][k] = number of
+    // blocks in levels 1..k; cube_total[d-3] = level_end[d-3][logN]
+    uint64_t level_end[kMaxM - 2][kMaxLevels + 1];
+    uint64_t cube_total[kMaxM - 2];
 };
 
 // floor(log2 x) for x >= 1 from the count of leading zeros (Sec. 4.1: the
@@ -212,10 +212,10 @@ SX_HD bool cubes_generic(const Plan &p, uint64_t v, int32_t *X)
 {
     const int32_t N = p.N, logN = p.logN;
     int k = 1;
-    while (k < logN && v >= p.level_end[D][k]) ++k;
+    while (k < logN && v >= p.level_end[D - 3][k]) ++k;
     const int lb = logN - k;
     const int32_t b = 1 << lb;
-    const uint64_t local = v - p.level_end[D][k - 1];
+    const uint64_t local = v - p.level_end[D - 3][k - 1];
     uint64_t c = local >> (D * lb);
     const uint64_t l = local & ((1ull << (D * lb)) - 1ull);
     int32_t corner[D];
@@ -244,8 +244,8 @@ template <int D>
 struct Cover {
     static SX_HD bool run(const Plan &p, uint64_t v, int32_t *X)
     {
-        if (v < p.cube_total[D]) return cubes_generic<D>(p, v, X);
-        v -= p.cube_total[D];
+        if (v < p.cube_total[D - 3]) return cubes_generic<D>(p, v, X);
+        v -= p.cube_total[D - 3];
         const bool ok = Cover<D - 1>::run(p, v, X);
         int32_t s = 0;
 #pragma unroll

@@ -1,0 +1,197 @@
+// k_batch.cu -- the batched automaton engine: one persistent launch per step
+// over every instance of a batch, fed by a device-side work queue.
+//
+// The work of a step is the union of the CUDA blocks of every instance's map
+// (H in its trapezoid form for m = 2, H3 with the hinge for m = 3), cut into
+// work items of up to kBatchChunk consecutive blocks of one instance.  Each
+// CTA pops items from a global counter (one atomic per item; the next pop is
+// issued while the current item runs), loads the item's instance description
+// into shared memory when it changes, decodes each block with that instance's
+// map and runs the same per-tile body as the single-instance kernels.
+#include "batch.h"
+#include "ca_tiles.cuh"
+#include "common.cuh"
+#include "hmap.cuh"
+#include "kernels.h"
+#include "tile.cuh"
+
+namespace sx {
+
+static __device__ uint32_t g_batch_status;
+
+constexpr int kBatchStageBytes = 160 * 130;  // largest box: m = 2, 128 x 128 tiles
+
+__device__ __forceinline__ uint32_t body_box_bytes(int body)
+{
+    return body == kBody2x64 ? 96u * 66u : body == kBody2x128 ? 160u * 130u : 48u * 18u * 18u;
+}
+
+// Live cells of one tile of grid `g`, read straight from global memory in
+// 16-cell chunks (the count pass that gives live[0]).
+template <int M>
+__device__ __forceinline__ uint32_t count_tile(const Plan &p, const int32_t *X, const uint8_t *g, bool partial)
+{
+    const uint32_t nchunks = 1u << (M * p.log_rho - 4);
+    uint32_t c_live = 0;
+    for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+        const ChunkPos<M> q = chunk_pos<M>(p, X, c, 4);
+        if (partial && q.sum > p.n) continue;
+        const uint4 w = *reinterpret_cast<const uint4 *>(g + q.addr);
+        const int64_t rem = p.n - q.sum + 1;
+        const int cnt = partial ? (int)(rem < 16 ? rem : 16) : 16;
+        c_live += __popc(w.x & chunk_word_mask(cnt, 0)) + __popc(w.y & chunk_word_mask(cnt, 1)) +
+                  __popc(w.z & chunk_word_mask(cnt, 2)) + __popc(w.w & chunk_word_mask(cnt, 3));
+    }
+    return c_live;
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+    batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items, uint32_t nitems,
+                 const CUtensorMap *__restrict__ tmaps, uint8_t *__restrict__ arena, int in_parity,
+                 unsigned int *__restrict__ queue, unsigned long long *__restrict__ live, int live_stride,
+                 int live_index, int count_only)
+{
+    extern __shared__ uint8_t dsmem[];
+    __shared__ BatchInst si;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t red[32];
+    __shared__ uint32_t s_item, s_next;
+    __shared__ int s_cur;
+    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x;
+    uint32_t phase = 0;
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        s_cur = -1;
+        s_next = atomicAdd(queue, 1u);
+    }
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) {
+            s_item = s_next;
+            if (s_item < nitems) s_next = atomicAdd(queue, 1u);  // prefetch the next pop
+        }
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= nitems) break;
+        const BatchItem item = items[it];
+        if ((int)item.inst != s_cur) {
+            // load the instance description into shared memory (all threads)
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + item.inst);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&si);
+            for (int w = tid; w < (int)(sizeof(BatchInst) / 4); w += kBatchThreads) dst[w] = src[w];
+            __syncthreads();
+            if (tid == 0) {
+                s_cur = (int)item.inst;
+                if (!count_only) prefetch_tmap(tmaps + si.tmap + in_parity);
+            }
+        }
+        const Plan &p = si.plan;
+        const uint8_t *gin = arena + si.grid[in_parity];
+        uint8_t *gout = arena + si.grid[in_parity ^ 1];
+        uint32_t my_live = 0;
+        for (uint32_t j = 0; j < item.cnt; ++j) {
+            const uint64_t v = (uint64_t)item.v0 + j;
+            int32_t X[3] = {0, 0, 0};
+            const bool ok = p.m == 2 ? decode<2>(p, kMapH, v, X) : decode<3>(p, kMapH, v, X);
+            if (!ok) continue;
+            const int64_t s0 = tile_base_sum<3>(p, X);  // X[2] = 0 for m = 2
+            if (s0 > p.n) continue;
+            const bool partial = s0 + (int64_t)p.m * (p.rho - 1) > p.n;
+            if (count_only) {
+                my_live += p.m == 2 ? count_tile<2>(p, X, gin, partial) : count_tile<3>(p, X, gin, partial);
+                continue;
+            }
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar, body_box_bytes(si.body));
+                const CUtensorMap *tm = tmaps + si.tmap + in_parity;
+                if (p.m == 2)
+                    tma_load_2d(tile, tm, X[1] * p.rho - 16, X[0] * p.rho - 1, &bar);
+                else
+                    tma_load_3d(tile, tm, X[2] * p.rho - 16, X[1] * p.rho - 1, X[0] * p.rho - 1, &bar);
+            }
+            const bool done = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
+            phase ^= 1u;
+            if (__syncthreads_or(!done)) {
+                if (tid == 0) {
+                    atomicOr(&g_batch_status, 1u);
+                    mbar_wait_bounded(&bar, phase ^ 1u, kWaitLimitNs);
+                }
+                return;
+            }
+            const bool ork = si.rule.or_k != 0;
+            switch (si.body) {
+            case kBody2x64:
+                my_live += ork ? ca2_tile<64, 2, true>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 64,
+                                                       (int64_t)X[0] * 64, partial, tid & 3, tid >> 2)
+                               : ca2_tile<64, 2, false>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 64,
+                                                        (int64_t)X[0] * 64, partial, tid & 3, tid >> 2);
+                break;
+            case kBody2x128:
+                my_live += ork ? ca2_tile<128, 8, true>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 128,
+                                                        (int64_t)X[0] * 128, partial, tid & 7, tid >> 3)
+                               : ca2_tile<128, 8, false>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 128,
+                                                         (int64_t)X[0] * 128, partial, tid & 7, tid >> 3);
+                break;
+            default:
+                my_live += ork ? ca3_tile<16, 2, true>(tile, p.n, p.side, si.rule, gout, (int64_t)X[2] * 16,
+                                                       (int64_t)X[1] * 16, (int64_t)X[0] * 16, partial, 0,
+                                                       tid & 15, tid >> 4)
+                               : ca3_tile<16, 2, false>(tile, p.n, p.side, si.rule, gout, (int64_t)X[2] * 16,
+                                                        (int64_t)X[1] * 16, (int64_t)X[0] * 16, partial, 0,
+                                                        tid & 15, tid >> 4);
+                break;
+            }
+            __syncthreads();  // the staged box is fully read before the next load
+        }
+        if (live) block_add_u64(live + (uint64_t)item.inst * live_stride + live_index, my_live, red);
+        __syncthreads();
+    }
+}
+
+cudaError_t batch_prepare()
+{
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchStageBytes + 128);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
+    return e;
+}
+
+cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
+                              const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
+                              unsigned long long *live, int live_stride, int live_index, bool count_only,
+                              cudaStream_t st)
+{
+    cudaError_t e = batch_prepare();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads,
+                                                           kBatchStageBytes + 128)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t g = (uint64_t)sms * (uint64_t)per_sm;  // persistent: every CTA resident
+    if (g > nitems) g = nitems ? nitems : 1;
+    batch_kernel<<<(unsigned)g, kBatchThreads, kBatchStageBytes + 128, st>>>(
+        insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_read_status(uint32_t *out)
+{
+    uint32_t zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_batch_status, sizeof(uint32_t));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(g_batch_status, &zero, sizeof(uint32_t));
+}
+
+}  // namespace sx

@@ -16,6 +16,7 @@
 //      summed byte-wise per thread, folded once per tile, reduced per CTA and
 //      added with one atomic per CTA.
 // Only tiles on the diagonal band mask cells past x1 + x2 = n.
+#include "ca_tiles.cuh"
 #include "common.cuh"
 #include "hmap.cuh"
 #include "kernels.h"
@@ -74,38 +75,7 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R), ca2_min_blocks<RHO>())
             return;
         }
 
-        const uint8_t *col = tile + 16 + 16 * tx;
-        const int r0 = ty * R;                  // first output row of this thread
-        const int64_t xc = x0 + 16 * tx;        // first cell of the chunk
-        uint32_t hp[4], hc[4], ac[4], tmp[4], lacc = 0;
-        hsum_row(col + r0 * BW, hp, tmp);
-        hsum_row(col + (r0 + 1) * BW, hc, ac);
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            uint32_t hn[4], an[4], s[4], nw[4];
-            hsum_row(col + (r0 + i + 2) * BW, hn, an);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) s[w] = hp[w] + hc[w] + hn[w];
-            next_state4<ORK>(s, ac, rule, nw);
-            const int64_t y = y0 + r0 + i;
-            bool store = true;
-            if (partial) {
-                const int64_t c64 = p.n - y - xc + 1;  // domain cells in this chunk
-                const int c = (int)(c64 < 0 ? 0 : (c64 > 16 ? 16 : c64));
-#pragma unroll
-                for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(c, w);
-                store = c > 0;
-            }
-            if (store) store16(out + y * p.side + xc, nw);
-            lacc += nw[0] + nw[1] + nw[2] + nw[3];  // bytes <= 4R: no carry
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                hp[w] = hc[w];
-                hc[w] = hn[w];
-                ac[w] = an[w];
-            }
-        }
-        my_live += byte_sum(lacc);
+        my_live += ca2_tile<RHO, R, ORK>(tile, p.n, p.side, rule, out, x0, y0, partial, tx, ty);
         __syncthreads();  // the tile is fully read before the next load reuses it
     }
     if (live) block_add_u64(live, my_live, red);

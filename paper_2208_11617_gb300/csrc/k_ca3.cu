@@ -13,6 +13,7 @@
 // For RHO = 32 the staged rows are 64 bytes and the tensor map uses the 64-byte
 // swizzle: 16-byte chunk c of staged row r sits at chunk c ^ ((r >> 1) & 3),
 // which spreads the rows a warp reads at once over all shared-memory banks.
+#include "ca_tiles.cuh"
 #include "common.cuh"
 #include "hmap.cuh"
 #include "kernels.h"
@@ -21,100 +22,9 @@ namespace sx {
 
 static __device__ uint32_t g_ca3_status;
 
-// Byte offset of 16-byte chunk c within a staged row r (row pitch BW bytes).
-template <int BW, bool SWZ>
-__device__ __forceinline__ int chunk_off(int r, int c)
-{
-    if (SWZ) return r * BW + 16 * (c ^ ((r >> 1) & 3));
-    return r * BW + 16 * c;
-}
-
-// Horizontal 3-sums of chunk c of staged row r (chunks c-1 and c+1 give the
-// neighbour bytes at the chunk's edges).
-template <int BW, bool SWZ>
-__device__ __forceinline__ void hsum_staged(const uint8_t *tile, int r, int c, uint32_t h[4], uint32_t cc[4])
-{
-    const uint4 w = *reinterpret_cast<const uint4 *>(tile + chunk_off<BW, SWZ>(r, c));
-    const uint32_t lw = *reinterpret_cast<const uint32_t *>(tile + chunk_off<BW, SWZ>(r, c - 1) + 12);
-    const uint32_t rw = *reinterpret_cast<const uint32_t *>(tile + chunk_off<BW, SWZ>(r, c + 1));
-    h[0] = w.x + __funnelshift_l(lw, w.x, 8) + __funnelshift_r(w.x, w.y, 8);
-    h[1] = w.y + __funnelshift_l(w.x, w.y, 8) + __funnelshift_r(w.y, w.z, 8);
-    h[2] = w.z + __funnelshift_l(w.y, w.z, 8) + __funnelshift_r(w.z, w.w, 8);
-    h[3] = w.w + __funnelshift_l(w.z, w.w, 8) + __funnelshift_r(w.w, rw, 8);
-    cc[0] = w.x;
-    cc[1] = w.y;
-    cc[2] = w.z;
-    cc[3] = w.w;
-}
-
 // CTAs per SM the kernel is built for (shared memory allows 3 at RHO = 32).
 template <int RHO>
 constexpr int ca3_min_blocks() { return RHO == 32 ? 3 : 12; }
-
-// One tile's step from its staged box: thread (tx, ty, tz) owns the 16-byte
-// chunk tx of row x2 = y0 + ty and walks RZ planes x1 = z0 + tz*RZ ... along
-// x1.  Returns the live cells it wrote.
-template <int RHO, int RZ, bool ORK>
-__device__ __forceinline__ uint32_t ca3_tile(const uint8_t *tile, const Plan &p, const Rule &rule,
-                                             uint8_t *__restrict__ out, int64_t x0, int64_t y0, int64_t z0,
-                                             bool partial, int tx, int ty, int tz)
-{
-    constexpr int BW = RHO + 32, BH = RHO + 2;
-    constexpr bool SWZ = (BW == 64);
-    const int c = 1 + tx;  // staged chunk (chunk 0 is the left halo)
-    // staged row r = zz * BH + yy holds x1 = z0 + zz - 1, x2 = y0 + yy - 1
-    const int64_t xc = x0 + 16 * tx;
-    const int64_t x2 = y0 + ty;
-    const int zb = tz * RZ;  // first output plane of this thread
-    uint32_t pp[4], pc[4], ac[4], lacc = 0;
-    {
-        uint32_t h0[4], h1[4], h2[4], cc[4];
-        int r = zb * BH + ty;
-        hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
-        hsum_staged<BW, SWZ>(tile, r + 1, c, h1, cc);
-        hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) pp[w] = h0[w] + h1[w] + h2[w];
-        r += BH;
-        hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
-        hsum_staged<BW, SWZ>(tile, r + 1, c, h1, ac);
-        hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) pc[w] = h0[w] + h1[w] + h2[w];
-    }
-#pragma unroll
-    for (int i = 0; i < RZ; ++i) {
-        uint32_t h0[4], h1[4], h2[4], cc[4], an[4], pn[4], s[4], nw[4];
-        const int r = (zb + i + 2) * BH + ty;
-        hsum_staged<BW, SWZ>(tile, r, c, h0, cc);
-        hsum_staged<BW, SWZ>(tile, r + 1, c, h1, an);
-        hsum_staged<BW, SWZ>(tile, r + 2, c, h2, cc);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            pn[w] = h0[w] + h1[w] + h2[w];
-            s[w] = pp[w] + pc[w] + pn[w];
-        }
-        next_state4<ORK>(s, ac, rule, nw);
-        const int64_t x1 = z0 + zb + i;
-        bool store = true;
-        if (partial) {
-            const int64_t c64 = p.n - x1 - x2 - xc + 1;
-            const int cnt = (int)(c64 < 0 ? 0 : (c64 > 16 ? 16 : c64));
-#pragma unroll
-            for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(cnt, w);
-            store = cnt > 0;
-        }
-        if (store) store16(out + (x1 * p.side + x2) * p.side + xc, nw);
-        lacc += nw[0] + nw[1] + nw[2] + nw[3];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            pp[w] = pc[w];
-            pc[w] = pn[w];
-            ac[w] = an[w];
-        }
-    }
-    return byte_sum(lacc);
-}
 
 template <int RHO, int RZ, bool ORK>
 __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<RHO>())
@@ -163,7 +73,7 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<
             return;
         }
 
-        my_live += ca3_tile<RHO, RZ, ORK>(tile, p, rule, out, x0, y0, z0, partial, tx, ty, tz);
+        my_live += ca3_tile<RHO, RZ, ORK>(tile, p.n, p.side, rule, out, x0, y0, z0, partial, tx, ty, tz);
         __syncthreads();
     }
     if (live) block_add_u64(live, my_live, red);
@@ -246,7 +156,7 @@ __global__ void __launch_bounds__(T, 1)
             }
             return;
         }
-        my_live += ca3_tile<RHO, C::RZ, ORK>(base + s * C::kStage, p, rule, out, inf.x, inf.y, inf.z,
+        my_live += ca3_tile<RHO, C::RZ, ORK>(base + s * C::kStage, p.n, p.side, rule, out, inf.x, inf.y, inf.z,
                                               (inf.w & 2) != 0, tx, ty, tz);
         __syncthreads();  // stage s fully read
         if (tid == 0) produce(s);

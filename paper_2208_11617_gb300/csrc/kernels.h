@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "batch.h"
 #include "hmap.cuh"
 #include "rule.h"
 
@@ -37,6 +38,15 @@ cudaError_t ca3_prepare(int rho);
 
 // One CTA whose mbarrier wait runs out after limit_ns (tests the bounded-wait path).
 cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
+
+// Batched engine: one persistent pass (count_only: live counts of the input
+// grids; else one automaton step in -> out) over every work item.
+cudaError_t batch_prepare();
+cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
+                              const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
+                              unsigned long long *live, int live_stride, int live_index, bool count_only,
+                              cudaStream_t st);
+cudaError_t batch_read_status(uint32_t *out);
 
 // Device error words of the TMA kernels (bounded waits that gave up).
 // Reads and clears; synchronous.

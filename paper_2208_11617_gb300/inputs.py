@@ -69,3 +69,31 @@ CA_M2_SMALL = CAWorkload("ca m=2 n=4095 B3/S23", m=2, n=4095, block=128, steps=1
 # B5/S45, 50 steps.
 CA_M3 = CAWorkload("ca m=3 n=1023 B5/S45", m=3, n=1023, block=32, steps=50,
                    p=0.3, rule=B5S45)
+
+
+# Batched workload: 2048 automata on 2-simplices with n log-uniform in
+# [64, 2048] and 256 on 3-simplices with n log-uniform in [32, 256], each
+# Bernoulli(0.4) seeded by its index, B3/S23 (m = 2) or B5/S45 (m = 3), 16 steps.
+BATCH_STEPS = 16
+
+
+def log_uniform_sizes(rng, count: int, lo: int, hi: int):
+    """n = floor(exp(U(ln lo, ln hi))), drawn from a numpy Generator."""
+    import numpy as np
+    return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi), size=count))).astype(np.int64)
+
+
+def batch_instances(seed: int = 1, n2: int = 2048, n3: int = 256, p: float = 0.4):
+    """The batched workload as a list of dicts (m, n, rule, seed, threshold);
+    tile sizes are left to the caller (autotuner or defaults)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes2 = log_uniform_sizes(rng, n2, 64, 2048)
+    sizes3 = log_uniform_sizes(rng, n3, 32, 256)
+    thr = bernoulli_threshold(p)
+    out = []
+    for i, n in enumerate(sizes2):
+        out.append(dict(m=2, n=int(n), birth=B3S23[0], survive=B3S23[1], seed=i, threshold=thr))
+    for j, n in enumerate(sizes3):
+        out.append(dict(m=3, n=int(n), birth=B5S45[0], survive=B5S45[1], seed=n2 + j, threshold=thr))
+    return out

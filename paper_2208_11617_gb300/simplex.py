@@ -34,7 +34,8 @@ EXPORTED = (
     "simplex_map_create", "simplex_map_create_padded", "simplex_map_create_ex", "simplex_map_destroy", "simplex_map_info",
     "simplex_map_block", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
     "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
-    "simplex_version", "simplex_selftest_wait_timeout",
+    "simplex_version", "simplex_selftest_wait_timeout", "simplex_batch_create", "simplex_batch_destroy",
+    "simplex_batch_info", "simplex_batch_bind", "simplex_batch_init", "simplex_batch_run", "simplex_batch_grid",
 )
 
 if not os.path.exists(LIB_PATH):
@@ -66,6 +67,20 @@ class SimplexMapParams(ctypes.Structure):
                 ("band", ctypes.c_int32), ("launch", ctypes.c_int32)]
 
 
+class SimplexInstance(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("block", ctypes.c_int32), ("beta", ctypes.c_int32),
+                ("band", ctypes.c_int32), ("n", ctypes.c_int64), ("birth", ctypes.c_uint32),
+                ("survive", ctypes.c_uint32), ("seed", ctypes.c_uint32), ("threshold", ctypes.c_uint32)]
+
+
+class SimplexBatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("parity", ctypes.c_int32), ("items", ctypes.c_uint64),
+                ("blocks", ctypes.c_uint64), ("cells", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def _sig(name, args):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -87,6 +102,13 @@ _sig("simplex_ca_run_host", [_vp, _vp, _vp, _vp, _vp, _i32, _u32, _u32, _vp, _vp
 _sig("simplex_visit_count", [_vp, _vp, _i32, _i32, _vp])
 _sig("simplex_device_status", [ctypes.POINTER(_u32)])
 _sig("simplex_selftest_wait_timeout", [_u64, _vp])
+_sig("simplex_batch_create", [ctypes.POINTER(SimplexInstance), _i32, ctypes.POINTER(_vp)])
+_sig("simplex_batch_destroy", [_vp])
+_sig("simplex_batch_info", [_vp, ctypes.POINTER(SimplexBatchInfo)])
+_sig("simplex_batch_bind", [_vp, _vp, _u64, _vp])
+_sig("simplex_batch_init", [_vp, _vp])
+_sig("simplex_batch_run", [_vp, _i32, _vp, _i32, _vp])
+_sig("simplex_batch_grid", [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64)])
 _lib.simplex_last_error.argtypes = []
 _lib.simplex_last_error.restype = ctypes.c_char_p
 _lib.simplex_version.argtypes = []
@@ -264,6 +286,76 @@ def simplex_device_status() -> int:
 
 def simplex_selftest_wait_timeout(limit_ns: int):
     _check(_lib.simplex_selftest_wait_timeout(limit_ns, _stream()), "simplex_selftest_wait_timeout")
+
+
+class SimplexBatch:
+    """A planned batch (owns the C handle); `arena` keeps the bound device memory alive."""
+
+    def __init__(self, handle: int, count: int):
+        self.handle = handle
+        self.count = count
+        self.arena = None
+
+    def close(self):
+        if self.handle:
+            _lib.simplex_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simplex_batch_create(instances) -> SimplexBatch:
+    """instances: sequence of dicts/tuples with the SimplexInstance fields."""
+    arr = (SimplexInstance * len(instances))()
+    for k, inst in enumerate(instances):
+        if isinstance(inst, dict):
+            for f, _ in SimplexInstance._fields_:
+                setattr(arr[k], f, inst.get(f, 0))
+        else:
+            arr[k] = SimplexInstance(*inst)
+    h = _vp()
+    _check(_lib.simplex_batch_create(arr, len(instances), ctypes.byref(h)), "simplex_batch_create")
+    return SimplexBatch(h.value, len(instances))
+
+
+def simplex_batch_info(b: SimplexBatch) -> dict:
+    info = SimplexBatchInfo()
+    _check(_lib.simplex_batch_info(b.handle, ctypes.byref(info)), "simplex_batch_info")
+    return info.as_dict()
+
+
+def simplex_batch_bind(b: SimplexBatch, arena: torch.Tensor | None = None) -> torch.Tensor:
+    """Binds (allocating a uint8 arena tensor when none is given) and returns the arena."""
+    need = simplex_batch_info(b)["arena_bytes"]
+    if arena is None:
+        arena = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    base = arena.data_ptr()
+    off = (-base) % 256
+    _check(_lib.simplex_batch_bind(b.handle, base + off, arena.numel() - off, _stream()), "simplex_batch_bind")
+    b.arena = arena
+    return arena
+
+
+def simplex_batch_init(b: SimplexBatch):
+    _check(_lib.simplex_batch_init(b.handle, _stream()), "simplex_batch_init")
+
+
+def simplex_batch_run(b: SimplexBatch, steps: int, live: torch.Tensor | None = None, use_graph: bool = True):
+    _check(_lib.simplex_batch_run(b.handle, steps, _dptr(live, torch.int64, "live", b.count * (steps + 1)),
+                                  1 if use_graph else 0, _stream()), "simplex_batch_run")
+
+
+def simplex_batch_grid(b: SimplexBatch, i: int, m: int) -> torch.Tensor:
+    """Instance i's current grid as a (side,)*m uint8 view into the arena."""
+    ptr, side = _vp(), _i64()
+    _check(_lib.simplex_batch_grid(b.handle, i, ctypes.byref(ptr), ctypes.byref(side)), "simplex_batch_grid")
+    off = ptr.value - b.arena.data_ptr()
+    n = side.value ** m
+    return b.arena[off: off + n].view((side.value,) * m)
 
 
 def simplex_last_error() -> str:

@@ -1,0 +1,53 @@
+"""Host-side tests of the batched engine's planning (no GPU needed)."""
+import math
+
+import pytest
+
+from paper_2208_11617_gb300 import inputs
+from paper_2208_11617_gb300 import simplex as sx
+
+
+def _inst(m, n, block, beta=2, band=0, rule=None, seed=0, thr=1 << 31):
+    rule = rule or (inputs.B3S23 if m == 2 else inputs.B5S45)
+    return dict(m=m, n=n, block=block, beta=beta, band=band, birth=rule[0], survive=rule[1], seed=seed,
+                threshold=thr)
+
+
+def test_batch_counts_and_layout():
+    insts = [_inst(2, 100, 64), _inst(2, 1000, 128), _inst(3, 63, 16), _inst(3, 100, 16, beta=3), _inst(2, 0, 64)]
+    b = sx.simplex_batch_create(insts)
+    info = sx.simplex_batch_info(b)
+    assert info["count"] == 5
+    assert info["cells"] == sum(math.comb(d["n"] + d["m"], d["m"]) for d in insts)
+    blocks = 0
+    items = 0
+    for d in insts:
+        side = (d["n"] + 16) // 16 * 16
+        mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], d["block"], side=side,
+                                   band=(min(8, 1 << ((d["n"] + d["block"]) // d["block"]).bit_length() - 1)
+                                         if d["m"] == 2 else None))
+        blocks += mp.info.h_blocks
+        items += -(-mp.info.h_blocks // 8)
+    assert info["blocks"] == blocks
+    assert info["items"] == items
+    grids = sum(2 * (-(-((d["n"] + 16) // 16 * 16) ** d["m"] // 256) * 256) for d in insts)
+    assert info["arena_bytes"] >= grids
+
+
+@pytest.mark.parametrize("bad", [_inst(2, 100, 32), _inst(3, 63, 32), _inst(4, 31, 16), _inst(2, -1, 64),
+                                 _inst(3, 63, 16, beta=4)])
+def test_batch_rejects_unsupported_instances(bad):
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_batch_create([_inst(2, 10, 64), bad])
+    assert "instance 1" in str(ei.value)
+
+
+def test_batch_workload_generator():
+    insts = inputs.batch_instances()
+    assert len(insts) == 2304
+    n2 = [d["n"] for d in insts if d["m"] == 2]
+    n3 = [d["n"] for d in insts if d["m"] == 3]
+    assert len(n2) == 2048 and min(n2) >= 64 and max(n2) < 2048
+    assert len(n3) == 256 and min(n3) >= 32 and max(n3) < 256
+    assert insts == inputs.batch_instances()          # seeded
+    assert [d["seed"] for d in insts] == list(range(2304))

@@ -1,0 +1,84 @@
+"""GPU parity of the batched engine: every instance of a mixed batch equals
+the oracle (and the single-instance path) bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2208_11617_gb300 import autotune, inputs
+from paper_2208_11617_gb300 import simplex as sx
+
+pytestmark = pytest.mark.gpu
+
+
+def _inst(m, n, block, beta=2, band=0, rule=None, seed=0, p=0.5):
+    rule = rule or (inputs.B3S23 if m == 2 else inputs.B5S45)
+    return dict(m=m, n=n, block=block, beta=beta, band=band, birth=rule[0], survive=rule[1], seed=seed,
+                threshold=inputs.bernoulli_threshold(p))
+
+
+MIXED = [
+    _inst(2, 0, 64, seed=1), _inst(2, 17, 64, seed=2), _inst(2, 100, 64, seed=3), _inst(2, 255, 128, seed=4),
+    _inst(2, 1000, 64, seed=5), _inst(2, 1000, 128, band=4, seed=6),
+    _inst(2, 300, 64, rule=(1 << 3 | 1 << 6, 1 << 2 | 1 << 3), seed=7, p=0.4),
+    _inst(2, 200, 128, rule=(1, 0), seed=8, p=0.3),
+    _inst(3, 0, 16, seed=9), _inst(3, 20, 16, seed=10, p=0.3), _inst(3, 63, 16, seed=11, p=0.3),
+    _inst(3, 100, 16, beta=3, seed=12, p=0.3), _inst(3, 150, 16, rule=(1 << 4, 1 << 2 | 1 << 3 | 1 << 4), seed=13),
+    _inst(2, 4095, 128, seed=14), _inst(3, 255, 16, seed=15, p=0.3),
+]
+
+
+def _logical(t, n):
+    return t[tuple(slice(0, n + 1) for _ in range(t.dim()))].cpu().numpy()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_mixed_batch_matches_oracle(use_graph):
+    b = sx.simplex_batch_create(MIXED)
+    sx.simplex_batch_bind(b)
+    sx.simplex_batch_init(b)
+    refs = [oracle.ca_init(d["m"], d["n"], d["seed"], d["threshold"]) for d in MIXED]
+    for steps in (5, 3):                    # two runs: parity 0 then parity 1
+        live = torch.zeros(len(MIXED) * (steps + 1), dtype=torch.int64, device="cuda")
+        sx.simplex_batch_run(b, steps, live, use_graph)
+        torch.cuda.synchronize()
+        live = live.view(len(MIXED), steps + 1).cpu().numpy().astype(np.uint64)
+        for i, d in enumerate(MIXED):
+            ref, ref_live = oracle.ca_run(d["m"], d["n"], steps, d["birth"], d["survive"], refs[i])
+            g = sx.simplex_batch_grid(b, i, d["m"])
+            np.testing.assert_array_equal(_logical(g, d["n"]), ref, err_msg=f"instance {i}")
+            np.testing.assert_array_equal(live[i], ref_live, err_msg=f"instance {i} live")
+            refs[i] = ref
+    assert sx.simplex_device_status() == 0
+
+
+def test_batch_workload_equals_single_instance_path():
+    """The batched workload (2048 + 256 instances, 16 steps): every instance's
+    final grid and live counts equal simplex_ca_run on that instance alone."""
+    insts = autotune.apply(inputs.batch_instances())
+    steps = inputs.BATCH_STEPS
+    b = sx.simplex_batch_create(insts)
+    sx.simplex_batch_bind(b)
+    sx.simplex_batch_init(b)
+    live = torch.zeros(len(insts) * (steps + 1), dtype=torch.int64, device="cuda")
+    sx.simplex_batch_run(b, steps, live)
+    torch.cuda.synchronize()
+    live = live.view(len(insts), steps + 1)
+    rng = np.random.default_rng(5)
+    oracle_check = set(rng.choice(len(insts), size=12, replace=False).tolist())
+    for i, d in enumerate(insts):
+        side = (d["n"] + 16) // 16 * 16
+        mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], 32 if d["m"] == 3 else d["block"], side=side)
+        a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
+        bb = torch.zeros_like(a)
+        sx.simplex_ca_init(mp, a, d["seed"], d["threshold"])
+        l1 = torch.zeros(steps + 1, dtype=torch.int64, device="cuda")
+        fin = sx.simplex_ca_run(mp, a, bb, steps, d["birth"], d["survive"], l1, False)
+        g = sx.simplex_batch_grid(b, i, d["m"])
+        assert torch.equal(g.reshape(-1), fin), f"instance {i}"
+        assert torch.equal(live[i], l1), f"instance {i} live"
+        if i in oracle_check and d["n"] <= 600:
+            ref, ref_live = oracle.ca_run(d["m"], d["n"], steps, d["birth"], d["survive"],
+                                          oracle.ca_init(d["m"], d["n"], d["seed"], d["threshold"]))
+            np.testing.assert_array_equal(_logical(g, d["n"]), ref)
+    assert sx.simplex_device_status() == 0
