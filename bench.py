@@ -170,6 +170,8 @@ def _workload(name, args=None):
         wl = inputs.WRITE_M2
     elif name == "write4":
         wl = inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
+    elif name == "batch":
+        return "batch"
     else:
         raise SystemExit(f"unknown workload {name}")
     if args is not None:
@@ -227,12 +229,80 @@ def _per_launch_ms(launch, reps):
     return statistics.mean(ts), statistics.median(ts)
 
 
+def run_batch(args, rank, world):
+    """Batched workload: 2048 + 256 automata, 16 steps per benchmark step, one
+    persistent launch per automaton step (graph replay), against looping the
+    single-instance path over the instances."""
+    import torch
+    from paper_2208_11617_gb300 import autotune
+    from paper_2208_11617_gb300 import simplex as sx
+
+    base = inputs.batch_instances()
+    t0 = time.perf_counter()
+    table = {} if args.no_tune else autotune.tune(base)
+    tune_s = time.perf_counter() - t0
+    insts = autotune.apply(base, table)
+    steps = inputs.BATCH_STEPS
+    b = sx.simplex_batch_create(insts)
+    info = sx.simplex_batch_info(b)
+    sx.simplex_batch_bind(b)
+    sx.simplex_batch_init(b)
+    live = torch.zeros(len(insts) * (steps + 1), dtype=torch.int64, device="cuda")
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    secs = _time_region(lambda: sx.simplex_batch_run(b, steps, live), args.steps, args.warmup, world)
+    clk = clocks.stop()
+    cells = info["cells"]
+    value, tmax = aggregate(cells * steps * args.steps, secs, world)
+    # one automaton step of every instance = one launch: time a live-less run / steps
+    run_ms, _ = _per_launch_ms(lambda: sx.simplex_batch_run(b, steps, None), 5)
+    step_ms = run_ms / steps
+    hbm_peak, peak_kind = _peaks()
+    achieved = 2 * cells / (step_ms * 1e-3) / 1e9
+    # baseline: the single-instance path looped over the instances (each a graph of 16 steps)
+    maps = []
+    for d in insts:
+        side = (d["n"] + 16) // 16 * 16
+        mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], d["block"], side=side)
+        a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
+        bb = torch.zeros_like(a)
+        sx.simplex_ca_init(mp, a, d["seed"], d["threshold"])
+        maps.append((mp, a, bb, d))
+
+    def loop():
+        for mp, a, bb, d in maps:
+            sx.simplex_ca_run(mp, a, bb, steps, d["birth"], d["survive"], None, True)
+
+    secs_loop = _time_region(loop, 1, 1, world)
+    value_loop, _ = aggregate(cells * steps, secs_loop, world)
+    assert sx.simplex_device_status() == 0
+    return dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="u8", data="synthetic",
+        config={"workload": "batched: 2048 m=2 (n log-U[64,2048]) + 256 m=3 (n log-U[32,256]), Bernoulli(0.4), "
+                            "B3/S23 / B5/S45, 16 steps", "instances": len(insts), "cells": cells,
+                "work_items_per_step": info["items"], "map_blocks_per_step": info["blocks"],
+                "autotuned": {f"m={k[0]} log2n={k[1]}": v for k, v in table.items()}, "tune_seconds": tune_s,
+                "parallelism": "replicas" if world > 1 else "single"},
+        roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                  "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind, "kernel": "batch_kernel",
+                  "alg_bytes_per_launch": 2 * cells, "launch_ms_mean": step_ms},
+        clocks=clk, gpu_launches=args.steps * (steps + 1),
+        single_instance_loop={"value": value_loop, "speedup_batched": value / value_loop,
+                              "ms_per_step": secs_loop * 1e3},
+        e2e={"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    )
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2208_11617_gb300 import simplex as sx
 
     torch.cuda.set_device(local)
     wl = _workload(args.workload, args)
+    if wl == "batch":
+        return run_batch(args, rank, world)
     hbm_peak, peak_kind = _peaks()
     res = {}
     if isinstance(wl, inputs.CAWorkload):
@@ -437,7 +507,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4"])
+    ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4", "batch"])
+    ap.add_argument("--no-tune", action="store_true", help="batch: untuned tile choices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
