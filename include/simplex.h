@@ -279,6 +279,8 @@ typedef struct simplex_batch_info {
     uint64_t blocks;          /* CUDA blocks (map blocks) per step, all instances */
     uint64_t cells;           /* simplex cells, all instances */
     uint64_t arena_bytes;     /* device memory simplex_batch_bind needs */
+    uint64_t grids_offset;    /* where the instances' grids start in the arena */
+    uint64_t grids_bytes;     /* bytes of all grids (two per instance), from grids_offset on */
 } simplex_batch_info_t;
 
 /* Plans every instance (host memory only).  Each instance's grids have side

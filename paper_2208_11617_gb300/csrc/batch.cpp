@@ -85,6 +85,22 @@ int enqueue_batch_run(simplex_batch_t b, int steps, unsigned long long *live, in
 
 }  // namespace
 
+namespace sxh {
+
+int batch_view(simplex_batch_t b, BatchView *out)
+{
+    if (!b) return fail(SIMPLEX_EINVAL, "batch is NULL");
+    out->insts = b->insts.data();
+    out->count = b->insts.size();
+    out->items = b->items.data();
+    out->nitems = b->items.size();
+    out->grids_offset = b->off_grids;
+    out->grids_bytes = b->bytes - b->off_grids;
+    return SIMPLEX_OK;
+}
+
+}  // namespace sxh
+
 extern "C" {
 
 int simplex_batch_create(const simplex_instance_t *instances, int count, simplex_batch_t *out)
@@ -196,6 +212,8 @@ int simplex_batch_info(simplex_batch_t b, simplex_batch_info_t *out)
     out->blocks = b->blocks;
     out->cells = b->cells;
     out->arena_bytes = b->bytes;
+    out->grids_offset = b->off_grids;
+    out->grids_bytes = b->bytes - b->off_grids;
     return SIMPLEX_OK;
 }
 

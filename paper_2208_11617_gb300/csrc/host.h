@@ -8,6 +8,7 @@
 
 #include <string>
 
+#include "batch.h"
 #include "hmap.cuh"
 #include "rule.h"
 
@@ -28,5 +29,17 @@ sx::Rule make_rule(int m, uint32_t birth, uint32_t survive);
 // TMA tensor map over a uint8 grid of the plan's layout (extent n + 1 per
 // axis, pitch side), box = tile + halo; SIMPLEX_OK or an error code.
 int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm);
+
+// Read-only view of a batch's host-side plans and work items; grid offsets in
+// the BatchInst records count from the start of the arena, and the grids
+// occupy [grids_offset, grids_offset + grids_bytes).
+struct BatchView {
+    const sx::BatchInst *insts;
+    size_t count;
+    const sx::BatchItem *items;
+    size_t nitems;
+    uint64_t grids_offset, grids_bytes;
+};
+int batch_view(struct simplex_batch *b, BatchView *out);
 
 }  // namespace sxh

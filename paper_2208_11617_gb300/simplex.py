@@ -75,7 +75,8 @@ class SimplexInstance(ctypes.Structure):
 
 class SimplexBatchInfo(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("parity", ctypes.c_int32), ("items", ctypes.c_uint64),
-                ("blocks", ctypes.c_uint64), ("cells", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64)]
+                ("blocks", ctypes.c_uint64), ("cells", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
+                ("grids_offset", ctypes.c_uint64), ("grids_bytes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
