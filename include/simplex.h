@@ -316,6 +316,41 @@ int simplex_batch_run(simplex_batch_t batch, int steps, unsigned long long *live
 int simplex_batch_grid(simplex_batch_t batch, int i, uint8_t **grid, int64_t *side);
 
 /*
+ * simplex_batch_run_static -- simplex_batch_run for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is a service
+ * of the library, not part of the method.
+ *
+ * Who needs it: a host that owns every byte of device memory through its own
+ * pool or budget and hands libraries fixed buffers only, or a latency-critical
+ * loop that must not pay for an allocator call (cudaMalloc can synchronise
+ * the device) on its hot path.  Such a caller cannot provide the arena that
+ * simplex_batch_bind wants.  This entry point needs only the grids: it keeps
+ * the batch's descriptors, work items, TMA maps and work-queue counters in a
+ * fixed 8 MiB array of device memory compiled into the library (one per device
+ * that loads the library, held until the process exits) and allocates nothing,
+ * on the device or on the host.
+ *
+ *   grids        device, 256-byte aligned, at least grids_bytes of
+ *                simplex_batch_info: both grids of every instance, laid out as
+ *                in a bound arena from grids_offset on.  The instances' state
+ *                is read from grid `parity` (0 or 1) and the result lands in
+ *                grid (parity + steps) % 2; grids must be zero outside each
+ *                domain.  The batch need not be bound.
+ *   steps, live  as simplex_batch_run (live is zeroed, then filled).
+ * Runs `steps` launches on `stream`, asynchronously.  The first call on a
+ * device looks up the fixed array's address there (cudaGetSymbolAddress);
+ * make that first call before any stream capture on that device.  Every call
+ * overwrites the fixed array (its work-queue counters are zeroed each call), so
+ * calls whose work overlaps on the GPU -- other streams, other host threads --
+ * race and give wrong results: serialise them.  A batch whose descriptors,
+ * work items and counters exceed 8 MiB (about 1.2 KB per instance: several
+ * thousand instances; the 2,304-instance batched workload needs 2.8 MB) is
+ * rejected with SIMPLEX_EINVAL.
+ */
+int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t grids_bytes, int parity, int steps,
+                             unsigned long long *live, void *stream);
+
+/*
  * simplex_device_status -- reads and clears the library's device-side error
  * word on the current device (synchronous).  *out receives 0 when no kernel
  * gave up a bounded wait since the last call; the call returns

@@ -8,10 +8,14 @@
 // issued while the current item runs), loads the item's instance description
 // into shared memory when it changes, decodes each block with that instance's
 // map and runs the same per-tile body as the single-instance kernels.
+#include <mutex>
+
+#include "../../include/simplex.h"
 #include "batch.h"
 #include "ca_tiles.cuh"
 #include "common.cuh"
 #include "hmap.cuh"
+#include "host.h"
 #include "kernels.h"
 #include "tile.cuh"
 
@@ -195,3 +199,118 @@ cudaError_t batch_read_status(uint32_t *out)
 }
 
 }  // namespace sx
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched run.
+//
+// simplex_batch_run needs an arena from the caller for the batch's descriptors,
+// work items, TMA maps and work-queue counters.  Some callers cannot provide
+// one: a host that owns every byte of device memory through its own pool or
+// budget and hands libraries fixed buffers only, or a latency-critical loop
+// that must not pay for an allocator call (cudaMalloc can synchronise the
+// device) on its hot path.  For them the scratch lives in this fixed-size
+// array instead; the caller passes only the grids (the inputs and outputs).
+// The array exists once per device that loads the library and stays allocated
+// until the process exits.
+namespace sx {
+
+constexpr uint64_t kStaticScratchBytes = 8ull << 20;  // 8 MiB
+
+static __device__ __align__(256) uint8_t g_batch_static_scratch[kStaticScratchBytes];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress with that device current).
+static cudaError_t static_scratch_address(uint8_t **out)
+{
+    static std::mutex mu;
+    static uint8_t *addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_batch_static_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = static_cast<uint8_t *>(p);
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace sx
+
+extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t grids_bytes, int parity,
+                                        int steps, unsigned long long *live, void *stream)
+{
+    using namespace sxh;
+    BatchView bv;
+    int rc = batch_view(batch, &bv);
+    if (rc) return rc;
+    if (!grids) return fail(SIMPLEX_EINVAL, "grids is NULL");
+    if ((reinterpret_cast<uintptr_t>(grids) & 255u) != 0) return fail(SIMPLEX_EINVAL, "grids must be 256-byte aligned");
+    if (grids_bytes < bv.grids_bytes)
+        return fail(SIMPLEX_EINVAL, "grids too small: %llu bytes, the batch's grids need %llu",
+                    (unsigned long long)grids_bytes, (unsigned long long)bv.grids_bytes);
+    if (parity != 0 && parity != 1) return fail(SIMPLEX_EINVAL, "parity must be 0 or 1 (got %d)", parity);
+    if (steps < 1 || steps > sx::kBatchMaxSteps)
+        return fail(SIMPLEX_EINVAL, "steps must be in [1, %d] (got %d)", sx::kBatchMaxSteps, steps);
+    // scratch layout: descriptors, work items, tensor maps, queue counters
+    auto up = [](uint64_t x) { return (x + 255) / 256 * 256; };
+    const uint64_t off_items = up(sizeof(sx::BatchInst) * bv.count);
+    const uint64_t off_tmaps = up(off_items + sizeof(sx::BatchItem) * bv.nitems);
+    const uint64_t off_queue = up(off_tmaps + sizeof(CUtensorMap) * 2 * bv.count);
+    const uint64_t need = off_queue + sizeof(unsigned int) * (uint64_t)(steps + 1);
+    if (need > sx::kStaticScratchBytes)
+        return fail(SIMPLEX_EINVAL,
+                    "batch too large for the fixed scratch: needs %llu bytes of descriptors, work items and "
+                    "queue counters, the limit is %llu (use simplex_batch_bind / simplex_batch_run)",
+                    (unsigned long long)need, (unsigned long long)sx::kStaticScratchBytes);
+    uint8_t *scratch = nullptr;
+    cudaError_t e = sx::static_scratch_address(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static batch scratch)");
+    // the grid offsets of the descriptors count from the arena start; the
+    // caller's buffer starts at the grids, so shift the base accordingly
+    uint8_t *base = grids - bv.grids_offset;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((e = sx::batch_prepare()) != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
+    unsigned int *queue = reinterpret_cast<unsigned int *>(scratch + off_queue);
+    if ((e = cudaMemcpyAsync(scratch, bv.insts, sizeof(sx::BatchInst) * bv.count, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(scratch + off_items, bv.items, sizeof(sx::BatchItem) * bv.nitems,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * (size_t)(steps + 1), st)) != cudaSuccess)
+        return cuda_fail(e, "filling the static batch scratch");
+    // TMA maps of the caller's grids, encoded in a fixed host buffer and copied
+    // in pieces (a copy from pageable memory has read its source on return)
+    CUtensorMap piece[32];
+    for (size_t k0 = 0; k0 < 2 * bv.count; k0 += 32) {
+        const size_t k1 = k0 + 32 < 2 * bv.count ? k0 + 32 : 2 * bv.count;
+        for (size_t k = k0; k < k1; ++k) {
+            rc = make_tensor_map(bv.insts[k / 2].plan, base + bv.insts[k / 2].grid[k % 2], &piece[k - k0]);
+            if (rc) return rc;
+        }
+        if ((e = cudaMemcpyAsync(scratch + off_tmaps + sizeof(CUtensorMap) * k0, piece,
+                                 sizeof(CUtensorMap) * (k1 - k0), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "filling the static batch scratch");
+    }
+    const sx::BatchInst *insts = reinterpret_cast<const sx::BatchInst *>(scratch);
+    const sx::BatchItem *items = reinterpret_cast<const sx::BatchItem *>(scratch + off_items);
+    const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(scratch + off_tmaps);
+    const uint32_t nitems = (uint32_t)bv.nitems;
+    if (live) {
+        if ((e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * bv.count * (size_t)(steps + 1), st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync(live)");
+        if ((e = sx::launch_batch_pass(insts, items, nitems, tm, base, parity, queue, live, steps + 1, 0, true,
+                                       st)) != cudaSuccess)
+            return cuda_fail(e, "batch count launch");
+    }
+    for (int s = 1; s <= steps; ++s) {
+        if ((e = sx::launch_batch_pass(insts, items, nitems, tm, base, (parity + s - 1) & 1, queue + s, live,
+                                       steps + 1, s, false, st)) != cudaSuccess)
+            return cuda_fail(e, "batch step launch");
+    }
+    return SIMPLEX_OK;
+}

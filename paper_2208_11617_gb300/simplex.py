@@ -36,6 +36,7 @@ EXPORTED = (
     "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
     "simplex_version", "simplex_selftest_wait_timeout", "simplex_batch_create", "simplex_batch_destroy",
     "simplex_batch_info", "simplex_batch_bind", "simplex_batch_init", "simplex_batch_run", "simplex_batch_grid",
+    "simplex_batch_run_static",
 )
 
 if not os.path.exists(LIB_PATH):
@@ -110,6 +111,7 @@ _sig("simplex_batch_bind", [_vp, _vp, _u64, _vp])
 _sig("simplex_batch_init", [_vp, _vp])
 _sig("simplex_batch_run", [_vp, _i32, _vp, _i32, _vp])
 _sig("simplex_batch_grid", [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64)])
+_sig("simplex_batch_run_static", [_vp, _vp, _u64, _i32, _i32, _vp, _vp])
 _lib.simplex_last_error.argtypes = []
 _lib.simplex_last_error.restype = ctypes.c_char_p
 _lib.simplex_version.argtypes = []
@@ -357,6 +359,15 @@ def simplex_batch_grid(b: SimplexBatch, i: int, m: int) -> torch.Tensor:
     off = ptr.value - b.arena.data_ptr()
     n = side.value ** m
     return b.arena[off: off + n].view((side.value,) * m)
+
+
+def simplex_batch_run_static(b: SimplexBatch, grids: torch.Tensor, parity: int, steps: int,
+                             live: torch.Tensor | None = None):
+    """Allocation-free run: `grids` (uint8, 256-byte aligned) holds both grids of
+    every instance; the library keeps its own bookkeeping in a fixed array."""
+    _check(_lib.simplex_batch_run_static(b.handle, _dptr(grids, torch.uint8, "grids"), grids.numel(), parity, steps,
+                                         _dptr(live, torch.int64, "live", b.count * (steps + 1)), _stream()),
+           "simplex_batch_run_static")
 
 
 def simplex_last_error() -> str:
