@@ -172,6 +172,8 @@ def _workload(name, args=None):
         wl = inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
     elif name == "batch":
         return "batch"
+    elif name == "serve":
+        return "serve"
     else:
         raise SystemExit(f"unknown workload {name}")
     if args is not None:
@@ -295,6 +297,88 @@ def run_batch(args, rank, world):
     )
 
 
+def _fifo_latency(arrivals_s, service_s):
+    """FIFO single-server queue (Lindley): completion - arrival per job, seconds."""
+    free_at = 0.0
+    out = []
+    for a, sv in zip(arrivals_s, service_s):
+        start = max(a, free_at)
+        free_at = start + sv
+        out.append(free_at - a)
+    return out
+
+
+def run_serve(args, rank, world):
+    """Serving workload: Poisson arrivals at 2000 jobs/s, continuous batching
+    under a 64 GiB grid budget; p50/p99 latency and cell-updates/s, against
+    serial per-job execution on the single-instance path."""
+    import torch
+    from paper_2208_11617_gb300 import simplex as sx
+
+    seconds = args.serve_seconds
+    jobs, t = inputs.serve_trace(seconds=seconds)
+    srv = sx.SimplexServer(hbm_budget=inputs.SERVE_BUDGET, max_jobs=8192, max_steps=64, max_items=1 << 21,
+                           max_inflight=3)
+    warm, wt = inputs.serve_trace(seconds=0.05, seed=5)
+    srv.run(warm, wt, realtime=True)                  # warm-up trace (not timed)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t0 = time.perf_counter()
+    srv.run(jobs, t, realtime=True)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    value = st["cell_updates"] / wall
+    # serial per-job execution: service time of each job alone (a sample), then a FIFO queue
+    rng = np.random.default_rng(7)
+    sample = sorted(rng.choice(len(jobs), size=min(args.serve_sample, len(jobs)), replace=False).tolist())
+    svc, cu, mismatches = [], 0, 0
+    for i in sample:
+        d = jobs[i]
+        side = (d["n"] + 16) // 16 * 16
+        block = (128 if d["n"] >= 1024 else 64) if d["m"] == 2 else 16
+        mp = sx.simplex_map_create(d["m"], d["n"], 2, 2, block, side=side)
+        a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
+        b = torch.zeros_like(a)
+        dig = torch.zeros(1, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        sx.simplex_ca_init(mp, a, d["seed"], d["threshold"])
+        fin = sx.simplex_ca_run(mp, a, b, d["steps"], d["birth"], d["survive"], None, False)
+        sx.simplex_ca_digest(mp, fin, dig)
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - s0)
+        cu += mp.info.cells * d["steps"]
+        if (int(dig.item()) & ((1 << 64) - 1)) != srv.result(i)["digest"]:
+            mismatches += 1
+    serial_rate = cu / sum(svc)
+    mean_svc = sum(svc) / len(svc)
+    # serial latency under the same arrivals, service times resampled from the sample
+    svc_all = [svc[k % len(svc)] for k in range(len(jobs))]
+    lat = sorted(_fifo_latency(list(t), svc_all))
+    q = lambda f: lat[min(len(lat) - 1, int(f * (len(lat) - 1) + 0.5))] * 1e3
+    assert mismatches == 0, f"{mismatches} jobs differ between the server and the single-instance path"
+    assert sx.simplex_device_status() == 0
+    return dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=1, warmup=1, ms_per_step=wall * 1e3,
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u8", data="synthetic",
+        config={"workload": f"serving: Poisson {inputs.SERVE_RATE:g} jobs/s for {seconds:g} s, 80/20 m=2/m=3, "
+                            "n log-U[128,8192]/[32,512], steps U{1..64}, Bernoulli(0.5), 64 GiB grid budget",
+                "jobs": len(jobs), "parallelism": "replicas" if world > 1 else "single"},
+        serve={"p50_ms": st["p50_ms"], "p90_ms": st["p90_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+               "mean_ms": st["mean_ms"], "completed": st["completed"], "rejected": st["rejected"],
+               "rounds": st["rounds"], "mean_resident_jobs": st["mean_active"],
+               "peak_pool_gib": st["peak_pool_bytes"] / 2 ** 30, "offered_cell_updates_per_s":
+                   st["cell_updates"] / seconds},
+        serial={"cell_updates_per_s": serial_rate, "mean_service_ms": mean_svc * 1e3,
+                "utilisation_at_this_rate": inputs.SERVE_RATE * mean_svc, "p50_ms": q(0.5), "p99_ms": q(0.99),
+                "sample_jobs": len(sample), "digest_mismatches": mismatches},
+        roofline=None, clocks=clk, gpu_launches=None,
+        e2e={"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    )
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2208_11617_gb300 import simplex as sx
@@ -303,6 +387,8 @@ def run_ours(args, rank, world, local):
     wl = _workload(args.workload, args)
     if wl == "batch":
         return run_batch(args, rank, world)
+    if wl == "serve":
+        return run_serve(args, rank, world)
     hbm_peak, peak_kind = _peaks()
     res = {}
     if isinstance(wl, inputs.CAWorkload):
@@ -507,7 +593,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4", "batch"])
+    ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4", "batch", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=inputs.SERVE_SECONDS, help="serve: trace length")
+    ap.add_argument("--serve-sample", type=int, default=400, help="serve: jobs re-run alone for the serial baseline")
     ap.add_argument("--no-tune", action="store_true", help="batch: untuned tile choices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")

@@ -350,6 +350,91 @@ int simplex_batch_grid(simplex_batch_t batch, int i, uint8_t **grid, int64_t *si
 int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t grids_bytes, int parity, int steps,
                              unsigned long long *live, void *stream);
 
+/* ---- serving with continuous batching --------------------------------------
+ *
+ * Jobs -- an automaton on an m-simplex of size n for a number of steps --
+ * arrive over time.  The server keeps each admitted job's two grids resident
+ * in a device pool capped by an HBM budget and works in rounds: one round is
+ * ONE launch of the batched persistent kernel that advances every resident
+ * job by one step, whatever step each is at.  Between rounds it admits
+ * arrived jobs first come first served as soon as a job slot and pool memory
+ * are free, and retires finished jobs: their live count after every step and
+ * a digest of their final grid are copied to host memory and their memory
+ * returns to the pool.  A job's result is identical whether it runs alone or
+ * among others.  Tiles: m = 2: 128 from n = 1024 up, else 64; m = 3: 16.
+ */
+typedef struct simplex_server *simplex_server_t;
+
+typedef struct simplex_server_params {
+    uint64_t hbm_budget;     /* bytes of the grid pool (both grids of every resident job) */
+    int32_t max_jobs;        /* resident job slots */
+    int32_t max_steps;       /* largest steps of a job (<= 4095) */
+    int32_t max_items;       /* work items per round (8 blocks each), >= 1024 */
+    int32_t max_inflight;    /* rounds the host may queue ahead of the GPU (1..64) */
+} simplex_server_params_t;
+
+typedef struct simplex_job {
+    int32_t m;               /* 2 or 3 */
+    int32_t steps;           /* 1 .. max_steps */
+    int64_t n;               /* >= 0 */
+    uint32_t birth, survive; /* rule masks */
+    uint32_t seed, threshold;/* initial state as simplex_ca_init */
+} simplex_job_t;
+
+typedef struct simplex_job_result {
+    int32_t status;          /* 0 pending, 1 running, 2 done, 3 rejected (larger than the budget) */
+    int32_t steps;
+    double arrival_ms;       /* from the trace */
+    double admit_ms;         /* host time of admission */
+    double done_ms;          /* device time at which its last step had completed */
+    uint64_t digest;         /* sum over live cells x of splitmix32(0x00D16E57 ^ lin(x)), mod 2^64 */
+    uint64_t live_final;     /* live cells after the last step */
+} simplex_job_result_t;
+
+typedef struct simplex_server_stats {
+    uint64_t submitted, completed, rejected, rounds;
+    uint64_t cell_updates;   /* sum over completed work of cells x steps */
+    uint64_t peak_pool_bytes;
+    double wall_ms;          /* from the start of the trace to the last completion seen */
+    double mean_active;      /* resident jobs per round */
+    double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* latency: done - arrival */
+} simplex_server_stats_t;
+
+/* Device bytes the server's arena needs for these parameters (tables + pool). */
+int simplex_server_arena_bytes(const simplex_server_params_t *params, uint64_t *out);
+
+/* Creates a server over `arena` (device, 256-byte aligned, >= the size above,
+ * owned by the caller).  Allocates pinned host buffers for results. */
+int simplex_server_create(const simplex_server_params_t *params, void *arena, uint64_t arena_bytes,
+                          simplex_server_t *out);
+
+int simplex_server_destroy(simplex_server_t server);
+
+/*
+ * simplex_server_run -- serves a trace to completion (blocking).  Job i
+ * arrives at arrival_s[i] seconds after the call starts (realtime != 0; with
+ * realtime = 0 or arrival_s = NULL every job is available at once).  Work is
+ * issued on `stream`.  Results and statistics stay queryable until the next
+ * run.  Errors: SIMPLEX_EINVAL (a job's parameters), SIMPLEX_ENOMEM (a round
+ * larger than max_items), SIMPLEX_ECUDA.
+ */
+int simplex_server_run(simplex_server_t server, const simplex_job_t *jobs, const double *arrival_s, int count,
+                       int realtime, void *stream);
+
+/* Result of job `job` (index into the last trace); `live` (nullable, host,
+ * steps + 1 entries) receives the live count before the first and after
+ * every step. */
+int simplex_server_result(simplex_server_t server, int64_t job, simplex_job_result_t *out, unsigned long long *live);
+
+int simplex_server_stats(simplex_server_t server, simplex_server_stats_t *out);
+
+/* The result digest of one grid: *digest += sum over live cells x of
+ * splitmix32(0x00D16E57 ^ lin(x)), and *live (nullable) += the live cells.
+ * Same layout rules as simplex_ca_step.  Lets a caller compare a job run alone
+ * with the server's result. */
+int simplex_ca_digest(simplex_map_t map, const uint8_t *grid, unsigned long long *digest, unsigned long long *live,
+                      void *stream);
+
 /*
  * simplex_device_status -- reads and clears the library's device-side error
  * word on the current device (synchronous).  *out receives 0 when no kernel

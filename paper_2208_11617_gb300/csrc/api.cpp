@@ -535,6 +535,17 @@ int simplex_visit_count(simplex_map_t map, uint32_t *counts, int level, int mode
     return SIMPLEX_OK;
 }
 
+int simplex_ca_digest(simplex_map_t map, const uint8_t *grid, unsigned long long *digest, unsigned long long *live,
+                      void *stream)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_ca_layout(map->plan, grid, "grid"))) return rc;
+    if (!digest) return fail(SIMPLEX_EINVAL, "digest is NULL");
+    cudaError_t e = sx::launch_ca_count(map->plan, grid, live, static_cast<cudaStream_t>(stream), digest);
+    if (e != cudaSuccess) return cuda_fail(e, "digest launch");
+    return SIMPLEX_OK;
+}
+
 int simplex_device_status(uint32_t *out)
 {
     if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");

@@ -27,10 +27,15 @@ constexpr int kBatchChunk = 8;         // CUDA blocks of one instance per work i
 constexpr int kBatchMaxSteps = 4096;   // steps per simplex_batch_run call
 
 // One work item of the device queue: up to kBatchChunk consecutive CUDA
-// blocks v0 .. v0 + cnt - 1 of instance `inst`'s map.
+// blocks v0 .. v0 + cnt - 1 of instance `inst`'s map.  `tag` lets instances
+// that are at different steps share one launch: bit 0 flips the grid the
+// instance reads, bits 1.. add to the live-count index of the pass.
 struct BatchItem {
-    uint32_t inst, v0, cnt, pad;
+    uint32_t inst, v0, cnt, tag;
 };
+
+// Salt of the result digest: sum over live cells x of splitmix32(kDigestSalt ^ lin(x)).
+constexpr uint32_t kDigestSalt = 0x00D16E57u;
 
 struct BatchInst {
     Plan plan;

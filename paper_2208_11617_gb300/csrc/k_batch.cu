@@ -31,21 +31,31 @@ __device__ __forceinline__ uint32_t body_box_bytes(int body)
 }
 
 // Live cells of one tile of grid `g`, read straight from global memory in
-// 16-cell chunks (the count pass that gives live[0]).
+// 16-cell chunks (the count pass that gives live[0]); with `dig` it also sums
+// splitmix32(kDigestSalt ^ lin(x)) over the live cells into *dig.
 template <int M>
-__device__ __forceinline__ uint32_t count_tile(const Plan &p, const int32_t *X, const uint8_t *g, bool partial)
+__device__ __forceinline__ uint32_t count_tile(const Plan &p, const int32_t *X, const uint8_t *g, bool partial,
+                                               unsigned long long *dig_acc)
 {
     const uint32_t nchunks = 1u << (M * p.log_rho - 4);
     uint32_t c_live = 0;
+    unsigned long long d = 0;
     for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
         const ChunkPos<M> q = chunk_pos<M>(p, X, c, 4);
         if (partial && q.sum > p.n) continue;
         const uint4 w = *reinterpret_cast<const uint4 *>(g + q.addr);
         const int64_t rem = p.n - q.sum + 1;
         const int cnt = partial ? (int)(rem < 16 ? rem : 16) : 16;
-        c_live += __popc(w.x & chunk_word_mask(cnt, 0)) + __popc(w.y & chunk_word_mask(cnt, 1)) +
-                  __popc(w.z & chunk_word_mask(cnt, 2)) + __popc(w.w & chunk_word_mask(cnt, 3));
+        const uint32_t ww[4] = {w.x & chunk_word_mask(cnt, 0), w.y & chunk_word_mask(cnt, 1),
+                                w.z & chunk_word_mask(cnt, 2), w.w & chunk_word_mask(cnt, 3)};
+        c_live += __popc(ww[0]) + __popc(ww[1]) + __popc(ww[2]) + __popc(ww[3]);
+        if (dig_acc) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if ((ww[j >> 2] >> (8 * (j & 3))) & 1u) d += splitmix32(kDigestSalt ^ ((uint32_t)q.lin + (uint32_t)j));
+        }
     }
+    if (dig_acc) *dig_acc += d;
     return c_live;
 }
 
@@ -53,7 +63,7 @@ __global__ void __launch_bounds__(kBatchThreads)
     batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items, uint32_t nitems,
                  const CUtensorMap *__restrict__ tmaps, uint8_t *__restrict__ arena, int in_parity,
                  unsigned int *__restrict__ queue, unsigned long long *__restrict__ live, int live_stride,
-                 int live_index, int count_only)
+                 int live_index, int count_only, unsigned long long *__restrict__ digest)
 {
     extern __shared__ uint8_t dsmem[];
     __shared__ BatchInst si;
@@ -90,13 +100,15 @@ __global__ void __launch_bounds__(kBatchThreads)
             __syncthreads();
             if (tid == 0) {
                 s_cur = (int)item.inst;
-                if (!count_only) prefetch_tmap(tmaps + si.tmap + in_parity);
+                if (!count_only) prefetch_tmap(tmaps + si.tmap + (in_parity ^ (int)(item.tag & 1u)));
             }
         }
         const Plan &p = si.plan;
-        const uint8_t *gin = arena + si.grid[in_parity];
-        uint8_t *gout = arena + si.grid[in_parity ^ 1];
+        const int par = in_parity ^ (int)(item.tag & 1u);
+        const uint8_t *gin = arena + si.grid[par];
+        uint8_t *gout = arena + si.grid[par ^ 1];
         uint32_t my_live = 0;
+        unsigned long long my_dig = 0;
         for (uint32_t j = 0; j < item.cnt; ++j) {
             const uint64_t v = (uint64_t)item.v0 + j;
             int32_t X[3] = {0, 0, 0};
@@ -106,13 +118,14 @@ __global__ void __launch_bounds__(kBatchThreads)
             if (s0 > p.n) continue;
             const bool partial = s0 + (int64_t)p.m * (p.rho - 1) > p.n;
             if (count_only) {
-                my_live += p.m == 2 ? count_tile<2>(p, X, gin, partial) : count_tile<3>(p, X, gin, partial);
+                unsigned long long *acc = digest ? &my_dig : nullptr;
+                my_live += p.m == 2 ? count_tile<2>(p, X, gin, partial, acc) : count_tile<3>(p, X, gin, partial, acc);
                 continue;
             }
             if (tid == 0) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&bar, body_box_bytes(si.body));
-                const CUtensorMap *tm = tmaps + si.tmap + in_parity;
+                const CUtensorMap *tm = tmaps + si.tmap + par;
                 if (p.m == 2)
                     tma_load_2d(tile, tm, X[1] * p.rho - 16, X[0] * p.rho - 1, &bar);
                 else
@@ -152,7 +165,14 @@ __global__ void __launch_bounds__(kBatchThreads)
             }
             __syncthreads();  // the staged box is fully read before the next load
         }
-        if (live) block_add_u64(live + (uint64_t)item.inst * live_stride + live_index, my_live, red);
+        if (live)
+            block_add_u64(live + (uint64_t)item.inst * live_stride + live_index + (item.tag >> 1), my_live, red);
+        if (digest) {
+            unsigned long long w = my_dig;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+            if ((tid & 31) == 0 && w) atomicAdd(digest + item.inst, w);
+        }
         __syncthreads();
     }
 }
@@ -172,7 +192,7 @@ cudaError_t batch_prepare()
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
-                              cudaStream_t st)
+                              cudaStream_t st, unsigned long long *digest)
 {
     cudaError_t e = batch_prepare();
     if (e != cudaSuccess) return e;
@@ -186,7 +206,8 @@ cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, ui
     uint64_t g = (uint64_t)sms * (uint64_t)per_sm;  // persistent: every CTA resident
     if (g > nitems) g = nitems ? nitems : 1;
     batch_kernel<<<(unsigned)g, kBatchThreads, kBatchStageBytes + 128, st>>>(
-        insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0);
+        insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0,
+        digest);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // k_init.cu -- seeded Bernoulli initial state of the automaton and the live
 // count of a grid, both fused with the map H (one CUDA block per tile, chunks
 // of 16 uint8 cells along x_m with one 16-byte access each).
+#include "batch.h"
 #include "common.cuh"
 #include "hmap.cuh"
 #include "kernels.h"
@@ -48,9 +49,11 @@ __global__ void __launch_bounds__(256) ca_init_kernel(const Plan p, uint8_t *__r
 
 template <int M>
 __global__ void __launch_bounds__(256) ca_count_kernel(const Plan p, const uint8_t *__restrict__ grid,
-                                                       uint64_t nblocks, unsigned long long *live)
+                                                       uint64_t nblocks, unsigned long long *live,
+                                                       unsigned long long *digest)
 {
     __shared__ uint32_t red[8];
+    unsigned long long my_dig = 0;
     const uint32_t nchunks = 1u << (M * p.log_rho - 4);
     uint32_t my_live = 0;
     for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
@@ -67,10 +70,31 @@ __global__ void __launch_bounds__(256) ca_count_kernel(const Plan p, const uint8
             const int64_t rem = p.n - q.sum + 1;
             const int cnt = partial ? (int)(rem < 16 ? rem : 16) : 16;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) my_live += __popc(w[k] & chunk_word_mask(cnt, k));
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t wk = w[k] & chunk_word_mask(cnt, k);
+                my_live += __popc(wk);
+                if (digest) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if ((wk >> (8 * j)) & 1u)
+                            my_dig += splitmix32(kDigestSalt ^ ((uint32_t)q.lin + (uint32_t)(4 * k + j)));
+                }
+            }
         }
     }
-    block_add_u64(live, my_live, red);
+    if (live) block_add_u64(live, my_live, red);
+    if (digest) {
+        // 64-bit sum over the CTA's warps (partial warps included)
+        const int lane = threadIdx.x & 31;
+        const int in_warp = min(32, (int)blockDim.x - 32 * (int)(threadIdx.x >> 5));
+        const uint32_t mask = in_warp == 32 ? 0xffffffffu : ((1u << in_warp) - 1u);
+        unsigned long long w = my_dig;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_down_sync(mask, w, o);
+            if (lane + o < in_warp) w += other;
+        }
+        if (lane == 0 && w) atomicAdd(digest, w);
+    }
 }
 
 static unsigned grid_for(uint64_t nblocks)
@@ -93,14 +117,15 @@ cudaError_t launch_ca_init(const Plan &p, uint8_t *grid, uint32_t seed, uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_ca_count(const Plan &p, const uint8_t *grid, unsigned long long *live, cudaStream_t st)
+cudaError_t launch_ca_count(const Plan &p, const uint8_t *grid, unsigned long long *live, cudaStream_t st,
+                            unsigned long long *digest)
 {
     const uint64_t nchunks = 1ull << (p.m * p.log_rho - 4);
     const unsigned t = (unsigned)(nchunks < 256 ? nchunks : 256);
     const unsigned g = grid_for(p.h_blocks);
     switch (p.m) {
-    case 2: ca_count_kernel<2><<<g, t, 0, st>>>(p, grid, p.h_blocks, live); break;
-    case 3: ca_count_kernel<3><<<g, t, 0, st>>>(p, grid, p.h_blocks, live); break;
+    case 2: ca_count_kernel<2><<<g, t, 0, st>>>(p, grid, p.h_blocks, live, digest); break;
+    case 3: ca_count_kernel<3><<<g, t, 0, st>>>(p, grid, p.h_blocks, live, digest); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -20,7 +20,10 @@ cudaError_t launch_visit(const Plan &p, uint32_t *counts, int level, int kind, c
 cudaError_t launch_ca_init(const Plan &p, uint8_t *grid, uint32_t seed, uint32_t threshold,
                            unsigned long long *live, cudaStream_t st);
 
-cudaError_t launch_ca_count(const Plan &p, const uint8_t *grid, unsigned long long *live, cudaStream_t st);
+// Live cells of a grid added to *live (if given); with `digest`, the sum over
+// live cells x of splitmix32(kDigestSalt ^ lin(x)) is added to *digest.
+cudaError_t launch_ca_count(const Plan &p, const uint8_t *grid, unsigned long long *live, cudaStream_t st,
+                            unsigned long long *digest = nullptr);
 
 // TMA-staged automaton steps; `tin` maps the input grid (see make_tensor_map).
 bool ca2_supports(int rho);
@@ -45,7 +48,7 @@ cudaError_t batch_prepare();
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
-                              cudaStream_t st);
+                              cudaStream_t st, unsigned long long *digest = nullptr);
 cudaError_t batch_read_status(uint32_t *out);
 
 // Device error words of the TMA kernels (bounded waits that gave up).

@@ -1,0 +1,556 @@
+// server.cpp -- continuous-batching server for automaton jobs (C ABI in
+// include/simplex.h).
+//
+// Jobs (an m-simplex automaton of size n run for a number of steps) arrive
+// over time.  The server keeps every admitted job's two grids resident in a
+// device arena whose grid pool is capped by an HBM budget, and works in
+// rounds: each round is ONE launch of the batched persistent kernel that
+// advances every resident job by one step, whatever step each job is at
+// (per-item tags select each job's input grid and live-count slot).  Between
+// rounds the host loop admits jobs that have arrived (first come, first
+// served) as soon as a slot and enough pool memory are free, and retires jobs
+// whose last step has completed (their results -- live counts of every step
+// and a digest of the final grid -- are copied to host memory and their
+// memory returns to the pool).  Completion times are device times (CUDA
+// events), arrival times come from the trace.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/simplex.h"
+#include "batch.h"
+#include "host.h"
+#include "kernels.h"
+
+using namespace sxh;
+
+namespace {
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+uint64_t binom(uint64_t n, int k)
+{
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return (uint64_t)r;
+}
+
+// First-fit allocator over the grid pool [0, size), 256-byte granules; free
+// ranges are coalesced on release.
+class FreeList {
+  public:
+    void reset(uint64_t size)
+    {
+        free_.clear();
+        if (size) free_[0] = size;
+        size_ = size;
+        used_ = 0;
+        peak_ = 0;
+    }
+    bool alloc(uint64_t bytes, uint64_t *off)
+    {
+        bytes = align_up(bytes, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= bytes) {
+                *off = it->first;
+                const uint64_t rest = it->second - bytes, start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_ += bytes;
+                peak_ = std::max(peak_, used_);
+                return true;
+            }
+        return false;
+    }
+    void release(uint64_t off, uint64_t bytes)
+    {
+        bytes = align_up(bytes, 256);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    uint64_t used() const { return used_; }
+    uint64_t peak() const { return peak_; }
+
+  private:
+    std::map<uint64_t, uint64_t> free_;
+    uint64_t size_ = 0, used_ = 0, peak_ = 0;
+};
+
+enum JobStatus : int32_t { kPending = 0, kActive = 1, kDone = 2, kRejected = 3 };
+
+struct ServerJob {
+    simplex_job_t spec;
+    double arrival_ms = 0, admit_ms = 0, done_ms = 0;
+    int32_t status = kPending;
+    int slot = -1;
+    uint64_t off = 0, bytes = 0;
+    int step = 0, parity = 0;
+    uint64_t digest = 0;
+    std::vector<uint64_t> live;
+    uint64_t cells = 0;
+};
+
+struct Round {
+    cudaEvent_t ev;
+    std::vector<int64_t> finishing;
+};
+
+int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
+
+}  // namespace
+
+struct simplex_server {
+    simplex_server_params_t prm;
+    uint8_t *arena = nullptr;
+    uint64_t off_insts = 0, off_tmaps = 0, off_items = 0, off_queue = 0, off_live = 0, off_digest = 0,
+             off_pool = 0, bytes = 0;
+    uint64_t max_items = 0;
+    FreeList pool;
+    std::vector<int> free_slots;
+    std::vector<sx::BatchInst> slot_inst;        // host copies uploaded at admission
+    std::vector<CUtensorMap> slot_tmap;          // 2 per slot
+    std::vector<ServerJob> jobs;
+    std::deque<int64_t> pending;
+    std::vector<int64_t> active;
+    std::deque<Round> inflight;
+    std::vector<cudaEvent_t> spare_events;
+    std::vector<sx::BatchItem> items, fin_items;
+    unsigned long long *host_live = nullptr;     // pinned [max_jobs][max_steps + 1]
+    unsigned long long *host_digest = nullptr;   // pinned [max_jobs]
+    cudaEvent_t t0 = nullptr;
+    std::chrono::steady_clock::time_point h0;
+    // stats
+    uint64_t rounds = 0, cell_updates = 0, active_sum = 0;
+    double wall_ms = 0;
+};
+
+namespace {
+
+uint64_t layout(const simplex_server_params_t &p, simplex_server *s)
+{
+    const uint64_t slots = (uint64_t)p.max_jobs;
+    uint64_t off = 0;
+    const uint64_t max_items = (uint64_t)p.max_items;
+    if (s) s->off_insts = off;
+    off = align_up(off + sizeof(sx::BatchInst) * slots, 256);
+    if (s) s->off_tmaps = off;
+    off = align_up(off + sizeof(CUtensorMap) * 2 * slots, 256);
+    if (s) s->off_items = off;
+    off = align_up(off + sizeof(sx::BatchItem) * max_items * 2, 256);  // round items + finishing items
+    if (s) s->off_queue = off;
+    off = align_up(off + 256, 256);
+    if (s) s->off_live = off;
+    off = align_up(off + sizeof(unsigned long long) * slots * (uint64_t)(p.max_steps + 1), 256);
+    if (s) s->off_digest = off;
+    off = align_up(off + sizeof(unsigned long long) * slots, 256);
+    if (s) {
+        s->off_pool = off;
+        s->max_items = max_items;
+    }
+    return off + p.hbm_budget;
+}
+
+int check_params(const simplex_server_params_t *p)
+{
+    if (!p) return fail(SIMPLEX_EINVAL, "params is NULL");
+    if (p->hbm_budget < (1ull << 20)) return fail(SIMPLEX_EINVAL, "hbm_budget must be at least 1 MiB");
+    if (p->max_jobs < 1 || p->max_jobs > (1 << 20)) return fail(SIMPLEX_EINVAL, "max_jobs must be in [1, 2^20]");
+    if (p->max_steps < 1 || p->max_steps > 4095) return fail(SIMPLEX_EINVAL, "max_steps must be in [1, 4095]");
+    if (p->max_items < 1024 || p->max_items > (1 << 26)) return fail(SIMPLEX_EINVAL, "max_items must be in [1024, 2^26]");
+    if (p->max_inflight < 1 || p->max_inflight > 64) return fail(SIMPLEX_EINVAL, "max_inflight must be in [1, 64]");
+    return SIMPLEX_OK;
+}
+
+double host_ms(simplex_server *s)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s->h0).count();
+}
+
+// Tries to admit job j: a slot, pool memory for both grids, plan, tensor maps,
+// zeroed grids, initial state.  Returns 1 admitted, 0 must wait, <0 error.
+int admit(simplex_server *s, int64_t j, cudaStream_t st)
+{
+    ServerJob &job = s->jobs[j];
+    const simplex_job_t &sp = job.spec;
+    if (s->free_slots.empty()) return 0;
+    const int block = tile_for(sp.m, sp.n);
+    const int64_t side = (sp.n + 16) / 16 * 16;
+    uint64_t gb = 1;
+    for (int d = 0; d < sp.m; ++d) gb *= (uint64_t)side;
+    const uint64_t bytes = 2 * align_up(gb, 256);
+    if (bytes > s->prm.hbm_budget) return -2;  // can never fit
+    uint64_t off = 0;
+    if (!s->pool.alloc(bytes, &off)) return 0;
+    const int slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    sx::BatchInst &bi = s->slot_inst[slot];
+    std::memset(&bi, 0, sizeof bi);
+    int band = 0;
+    if (sp.m == 2) {
+        const int64_t nb = (sp.n + block) / block;
+        band = 1;
+        while (band < 8 && band * 2 <= nb) band *= 2;
+    }
+    int rc = build_plan(sp.m, sp.n, 2, 2, block, side, band, &bi.plan);
+    if (rc) return -1;
+    bi.rule = make_rule(sp.m, sp.birth, sp.survive);
+    bi.body = sp.m == 2 ? (block == 64 ? sx::kBody2x64 : sx::kBody2x128) : sx::kBody3x16;
+    bi.tmap = 2 * slot;
+    bi.grid[0] = s->off_pool + off;
+    bi.grid[1] = s->off_pool + off + align_up(gb, 256);
+    for (int g = 0; g < 2; ++g) {
+        rc = make_tensor_map(bi.plan, s->arena + bi.grid[g], &s->slot_tmap[2 * slot + g]);
+        if (rc) return -1;
+    }
+    cudaError_t e;
+    unsigned long long *live = reinterpret_cast<unsigned long long *>(s->arena + s->off_live) +
+                               (uint64_t)slot * (uint64_t)(s->prm.max_steps + 1);
+    unsigned long long *dig = reinterpret_cast<unsigned long long *>(s->arena + s->off_digest) + slot;
+    if ((e = cudaMemcpyAsync(s->arena + s->off_insts + sizeof(sx::BatchInst) * slot, &bi, sizeof bi,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s->arena + s->off_tmaps + sizeof(CUtensorMap) * 2 * slot, &s->slot_tmap[2 * slot],
+                             sizeof(CUtensorMap) * 2, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(s->arena + bi.grid[0], 0, bytes, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * (size_t)(s->prm.max_steps + 1), st)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(dig, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+        (e = sx::launch_ca_init(bi.plan, s->arena + bi.grid[0], sp.seed, sp.threshold, live, st)) != cudaSuccess) {
+        cuda_fail(e, "admitting a job");
+        return -1;
+    }
+    job.status = kActive;
+    job.slot = slot;
+    job.off = off;
+    job.bytes = bytes;
+    job.step = 0;
+    job.parity = 0;
+    job.admit_ms = host_ms(s);
+    s->active.push_back(j);
+    return 1;
+}
+
+// One round: advance every active job by one step; jobs reaching their step
+// count get a digest pass and their results queued for copy to the host.
+int launch_round(simplex_server *s, cudaStream_t st)
+{
+    s->items.clear();
+    s->fin_items.clear();
+    Round r;
+    for (int64_t j : s->active) {
+        ServerJob &job = s->jobs[j];
+        const sx::BatchInst &bi = s->slot_inst[job.slot];
+        const uint32_t tag = (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1);
+        for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += sx::kBatchChunk) {
+            const uint64_t cnt = std::min<uint64_t>(sx::kBatchChunk, bi.plan.h_blocks - v0);
+            s->items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt, tag});
+        }
+        job.step += 1;
+        job.parity ^= 1;
+        s->cell_updates += job.cells;
+        if (job.step == job.spec.steps) {
+            r.finishing.push_back(j);
+            for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += sx::kBatchChunk) {
+                const uint64_t cnt = std::min<uint64_t>(sx::kBatchChunk, bi.plan.h_blocks - v0);
+                s->fin_items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt,
+                                                     (uint32_t)job.parity});
+            }
+        }
+    }
+    if (s->items.size() > s->max_items || s->fin_items.size() > s->max_items)
+        return fail(SIMPLEX_ENOMEM, "a round needs %zu work items, max_items is %llu", s->items.size(),
+                    (unsigned long long)s->max_items);
+    s->active_sum += s->active.size();
+    const sx::BatchInst *insts = reinterpret_cast<const sx::BatchInst *>(s->arena + s->off_insts);
+    const CUtensorMap *tmaps = reinterpret_cast<const CUtensorMap *>(s->arena + s->off_tmaps);
+    sx::BatchItem *items = reinterpret_cast<sx::BatchItem *>(s->arena + s->off_items);
+    sx::BatchItem *fitems = items + s->max_items;
+    unsigned int *queue = reinterpret_cast<unsigned int *>(s->arena + s->off_queue);
+    unsigned long long *live = reinterpret_cast<unsigned long long *>(s->arena + s->off_live);
+    unsigned long long *dig = reinterpret_cast<unsigned long long *>(s->arena + s->off_digest);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(items, s->items.data(), sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess ||
+        (e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, queue, live,
+                                   s->prm.max_steps + 1, 0, false, st)) != cudaSuccess)
+        return cuda_fail(e, "launching a serving round");
+    if (!s->fin_items.empty()) {
+        if ((e = cudaMemcpyAsync(fitems, s->fin_items.data(), sizeof(sx::BatchItem) * s->fin_items.size(),
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = sx::launch_batch_pass(insts, fitems, (uint32_t)s->fin_items.size(), tmaps, s->arena, 0, queue + 1,
+                                       nullptr, 0, 0, true, st, dig)) != cudaSuccess)
+            return cuda_fail(e, "launching the digest pass");
+        for (int64_t j : r.finishing) {
+            const int slot = s->jobs[j].slot;
+            const size_t row = (size_t)(s->prm.max_steps + 1);
+            if ((e = cudaMemcpyAsync(s->host_live + slot * row, live + slot * row,
+                                     sizeof(unsigned long long) * (size_t)(s->jobs[j].spec.steps + 1),
+                                     cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(s->host_digest + slot, dig + slot, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(e, "copying job results");
+        }
+        // finishing jobs leave the active set now; their memory is released at retirement
+        std::vector<int64_t> still;
+        still.reserve(s->active.size());
+        for (int64_t j : s->active)
+            if (s->jobs[j].step < s->jobs[j].spec.steps) still.push_back(j);
+        s->active.swap(still);
+    }
+    if (s->spare_events.empty()) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        s->spare_events.push_back(ev);
+    }
+    r.ev = s->spare_events.back();
+    s->spare_events.pop_back();
+    if ((e = cudaEventRecord(r.ev, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    s->inflight.push_back(std::move(r));
+    s->rounds += 1;
+    return SIMPLEX_OK;
+}
+
+// Retires the oldest in-flight rounds whose event has completed (or, with
+// `wait`, the oldest one regardless).  Returns the number of jobs that
+// finished, or <0.
+int retire(simplex_server *s, bool wait)
+{
+    int n = 0, finished = 0;
+    while (!s->inflight.empty()) {
+        Round &r = s->inflight.front();
+        cudaError_t e = wait && n == 0 ? cudaEventSynchronize(r.ev) : cudaEventQuery(r.ev);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) return cuda_fail(e, "waiting for a serving round");
+        float ms = 0;
+        if ((e = cudaEventElapsedTime(&ms, s->t0, r.ev)) != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        for (int64_t j : r.finishing) {
+            ServerJob &job = s->jobs[j];
+            const size_t row = (size_t)(s->prm.max_steps + 1);
+            job.live.assign(s->host_live + job.slot * row, s->host_live + job.slot * row + job.spec.steps + 1);
+            job.digest = s->host_digest[job.slot];
+            job.done_ms = ms;
+            job.status = kDone;
+            s->pool.release(job.off, job.bytes);
+            s->free_slots.push_back(job.slot);
+            job.slot = -1;
+            ++finished;
+        }
+        s->spare_events.push_back(r.ev);
+        s->inflight.pop_front();
+        ++n;
+    }
+    return finished;
+}
+
+}  // namespace
+
+extern "C" {
+
+int simplex_server_arena_bytes(const simplex_server_params_t *params, uint64_t *out)
+{
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    *out = layout(*params, nullptr);
+    return SIMPLEX_OK;
+}
+
+int simplex_server_create(const simplex_server_params_t *params, void *arena, uint64_t arena_bytes,
+                          simplex_server_t *out)
+{
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!arena || (reinterpret_cast<uintptr_t>(arena) & 255u))
+        return fail(SIMPLEX_EINVAL, "arena must be a 256-byte aligned device pointer");
+    simplex_server *s = new (std::nothrow) simplex_server();
+    if (!s) return fail(SIMPLEX_ENOMEM, "host allocation failed");
+    s->prm = *params;
+    const uint64_t need = layout(*params, s);
+    if (arena_bytes < need) {
+        delete s;
+        return fail(SIMPLEX_EINVAL, "arena too small: %llu bytes, need %llu", (unsigned long long)arena_bytes,
+                    (unsigned long long)need);
+    }
+    s->arena = static_cast<uint8_t *>(arena);
+    s->bytes = need;
+    s->pool.reset(params->hbm_budget);
+    try {
+        s->slot_inst.resize(params->max_jobs);
+        s->slot_tmap.resize(2 * (size_t)params->max_jobs);
+        for (int i = params->max_jobs - 1; i >= 0; --i) s->free_slots.push_back(i);
+    } catch (...) {
+        delete s;
+        return fail(SIMPLEX_ENOMEM, "host allocation failed");
+    }
+    cudaError_t e;
+    const size_t row = (size_t)(params->max_steps + 1);
+    if ((e = cudaMallocHost(&s->host_live, sizeof(unsigned long long) * row * params->max_jobs)) != cudaSuccess ||
+        (e = cudaMallocHost(&s->host_digest, sizeof(unsigned long long) * params->max_jobs)) != cudaSuccess ||
+        (e = cudaEventCreate(&s->t0)) != cudaSuccess) {
+        if (s->host_live) cudaFreeHost(s->host_live);
+        if (s->host_digest) cudaFreeHost(s->host_digest);
+        delete s;
+        return cuda_fail(e, "allocating the server's pinned result buffers");
+    }
+    *out = s;
+    return SIMPLEX_OK;
+}
+
+int simplex_server_destroy(simplex_server_t s)
+{
+    if (!s) return SIMPLEX_OK;
+    for (auto &r : s->inflight) {
+        cudaEventSynchronize(r.ev);
+        cudaEventDestroy(r.ev);
+    }
+    for (auto ev : s->spare_events) cudaEventDestroy(ev);
+    if (s->t0) cudaEventDestroy(s->t0);
+    if (s->host_live) cudaFreeHost(s->host_live);
+    if (s->host_digest) cudaFreeHost(s->host_digest);
+    delete s;
+    return SIMPLEX_OK;
+}
+
+int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const double *arrival_s, int count,
+                       int realtime, void *stream)
+{
+    if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
+    if (!jobs || count < 0) return fail(SIMPLEX_EINVAL, "jobs is NULL");
+    if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty())
+        return fail(SIMPLEX_EINVAL, "the server is still running another trace");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // validate and queue every job (arrival order)
+    s->jobs.clear();
+    s->jobs.resize(count);
+    std::vector<int64_t> order(count);
+    for (int i = 0; i < count; ++i) {
+        const simplex_job_t &sp = jobs[i];
+        if ((sp.m != 2 && sp.m != 3) || sp.n < 0 || sp.steps < 1 || sp.steps > s->prm.max_steps)
+            return fail(SIMPLEX_EINVAL, "job %d: m must be 2 or 3, n >= 0, steps in [1, %d]", i, s->prm.max_steps);
+        s->jobs[i].spec = sp;
+        s->jobs[i].arrival_ms = arrival_s ? arrival_s[i] * 1e3 : 0.0;
+        s->jobs[i].cells = binom((uint64_t)sp.n + (uint64_t)sp.m, sp.m);
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return s->jobs[a].arrival_ms < s->jobs[b].arrival_ms; });
+    for (int64_t j : order) s->pending.push_back(j);
+    s->rounds = s->cell_updates = s->active_sum = 0;
+    s->pool.reset(s->prm.hbm_budget);
+    cudaError_t e = sx::batch_prepare();
+    if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if ((e = cudaEventRecord(s->t0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    s->h0 = std::chrono::steady_clock::now();
+    int64_t done = 0;
+    while (done < count) {
+        // admission, first come first served, as slots and pool memory allow
+        const double now = host_ms(s);
+        while (!s->pending.empty()) {
+            const int64_t j = s->pending.front();
+            if (realtime && s->jobs[j].arrival_ms > now) break;
+            int a = admit(s, j, st);
+            if (a < 0) {
+                if (a == -2) {
+                    s->jobs[j].status = kRejected;
+                    s->pending.pop_front();
+                    ++done;
+                    continue;
+                }
+                return SIMPLEX_ECUDA;
+            }
+            if (a == 0) break;
+            s->pending.pop_front();
+        }
+        if (!s->active.empty()) {
+            int rc = launch_round(s, st);
+            if (rc) return rc;
+        }
+        // keep at most max_inflight rounds queued ahead of the GPU
+        const bool must_wait = (int)s->inflight.size() >= s->prm.max_inflight ||
+                               (s->active.empty() && !s->inflight.empty() &&
+                                (s->pending.empty() || !realtime ||
+                                 s->jobs[s->pending.front()].arrival_ms <= host_ms(s)));
+        const int r = retire(s, must_wait);
+        if (r < 0) return SIMPLEX_ECUDA;
+        done += r;
+        if (s->active.empty() && s->inflight.empty() && !s->pending.empty() && realtime) {
+            const double wait_ms = s->jobs[s->pending.front()].arrival_ms - host_ms(s);
+            if (wait_ms > 0.05) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)(wait_ms * 900)));
+        }
+    }
+    s->wall_ms = host_ms(s);
+    return SIMPLEX_OK;
+}
+
+int simplex_server_result(simplex_server_t s, int64_t job, simplex_job_result_t *out, unsigned long long *live)
+{
+    if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
+    if (job < 0 || job >= (int64_t)s->jobs.size()) return fail(SIMPLEX_EINVAL, "job %lld out of range", (long long)job);
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    const ServerJob &j = s->jobs[job];
+    std::memset(out, 0, sizeof *out);
+    out->status = j.status;
+    out->steps = j.spec.steps;
+    out->arrival_ms = j.arrival_ms;
+    out->admit_ms = j.admit_ms;
+    out->done_ms = j.done_ms;
+    out->digest = j.digest;
+    out->live_final = j.live.empty() ? 0 : j.live.back();
+    if (live && !j.live.empty()) std::memcpy(live, j.live.data(), sizeof(unsigned long long) * j.live.size());
+    return SIMPLEX_OK;
+}
+
+int simplex_server_stats(simplex_server_t s, simplex_server_stats_t *out)
+{
+    if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
+    if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof *out);
+    std::vector<double> lat;
+    for (const auto &j : s->jobs)
+        if (j.status == kDone) lat.push_back(j.done_ms - j.arrival_ms);
+        else if (j.status == kRejected) out->rejected += 1;
+    out->submitted = s->jobs.size();
+    out->completed = lat.size();
+    out->rounds = s->rounds;
+    out->cell_updates = s->cell_updates;
+    out->wall_ms = s->wall_ms;
+    out->mean_active = s->rounds ? (double)s->active_sum / (double)s->rounds : 0.0;
+    out->peak_pool_bytes = s->pool.peak();
+    if (!lat.empty()) {
+        std::sort(lat.begin(), lat.end());
+        auto q = [&](double f) { return lat[std::min(lat.size() - 1, (size_t)(f * (double)(lat.size() - 1) + 0.5))]; };
+        out->p50_ms = q(0.50);
+        out->p90_ms = q(0.90);
+        out->p99_ms = q(0.99);
+        out->max_ms = lat.back();
+        double sum = 0;
+        for (double x : lat) sum += x;
+        out->mean_ms = sum / (double)lat.size();
+    }
+    return SIMPLEX_OK;
+}
+
+}  // extern "C"

@@ -97,3 +97,36 @@ def batch_instances(seed: int = 1, n2: int = 2048, n3: int = 256, p: float = 0.4
     for j, n in enumerate(sizes3):
         out.append(dict(m=3, n=int(n), birth=B5S45[0], survive=B5S45[1], seed=n2 + j, threshold=thr))
     return out
+
+
+# Serving workload: Poisson arrivals at 2000 jobs/s for 60 s; each job is an
+# automaton on a 2-simplex (80 %, n log-uniform in [128, 8192], B3/S23) or a
+# 3-simplex (20 %, n log-uniform in [32, 512], B5/S45), steps uniform in
+# 1..64, Bernoulli(0.5) seeded by the job's index; 64 GiB grid budget.
+SERVE_RATE = 2000.0
+SERVE_SECONDS = 60.0
+SERVE_BUDGET = 64 << 30
+
+
+def serve_trace(rate: float = SERVE_RATE, seconds: float = SERVE_SECONDS, seed: int = 2,
+                n2=(128, 8192), n3=(32, 512), max_steps: int = 64, p: float = 0.5):
+    """(jobs, arrival times in seconds) of the serving workload."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    arr_rng = np.random.default_rng(seed + 1)
+    gaps = arr_rng.exponential(1.0 / rate, size=int(rate * seconds * 1.2) + 16)
+    t = np.cumsum(gaps)
+    t = t[t < seconds]
+    count = len(t)
+    is3 = rng.random(count) < 0.2
+    sizes2 = log_uniform_sizes(rng, count, *n2)
+    sizes3 = log_uniform_sizes(rng, count, *n3)
+    steps = rng.integers(1, max_steps + 1, size=count)
+    thr = bernoulli_threshold(p)
+    jobs = []
+    for i in range(count):
+        m = 3 if is3[i] else 2
+        rule = B5S45 if m == 3 else B3S23
+        jobs.append(dict(m=m, n=int(sizes3[i] if m == 3 else sizes2[i]), steps=int(steps[i]), birth=rule[0],
+                         survive=rule[1], seed=i, threshold=thr))
+    return jobs, t

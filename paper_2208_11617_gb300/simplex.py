@@ -36,7 +36,8 @@ EXPORTED = (
     "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
     "simplex_version", "simplex_selftest_wait_timeout", "simplex_batch_create", "simplex_batch_destroy",
     "simplex_batch_info", "simplex_batch_bind", "simplex_batch_init", "simplex_batch_run", "simplex_batch_grid",
-    "simplex_batch_run_static",
+    "simplex_batch_run_static", "simplex_server_arena_bytes", "simplex_server_create", "simplex_server_destroy",
+    "simplex_server_run", "simplex_server_result", "simplex_server_stats", "simplex_ca_digest",
 )
 
 if not os.path.exists(LIB_PATH):
@@ -83,6 +84,37 @@ class SimplexBatchInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SimplexServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_jobs", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("max_items", ctypes.c_int32), ("max_inflight", ctypes.c_int32)]
+
+
+class SimplexJob(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("steps", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("birth", ctypes.c_uint32), ("survive", ctypes.c_uint32), ("seed", ctypes.c_uint32),
+                ("threshold", ctypes.c_uint32)]
+
+
+class SimplexJobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("arrival_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("digest", ctypes.c_uint64),
+                ("live_final", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SimplexServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("cell_updates", ctypes.c_uint64), ("peak_pool_bytes", ctypes.c_uint64),
+                ("wall_ms", ctypes.c_double), ("mean_active", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p90_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def _sig(name, args):
     f = getattr(_lib, name)
     f.argtypes = args
@@ -112,6 +144,13 @@ _sig("simplex_batch_init", [_vp, _vp])
 _sig("simplex_batch_run", [_vp, _i32, _vp, _i32, _vp])
 _sig("simplex_batch_grid", [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64)])
 _sig("simplex_batch_run_static", [_vp, _vp, _u64, _i32, _i32, _vp, _vp])
+_sig("simplex_server_arena_bytes", [ctypes.POINTER(SimplexServerParams), ctypes.POINTER(_u64)])
+_sig("simplex_server_create", [ctypes.POINTER(SimplexServerParams), _vp, _u64, ctypes.POINTER(_vp)])
+_sig("simplex_server_destroy", [_vp])
+_sig("simplex_server_run", [_vp, ctypes.POINTER(SimplexJob), ctypes.POINTER(ctypes.c_double), _i32, _i32, _vp])
+_sig("simplex_server_result", [_vp, _i64, ctypes.POINTER(SimplexJobResult), _vp])
+_sig("simplex_server_stats", [_vp, ctypes.POINTER(SimplexServerStats)])
+_sig("simplex_ca_digest", [_vp, _vp, _vp, _vp, _vp])
 _lib.simplex_last_error.argtypes = []
 _lib.simplex_last_error.restype = ctypes.c_char_p
 _lib.simplex_version.argtypes = []
@@ -368,6 +407,67 @@ def simplex_batch_run_static(b: SimplexBatch, grids: torch.Tensor, parity: int, 
     _check(_lib.simplex_batch_run_static(b.handle, _dptr(grids, torch.uint8, "grids"), grids.numel(), parity, steps,
                                          _dptr(live, torch.int64, "live", b.count * (steps + 1)), _stream()),
            "simplex_batch_run_static")
+
+
+def simplex_ca_digest(mp: SimplexMap, grid: torch.Tensor, digest: torch.Tensor, live: torch.Tensor | None = None):
+    _check(_lib.simplex_ca_digest(mp.handle, _dptr(grid, torch.uint8, "grid", mp.numel),
+                                  _dptr(digest, torch.int64, "digest", 1), _dptr(live, torch.int64, "live", 1),
+                                  _stream()), "simplex_ca_digest")
+
+
+class SimplexServer:
+    """A serving engine over a torch-allocated arena (owns the C handle)."""
+
+    def __init__(self, hbm_budget: int, max_jobs: int = 4096, max_steps: int = 64, max_items: int = 1 << 20,
+                 max_inflight: int = 3):
+        self.params = SimplexServerParams(hbm_budget, max_jobs, max_steps, max_items, max_inflight)
+        need = _u64()
+        _check(_lib.simplex_server_arena_bytes(ctypes.byref(self.params), ctypes.byref(need)),
+               "simplex_server_arena_bytes")
+        self.arena = torch.empty(need.value + 256, dtype=torch.uint8, device="cuda")
+        off = (-self.arena.data_ptr()) % 256
+        h = _vp()
+        _check(_lib.simplex_server_create(ctypes.byref(self.params), self.arena.data_ptr() + off,
+                                          self.arena.numel() - off, ctypes.byref(h)), "simplex_server_create")
+        self.handle = h.value
+        self.count = 0
+
+    def run(self, jobs, arrival_s=None, realtime: bool = True):
+        arr = (SimplexJob * len(jobs))()
+        for k, d in enumerate(jobs):
+            for f, _ in SimplexJob._fields_:
+                setattr(arr[k], f, d[f])
+        times = None
+        if arrival_s is not None:
+            times = (ctypes.c_double * len(jobs))(*[float(t) for t in arrival_s])
+        _check(_lib.simplex_server_run(self.handle, arr, times, len(jobs), 1 if realtime else 0, _stream()),
+               "simplex_server_run")
+        self.count = len(jobs)
+
+    def result(self, job: int, steps: int | None = None):
+        res = SimplexJobResult()
+        live = (ctypes.c_uint64 * ((steps or 0) + 1))() if steps else None
+        _check(_lib.simplex_server_result(self.handle, job, ctypes.byref(res), live), "simplex_server_result")
+        out = res.as_dict()
+        if live is not None:
+            out["live"] = list(live)
+        return out
+
+    def stats(self) -> dict:
+        st = SimplexServerStats()
+        _check(_lib.simplex_server_stats(self.handle, ctypes.byref(st)), "simplex_server_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            _lib.simplex_server_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def simplex_last_error() -> str:

@@ -1,0 +1,100 @@
+"""GPU tests of the continuous-batching server: every job's result is the same
+in the mix as alone (and as the oracle's for small jobs), admission respects
+the HBM budget, and resident jobs really share rounds."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2208_11617_gb300 import inputs
+from paper_2208_11617_gb300 import simplex as sx
+
+pytestmark = pytest.mark.gpu
+SALT = 0x00D16E57
+
+
+def _oracle_digest(grid, n):
+    """Sum over live cells of splitmix32(SALT ^ row-major index on side n + 1)."""
+    m = grid.ndim
+    d = 0
+    for x in np.argwhere(grid):
+        lin = 0
+        for xi in x:
+            lin = lin * (n + 1) + int(xi)
+        d += oracle.splitmix32(SALT ^ (lin & 0xFFFFFFFF))
+    return d % (1 << 64)
+
+
+def _alone(job):
+    """The job on the single-instance path: final digest and live counts."""
+    m, n = job["m"], job["n"]
+    side = (n + 16) // 16 * 16
+    mp = sx.simplex_map_create(m, n, 2, 2, 64 if m == 2 else 16, side=side)
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
+    b = torch.zeros_like(a)
+    sx.simplex_ca_init(mp, a, job["seed"], job["threshold"])
+    live = torch.zeros(job["steps"] + 1, dtype=torch.int64, device="cuda")
+    fin = sx.simplex_ca_run(mp, a, b, job["steps"], job["birth"], job["survive"], live, False)
+    dig = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sx.simplex_ca_digest(mp, fin, dig)
+    torch.cuda.synchronize()
+    return int(dig.item()) & ((1 << 64) - 1), [int(v) for v in live.cpu().tolist()], fin, mp
+
+
+def test_jobs_equal_alone_and_in_the_mix():
+    jobs, t = inputs.serve_trace(rate=4000, seconds=0.08, seed=11, n2=(16, 1500), n3=(8, 200), max_steps=12)
+    assert len(jobs) > 100
+    srv = sx.SimplexServer(hbm_budget=2 << 30, max_jobs=512, max_steps=12)
+    srv.run(jobs, t, realtime=True)
+    st = srv.stats()
+    assert st["completed"] == len(jobs) and st["rejected"] == 0
+    assert st["mean_active"] > 1.5, st          # resident jobs shared rounds
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(len(jobs), size=min(60, len(jobs)), replace=False).tolist())
+    for i, job in enumerate(jobs):
+        res = srv.result(i, job["steps"])
+        assert res["status"] == 2
+        assert res["done_ms"] >= res["arrival_ms"] - 1.0
+        if i not in sample:
+            continue
+        dig, live, fin, mp = _alone(job)
+        assert res["digest"] == dig, f"job {i}"
+        assert res["live"] == live, f"job {i}"
+        if job["n"] <= 120:
+            ref, ref_live = oracle.ca_run(job["m"], job["n"], job["steps"], job["birth"], job["survive"],
+                                          oracle.ca_init(job["m"], job["n"], job["seed"], job["threshold"]))
+            assert [int(v) for v in ref_live] == res["live"]
+            assert _oracle_digest(ref, job["n"]) == res["digest"]
+
+
+def test_budget_limits_resident_memory_and_rejects_oversized_jobs():
+    rule = inputs.B3S23
+    thr = inputs.bernoulli_threshold(0.5)
+    jobs = [dict(m=2, n=2047, steps=6, birth=rule[0], survive=rule[1], seed=k, threshold=thr) for k in range(12)]
+    jobs.append(dict(m=2, n=8191, steps=2, birth=rule[0], survive=rule[1], seed=99, threshold=thr))  # 2 x 64 MiB
+    budget = 40 << 20                                                                                # 40 MiB
+    srv = sx.SimplexServer(hbm_budget=budget, max_jobs=64, max_steps=8)
+    srv.run(jobs, None, realtime=False)
+    st = srv.stats()
+    assert st["completed"] == 12 and st["rejected"] == 1
+    assert st["peak_pool_bytes"] <= budget
+    assert srv.result(12)["status"] == 3
+    for i in (0, 5, 11):
+        dig, live, _, _ = _alone(jobs[i])
+        r = srv.result(i, 6)
+        assert r["digest"] == dig and r["live"] == live
+
+
+def test_server_is_reusable_and_rejects_bad_jobs():
+    srv = sx.SimplexServer(hbm_budget=256 << 20, max_jobs=16, max_steps=4)
+    rule = inputs.B3S23
+    good = [dict(m=2, n=100, steps=3, birth=rule[0], survive=rule[1], seed=1, threshold=1 << 31)]
+    srv.run(good, None, realtime=False)
+    first = srv.result(0, 3)
+    srv.run(good, None, realtime=False)
+    assert srv.result(0, 3) == first
+    with pytest.raises(sx.SimplexError):
+        srv.run([dict(good[0], steps=9)], None, realtime=False)
+    with pytest.raises(sx.SimplexError):
+        srv.run([dict(good[0], m=4)], None, realtime=False)
+    assert sx.simplex_device_status() == 0
