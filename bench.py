@@ -317,7 +317,7 @@ def run_serve(args, rank, world):
 
     seconds = args.serve_seconds
     jobs, t = inputs.serve_trace(seconds=seconds)
-    srv = sx.SimplexServer(hbm_budget=inputs.SERVE_BUDGET, max_jobs=8192, max_steps=64, max_items=1 << 21,
+    srv = sx.SimplexServer(hbm_budget=inputs.SERVE_BUDGET, max_jobs=8192, max_steps=64, max_items=1 << 18,
                            max_inflight=3)
     warm, wt = inputs.serve_trace(seconds=0.05, seed=5)
     srv.run(warm, wt, realtime=True)                  # warm-up trace (not timed)
@@ -358,6 +358,23 @@ def run_serve(args, rank, world):
     svc_all = [svc[k % len(svc)] for k in range(len(jobs))]
     lat = sorted(_fifo_latency(list(t), svc_all))
     q = lambda f: lat[min(len(lat) - 1, int(f * (len(lat) - 1) + 0.5))] * 1e3
+    # capacity: the first jobs of the trace all available at once (no arrival gaps)
+    cap_jobs = jobs[: args.serve_capacity_jobs]
+    t1 = time.perf_counter()
+    srv.run(cap_jobs, None, realtime=False)
+    cap_wall = time.perf_counter() - t1
+    cap = srv.stats()
+    cap_svc = [svc[k % len(svc)] for k in range(len(cap_jobs))]
+    serial_cap_rate = sum(
+        ((d["n"] + 1) * (d["n"] + 2) // 2 if d["m"] == 2 else (d["n"] + 1) * (d["n"] + 2) * (d["n"] + 3) // 6)
+        * d["steps"] for d in cap_jobs) / sum(cap_svc)
+    # heavier load: where the serial path saturates
+    hl_rate = args.serve_high_rate
+    hjobs, ht = inputs.serve_trace(rate=hl_rate, seconds=args.serve_high_seconds, seed=9)
+    srv.run(hjobs, ht, realtime=True)
+    hl = srv.stats()
+    hlat = sorted(_fifo_latency(list(ht), [svc[k % len(svc)] for k in range(len(hjobs))]))
+    hq = lambda f: hlat[min(len(hlat) - 1, int(f * (len(hlat) - 1) + 0.5))] * 1e3
     assert mismatches == 0, f"{mismatches} jobs differ between the server and the single-instance path"
     assert sx.simplex_device_status() == 0
     return dict(
@@ -374,6 +391,15 @@ def run_serve(args, rank, world):
         serial={"cell_updates_per_s": serial_rate, "mean_service_ms": mean_svc * 1e3,
                 "utilisation_at_this_rate": inputs.SERVE_RATE * mean_svc, "p50_ms": q(0.5), "p99_ms": q(0.99),
                 "sample_jobs": len(sample), "digest_mismatches": mismatches},
+        host_issue_ms_per_round=st["host_issue_ms"] / max(1, st["rounds"]),
+        capacity={"jobs": len(cap_jobs), "server_cell_updates_per_s": cap["cell_updates"] / cap_wall,
+                  "serial_cell_updates_per_s": serial_cap_rate, "server_over_serial":
+                      (cap["cell_updates"] / cap_wall) / serial_cap_rate, "mean_resident_jobs": cap["mean_active"]},
+        high_load={"rate_jobs_per_s": hl_rate, "seconds": args.serve_high_seconds, "jobs": len(hjobs),
+                   "server_p50_ms": hl["p50_ms"], "server_p99_ms": hl["p99_ms"],
+                   "server_cell_updates_per_s": hl["cell_updates"] / (hl["wall_ms"] * 1e-3),
+                   "mean_resident_jobs": hl["mean_active"], "serial_utilisation": hl_rate * mean_svc,
+                   "serial_fifo_p50_ms": hq(0.5), "serial_fifo_p99_ms": hq(0.99)},
         roofline=None, clocks=clk, gpu_launches=None,
         e2e={"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     )
@@ -596,6 +622,9 @@ def main():
     ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4", "batch", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=inputs.SERVE_SECONDS, help="serve: trace length")
     ap.add_argument("--serve-sample", type=int, default=400, help="serve: jobs re-run alone for the serial baseline")
+    ap.add_argument("--serve-capacity-jobs", type=int, default=4000, help="serve: jobs of the offline capacity run")
+    ap.add_argument("--serve-high-rate", type=float, default=8000.0, help="serve: arrival rate of the heavy-load run")
+    ap.add_argument("--serve-high-seconds", type=float, default=5.0, help="serve: length of the heavy-load run")
     ap.add_argument("--no-tune", action="store_true", help="batch: untuned tile choices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")

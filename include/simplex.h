@@ -398,6 +398,7 @@ typedef struct simplex_server_stats {
     double wall_ms;          /* from the start of the trace to the last completion seen */
     double mean_active;      /* resident jobs per round */
     double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* latency: done - arrival */
+    double host_issue_ms;    /* host time spent building and issuing rounds */
 } simplex_server_stats_t;
 
 /* Device bytes the server's arena needs for these parameters (tables + pool). */

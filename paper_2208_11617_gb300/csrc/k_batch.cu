@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(kBatchThreads)
     batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items, uint32_t nitems,
                  const CUtensorMap *__restrict__ tmaps, uint8_t *__restrict__ arena, int in_parity,
                  unsigned int *__restrict__ queue, unsigned long long *__restrict__ live, int live_stride,
-                 int live_index, int count_only, unsigned long long *__restrict__ digest)
+                 int live_index, int count_only, unsigned long long *__restrict__ digest,
+                 unsigned int *__restrict__ zero_next)
 {
     extern __shared__ uint8_t dsmem[];
     __shared__ BatchInst si;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kBatchThreads)
         fence_mbar_init();
         s_cur = -1;
         s_next = atomicAdd(queue, 1u);
+        if (zero_next && blockIdx.x == 0) *zero_next = 0u;  // a later pass's counter, idle now
     }
     __syncthreads();
 
@@ -189,25 +191,41 @@ cudaError_t batch_prepare()
     return e;
 }
 
-cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
-                              const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
-                              unsigned long long *live, int live_stride, int live_index, bool count_only,
-                              cudaStream_t st, unsigned long long *digest)
+// Resident CTAs of the persistent launch on the current device (SM count x
+// occupancy), looked up once per device.
+static cudaError_t persistent_grid(uint64_t *out)
 {
-    cudaError_t e = batch_prepare();
-    if (e != cudaSuccess) return e;
+    static uint64_t cached[64] = {};
     int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && cached[dev]) {
+        *out = cached[dev];
+        return cudaSuccess;
+    }
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads,
                                                            kBatchStageBytes + 128)) != cudaSuccess)
         return e;
     if (per_sm < 1) per_sm = 1;
-    uint64_t g = (uint64_t)sms * (uint64_t)per_sm;  // persistent: every CTA resident
+    *out = (uint64_t)sms * (uint64_t)per_sm;
+    if (dev >= 0 && dev < 64) cached[dev] = *out;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
+                              const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
+                              unsigned long long *live, int live_stride, int live_index, bool count_only,
+                              cudaStream_t st, unsigned long long *digest, unsigned int *zero_next)
+{
+    cudaError_t e = batch_prepare();
+    if (e != cudaSuccess) return e;
+    uint64_t g = 0;
+    if ((e = persistent_grid(&g)) != cudaSuccess) return e;  // persistent: every CTA resident
     if (g > nitems) g = nitems ? nitems : 1;
     batch_kernel<<<(unsigned)g, kBatchThreads, kBatchStageBytes + 128, st>>>(
         insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0,
-        digest);
+        digest, zero_next);
     return cudaGetLastError();
 }
 

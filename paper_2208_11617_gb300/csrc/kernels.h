@@ -43,12 +43,15 @@ cudaError_t ca3_prepare(int rho);
 cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
 
 // Batched engine: one persistent pass (count_only: live counts of the input
-// grids; else one automaton step in -> out) over every work item.
+// grids, plus a result digest when `digest` is given; else one automaton step
+// in -> out) over every work item.  `zero_next`, when given, is a work-queue
+// counter of a later pass that this pass sets to zero (it must not be in use).
 cudaError_t batch_prepare();
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
-                              cudaStream_t st, unsigned long long *digest = nullptr);
+                              cudaStream_t st, unsigned long long *digest = nullptr,
+                              unsigned int *zero_next = nullptr);
 cudaError_t batch_read_status(uint32_t *out);
 
 // Device error words of the TMA kernels (bounded waits that gave up).

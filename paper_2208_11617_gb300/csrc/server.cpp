@@ -117,6 +117,11 @@ struct Round {
 
 int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
 
+// Work-queue counters: round r uses counters 2 (r % kQueueRing/2) and the next
+// one (its digest pass); each round's step pass zeroes the pair that round
+// r + 2 will use, so no round needs a memset of its own.
+constexpr int kQueueRing = 16;
+
 }  // namespace
 
 struct simplex_server {
@@ -135,6 +140,9 @@ struct simplex_server {
     std::deque<Round> inflight;
     std::vector<cudaEvent_t> spare_events;
     std::vector<sx::BatchItem> items, fin_items;
+    sx::BatchItem *stage = nullptr;              // pinned ring: (max_inflight + 1) x 2 x max_items
+    uint64_t round_no = 0;                       // selects the work-queue counters of a round
+    double host_round_ms = 0;                    // host time spent issuing rounds
     unsigned long long *host_live = nullptr;     // pinned [max_jobs][max_steps + 1]
     unsigned long long *host_digest = nullptr;   // pinned [max_jobs]
     cudaEvent_t t0 = nullptr;
@@ -158,7 +166,7 @@ uint64_t layout(const simplex_server_params_t &p, simplex_server *s)
     if (s) s->off_items = off;
     off = align_up(off + sizeof(sx::BatchItem) * max_items * 2, 256);  // round items + finishing items
     if (s) s->off_queue = off;
-    off = align_up(off + 256, 256);
+    off = align_up(off + sizeof(unsigned int) * kQueueRing, 256);
     if (s) s->off_live = off;
     off = align_up(off + sizeof(unsigned long long) * slots * (uint64_t)(p.max_steps + 1), 256);
     if (s) s->off_digest = off;
@@ -251,7 +259,17 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
 
 // One round: advance every active job by one step; jobs reaching their step
 // count get a digest pass and their results queued for copy to the host.
+int launch_round_impl(simplex_server *s, cudaStream_t st);
+
 int launch_round(simplex_server *s, cudaStream_t st)
+{
+    const auto t = std::chrono::steady_clock::now();
+    const int rc = launch_round_impl(s, st);
+    s->host_round_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+    return rc;
+}
+
+int launch_round_impl(simplex_server *s, cudaStream_t st)
 {
     s->items.clear();
     s->fin_items.clear();
@@ -288,17 +306,26 @@ int launch_round(simplex_server *s, cudaStream_t st)
     unsigned long long *live = reinterpret_cast<unsigned long long *>(s->arena + s->off_live);
     unsigned long long *dig = reinterpret_cast<unsigned long long *>(s->arena + s->off_digest);
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(items, s->items.data(), sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice,
-                             st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess ||
-        (e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, queue, live,
-                                   s->prm.max_steps + 1, 0, false, st)) != cudaSuccess)
+    const int pair = (int)(s->round_no % (kQueueRing / 2));
+    unsigned int *q = queue + 2 * pair;
+    unsigned int *q_next = queue + 2 * (int)((s->round_no + 2) % (kQueueRing / 2));
+    // stage in pinned memory so the copy runs asynchronously; a ring slot is
+    // rewritten max_inflight + 1 rounds later, when the round that read it has
+    // completed (the run loop never keeps more than max_inflight in flight)
+    sx::BatchItem *stage =
+        s->stage + (s->round_no % (uint64_t)(s->prm.max_inflight + 1)) * 2 * s->max_items;
+    std::memcpy(stage, s->items.data(), sizeof(sx::BatchItem) * s->items.size());
+    if ((e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q, live,
+                                   s->prm.max_steps + 1, 0, false, st, nullptr, q_next)) != cudaSuccess)
         return cuda_fail(e, "launching a serving round");
     if (!s->fin_items.empty()) {
-        if ((e = cudaMemcpyAsync(fitems, s->fin_items.data(), sizeof(sx::BatchItem) * s->fin_items.size(),
+        std::memcpy(stage + s->max_items, s->fin_items.data(), sizeof(sx::BatchItem) * s->fin_items.size());
+        if ((e = cudaMemcpyAsync(fitems, stage + s->max_items, sizeof(sx::BatchItem) * s->fin_items.size(),
                                  cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = sx::launch_batch_pass(insts, fitems, (uint32_t)s->fin_items.size(), tmaps, s->arena, 0, queue + 1,
-                                       nullptr, 0, 0, true, st, dig)) != cudaSuccess)
+            (e = sx::launch_batch_pass(insts, fitems, (uint32_t)s->fin_items.size(), tmaps, s->arena, 0, q + 1,
+                                       nullptr, 0, 0, true, st, dig, q_next + 1)) != cudaSuccess)
             return cuda_fail(e, "launching the digest pass");
         for (int64_t j : r.finishing) {
             const int slot = s->jobs[j].slot;
@@ -327,6 +354,7 @@ int launch_round(simplex_server *s, cudaStream_t st)
     if ((e = cudaEventRecord(r.ev, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     s->inflight.push_back(std::move(r));
     s->rounds += 1;
+    s->round_no += 1;
     return SIMPLEX_OK;
 }
 
@@ -408,9 +436,12 @@ int simplex_server_create(const simplex_server_params_t *params, void *arena, ui
     const size_t row = (size_t)(params->max_steps + 1);
     if ((e = cudaMallocHost(&s->host_live, sizeof(unsigned long long) * row * params->max_jobs)) != cudaSuccess ||
         (e = cudaMallocHost(&s->host_digest, sizeof(unsigned long long) * params->max_jobs)) != cudaSuccess ||
+        (e = cudaMallocHost(&s->stage, sizeof(sx::BatchItem) * 2 * (size_t)params->max_items *
+                                           (size_t)(params->max_inflight + 1))) != cudaSuccess ||
         (e = cudaEventCreate(&s->t0)) != cudaSuccess) {
         if (s->host_live) cudaFreeHost(s->host_live);
         if (s->host_digest) cudaFreeHost(s->host_digest);
+        if (s->stage) cudaFreeHost(s->stage);
         delete s;
         return cuda_fail(e, "allocating the server's pinned result buffers");
     }
@@ -429,6 +460,7 @@ int simplex_server_destroy(simplex_server_t s)
     if (s->t0) cudaEventDestroy(s->t0);
     if (s->host_live) cudaFreeHost(s->host_live);
     if (s->host_digest) cudaFreeHost(s->host_digest);
+    if (s->stage) cudaFreeHost(s->stage);
     delete s;
     return SIMPLEX_OK;
 }
@@ -458,10 +490,14 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
                      [&](int64_t a, int64_t b) { return s->jobs[a].arrival_ms < s->jobs[b].arrival_ms; });
     for (int64_t j : order) s->pending.push_back(j);
     s->rounds = s->cell_updates = s->active_sum = 0;
+    s->host_round_ms = 0;
     s->pool.reset(s->prm.hbm_budget);
     cudaError_t e = sx::batch_prepare();
     if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if ((e = cudaMemsetAsync(s->arena + s->off_queue, 0, sizeof(unsigned int) * kQueueRing, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(e, "resetting the work queue");
+    s->round_no = 0;
     if ((e = cudaEventRecord(s->t0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     s->h0 = std::chrono::steady_clock::now();
     int64_t done = 0;
@@ -539,6 +575,7 @@ int simplex_server_stats(simplex_server_t s, simplex_server_stats_t *out)
     out->wall_ms = s->wall_ms;
     out->mean_active = s->rounds ? (double)s->active_sum / (double)s->rounds : 0.0;
     out->peak_pool_bytes = s->pool.peak();
+    out->host_issue_ms = s->host_round_ms;
     if (!lat.empty()) {
         std::sort(lat.begin(), lat.end());
         auto q = [&](double f) { return lat[std::min(lat.size() - 1, (size_t)(f * (double)(lat.size() - 1) + 0.5))]; };

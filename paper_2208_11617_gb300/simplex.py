@@ -109,7 +109,7 @@ class SimplexServerStats(ctypes.Structure):
                 ("rounds", ctypes.c_uint64), ("cell_updates", ctypes.c_uint64), ("peak_pool_bytes", ctypes.c_uint64),
                 ("wall_ms", ctypes.c_double), ("mean_active", ctypes.c_double), ("p50_ms", ctypes.c_double),
                 ("p90_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("mean_ms", ctypes.c_double)]
+                ("mean_ms", ctypes.c_double), ("host_issue_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -418,7 +418,7 @@ def simplex_ca_digest(mp: SimplexMap, grid: torch.Tensor, digest: torch.Tensor, 
 class SimplexServer:
     """A serving engine over a torch-allocated arena (owns the C handle)."""
 
-    def __init__(self, hbm_budget: int, max_jobs: int = 4096, max_steps: int = 64, max_items: int = 1 << 20,
+    def __init__(self, hbm_budget: int, max_jobs: int = 4096, max_steps: int = 64, max_items: int = 1 << 18,
                  max_inflight: int = 3):
         self.params = SimplexServerParams(hbm_budget, max_jobs, max_steps, max_items, max_inflight)
         need = _u64()
