@@ -81,7 +81,10 @@ __global__ void __launch_bounds__(kBatchThreads)
         fence_mbar_init();
         s_cur = -1;
         s_next = atomicAdd(queue, 1u);
-        if (zero_next && blockIdx.x == 0) *zero_next = 0u;  // a later pass's counter, idle now
+        if (zero_next && blockIdx.x == 0) {  // a later round's pair of counters, idle now
+            zero_next[0] = 0u;
+            zero_next[1] = 0u;
+        }
     }
     __syncthreads();
 

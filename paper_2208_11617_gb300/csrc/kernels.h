@@ -44,8 +44,9 @@ cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
 
 // Batched engine: one persistent pass (count_only: live counts of the input
 // grids, plus a result digest when `digest` is given; else one automaton step
-// in -> out) over every work item.  `zero_next`, when given, is a work-queue
-// counter of a later pass that this pass sets to zero (it must not be in use).
+// in -> out) over every work item.  `zero_next`, when given, points to two
+// work-queue counters of a later round that this pass sets to zero (they must
+// not be in use).
 cudaError_t batch_prepare();
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,

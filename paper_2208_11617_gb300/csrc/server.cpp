@@ -117,9 +117,9 @@ struct Round {
 
 int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
 
-// Work-queue counters: round r uses counters 2 (r % kQueueRing/2) and the next
-// one (its digest pass); each round's step pass zeroes the pair that round
-// r + 2 will use, so no round needs a memset of its own.
+// Work-queue counters: round r uses counters 2 (r % kQueueRing/2) (its step
+// pass) and the next one (its digest pass); each round's step pass zeroes the
+// pair that round r + 2 will use, so no round needs a memset of its own.
 constexpr int kQueueRing = 16;
 
 }  // namespace
@@ -325,7 +325,7 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
         if ((e = cudaMemcpyAsync(fitems, stage + s->max_items, sizeof(sx::BatchItem) * s->fin_items.size(),
                                  cudaMemcpyHostToDevice, st)) != cudaSuccess ||
             (e = sx::launch_batch_pass(insts, fitems, (uint32_t)s->fin_items.size(), tmaps, s->arena, 0, q + 1,
-                                       nullptr, 0, 0, true, st, dig, q_next + 1)) != cudaSuccess)
+                                       nullptr, 0, 0, true, st, dig)) != cudaSuccess)
             return cuda_fail(e, "launching the digest pass");
         for (int64_t j : r.finishing) {
             const int slot = s->jobs[j].slot;
