@@ -357,8 +357,8 @@ int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t gri
  * in a device pool capped by an HBM budget and works in rounds: one round is
  * ONE launch of the batched persistent kernel that advances every resident
  * job by one step, whatever step each is at.  Between rounds it admits
- * arrived jobs first come first served as soon as a job slot and pool memory
- * are free, and retires finished jobs: their live count after every step and
+ * arrived jobs first come first served as soon as a job slot, pool memory and
+ * room in the round's work list (max_items) are free, and retires finished jobs: their live count after every step and
  * a digest of their final grid are copied to host memory and their memory
  * returns to the pool.  A job's result is identical whether it runs alone or
  * among others.  Tiles: m = 2: 128 from n = 1024 up, else 64; m = 3: 16.
@@ -382,7 +382,7 @@ typedef struct simplex_job {
 } simplex_job_t;
 
 typedef struct simplex_job_result {
-    int32_t status;          /* 0 pending, 1 running, 2 done, 3 rejected (larger than the budget) */
+    int32_t status;          /* 0 pending, 1 running, 2 done, 3 rejected (larger than the budget or a round) */
     int32_t steps;
     double arrival_ms;       /* from the trace */
     double admit_ms;         /* host time of admission */
@@ -416,8 +416,9 @@ int simplex_server_destroy(simplex_server_t server);
  * arrives at arrival_s[i] seconds after the call starts (realtime != 0; with
  * realtime = 0 or arrival_s = NULL every job is available at once).  Work is
  * issued on `stream`.  Results and statistics stay queryable until the next
- * run.  Errors: SIMPLEX_EINVAL (a job's parameters), SIMPLEX_ENOMEM (a round
- * larger than max_items), SIMPLEX_ECUDA.
+ * run.  A job whose grids exceed the budget, or whose work list exceeds
+ * max_items, is rejected (status 3) and the others still run.  Errors:
+ * SIMPLEX_EINVAL (a job's parameters), SIMPLEX_ECUDA.
  */
 int simplex_server_run(simplex_server_t server, const simplex_job_t *jobs, const double *arrival_s, int count,
                        int realtime, void *stream);

@@ -108,6 +108,7 @@ struct ServerJob {
     uint64_t digest = 0;
     std::vector<uint64_t> live;
     uint64_t cells = 0;
+    uint64_t items = 0;  // work items per round
 };
 
 struct Round {
@@ -137,6 +138,7 @@ struct simplex_server {
     std::vector<ServerJob> jobs;
     std::deque<int64_t> pending;
     std::vector<int64_t> active;
+    uint64_t active_items = 0;                   // work items of one round over the active jobs
     std::deque<Round> inflight;
     std::vector<cudaEvent_t> spare_events;
     std::vector<sx::BatchItem> items, fin_items;
@@ -207,20 +209,26 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
     for (int d = 0; d < sp.m; ++d) gb *= (uint64_t)side;
     const uint64_t bytes = 2 * align_up(gb, 256);
     if (bytes > s->prm.hbm_budget) return -2;  // can never fit
-    uint64_t off = 0;
-    if (!s->pool.alloc(bytes, &off)) return 0;
-    const int slot = s->free_slots.back();
-    s->free_slots.pop_back();
-    sx::BatchInst &bi = s->slot_inst[slot];
-    std::memset(&bi, 0, sizeof bi);
+    // work items per round: plan first (host only), then check the round budget
+    sx::Plan plan;
     int band = 0;
     if (sp.m == 2) {
         const int64_t nb = (sp.n + block) / block;
         band = 1;
         while (band < 8 && band * 2 <= nb) band *= 2;
     }
-    int rc = build_plan(sp.m, sp.n, 2, 2, block, side, band, &bi.plan);
-    if (rc) return -1;
+    if (build_plan(sp.m, sp.n, 2, 2, block, side, band, &plan)) return -1;
+    const uint64_t nitems = (plan.h_blocks + sx::kBatchChunk - 1) / sx::kBatchChunk;
+    if (nitems > s->max_items) return -2;                   // can never fit in a round
+    if (s->active_items + nitems > s->max_items) return 0;  // wait for the round to shrink
+    uint64_t off = 0;
+    if (!s->pool.alloc(bytes, &off)) return 0;
+    const int slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    sx::BatchInst &bi = s->slot_inst[slot];
+    std::memset(&bi, 0, sizeof bi);
+    bi.plan = plan;
+    int rc;
     bi.rule = make_rule(sp.m, sp.birth, sp.survive);
     bi.body = sp.m == 2 ? (block == 64 ? sx::kBody2x64 : sx::kBody2x128) : sx::kBody3x16;
     bi.tmap = 2 * slot;
@@ -253,6 +261,8 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
     job.step = 0;
     job.parity = 0;
     job.admit_ms = host_ms(s);
+    job.items = nitems;
+    s->active_items += nitems;
     s->active.push_back(j);
     return 1;
 }
@@ -340,8 +350,10 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
         // finishing jobs leave the active set now; their memory is released at retirement
         std::vector<int64_t> still;
         still.reserve(s->active.size());
-        for (int64_t j : s->active)
+        for (int64_t j : s->active) {
             if (s->jobs[j].step < s->jobs[j].spec.steps) still.push_back(j);
+            else s->active_items -= s->jobs[j].items;
+        }
         s->active.swap(still);
     }
     if (s->spare_events.empty()) {
@@ -490,6 +502,7 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
                      [&](int64_t a, int64_t b) { return s->jobs[a].arrival_ms < s->jobs[b].arrival_ms; });
     for (int64_t j : order) s->pending.push_back(j);
     s->rounds = s->cell_updates = s->active_sum = 0;
+    s->active_items = 0;
     s->host_round_ms = 0;
     s->pool.reset(s->prm.hbm_budget);
     cudaError_t e = sx::batch_prepare();
