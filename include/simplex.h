@@ -369,7 +369,8 @@ typedef struct simplex_server_params {
     uint64_t hbm_budget;     /* bytes of the grid pool (both grids of every resident job) */
     int32_t max_jobs;        /* resident job slots */
     int32_t max_steps;       /* largest steps of a job (<= 4095) */
-    int32_t max_items;       /* work items per round (8 blocks each), >= 1024 */
+    int32_t max_items;       /* map blocks of all resident jobs together, >= 1024 (a round's
+                                work items hold 1..8 blocks: fewer when the round is light) */
     int32_t max_inflight;    /* rounds the host may queue ahead of the GPU (1..64) */
 } simplex_server_params_t;
 

@@ -196,7 +196,7 @@ cudaError_t batch_prepare()
 
 // Resident CTAs of the persistent launch on the current device (SM count x
 // occupancy), looked up once per device.
-static cudaError_t persistent_grid(uint64_t *out)
+cudaError_t batch_resident_ctas(uint64_t *out)
 {
     static uint64_t cached[64] = {};
     int dev = 0, sms = 0, per_sm = 0;
@@ -224,7 +224,7 @@ cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, ui
     cudaError_t e = batch_prepare();
     if (e != cudaSuccess) return e;
     uint64_t g = 0;
-    if ((e = persistent_grid(&g)) != cudaSuccess) return e;  // persistent: every CTA resident
+    if ((e = batch_resident_ctas(&g)) != cudaSuccess) return e;  // persistent: every CTA resident
     if (g > nitems) g = nitems ? nitems : 1;
     batch_kernel<<<(unsigned)g, kBatchThreads, kBatchStageBytes + 128, st>>>(
         insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0,

@@ -54,6 +54,8 @@ cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, ui
                               cudaStream_t st, unsigned long long *digest = nullptr,
                               unsigned int *zero_next = nullptr);
 cudaError_t batch_read_status(uint32_t *out);
+// CTAs of the batched kernel resident at once on the current device (SMs x occupancy).
+cudaError_t batch_resident_ctas(uint64_t *out);
 
 // Device error words of the TMA kernels (bounded waits that gave up).
 // Reads and clears; synchronous.

@@ -138,7 +138,8 @@ struct simplex_server {
     std::vector<ServerJob> jobs;
     std::deque<int64_t> pending;
     std::vector<int64_t> active;
-    uint64_t active_items = 0;                   // work items of one round over the active jobs
+    uint64_t active_items = 0;                   // blocks of one round over the active jobs
+    uint64_t ctas = 1216;                        // resident CTAs of a batched launch
     std::deque<Round> inflight;
     std::vector<cudaEvent_t> spare_events;
     std::vector<sx::BatchItem> items, fin_items;
@@ -218,7 +219,7 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
         while (band < 8 && band * 2 <= nb) band *= 2;
     }
     if (build_plan(sp.m, sp.n, 2, 2, block, side, band, &plan)) return -1;
-    const uint64_t nitems = (plan.h_blocks + sx::kBatchChunk - 1) / sx::kBatchChunk;
+    const uint64_t nitems = plan.h_blocks;  // work items at the finest chunk (one block each)
     if (nitems > s->max_items) return -2;                   // can never fit in a round
     if (s->active_items + nitems > s->max_items) return 0;  // wait for the round to shrink
     uint64_t off = 0;
@@ -284,12 +285,19 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     s->items.clear();
     s->fin_items.clear();
     Round r;
+    // blocks per work item: 8 when the round has work for every resident CTA
+    // several times over, fewer (down to 1) when it has not, so that a light
+    // round is spread over more CTAs instead of queueing blocks behind each other
+    uint64_t blocks = 0;
+    for (int64_t j : s->active) blocks += s->slot_inst[s->jobs[j].slot].plan.h_blocks;
+    uint64_t chunk = blocks / (2 * s->ctas + 1);
+    chunk = chunk < 1 ? 1 : (chunk > (uint64_t)sx::kBatchChunk ? (uint64_t)sx::kBatchChunk : chunk);
     for (int64_t j : s->active) {
         ServerJob &job = s->jobs[j];
         const sx::BatchInst &bi = s->slot_inst[job.slot];
         const uint32_t tag = (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1);
-        for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += sx::kBatchChunk) {
-            const uint64_t cnt = std::min<uint64_t>(sx::kBatchChunk, bi.plan.h_blocks - v0);
+        for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += chunk) {
+            const uint64_t cnt = std::min<uint64_t>(chunk, bi.plan.h_blocks - v0);
             s->items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt, tag});
         }
         job.step += 1;
@@ -511,6 +519,7 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "resetting the work queue");
     s->round_no = 0;
+    if ((e = sx::batch_resident_ctas(&s->ctas)) != cudaSuccess) return cuda_fail(e, "occupancy query");
     if ((e = cudaEventRecord(s->t0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     s->h0 = std::chrono::steady_clock::now();
     int64_t done = 0;
