@@ -239,7 +239,7 @@ def run_batch(args, rank, world):
     from paper_2208_11617_gb300 import autotune
     from paper_2208_11617_gb300 import simplex as sx
 
-    base = inputs.batch_instances()
+    base = inputs.batch_instances(n2=args.batch_m2, n3=args.batch_m3)
     t0 = time.perf_counter()
     table = {} if args.no_tune else autotune.tune(base)
     tune_s = time.perf_counter() - t0
@@ -263,7 +263,7 @@ def run_batch(args, rank, world):
     achieved = 2 * cells / (step_ms * 1e-3) / 1e9
     # baseline: the single-instance path looped over the instances (each a graph of 16 steps)
     maps = []
-    for d in insts:
+    for d in ([] if args.no_loop else insts):
         side = (d["n"] + 16) // 16 * 16
         mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], d["block"], side=side)
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
@@ -275,8 +275,8 @@ def run_batch(args, rank, world):
         for mp, a, bb, d in maps:
             sx.simplex_ca_run(mp, a, bb, steps, d["birth"], d["survive"], None, True)
 
-    secs_loop = _time_region(loop, 1, 1, world)
-    value_loop, _ = aggregate(cells * steps, secs_loop, world)
+    secs_loop = _time_region(loop, 1, 1, world) if maps else float("nan")
+    value_loop = aggregate(cells * steps, secs_loop, world)[0] if maps else float("nan")
     assert sx.simplex_device_status() == 0
     return dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -626,6 +626,9 @@ def main():
     ap.add_argument("--serve-high-rate", type=float, default=8000.0, help="serve: arrival rate of the heavy-load run")
     ap.add_argument("--serve-high-seconds", type=float, default=5.0, help="serve: length of the heavy-load run")
     ap.add_argument("--no-tune", action="store_true", help="batch: untuned tile choices")
+    ap.add_argument("--no-loop", action="store_true", help="batch: skip the single-instance loop baseline")
+    ap.add_argument("--batch-m2", type=int, default=2048, help="batch: number of m = 2 instances")
+    ap.add_argument("--batch-m3", type=int, default=256, help="batch: number of m = 3 instances")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
