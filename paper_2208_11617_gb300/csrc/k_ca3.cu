@@ -32,7 +32,6 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<
                     const Rule rule, int kind, uint64_t nblocks, unsigned long long *__restrict__ live)
 {
     constexpr int TX = RHO / 16;
-    constexpr int T = (RHO / 16) * RHO * (RHO / RZ);
     constexpr int BW = RHO + 32, BH = RHO + 2, BD = RHO + 2;
     constexpr uint32_t kBoxBytes = BW * BH * BD;
     extern __shared__ uint8_t dsmem[];
@@ -73,11 +72,7 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<
             return;
         }
 
-        if constexpr (RHO == 32)
-            my_live += ca3_tile32<RHO * RHO / T, ORK>(tile, p.n, p.side, rule, out, x0, y0, z0, partial,
-                                                         tid % RHO, tid / RHO);
-        else
-            my_live += ca3_tile<RHO, RZ, ORK>(tile, p.n, p.side, rule, out, x0, y0, z0, partial, tx, ty, tz);
+        my_live += ca3_tile<RHO, RZ, ORK>(tile, p.n, p.side, rule, out, x0, y0, z0, partial, tx, ty, tz);
         __syncthreads();
     }
     if (live) block_add_u64(live, my_live, red);
@@ -160,12 +155,8 @@ __global__ void __launch_bounds__(T, 1)
             }
             return;
         }
-        if constexpr (RHO == 32)
-            my_live += ca3_tile32<RHO * RHO / T, ORK>(base + s * C::kStage, p.n, p.side, rule, out, inf.x, inf.y,
-                                                       inf.z, (inf.w & 2) != 0, tid % RHO, tid / RHO);
-        else
-            my_live += ca3_tile<RHO, C::RZ, ORK>(base + s * C::kStage, p.n, p.side, rule, out, inf.x, inf.y, inf.z,
-                                                  (inf.w & 2) != 0, tx, ty, tz);
+        my_live += ca3_tile<RHO, C::RZ, ORK>(base + s * C::kStage, p.n, p.side, rule, out, inf.x, inf.y, inf.z,
+                                              (inf.w & 2) != 0, tx, ty, tz);
         __syncthreads();  // stage s fully read
         if (tid == 0) produce(s);
     }
