@@ -5,14 +5,15 @@
 // block decodes its tile with H (Sec. 4.3 packing with the hinge, or the
 // generic beta = 3 cubes) or the bounding box, stages the tile plus a one-cell
 // halo with a single 3-D TMA tiled load of (RHO + 32) x (RHO + 2) x (RHO + 2)
-// bytes, and each thread walks RZ planes along x1 for one (x2, 16-byte x3
-// chunk) column: per plane it forms the 3 x 3 sums P = h(x2-1) + h(x2) +
-// h(x2+1) of horizontal 3-sums, and the Moore-26 sum of three consecutive
-// planes, all byte-parallel in 32-bit registers.
+// bytes, and its threads walk the planes along x1 keeping 3 x 3 column sums of
+// the staged rows in registers: the Moore-26 sum of a cell is one horizontal
+// 3-sum over the column sums of three consecutive planes, all byte-parallel in
+// 32-bit registers.
 //
 // For RHO = 32 the staged rows are 64 bytes and the tensor map uses the 64-byte
-// swizzle: 16-byte chunk c of staged row r sits at chunk c ^ ((r >> 1) & 3),
-// which spreads the rows a warp reads at once over all shared-memory banks.
+// swizzle (16-byte unit u of staged row R sits at u ^ ((R >> 1) & 3)); each
+// thread owns two output rows (ca3_tile32) and the lanes of one 16-byte load
+// instruction spread over all shared-memory banks.
 #include "ca_tiles.cuh"
 #include "common.cuh"
 #include "hmap.cuh"
@@ -26,18 +27,33 @@ static __device__ uint32_t g_ca3_status;
 template <int RHO>
 constexpr int ca3_min_blocks() { return RHO == 32 ? 3 : 12; }
 
+// Threads per tile: RHO = 32 -- 32 lanes (2 chunks x 16 row pairs) per run of
+// RZ planes; RHO = 16 -- one thread per (chunk, row, run of RZ planes).
+// Planes per thread run for 32^3 tiles in the grid form (128 threads per tile
+// at 8, 256 at 4).
+constexpr int kCa3Rz32 = 8;
+
+template <int RHO, int RZ>
+constexpr int ca3_threads() { return RHO == 32 ? 32 * (RHO / RZ) : (RHO / 16) * RHO * (RHO / RZ); }
+
+// Staged box bytes and the alignment its swizzle needs.
+template <int RHO>
+__host__ __device__ constexpr uint32_t ca3_box_bytes() { return (RHO + 32) * (RHO + 2) * (RHO + 2); }
+template <int RHO>
+__host__ __device__ constexpr int ca3_box_align() { return RHO == 32 ? 512 : 128; }
+
 template <int RHO, int RZ, bool ORK>
-__global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<RHO>())
+__global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
     ca3_step_kernel(const __grid_constant__ CUtensorMap tin, uint8_t *__restrict__ out, const Plan p,
                     const Rule rule, int kind, uint64_t nblocks, unsigned long long *__restrict__ live)
 {
     constexpr int TX = RHO / 16;
-    constexpr int BW = RHO + 32, BH = RHO + 2, BD = RHO + 2;
-    constexpr uint32_t kBoxBytes = BW * BH * BD;
+    constexpr uint32_t kBoxBytes = ca3_box_bytes<RHO>();
+    constexpr uintptr_t kAlign = ca3_box_align<RHO>();
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t red[32];
-    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 511) & ~uintptr_t(511));
+    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + kAlign - 1) & ~(kAlign - 1));
 
     const int tid = threadIdx.x;
     const int tx = tid % TX;
@@ -72,7 +88,11 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<
             return;
         }
 
-        my_live += ca3_tile<RHO, RZ, ORK>(tile, p.n, p.side, rule, out, x0, y0, z0, partial, tx, ty, tz);
+        if constexpr (RHO == 32)
+            my_live += ca3_tile32<RZ, ORK>(tile, p.n, p.side, rule, out, x0, y0, z0, partial, tid & 1, (tid >> 1) & 15,
+                                           tid >> 5);
+        else
+            my_live += ca3_tile<RHO, RZ, ORK>(tile, p.n, p.side, rule, out, x0, y0, z0, partial, tx, ty, tz);
         __syncthreads();
     }
     if (live) block_add_u64(live, my_live, red);
@@ -86,10 +106,10 @@ __global__ void __launch_bounds__((RHO / 16) * RHO * (RHO / RZ), ca3_min_blocks<
 // instead of every CTA waiting for its own load.
 template <int RHO, int T>
 struct Ca3Persist {
-    static constexpr int TX = RHO / 16;
-    static constexpr int ZS = T / (TX * RHO);  // plane segments per tile
+    static_assert(RHO == 32, "the persistent form stages 32^3 tiles");
+    static constexpr int ZS = T / 32;  // plane runs per tile (32 lanes each)
     static constexpr int RZ = RHO / ZS;
-    static constexpr uint32_t kBox = (RHO + 32) * (RHO + 2) * (RHO + 2);
+    static constexpr uint32_t kBox = ca3_box_bytes<RHO>();
     static constexpr uint32_t kStage = (kBox + 511u) & ~511u;
     static constexpr int S = (3 * kStage + 512 <= 227 * 1024) ? 3 : 2;
     static constexpr int kSmem = S * kStage + 512;
@@ -108,7 +128,6 @@ __global__ void __launch_bounds__(T, 1)
     __shared__ uint32_t red[32];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 511) & ~uintptr_t(511));
     const int tid = threadIdx.x;
-    const int tx = tid % C::TX, ty = (tid / C::TX) % RHO, tz = tid / (C::TX * RHO);
     uint64_t vnext = blockIdx.x;  // producer state (thread 0)
     uint32_t my_live = 0;
 
@@ -155,8 +174,8 @@ __global__ void __launch_bounds__(T, 1)
             }
             return;
         }
-        my_live += ca3_tile<RHO, C::RZ, ORK>(base + s * C::kStage, p.n, p.side, rule, out, inf.x, inf.y, inf.z,
-                                              (inf.w & 2) != 0, tx, ty, tz);
+        my_live += ca3_tile32<C::RZ, ORK>(base + s * C::kStage, p.n, p.side, rule, out, inf.x, inf.y, inf.z,
+                                           (inf.w & 2) != 0, tid & 1, (tid >> 1) & 15, tid >> 5);
         __syncthreads();  // stage s fully read
         if (tid == 0) produce(s);
     }
@@ -166,12 +185,12 @@ __global__ void __launch_bounds__(T, 1)
 bool ca3_supports(int rho) { return rho == 16 || rho == 32; }
 
 // The 64-byte swizzle the tensor map must use for this tile side (see above).
-bool ca3_swizzled(int rho) { return rho + 32 == 64; }
+bool ca3_swizzled(int rho) { return rho == 32; }
 
 template <int RHO, int RZ, bool ORK>
 static cudaError_t prepare_one()
 {
-    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 512;
+    constexpr int smem = ca3_box_bytes<RHO>() + ca3_box_align<RHO>();
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -193,8 +212,8 @@ template <int RHO, int RZ>
 static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
                             unsigned long long *live, cudaStream_t st)
 {
-    constexpr int T = (RHO / 16) * RHO * (RHO / RZ);
-    constexpr int smem = (RHO + 32) * (RHO + 2) * (RHO + 2) + 512;
+    constexpr int T = ca3_threads<RHO, RZ>();
+    constexpr int smem = ca3_box_bytes<RHO>() + ca3_box_align<RHO>();
     cudaError_t e = prepare_t<RHO, RZ>();
     if (e != cudaSuccess) return e;
     const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
@@ -206,7 +225,7 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     return cudaGetLastError();
 }
 
-constexpr int kCa3PersistThreads = 512;
+constexpr int kCa3PersistThreads = 256;
 
 template <bool ORK>
 static cudaError_t prepare_persist_one()
@@ -250,7 +269,7 @@ cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     if (p.persistent && p.rho == 32) return launch_persist(p, tin, out, rule, kind, live, st);
     switch (p.rho) {
     case 16: return launch_t<16, 4>(p, tin, out, rule, kind, live, st);
-    case 32: return launch_t<32, 8>(p, tin, out, rule, kind, live, st);
+    case 32: return launch_t<32, kCa3Rz32>(p, tin, out, rule, kind, live, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -264,7 +283,7 @@ cudaError_t ca3_prepare(int rho)
     }
     switch (rho) {
     case 16: return prepare_t<16, 4>();
-    case 32: return prepare_t<32, 8>();
+    case 32: return prepare_t<32, kCa3Rz32>();
     default: return cudaErrorInvalidValue;
     }
 }
