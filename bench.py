@@ -196,6 +196,8 @@ def _map_name(info):
         return f"H, trapezoid bands of {info['band']} tile rows (r=1/2, beta=2)"
     if info["m"] == 2:
         return "H, single Eq. map2d grid (r=1/2, beta=2)"
+    if info.get("launch") == 2:
+        return "x-stream: H2 (Eq. map2d) over the tile columns, runs of up to 16 tiles along x3"
     return f"H (r=1/{info['r_inv']}, beta={info['beta']})"
 
 
@@ -446,8 +448,7 @@ def run_ours(args, rank, world, local):
             lambda: sx.simplex_ca_step(mp, a, nxt, birth, survive, None, sx.SIMPLEX_MODE_BB), 20)[0]
         alg_bytes = 2 * cells
         achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
-        kname = (f"ca{wl.m}_step_persistent<{wl.block}>" if info["launch"] == 2
-                 else f"ca{wl.m}_step_kernel<{wl.block}>")
+        kname = ("ca3_step_stream" if info["launch"] == 2 else f"ca{wl.m}_step_kernel<{wl.block}>")
         res.update(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,

@@ -71,6 +71,8 @@ uint64_t binom(uint64_t n, int k)
 
 // Trapezoid band height (tiles) the automatic plan uses for m = 2.
 constexpr int kDefaultBand = 8;
+// m = 3 x-stream form: tiles per run along x3 (a run reads 2 extra x-columns)
+constexpr int kStreamRun = 16;
 
 struct GraphEntry {
     uint8_t *a, *b;
@@ -89,6 +91,9 @@ struct simplex_map {
     int device = -1;
     cudaStream_t capture = nullptr;
     std::vector<GraphEntry> graphs;
+    // m = 3 x-stream form: work counter and CTAs-done counter (zero between launches)
+    unsigned long long *queue = nullptr;
+    int queue_device = -1;
 };
 
 namespace sxh {
@@ -131,6 +136,7 @@ int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, i
     p->n = n;
     p->side = side;
     p->bb_blocks = ipow((uint64_t)N, m);
+    p->seg_len = (int32_t)(N < kStreamRun ? N : kStreamRun);
     const uint64_t h2 = sx::h2_cover_blocks((int32_t)N);
     if (m != 2 && band > 0)
         return fail(SIMPLEX_EINVAL, "band (trapezoid height) applies to m = 2 only (got %d for m = %d)", band, m);
@@ -205,7 +211,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 // Tensor map over a uint8 grid: extent n + 1 along every axis (cells past the
 // domain's bounding box read as zero), row pitch `side`, box of the tile plus
-// its halo: (rho + 32) x (rho + 2) [x (rho + 2)].
+// its halo: (rho + 32) x (rho + 2) [x (rho + 2)], or for the m = 3 x-stream
+// form one x-column rho x (rho + 2) x (rho + 2).
 int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
 {
     auto fn = encode_fn();
@@ -215,11 +222,13 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
     for (int i = 0; i < p.m; ++i) dims[i] = (cuuint64_t)(p.n + 1);
     strides[0] = (cuuint64_t)p.side;
     if (p.m == 3) strides[1] = (cuuint64_t)(p.side * p.side);
-    box[0] = (cuuint32_t)(p.rho + 32);
+    // the m = 3 x-stream form stages x-columns of the tile's own width
+    const bool xcols = p.m == 3 && p.persistent;
+    box[0] = (cuuint32_t)(xcols ? p.rho : p.rho + 32);
     box[1] = (cuuint32_t)(p.rho + 2);
     box[2] = (cuuint32_t)(p.rho + 2);
-    const CUtensorMapSwizzle swz =
-        (p.m == 3 && sx::ca3_swizzled(p.rho)) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE;
+    const CUtensorMapSwizzle swz = (p.m == 3 && !xcols && sx::ca3_swizzled(p.rho)) ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                                                  : CU_TENSOR_MAP_SWIZZLE_NONE;
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, (cuuint32_t)p.m, const_cast<void *>(base), dims, strides, box,
                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -256,15 +265,41 @@ int check_ca_layout(const sx::Plan &p, const void *grid, const char *name)
     return SIMPLEX_OK;
 }
 
+// The x-stream form's work counters: allocated (zeroed) on first use on the
+// current device; not during stream capture (simplex_ca_run calls this first).
+int ensure_queue(simplex_map_t map)
+{
+    if (!(map->plan.m == 3 && map->plan.persistent)) return SIMPLEX_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (map->queue) {
+        if (map->queue_device != dev)
+            return fail(SIMPLEX_EINVAL, "the map's work counters live on device %d, not %d", map->queue_device, dev);
+        return SIMPLEX_OK;
+    }
+    void *q = nullptr;
+    if ((e = cudaMalloc(&q, 2 * sizeof(unsigned long long))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(work counters)");
+    if ((e = cudaMemset(q, 0, 2 * sizeof(unsigned long long))) != cudaSuccess) {
+        cudaFree(q);
+        return cuda_fail(e, "cudaMemset(work counters)");
+    }
+    map->queue = static_cast<unsigned long long *>(q);
+    map->queue_device = dev;
+    return SIMPLEX_OK;
+}
+
 int step_once(simplex_map_t map, const uint8_t *in, uint8_t *out, const sx::Rule &rule,
               unsigned long long *live, int mode, cudaStream_t st)
 {
     const sx::Plan &p = map->plan;
+    int rc = ensure_queue(map);
+    if (rc) return rc;
     CUtensorMap tm;
-    int rc = make_tensor_map(p, in, &tm);
+    rc = make_tensor_map(p, in, &tm);
     if (rc) return rc;
     cudaError_t e = p.m == 2 ? sx::launch_ca2_step(p, tm, out, rule, mode, live, st)
-                             : sx::launch_ca3_step(p, tm, out, rule, mode, live, st);
+                             : sx::launch_ca3_step(p, tm, out, rule, mode, live, map->queue, st);
     if (e != cudaSuccess) return cuda_fail(e, "automaton step launch");
     return SIMPLEX_OK;
 }
@@ -352,6 +387,7 @@ int simplex_map_destroy(simplex_map_t map)
     if (!map) return SIMPLEX_OK;
     for (auto &g : map->graphs) cudaGraphExecDestroy(g.exec);
     if (map->capture) cudaStreamDestroy(map->capture);
+    if (map->queue) cudaFree(map->queue);
     delete map;
     return SIMPLEX_OK;
 }
@@ -464,6 +500,7 @@ int simplex_ca_run(simplex_map_t map, uint8_t *a, uint8_t *b, int steps, uint32_
     }
     e = map->plan.m == 2 ? sx::ca2_prepare(map->plan.rho) : sx::ca3_prepare(map->plan.rho);
     if (e != cudaSuccess) return cuda_fail(e, "setting the kernel shared-memory limit");
+    if ((rc = ensure_queue(map))) return rc;
     cudaGraphExec_t exec = nullptr;
     for (auto &g : map->graphs)
         if (g.a == a && g.b == b && g.steps == steps && g.birth == birth && g.survive == survive && g.live == live &&

@@ -264,4 +264,108 @@ __device__ __forceinline__ uint32_t ca3_tile32(const uint8_t *tile, int64_t n, i
     return byte_sum(lacc);
 }
 
+// m = 3, 32^3 tiles of the x-stream form: the tile's own x-column M and its
+// neighbours L (x3 - 32) and R (x3 + 32) are staged separately, 32 x 34 x 34
+// bytes each, unswizzled (row R = zz * 34 + yy at byte 32 R; x1 = z0 + zz - 1,
+// x2 = y0 + yy - 1, x3 = x0 ... x0 + 31 for M).  The thread layout and sums
+// are those of ca3_tile32; the halo word of lane tx = 0 is the last word of
+// the L row, of tx = 1 the first word of the R row (0 where has_l / has_r
+// is false: the neighbour column lies before x3 = 0 or past the domain).
+// Lanes whose row-pair index p has bit 1 set read their rows in reverse
+// order: with 32-byte rows that puts the lanes of each 16-byte load on all 8
+// bank groups.  Returns the live cells it wrote.
+template <int RZ, bool ORK>
+__device__ __forceinline__ uint32_t ca3_tile32c(const uint8_t *M, const uint8_t *L, const uint8_t *R, bool has_l,
+                                                bool has_r, int64_t n, int64_t side, const Rule &rule,
+                                                uint8_t *__restrict__ out, int64_t x0, int64_t y0, int64_t z0,
+                                                bool partial, int tx, int p, int tz)
+{
+    constexpr int kRow = 32, kPlane = 34 * kRow;
+    const int zb = tz * RZ;
+    const int rev = (p >> 1) & 1;
+    const uint8_t *hcol = tx ? R : L;
+    const bool has_h = tx ? has_r : has_l;
+    const int hoff = tx ? 0 : 28;
+    int ro[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ro[k] = zb * kPlane + (2 * p + (k ^ (3 * rev))) * kRow;
+    const int64_t xc = x0 + 16 * tx;
+    const int64_t x2f = y0 + 2 * p + rev;      // output row of the first result
+    const int64_t x2s = y0 + 2 * p + 1 - rev;  // and of the second
+
+    auto load_plane = [&](int j, uint32_t cf[5], uint32_t cs[5], uint32_t mf[4], uint32_t ms[4]) {
+        uint32_t v[4][4], h[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int o = ro[k] + j * kPlane;
+            const uint4 w = *reinterpret_cast<const uint4 *>(M + o + 16 * tx);
+            v[k][0] = w.x;
+            v[k][1] = w.y;
+            v[k][2] = w.z;
+            v[k][3] = w.w;
+            h[k] = has_h ? *reinterpret_cast<const uint32_t *>(hcol + o + hoff) : 0u;
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            cf[w] = v[0][w] + v[1][w] + v[2][w];
+            cs[w] = v[1][w] + v[2][w] + v[3][w];
+            mf[w] = v[1][w];
+            ms[w] = v[2][w];
+        }
+        cf[4] = h[0] + h[1] + h[2];
+        cs[4] = h[1] + h[2] + h[3];
+    };
+    auto row_next = [&](const uint32_t v[5], const uint32_t alive[4], uint32_t nw[4]) {
+        const uint32_t send = tx ? v[0] : v[3];
+        const uint32_t got = __shfl_xor_sync(0xffffffffu, send, 1);
+        uint32_t sum[4];
+        hsum4(v, tx ? got : v[4], tx ? v[4] : got, sum);
+        next_state4<ORK>(sum, alive, rule, nw);
+    };
+    auto put_row = [&](uint8_t *dst, int64_t cnt64, uint32_t nw[4]) {
+        if (partial) {
+            const int cnt = (int)(cnt64 < 0 ? 0 : (cnt64 > 16 ? 16 : cnt64));
+#pragma unroll
+            for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(cnt, w);
+            if (cnt > 0) store16(dst, nw);
+        } else {
+            store16(dst, nw);
+        }
+    };
+
+    uint32_t pf[5], ps[5], qf[5], qs[5], af[4], as[4], tmp[4], lacc = 0;
+    load_plane(0, pf, ps, tmp, tmp);
+    load_plane(1, qf, qs, af, as);
+#pragma unroll
+    for (int i = 0; i < RZ; ++i) {
+        uint32_t nf[5], ns[5], mf[4], ms[4], vf[5], vs[5], wf[4], ws[4];
+        load_plane(i + 2, nf, ns, mf, ms);
+#pragma unroll
+        for (int w = 0; w < 5; ++w) {
+            vf[w] = pf[w] + qf[w] + nf[w];
+            vs[w] = ps[w] + qs[w] + ns[w];
+        }
+        row_next(vf, af, wf);
+        row_next(vs, as, ws);
+        const int64_t x1 = z0 + zb + i;
+        const int64_t rem = n - x1 - xc + 1;
+        put_row(out + (x1 * side + x2f) * side + xc, rem - x2f, wf);
+        put_row(out + (x1 * side + x2s) * side + xc, rem - x2s, ws);
+        lacc += (wf[0] + wf[1]) + (wf[2] + wf[3]) + (ws[0] + ws[1]) + (ws[2] + ws[3]);
+#pragma unroll
+        for (int w = 0; w < 5; ++w) {
+            pf[w] = qf[w];
+            ps[w] = qs[w];
+            qf[w] = nf[w];
+            qs[w] = ns[w];
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            af[w] = mf[w];
+            as[w] = ms[w];
+        }
+    }
+    return byte_sum(lacc);
+}
+
 }  // namespace sx

@@ -63,8 +63,9 @@ struct Plan {
     int32_t band, log_band;
     int32_t Ne, nbands;
     // automaton launch form: 0 = one CTA per block of the map (the paper's
-    // execution model), 1 = persistent CTAs walking the map's blocks
-    int32_t persistent, pad_;
+    // execution model), 1 = persistent CTAs streaming runs of tiles along the
+    // fastest axis (m = 3, see xrun_decode); seg_len = tiles per run
+    int32_t persistent, seg_len;
     uint64_t h_blocks;   // CUDA blocks of one H launch
     uint64_t bb_blocks;  // N^m
     // H3 (beta = 2): region sizes
@@ -119,6 +120,42 @@ SX_HD bool h2_cover(uint64_t v, int32_t N, int32_t logN, int32_t *X)
     X[0] = d;
     X[1] = N - 1 - d;
     return true;
+}
+
+// x-stream form (m = 3).  Work unit w names a run of at most seg_len tiles
+// along the fastest axis X3 in one tile column (X1, X2): the column comes from
+// H2 plus its diagonal over the triangle X1 + X2 <= N - 1 (kMapH, the 2-D map
+// of Thm. 1 applied to the columns) or from the N x N square of columns
+// (kMapBB); run s of a column holds X3 = s * seg_len ... up to the last tile
+// with a simplex cell, rho * (X1 + X2 + X3) <= n.
+struct XRun {
+    int32_t X1, X2, a, b;  // tiles X3 = a ... b
+};
+
+SX_HD uint64_t xrun_units(const Plan &p, int kind)
+{
+    const uint64_t cols = kind == kMapBB ? (uint64_t)p.N * (uint64_t)p.N : h2_cover_blocks(p.N);
+    return cols * (uint64_t)(p.N / p.seg_len);
+}
+
+SX_HD bool xrun_decode(const Plan &p, int kind, uint64_t w, XRun &r)
+{
+    const uint32_t segs = (uint32_t)(p.N / p.seg_len);
+    const uint64_t col = w / segs;
+    const int32_t s = (int32_t)(w - col * segs);
+    int32_t Y[2];
+    if (kind == kMapBB) {
+        Y[0] = (int32_t)(col >> p.logN);
+        Y[1] = (int32_t)(col & (uint64_t)(p.N - 1));
+    } else {
+        h2_cover(col, p.N, p.logN, Y);
+    }
+    const int64_t last = (p.n >> p.log_rho) - Y[0] - Y[1];
+    r.X1 = Y[0];
+    r.X2 = Y[1];
+    r.a = s * p.seg_len;
+    r.b = (int32_t)(last < (int64_t)(r.a + p.seg_len - 1) ? last : (int64_t)(r.a + p.seg_len - 1));
+    return last >= (int64_t)r.a;
 }
 
 // Blocks before band k of the trapezoid form: sum over j < k of

@@ -99,85 +99,148 @@ __global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
 }
 
 // ---------------------------------------------------------------------------
-// Persistent form: one CTA per SM walks the map's blocks v = blockIdx.x,
-// blockIdx.x + gridDim.x, ... (the same H or bounding-box decode) through a
-// ring of S shared-memory stages.  Thread 0 keeps S - 1 TMA loads in flight
-// ahead of the tile the CTA is computing, so loads and compute overlap
-// instead of every CTA waiting for its own load.
-template <int RHO, int T>
-struct Ca3Persist {
-    static_assert(RHO == 32, "the persistent form stages 32^3 tiles");
-    static constexpr int ZS = T / 32;  // plane runs per tile (32 lanes each)
-    static constexpr int RZ = RHO / ZS;
-    static constexpr uint32_t kBox = ca3_box_bytes<RHO>();
-    static constexpr uint32_t kStage = (kBox + 511u) & ~511u;
-    static constexpr int S = (3 * kStage + 512 <= 227 * 1024) ? 3 : 2;
-    static constexpr int kSmem = S * kStage + 512;
-};
+// x-stream form (32^3 tiles): one CTA per SM takes work units from a device
+// counter; unit w is a run of up to seg_len tiles along x3 in one tile column
+// (xrun_decode: H2 over the triangle of columns, or the bounding square).  A
+// run of tiles X3 = a ... b needs the x-columns a - 1 ... b + 1 (32 x 34 x 34
+// bytes each: the tile's cells plus the x1/x2 halo), so every column is read
+// once per run instead of each tile reading a box with 16-byte x halos on both
+// sides (3 sectors of 32 bytes per 32-byte row).
+//
+// Warp 8 (one lane) is the producer: it fetches units, and TMA-loads their
+// columns in order into a ring of kStreamSlots stages, writing the run into
+// the stage's meta entry first (full[s] counts the bytes; empty[s] takes one
+// arrival per consumer warp when the stage may be refilled).  After the last
+// unit it publishes an end marker (a > b) with a plain arrival.  Warps 0-7
+// are the consumers: column c of the sequence is the centre of one tile, with
+// c - 1 and c + 1 its neighbours; after a tile they release its left column,
+// after a run's last tile the last two.  Every wait is bounded; a timeout sets
+// the status word and an abort flag that stops both sides, and the producer
+// then waits (bounded) for the loads it issued before the CTA exits.  The
+// last CTA to finish puts the work counter back to zero for the next launch.
+constexpr int kStreamSlots = 6;
+constexpr int kStreamConsumers = 256;  // 2 chunks x 16 row pairs x 8 runs of 4 planes
+constexpr int kStreamThreads = kStreamConsumers + 32;
+constexpr uint32_t kColBytes = 32u * 34u * 34u;  // 36,992 = 289 x 128
+constexpr int kStreamSmem = kStreamSlots * (int)kColBytes + 128;
 
-template <int RHO, int T, bool ORK>
-__global__ void __launch_bounds__(T, 1)
-    ca3_step_persistent(const __grid_constant__ CUtensorMap tin, uint8_t *__restrict__ out, const Plan p,
-                        const Rule rule, int kind, uint64_t nblocks, unsigned long long *__restrict__ live)
+template <bool ORK>
+__global__ void __launch_bounds__(kStreamThreads, 1)
+    ca3_step_stream(const __grid_constant__ CUtensorMap tcol, uint8_t *__restrict__ out, const Plan p,
+                    const Rule rule, int kind, uint64_t units, unsigned long long *__restrict__ live,
+                    unsigned long long *__restrict__ queue)
 {
-    using C = Ca3Persist<RHO, T>;
-    constexpr int S = C::S;
+    constexpr int S = kStreamSlots;
     extern __shared__ uint8_t dsmem[];
-    __shared__ __align__(8) uint64_t full[S];
-    __shared__ int4 info[S];  // x0, y0, z0 of the staged tile; w: 1 = valid, 2 = partial
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ int4 meta[S];  // run of the staged column: X1, X2, a, b (a > b: no more work)
     __shared__ uint32_t red[32];
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 511) & ~uintptr_t(511));
-    const int tid = threadIdx.x;
-    uint64_t vnext = blockIdx.x;  // producer state (thread 0)
+    __shared__ volatile int abort_flag;
+    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint32_t my_live = 0;
-
-    // thread 0: find the next block with a tile and start its load into stage s
-    auto produce = [&](int s) {
-        while (vnext < nblocks) {
-            const uint64_t v = vnext;
-            vnext += gridDim.x;
-            int32_t X[3];
-            if (!decode<3>(p, kind, v, X)) continue;
-            const int64_t z0 = (int64_t)X[0] * RHO, y0 = (int64_t)X[1] * RHO, x0 = (int64_t)X[2] * RHO;
-            if (z0 + y0 + x0 > p.n) continue;
-            const bool partial = z0 + y0 + x0 + 3 * (RHO - 1) > p.n;
-            info[s] = make_int4((int)x0, (int)y0, (int)z0, 1 | (partial ? 2 : 0));
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&full[s], C::kBox);
-            tma_load_3d(base + s * C::kStage, &tin, (int32_t)(x0 - 16), (int32_t)(y0 - 1), (int32_t)(z0 - 1),
-                        &full[s]);
-            return;
-        }
-        info[s] = make_int4(0, 0, 0, 0);
-    };
-
+    uint64_t issued = 0;  // producer: columns loaded
     if (tid == 0) {
-        prefetch_tmap(&tin);
-        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        prefetch_tmap(&tcol);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kStreamConsumers / 32);
+        }
         fence_mbar_init();
-        for (int s = 0; s < S; ++s) produce(s);
+        abort_flag = 0;
     }
     __syncthreads();
 
-    for (int k = 0;; ++k) {
-        const int s = k % S;
-        const int4 inf = info[s];
-        if (!(inf.w & 1)) break;  // the producer ran out of tiles (uniform)
-        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1), kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(&g_ca3_status, 1u);
-                // wait (bounded) for every load still in flight before leaving
-                for (int j = 0; j < S; ++j)
-                    if (info[(k + j) % S].w & 1)
-                        mbar_wait_bounded(&full[(k + j) % S], (uint32_t)(((k + j) / S) & 1), kWaitLimitNs);
+    if (warp == kStreamConsumers / 32) {
+        // producer
+        if (lane == 0) {
+            uint64_t seq = 0;
+            // stage for sequence number seq, once the consumers released its last use
+            auto acquire = [&](int &s) {
+                s = (int)(seq % S);
+                if (seq < (uint64_t)S) return true;
+                return mbar_wait_bounded(&empty[s], (uint32_t)((seq / S - 1) & 1), kWaitLimitNs);
+            };
+            bool ok = true;
+            while (ok) {
+                const uint64_t w = atomicAdd(&queue[0], 1ull);
+                if (w >= units) break;
+                XRun r;
+                if (!xrun_decode(p, kind, w, r)) continue;
+                for (int32_t c = r.a - 1; c <= r.b + 1; ++c, ++seq) {
+                    int s;
+                    if (!(ok = acquire(s))) break;
+                    meta[s] = make_int4(r.X1, r.X2, r.a, r.b);
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&full[s], kColBytes);
+                    tma_load_3d(ring + s * kColBytes, &tcol, c * 32, r.X2 * 32 - 1, r.X1 * 32 - 1, &full[s]);
+                }
             }
-            return;
+            issued = seq;
+            int s;
+            if (ok && (ok = acquire(s))) {
+                meta[s] = make_int4(0, 0, 1, 0);
+                mbar_arrive(&full[s]);
+            }
+            if (!ok) abort_flag = 1;
         }
-        my_live += ca3_tile32<C::RZ, ORK>(base + s * C::kStage, p.n, p.side, rule, out, inf.x, inf.y, inf.z,
-                                           (inf.w & 2) != 0, tid & 1, (tid >> 1) & 15, tid >> 5);
-        __syncthreads();  // stage s fully read
-        if (tid == 0) produce(s);
+    } else {
+        // consumers
+        const int tx = lane & 1, pr = lane >> 1, tz = warp;
+        uint64_t seq = 0;  // sequence number of the next run's first column
+        for (;;) {
+            if (abort_flag || !mbar_wait_bounded(&full[seq % S], (uint32_t)((seq / S) & 1), kWaitLimitNs)) {
+                abort_flag = 1;
+                break;
+            }
+            const int4 r = meta[seq % S];
+            if (r.z > r.w) break;  // end marker
+            const int64_t z0 = (int64_t)r.x * 32, y0 = (int64_t)r.y * 32;
+            bool ok = true;
+            for (int32_t x3 = r.z; x3 <= r.w; ++x3) {
+                const uint64_t c = seq + (uint64_t)(x3 - r.z) + 1;
+                // column c - 1 (and c) were awaited already: by the run start or the previous tile
+                for (uint64_t q = (x3 == r.z ? c : c + 1); q <= c + 1 && ok; ++q)
+                    ok = !abort_flag && mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
+                if (!ok) break;
+                const int64_t x0 = (int64_t)x3 * 32;
+                const bool partial = z0 + y0 + x0 + 3 * 31 > p.n;
+                my_live += ca3_tile32c<4, ORK>(ring + (c % S) * kColBytes, ring + ((c - 1) % S) * kColBytes,
+                                               ring + ((c + 1) % S) * kColBytes, x3 > 0, x0 + 32 <= p.n, p.n, p.side,
+                                               rule, out, x0, y0, z0, partial, tx, pr, tz);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(c - 1) % S]);
+            }
+            if (!ok) {
+                abort_flag = 1;
+                break;
+            }
+            const uint64_t last = seq + (uint64_t)(r.w - r.z) + 1;
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[last % S]);
+                mbar_arrive(&empty[(last + 1) % S]);
+            }
+            seq = last + 2;
+        }
+    }
+    __syncthreads();
+    if (tid == kStreamConsumers) {
+        if (abort_flag) {
+            atomicOr(&g_ca3_status, 2u);
+            // the last fill issued into each stage must land before the CTA exits
+            for (int j = 1; j <= S && (uint64_t)j <= issued; ++j) {
+                const uint64_t q = issued - j;
+                mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
+            }
+        }
+        // the last CTA out resets the work counter (every fetch of this launch is done)
+        __threadfence();
+        if (atomicAdd(&queue[1], 1ull) == (unsigned long long)gridDim.x - 1ull) {
+            queue[0] = 0;
+            queue[1] = 0;
+            __threadfence();
+        }
     }
     if (live) block_add_u64(live, my_live, red);
 }
@@ -225,48 +288,44 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     return cudaGetLastError();
 }
 
-constexpr int kCa3PersistThreads = 256;
-
 template <bool ORK>
-static cudaError_t prepare_persist_one()
+static cudaError_t prepare_stream_one()
 {
-    using C = Ca3Persist<32, kCa3PersistThreads>;
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(ca3_step_persistent<32, kCa3PersistThreads, ORK>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    e = cudaFuncSetAttribute(ca3_step_stream<ORK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
     if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
     return e;
 }
 
-static cudaError_t launch_persist(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
-                                  unsigned long long *live, cudaStream_t st)
+static cudaError_t launch_stream(const Plan &p, const CUtensorMap &tcol, uint8_t *out, const Rule &rule, int kind,
+                                 unsigned long long *live, unsigned long long *queue, cudaStream_t st)
 {
-    using C = Ca3Persist<32, kCa3PersistThreads>;
-    cudaError_t e = prepare_persist_one<false>();
-    if (e == cudaSuccess) e = prepare_persist_one<true>();
+    if (!queue) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_stream_one<false>();
+    if (e == cudaSuccess) e = prepare_stream_one<true>();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
-    const uint64_t g = nb < (uint64_t)sms ? (nb ? nb : 1) : (uint64_t)sms;  // one CTA per SM
+    const uint64_t units = xrun_units(p, kind);
+    const uint64_t g = units < (uint64_t)sms ? (units ? units : 1) : (uint64_t)sms;  // one CTA per SM
     if (rule.or_k)
-        ca3_step_persistent<32, kCa3PersistThreads, true><<<(unsigned)g, kCa3PersistThreads, C::kSmem, st>>>(
-            tin, out, p, rule, kind, nb, live);
+        ca3_step_stream<true><<<(unsigned)g, kStreamThreads, kStreamSmem, st>>>(tcol, out, p, rule, kind, units, live,
+                                                                                 queue);
     else
-        ca3_step_persistent<32, kCa3PersistThreads, false><<<(unsigned)g, kCa3PersistThreads, C::kSmem, st>>>(
-            tin, out, p, rule, kind, nb, live);
+        ca3_step_stream<false><<<(unsigned)g, kStreamThreads, kStreamSmem, st>>>(tcol, out, p, rule, kind, units, live,
+                                                                                  queue);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
-                            unsigned long long *live, cudaStream_t st)
+                            unsigned long long *live, unsigned long long *queue, cudaStream_t st)
 {
-    if (p.persistent && p.rho == 32) return launch_persist(p, tin, out, rule, kind, live, st);
+    if (p.persistent && p.rho == 32) return launch_stream(p, tin, out, rule, kind, live, queue, st);
     switch (p.rho) {
     case 16: return launch_t<16, 4>(p, tin, out, rule, kind, live, st);
     case 32: return launch_t<32, kCa3Rz32>(p, tin, out, rule, kind, live, st);
@@ -277,8 +336,8 @@ cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out,
 cudaError_t ca3_prepare(int rho)
 {
     if (rho == 32) {
-        cudaError_t e = prepare_persist_one<false>();
-        if (e == cudaSuccess) e = prepare_persist_one<true>();
+        cudaError_t e = prepare_stream_one<false>();
+        if (e == cudaSuccess) e = prepare_stream_one<true>();
         if (e != cudaSuccess) return e;
     }
     switch (rho) {

@@ -31,8 +31,10 @@ bool ca3_supports(int rho);
 bool ca3_swizzled(int rho);  // tensor map needs CU_TENSOR_MAP_SWIZZLE_64B
 cudaError_t launch_ca2_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
                             int kind, unsigned long long *live, cudaStream_t st);
+// queue: two zeroed 64-bit counters (work counter, CTAs done) that the x-stream
+// form (p.persistent) uses and leaves zeroed; unused by the grid form.
 cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
-                            int kind, unsigned long long *live, cudaStream_t st);
+                            int kind, unsigned long long *live, unsigned long long *queue, cudaStream_t st);
 
 // Sets the kernels' shared-memory limits for the current device (before any
 // stream capture).
