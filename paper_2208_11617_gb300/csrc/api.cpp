@@ -231,7 +231,8 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
                                                                                   : CU_TENSOR_MAP_SWIZZLE_NONE;
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, (cuuint32_t)p.m, const_cast<void *>(base), dims, strides, box,
                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    p.m == 3 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
     return SIMPLEX_OK;
 }
