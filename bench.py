@@ -170,6 +170,13 @@ def _workload(name, args=None):
         wl = inputs.WRITE_M2
     elif name == "write4":
         wl = inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
+    elif name == "map2":
+        wl = inputs.MAP_M2
+    elif name == "map3":
+        wl = inputs.MAP_M3
+    elif name == "edm":
+        wl = inputs.WriteWorkload(f"edm m=2 n={inputs.EDM_N} dim={inputs.EDM_DIM} rho={inputs.EDM_BLOCK}", m=2,
+                                  n=inputs.EDM_N, block=inputs.EDM_BLOCK)
     elif name == "batch":
         return "batch"
     elif name == "serve":
@@ -196,6 +203,8 @@ def _map_name(info):
         return f"H, trapezoid bands of {info['band']} tile rows (r=1/2, beta=2)"
     if info["m"] == 2:
         return "H, single Eq. map2d grid (r=1/2, beta=2)"
+    if info.get("layout") == 1:
+        return "H3, one block range per stack level (fully efficient, r=1/2, beta=2)"
     if info.get("launch") == 2:
         return "x-stream: H2 (Eq. map2d) over the tile columns, runs of up to 16 tiles along x3"
     return f"H (r=1/{info['r_inv']}, beta={info['beta']})"
@@ -417,11 +426,13 @@ def run_ours(args, rank, world, local):
         return run_batch(args, rank, world)
     if wl == "serve":
         return run_serve(args, rank, world)
+    if args.workload in ("map2", "map3", "edm"):
+        return run_diag(args, wl, rank, world)
     hbm_peak, peak_kind = _peaks()
     res = {}
     if isinstance(wl, inputs.CAWorkload):
         mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, band=args.band if wl.m == 2 else None,
-                                   launch=args.launch)
+                                   launch=args.launch, layout=args.layout if wl.m == 3 else 0)
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
@@ -562,6 +573,93 @@ def run_ours(args, rank, world, local):
     return res
 
 
+def run_diag(args, wl, rank, world):
+    """The paper's diagnostics (Table 1): MAP (the map alone; time per launch,
+    H against the bounding box and against the block-count ratio the theory
+    predicts) and EDM (float32 distance matrix of 3-D points, HBM-bound on its
+    4-byte stores).  A step is a graph of `reps` back-to-back launches."""
+    import torch
+    from paper_2208_11617_gb300 import simplex as sx
+    hbm_peak, peak_kind = _peaks()
+    beta = 2 if wl.m <= 3 else wl.m
+    mp = sx.simplex_map_create(wl.m, wl.n, 2, beta, wl.block, band=args.band if wl.m == 2 else None,
+                               layout=args.layout if wl.m == 3 else 0)
+    info = sx.simplex_map_info(mp)
+    cells = info["cells"]
+    edm = args.workload == "edm"
+    if edm:
+        pts = torch.from_numpy(inputs.edm_points(wl.n, inputs.EDM_DIM)).cuda()
+        out = torch.zeros(mp.numel, dtype=torch.float32, device="cuda")
+        launch = lambda mode: sx.simplex_edm(mp, pts, out, mode)  # noqa: E731
+        reps = 10
+    else:
+        launch = lambda mode: sx.simplex_map_test(mp, None, mode)  # noqa: E731
+        reps = 100
+
+    def graph_of(mode):
+        g = torch.cuda.CUDAGraph()
+        launch(mode)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                launch(mode)
+        return g
+
+    graphs = {m: graph_of(m) for m in (sx.SIMPLEX_MODE_H, sx.SIMPLEX_MODE_BB)}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    secs = _time_region(graphs[sx.SIMPLEX_MODE_H].replay, args.steps, args.warmup, world)
+    clk = clocks.stop()
+    secs_bb = _time_region(graphs[sx.SIMPLEX_MODE_BB].replay, args.steps, max(1, args.warmup), world)
+    units = cells * reps * args.steps
+    value, tmax = aggregate(units, secs, world)
+    value_bb, _ = aggregate(units, secs_bb, world)
+    mean_ms = _per_launch_ms(graphs[sx.SIMPLEX_MODE_H].replay, 10)[0] / reps
+    mean_bb = _per_launch_ms(graphs[sx.SIMPLEX_MODE_BB].replay, 10)[0] / reps
+    res = dict(
+        metric=METRIC, value=value, unit="cells/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32" if edm else "i32", data="synthetic",
+        config={"workload": wl.name, "m": wl.m, "n": wl.n, "tile": f"{wl.block}^{wl.m}", "launches_per_step": reps,
+                "cells": cells, "map": _map_name(info), "parallelism": "replicas" if world > 1 else "single"},
+        clocks=clk, gpu_launches=args.steps * reps,
+        bb={"value": value_bb, "speedup_h_over_bb": value / value_bb, "launch_ms_mean": mean_bb,
+            "kernel_speedup_h_over_bb": mean_bb / mean_ms},
+        blocks={"h": info["h_blocks"], "bb": info["bb_blocks"], "useful": info["useful_blocks"],
+                "bb_over_h": info["bb_blocks"] / info["h_blocks"]},
+    )
+    if edm:
+        alg_bytes = 4 * cells + (wl.n + 1) * inputs.EDM_DIM * 4
+        achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
+        res["config"]["array"] = f"{mp.side}^2 float32, {wl.n + 1} points x {inputs.EDM_DIM}"
+        res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                           "kernel": f"edm_kernel<{wl.block}>", "alg_bytes_per_launch": alg_bytes,
+                           "launch_ms_mean": mean_ms}
+        # end to end: points in from pinned host memory, matrix back to pinned host memory
+        h_pts = pts.cpu().pin_memory()
+        h_out = torch.empty(mp.numel, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(2):
+            pts.copy_(h_pts, non_blocking=True)
+            sx.simplex_edm(mp, pts, out)
+            h_out.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        res["e2e"] = {"value": aggregate(cells * 2, t1 - t0, world)[0], "unit": "cells/s",
+                      "h2d_bytes_per_step": h_pts.numel() * 4, "d2h_bytes_per_step": 4 * mp.numel}
+    else:
+        # the MAP test moves no memory: its bound is launching and retiring blocks
+        res["roofline"] = None
+        res["roofline_note"] = "MAP moves no memory; compare launch_ms against bb and blocks.bb_over_h"
+        res["theory_speedup"] = {2: 2.0, 3: 6.0}.get(wl.m)
+        res["e2e"] = {"value": None, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and edm:
+        res["cpu_baseline"] = cpu_baseline(wl, edm=True)
+    return res
+
+
 # ---------------------------------------------------------------- oracle (CPU) arm
 def _oracle_sample(wl, steps_sample):
     """Time the oracle on a bounded sample of the workload; returns (units/s, note, cores)."""
@@ -584,7 +682,20 @@ def _oracle_sample(wl, steps_sample):
     return cells * steps_sample / dt, f"{steps_sample} full write(s) of n={wl.n}", cores, dt
 
 
-def cpu_baseline(wl):
+def _oracle_edm_sample(n_sample):
+    """The oracle's distance matrix at a smaller n (whole triangle), cells/s."""
+    import oracle
+    pts = inputs.edm_points(n_sample, inputs.EDM_DIM)
+    t0 = time.perf_counter()
+    oracle.edm(n_sample, pts)
+    dt = time.perf_counter() - t0
+    return oracle.count_cells(2, n_sample) / dt, f"the whole EDM triangle at n={n_sample}", oracle.num_threads(), dt
+
+
+def cpu_baseline(wl, edm=False):
+    if edm:
+        v, note, cores, dt = _oracle_edm_sample(8191)
+        return {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": note, "seconds": dt}
     v, note, cores, dt = _oracle_sample(wl, 2 if isinstance(wl, inputs.CAWorkload) else 5)
     return {"value": v, "unit": UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s", "cores": cores,
             "kind": "oracle", "sample": note, "seconds": dt}
@@ -594,20 +705,28 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     wl = _workload(args.workload, args)
+    if wl in ("batch", "serve") or args.workload in ("map2", "map3"):
+        return {"impl": "reference", "unavailable": f"the oracle arm times the single-instance workloads "
+                f"(ca2, ca3, write2, write4, edm), not {args.workload}"}
     unit = UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s"
+    if args.workload == "edm":
+        sample = lambda k: _oracle_edm_sample(8191)  # noqa: E731
+    else:
+        sample = lambda k: _oracle_sample(wl, k)  # noqa: E731
     for _ in range(args.warmup):
-        _oracle_sample(wl, 1)
+        sample(1)
     vals, dts = [], []
     cores, note = 1, ""
     for _ in range(args.steps):
-        v, note, cores, dt = _oracle_sample(wl, 1)
+        v, note, cores, dt = sample(1)
         vals.append(v)
         dts.append(dt)
     total = sum(dts)
     value = len(vals) / sum(1.0 / v for v in vals)  # units over total time
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(dts) * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8" if unit == UNIT else "u32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.workload == "edm" else ("u8" if unit == UNIT else "u32"),
             "data": "synthetic", "config": {"workload": wl.name, "m": wl.m, "n": wl.n},
             "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
                              "sample": f"each step: {note}"},
@@ -620,7 +739,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ca2", choices=["ca2", "ca3", "write2", "write4", "batch", "serve"])
+    ap.add_argument("--workload", default="ca2",
+                    choices=["ca2", "ca3", "write2", "write4", "map2", "map3", "edm", "batch", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=inputs.SERVE_SECONDS, help="serve: trace length")
     ap.add_argument("--serve-sample", type=int, default=400, help="serve: jobs re-run alone for the serial baseline")
     ap.add_argument("--serve-capacity-jobs", type=int, default=4000, help="serve: jobs of the offline capacity run")
@@ -638,6 +758,8 @@ def main():
     ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
     ap.add_argument("--launch", type=int, default=0, help="automaton step form: 0 auto, 1 grid, 2 persistent")
     ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")
+    ap.add_argument("--layout", type=int, default=0,
+                    help="m = 3 H3 layout: 0 packed grid (Sec. 4.3), 1 one block range per stack level")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

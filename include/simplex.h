@@ -68,7 +68,7 @@ typedef struct simplex_map_info {
     int32_t band;           /* m = 2 trapezoid band height in tiles; 0 = single H2 grid */
     int32_t Ne;             /* m = 2 trapezoid form: block-triangle side (multiple of band) */
     int32_t launch;         /* automaton step form: 1 grid, 2 persistent */
-    int32_t reserved;
+    int32_t layout;         /* m = 3, beta = 2: 0 packed grid, 1 one block range per level */
     uint64_t cells;         /* C(n+m, m), Eq. 1 */
     uint64_t useful_blocks; /* tiles holding at least one cell: C(floor(n/rho)+m, m) */
     uint64_t h_blocks;      /* CUDA blocks one H launch starts */
@@ -108,6 +108,7 @@ typedef struct simplex_map_params {
     int64_t side;                  /* array side, >= n + 1; 0 means n + 1 */
     int32_t band;                  /* m = 2 only, see below; must be 0 or -1 for m > 2 */
     int32_t launch;                /* automaton step: 0 automatic, 1 grid, 2 persistent (see below) */
+    int32_t layout;                /* m = 3, beta = 2: 0 packed grid, 1 one range per level (see below) */
 } simplex_map_params_t;
 
 /*
@@ -131,7 +132,16 @@ typedef struct simplex_map_params {
  *     tiles in flight while it computes the current one (m = 3, block 32);
  *   0 (automatic): grid (the faster form on GB300 for every tile size
  *     implemented so far).
- * simplex_map_create and simplex_map_create_padded use band = 0, launch = 0.
+ * `layout` (m = 3, beta = 2 only) selects how H3 lays out its cubes:
+ *   0: the single packed grid of Sec. 4.3: the big cube (N/2)^3 and one layer
+ *     of height N/4 holding every smaller cube, whose blocks past the cube's
+ *     side exit (about 1/8 of the blocks for large N);
+ *   1: fully efficient (the alternative Sec. 4.3 closes with): every stack
+ *     level b = N/4, N/8, ..., 1 gets its own range of block indices, N/(2b)
+ *     cubes of b^3 blocks, in one launch: exactly (N^3 - N)/6 blocks below the
+ *     plane sum = N - 1, no waste.
+ * simplex_map_create and simplex_map_create_padded use band = 0, launch = 0,
+ * layout = 0.
  */
 int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out);
 
@@ -243,6 +253,39 @@ int simplex_ca_run_host(simplex_map_t map, const uint8_t *host_in, uint8_t *host
  * zeroed by the caller.
  */
 int simplex_visit_count(simplex_map_t map, uint32_t *counts, int level, int mode, void *stream);
+
+/*
+ * simplex_map_test -- the MAP test of Table 1 (Sec. 5.1): the map alone.
+ * Launches the map in `mode` with one CUDA block of block^m threads per block
+ * of the map and one thread per cell (the paper's model of Sec. 2): the block
+ * decodes its tile, each thread forms its cell coordinate x and the predicate
+ * x_1 + ... + x_m <= n, and the result is consumed without touching memory
+ * (the paper keeps it in a volatile variable).  The time of the call is the
+ * map plus the cost of launching its blocks, the quantity the paper's 2x (m =
+ * 2) and 6x (m = 3) theory is about.
+ *   cells  device uint64 or NULL: when given, every block ADDS the number of
+ *          its simplex cells to *cells, which must then total C(n + m, m).
+ * Needs block^m <= 1024 (m = 2: block <= 32; m = 3: block <= 8; m = 4:
+ * block <= 4).  Errors: SIMPLEX_EINVAL (mode, block), SIMPLEX_ECUDA.
+ */
+int simplex_map_test(simplex_map_t map, unsigned long long *cells, int mode, void *stream);
+
+/*
+ * simplex_edm -- the EDM test of Table 1 (Sec. 5.1) on the 2-simplex: cell
+ * x = (x1, x2), x1 + x2 <= n, stands for the pair of points (i, j) =
+ * (x1, n - x2) (so i <= j) and receives their Euclidean distance
+ *   out[x1 * side + x2] = sqrt(sum_k (p[i][k] - p[j][k])^2)
+ * in float32, summed over k = 0, 1, ... in that order with round-to-nearest
+ * and no fused multiply-add, then a correctly rounded square root: the upper
+ * triangle of the distance matrix of n + 1 points, diagonal (zeros) included.
+ *   points  device, float32, (n + 1) x dim, row-major (point i at i * dim).
+ *   dim     1 ... 16.
+ *   out     device, float32, side^2 elements, 4-byte aligned (a 16-byte
+ *           aligned base with side % 4 == 0 takes the 16-byte store path);
+ *           cells outside the domain are not written.
+ * Needs m = 2 and block 16, 32 or 64.  Errors: SIMPLEX_EINVAL, SIMPLEX_ECUDA.
+ */
+int simplex_edm(simplex_map_t map, const float *points, int dim, float *out, int mode, void *stream);
 
 /* ---- batched engine ------------------------------------------------------
  *

@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp]
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True, text=True)
@@ -68,6 +68,11 @@ def _load():
         lib.oracle_ca_cells.restype = None
         lib.oracle_block_indicator.argtypes = [i32, i64, i32, u32p]
         lib.oracle_block_indicator.restype = None
+        lib.oracle_edm.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_edm.restype = None
+        lib.oracle_edm_cells.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64), i64,
+                                         ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_edm_cells.restype = None
         _lib = lib
         return lib
 
@@ -146,3 +151,24 @@ def block_indicator(m: int, n: int, rho: int) -> np.ndarray:
     ind = np.zeros((nb,) * m, dtype=np.uint32)
     _load().oracle_block_indicator(m, n, rho, _ptr(ind, ctypes.c_uint32))
     return ind
+
+
+def edm(n: int, points: np.ndarray) -> np.ndarray:
+    """Distance matrix on the 2-simplex: dense (n+1) x (n+1) float64, entry
+    (x1, x2) with x1 + x2 <= n = |p[x1] - p[n - x2]|, others 0."""
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    assert pts.ndim == 2 and pts.shape[0] == n + 1
+    out = np.zeros((n + 1, n + 1), dtype=np.float64)
+    _load().oracle_edm(n, pts.shape[1], _ptr(pts, ctypes.c_float), _ptr(out, ctypes.c_double))
+    return out
+
+
+def edm_cells(n: int, points: np.ndarray, coords: np.ndarray) -> np.ndarray:
+    """Distances of the listed cells (coords: [k, 2] int64, x1 + x2 <= n), one by one."""
+    pts = np.ascontiguousarray(points, dtype=np.float32)
+    c = np.ascontiguousarray(coords, dtype=np.int64)
+    assert c.ndim == 2 and c.shape[1] == 2 and (c >= 0).all() and (c.sum(1) <= n).all()
+    out = np.zeros(len(c), dtype=np.float64)
+    _load().oracle_edm_cells(n, pts.shape[1], _ptr(pts, ctypes.c_float), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             len(c), _ptr(out, ctypes.c_double))
+    return out

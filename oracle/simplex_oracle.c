@@ -23,6 +23,10 @@
  *     `survive` is set.
  *   - Initial state: a cell of the domain is alive iff
  *     splitmix32(seed ^ lin(x)) < threshold  (Bernoulli(threshold / 2^32)).
+ *   - Euclidean distance matrix (Table 1 test 3, Sec. 5.1) on the 2-simplex:
+ *     cell (x1, x2) stands for the pair of points (i, j) = (x1, n - x2) and
+ *     holds d(p_i, p_j), computed here in double precision from the given
+ *     (float32) coordinates.
  *
  * splitmix32 is not in the paper.  It is the 32-bit golden-ratio counter step
  * (add 0x9E3779B9 = floor(2^32 / phi)) followed by the public-domain MurmurHash3
@@ -33,6 +37,7 @@
  * each iteration of the outer loop touches disjoint output cells, so the
  * result does not depend on the thread count.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stddef.h>
 #ifdef _OPENMP
@@ -289,5 +294,42 @@ void oracle_ca_cells(int m, int64_t n, uint32_t birth, uint32_t survive, const u
             alive = in[(x[0] * D + x[1]) * D + x[2]];
         }
         out[i] = alive ? (uint8_t)((survive >> k) & 1u) : (uint8_t)((birth >> k) & 1u);
+    }
+}
+
+/* Euclidean distance matrix on the 2-simplex (Table 1 test 3): out (dense
+ * D x D, D = n + 1, double) receives at (x1, x2), x1 + x2 <= n, the distance
+ * between points i = x1 and j = n - x2 of `points` ((n + 1) x dim, row-major,
+ * float32), in double precision; other entries are left untouched. */
+void oracle_edm(int64_t n, int dim, const float *points, double *out)
+{
+    const int64_t D = n + 1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t x1 = 0; x1 <= n; x1++)
+        for (int64_t x2 = 0; x1 + x2 <= n; x2++) {
+            const float *a = points + x1 * dim, *b = points + (n - x2) * dim;
+            double s = 0.0;
+            for (int k = 0; k < dim; k++) {
+                const double d = (double)a[k] - (double)b[k];
+                s += d * d;
+            }
+            out[x1 * D + x2] = sqrt(s);
+        }
+}
+
+/* The distances of `count` listed cells (x1, x2) of the 2-simplex (coords[2i],
+ * coords[2i + 1]), one by one, as oracle_edm defines them: checks sampled cells
+ * of a matrix too large for the CPU to fill as a whole. */
+void oracle_edm_cells(int64_t n, int dim, const float *points, const int64_t *coords, int64_t count, double *out)
+{
+    for (int64_t i = 0; i < count; i++) {
+        const int64_t x1 = coords[2 * i], x2 = coords[2 * i + 1];
+        const float *a = points + x1 * dim, *b = points + (n - x2) * dim;
+        double s = 0.0;
+        for (int k = 0; k < dim; k++) {
+            const double d = (double)a[k] - (double)b[k];
+            s += d * d;
+        }
+        out[i] = sqrt(s);
     }
 }

@@ -98,7 +98,7 @@ struct simplex_map {
 
 namespace sxh {
 
-int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, int band, sx::Plan *p)
+int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, int band, sx::Plan *p, int layout)
 {
     if (m < 2 || m > 4) return fail(SIMPLEX_EINVAL, "m must be 2, 3 or 4 (got %d)", m);
     if (n < 0) return fail(SIMPLEX_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
@@ -154,7 +154,11 @@ int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, i
     } else if (m == 3 && beta == 2) {
         const uint64_t half = (uint64_t)N / 2;
         p->h3_cube = half * half * half;
-        p->h3_layer = N >= 4 ? half * ((uint64_t)N / 4) * (half - 1) : 0;
+        p->h3_exact = layout == 1 ? 1 : 0;
+        if (p->h3_exact)
+            p->h3_layer = N >= 4 ? sx::h3_level_prefix((int32_t)N, logN + 1) : 0;
+        else
+            p->h3_layer = N >= 4 ? half * ((uint64_t)N / 4) * (half - 1) : 0;
         p->h_blocks = p->h3_cube + p->h3_layer + h2;
     } else {
         uint64_t total = h2;
@@ -231,7 +235,7 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
                                                                                   : CU_TENSOR_MAP_SWIZZLE_NONE;
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, (cuuint32_t)p.m, const_cast<void *>(base), dims, strides, box,
                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
-                    p.m == 3 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    p.m == 3 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
     return SIMPLEX_OK;
@@ -354,7 +358,11 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
     if (band == 0) band = params->m == 2 ? kDefaultBand : 0;  // automatic
     if (band < 0) band = 0;                                   // single H2 grid
     sx::Plan p;
-    int rc = build_plan(params->m, params->n, params->r_inv, params->beta, params->block, side, band, &p);
+    if (params->layout != 0 && !(params->layout == 1 && params->m == 3 && params->beta == 2))
+        return fail(SIMPLEX_EINVAL, "layout 1 (one block range per stack level) applies to m = 3, beta = 2 only "
+                    "(got layout %d, m = %d, beta = %d)", params->layout, params->m, params->beta);
+    int rc = build_plan(params->m, params->n, params->r_inv, params->beta, params->block, side, band, &p,
+                        params->layout);
     if (rc == SIMPLEX_OK) {
         // automatic: the grid form (measured faster on GB300 for every tile
         // size implemented); the persistent form on request (m = 3, block 32)
@@ -374,7 +382,7 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
 
 int simplex_map_create_padded(int m, int64_t n, int r_inv, int beta, int block, int64_t side, simplex_map_t *out)
 {
-    const simplex_map_params_t prm = {m, r_inv, beta, block, n, side, 0, 0};
+    const simplex_map_params_t prm = {m, r_inv, beta, block, n, side, 0, 0, 0};
     return simplex_map_create_ex(&prm, out);
 }
 
@@ -411,6 +419,7 @@ int simplex_map_info(simplex_map_t map, simplex_map_info_t *out)
     out->band = p.band;
     out->Ne = p.Ne;
     out->launch = p.persistent ? 2 : 1;
+    out->layout = p.h3_exact;
     out->cells = binom((uint64_t)p.n + (uint64_t)p.m, p.m);
     out->useful_blocks = binom((uint64_t)(p.n / p.rho) + (uint64_t)p.m, p.m);
     out->h_blocks = p.h_blocks;
@@ -457,6 +466,36 @@ int simplex_write(simplex_map_t map, uint32_t *out, uint32_t seed, int mode, voi
     const bool vec = aligned16(out) && (p.side % 4 == 0);
     cudaError_t e = sx::launch_write(p, out, seed, mode, vec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "write launch");
+    return SIMPLEX_OK;
+}
+
+int simplex_map_test(simplex_map_t map, unsigned long long *cells, int mode, void *stream)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    const sx::Plan &p = map->plan;
+    if (p.m * p.log_rho > 10)
+        return fail(SIMPLEX_EINVAL, "the MAP test runs block^m threads per CUDA block: needs block^m <= 1024 "
+                    "(m = %d, block = %d)", p.m, p.rho);
+    cudaError_t e = sx::launch_map_test(p, mode, cells, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "MAP test launch");
+    return SIMPLEX_OK;
+}
+
+int simplex_edm(simplex_map_t map, const float *points, int dim, float *out, int mode, void *stream)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    const sx::Plan &p = map->plan;
+    if (p.m != 2) return fail(SIMPLEX_EINVAL, "EDM is defined on the 2-simplex (map has m = %d)", p.m);
+    if (!sx::edm_supports(p.rho)) return fail(SIMPLEX_EINVAL, "EDM needs block 16, 32 or 64 (got %d)", p.rho);
+    if (dim < 1 || dim > 16) return fail(SIMPLEX_EINVAL, "dim must be in [1, 16] (got %d)", dim);
+    if (!points || !out) return fail(SIMPLEX_EINVAL, "points and out must not be NULL");
+    if ((reinterpret_cast<uintptr_t>(out) & 3u) != 0 || (reinterpret_cast<uintptr_t>(points) & 3u) != 0)
+        return fail(SIMPLEX_EINVAL, "points and out must be 4-byte aligned");
+    const bool vec = aligned16(out) && p.side % 4 == 0;
+    cudaError_t e = sx::launch_edm(p, points, dim, out, mode, vec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "EDM launch");
     return SIMPLEX_OK;
 }
 

@@ -25,7 +25,8 @@
 //          of height N/4 holding the smaller cubes laid out by the 2-D levels
 //          b, q of Thm. 1, and the hinge that reflects each cube's overhang
 //          onto the third corner; the plane sum = N-1 is a 2-simplex of blocks
-//          mapped by H2 plus its diagonal.
+//          mapped by H2 plus its diagonal.  Fully efficient form (h3_exact):
+//          the same cubes, one index range per stack level, no packing waste.
 //          beta = 3: the generic construction below.
 //   m >= 3 generic, r = 1/2, beta = m (Sec. 6, Eq. generic-m): level k holds
 //          m^(k-1) cubes of side b = N / 2^k; a cube is named by k-1 base-m
@@ -66,6 +67,10 @@ struct Plan {
     // execution model), 1 = persistent CTAs streaming runs of tiles along the
     // fastest axis (m = 3, see xrun_decode); seg_len = tiles per run
     int32_t persistent, seg_len;
+    // m = 3, beta = 2: 0 = the single packed grid of Sec. 4.3 (the layer of
+    // height N/4 with per-level exits), 1 = one block range per stack level
+    // (the fully efficient form of Sec. 4.3: no waste)
+    int32_t h3_exact, pad2_;
     uint64_t h_blocks;   // CUDA blocks of one H launch
     uint64_t bb_blocks;  // N^m
     // H3 (beta = 2): region sizes
@@ -242,6 +247,54 @@ SX_HD bool h3_cover(const Plan &p, uint64_t v, int32_t *X)
     return true;
 }
 
+// Fully efficient H3 (Sec. 4.3, closing paragraph): instead of packing the
+// cubes of side b <= N/4 into one layer of height N/4 (blocks with lz >= b
+// exit), each stack level k = 2 ... log2 N (b = N >> k) gets its own range of
+// block indices, N/(2b) cubes of b^3 blocks each, one after the other in a
+// single launch.  Blocks before level k: sum over j < k of N (N >> j)^2 / 2
+// = (N^3 - N^3 / 4^(k-2)) / 24.  Together with the big cube (N/2)^3 this is
+// exactly (N^3 - N) / 6, the blocks below the plane sum = N - 1.
+SX_HD uint64_t h3_level_prefix(int32_t N, int k)
+{
+    const uint64_t c = (uint64_t)N * (uint64_t)N * (uint64_t)N;
+    return (c - (c >> (2 * k - 4))) / 24;
+}
+
+SX_HD bool h3_exact(const Plan &p, uint64_t v, int32_t *X)
+{
+    const int32_t N = p.N, logN = p.logN, half = N >> 1;
+    if (v < p.h3_cube) {
+        const int lh = logN - 1;
+        const int32_t l3 = (int32_t)(v & (uint64_t)(half - 1));
+        const int32_t l2 = (int32_t)((v >> lh) & (uint64_t)(half - 1));
+        const int32_t l1 = (int32_t)(v >> (2 * lh));
+        h3_place(0, 0, half, l1, l2, l3, X);
+        return true;
+    }
+    v -= p.h3_cube;
+    if (v < p.h3_layer) {
+        int k = 2;
+        while (k < logN && h3_level_prefix(N, k + 1) <= v) ++k;
+        const int lb = logN - k;
+        const int32_t b = 1 << lb;
+        const uint64_t u = v - h3_level_prefix(N, k);
+        const int32_t q = (int32_t)(u >> (3 * lb));
+        const uint32_t l = (uint32_t)(u & ((1ull << (3 * lb)) - 1ull));
+        const int32_t l3 = (int32_t)(l & (uint32_t)(b - 1));
+        const int32_t l2 = (int32_t)((l >> lb) & (uint32_t)(b - 1));
+        const int32_t l1 = (int32_t)(l >> (2 * lb));
+        h3_place(N - 2 * b - 2 * q * b, 2 * q * b, b, l1, l2, l3, X);
+        return true;
+    }
+    v -= p.h3_layer;
+    int32_t Y[2];
+    h2_cover(v, N, logN, Y);
+    X[0] = Y[0];
+    X[1] = Y[1];
+    X[2] = N - 1 - Y[0] - Y[1];
+    return true;
+}
+
 // Generic self-similar cubes of dimension D (r = 1/2, beta = D), covering the
 // blocks with sum <= N - 2.
 template <int D>
@@ -310,7 +363,7 @@ SX_HD bool decode(const Plan &p, int kind, uint64_t v, int32_t *X)
         return true;
     }
     if (M == 2) return p.band ? h2_trapezoids(p, v, X) : h2_cover(v, p.N, p.logN, X);
-    if (M == 3 && p.beta == 2) return h3_cover(p, v, X);
+    if (M == 3 && p.beta == 2) return p.h3_exact ? h3_exact(p, v, X) : h3_cover(p, v, X);
     return Cover<M>::run(p, v, X);
 }
 

@@ -21,7 +21,8 @@ int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 
 // Validates the arguments and fills the launch plan (host memory only).
-int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, int band, sx::Plan *p);
+int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, int band, sx::Plan *p,
+               int layout = 0);
 
 // The byte-sliced rule tables for birth/survive masks of an m-dimensional automaton.
 sx::Rule make_rule(int m, uint32_t birth, uint32_t survive);

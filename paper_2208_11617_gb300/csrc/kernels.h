@@ -41,6 +41,13 @@ cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out,
 cudaError_t ca2_prepare(int rho);
 cudaError_t ca3_prepare(int rho);
 
+// Diagnostics of Table 1: MAP (rho^m threads per block, one per cell; with
+// `cells`, the simplex cells of every block are added to *cells) and EDM on
+// the 2-simplex (fp32 distances of points (x1, n - x2), dim <= 16).
+cudaError_t launch_map_test(const Plan &p, int kind, unsigned long long *cells, cudaStream_t st);
+bool edm_supports(int rho);
+cudaError_t launch_edm(const Plan &p, const float *pts, int dim, float *out, int kind, bool vec, cudaStream_t st);
+
 // One CTA whose mbarrier wait runs out after limit_ns (tests the bounded-wait path).
 cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
 

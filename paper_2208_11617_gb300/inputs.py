@@ -130,3 +130,21 @@ def serve_trace(rate: float = SERVE_RATE, seconds: float = SERVE_SECONDS, seed: 
         jobs.append(dict(m=m, n=int(sizes3[i] if m == 3 else sizes2[i]), steps=int(steps[i]), birth=rule[0],
                          survive=rule[1], seed=i, threshold=thr))
     return jobs, t
+
+
+# Diagnostics of Table 1.  MAP: the map alone, 16 x 16 threads per block on
+# the 2-simplex n = 32767 and 8 x 8 x 8 on the 3-simplex n = 1023 (the block
+# sizes the paper found fastest).  EDM: the distance matrix of 32768 points in
+# 3-D (coordinates uniform in [0, 1), float32) on the 2-simplex n = 32767,
+# 32 x 32 tiles.
+MAP_M2 = WriteWorkload("map m=2 n=32767 rho=16", m=2, n=32767, block=16)
+MAP_M3 = WriteWorkload("map m=3 n=1023 rho=8", m=3, n=1023, block=8)
+EDM_N = 32767
+EDM_DIM = 3
+EDM_BLOCK = 32
+
+
+def edm_points(n: int, dim: int = EDM_DIM, seed: int = DEFAULT_SEED):
+    """(n + 1) x dim float32 points, uniform in [0, 1), from numpy's seeded generator."""
+    import numpy as np
+    return np.random.default_rng(seed).random((n + 1, dim), dtype=np.float32)

@@ -38,6 +38,7 @@ EXPORTED = (
     "simplex_batch_info", "simplex_batch_bind", "simplex_batch_init", "simplex_batch_run", "simplex_batch_grid",
     "simplex_batch_run_static", "simplex_server_arena_bytes", "simplex_server_create", "simplex_server_destroy",
     "simplex_server_run", "simplex_server_result", "simplex_server_stats", "simplex_ca_digest",
+    "simplex_map_test", "simplex_edm",
 )
 
 if not os.path.exists(LIB_PATH):
@@ -54,7 +55,7 @@ class SimplexMapInfo(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("r_inv", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("n", ctypes.c_int64), ("side", ctypes.c_int64),
                 ("N", ctypes.c_int32), ("log2N", ctypes.c_int32), ("band", ctypes.c_int32),
-                ("Ne", ctypes.c_int32), ("launch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("Ne", ctypes.c_int32), ("launch", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("cells", ctypes.c_uint64),
                 ("useful_blocks", ctypes.c_uint64), ("h_blocks", ctypes.c_uint64),
                 ("bb_blocks", ctypes.c_uint64), ("h_set_blocks", ctypes.c_uint64)]
@@ -66,7 +67,7 @@ class SimplexMapInfo(ctypes.Structure):
 class SimplexMapParams(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("r_inv", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("n", ctypes.c_int64), ("side", ctypes.c_int64),
-                ("band", ctypes.c_int32), ("launch", ctypes.c_int32)]
+                ("band", ctypes.c_int32), ("launch", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
 
 class SimplexInstance(ctypes.Structure):
@@ -134,6 +135,8 @@ _sig("simplex_ca_step", [_vp, _vp, _vp, _u32, _u32, _vp, _i32, _vp])
 _sig("simplex_ca_run", [_vp, _vp, _vp, _i32, _u32, _u32, _vp, _i32, _i32, _vp])
 _sig("simplex_ca_run_host", [_vp, _vp, _vp, _vp, _vp, _i32, _u32, _u32, _vp, _vp, _i32, _i32, _vp])
 _sig("simplex_visit_count", [_vp, _vp, _i32, _i32, _vp])
+_sig("simplex_map_test", [_vp, _vp, _i32, _vp])
+_sig("simplex_edm", [_vp, _vp, _i32, _vp, _i32, _vp])
 _sig("simplex_device_status", [ctypes.POINTER(_u32)])
 _sig("simplex_selftest_wait_timeout", [_u64, _vp])
 _sig("simplex_batch_create", [ctypes.POINTER(SimplexInstance), _i32, ctypes.POINTER(_vp)])
@@ -226,17 +229,19 @@ class SimplexMap:
 
 
 def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, block: int = 16,
-                       side: int | None = None, band: int | None = None, launch: int = 0) -> SimplexMap:
+                       side: int | None = None, band: int | None = None, launch: int = 0,
+                       layout: int = 0) -> SimplexMap:
     """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4).
 
     band (m = 2): None/0 automatic trapezoid bands, > 0 band height, -1 the
     single grid of Eq. map2d.  launch: 0 automatic, 1 grid, 2 persistent
-    automaton step."""
+    automaton step.  layout (m = 3, beta = 2): 0 packed grid, 1 one block
+    range per stack level."""
     if beta is None:
         beta = 2 if m <= 3 else m
     h = _vp()
-    if band is not None or launch:
-        prm = SimplexMapParams(m, r_inv, beta, block, n, side or 0, band or 0, launch)
+    if band is not None or launch or layout:
+        prm = SimplexMapParams(m, r_inv, beta, block, n, side or 0, band or 0, launch, layout)
         _check(_lib.simplex_map_create_ex(ctypes.byref(prm), ctypes.byref(h)), "simplex_map_create_ex")
     elif side is None:
         _check(_lib.simplex_map_create(m, n, r_inv, beta, block, ctypes.byref(h)), "simplex_map_create")
@@ -316,6 +321,22 @@ def simplex_visit_count(mp: SimplexMap, counts: torch.Tensor, level: int, mode: 
         need = mp.numel
     _check(_lib.simplex_visit_count(mp.handle, _dptr(counts, torch.int32, "counts", need), level, mode,
                                     _stream()), "simplex_visit_count")
+
+
+def simplex_map_test(mp: SimplexMap, cells: torch.Tensor | None = None, mode: int = SIMPLEX_MODE_H):
+    """MAP test (the map alone); with `cells` (one int64), the simplex cells of
+    every block are added to cells[0]."""
+    _check(_lib.simplex_map_test(mp.handle, _dptr(cells, torch.int64, "cells", 1), mode, _stream()),
+           "simplex_map_test")
+
+
+def simplex_edm(mp: SimplexMap, points: torch.Tensor, out: torch.Tensor, mode: int = SIMPLEX_MODE_H):
+    """EDM test: out[x1, x2] = |p[x1] - p[n - x2]| (float32) for x1 + x2 <= n;
+    points is (n + 1) x dim float32."""
+    if points.dim() != 2 or points.shape[0] != mp.n + 1:
+        raise ValueError(f"points must be (n + 1) x dim = ({mp.n + 1}, dim), got {tuple(points.shape)}")
+    _check(_lib.simplex_edm(mp.handle, _dptr(points, torch.float32, "points", points.numel()), int(points.shape[1]),
+                            _dptr(out, torch.float32, "out", mp.numel), mode, _stream()), "simplex_edm")
 
 
 def simplex_device_status() -> int:

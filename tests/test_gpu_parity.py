@@ -356,3 +356,27 @@ def test_ca_m2_full_size_matches_oracle():
     live_all[w.steps] = int(step_live.item())
     np.testing.assert_array_equal(live_b, live_all)
     assert int(fin_b.sum(dtype=torch.int64).item()) == int(live_b[-1])
+
+
+@pytest.mark.parametrize("n,block,side", [(255, 32, None), (200, 32, 208), (127, 16, None), (1023, 32, None),
+                                          (63, 8, None)])
+def test_h3_level_layout_matches_oracle(n, block, side):
+    """The fully efficient H3 (one block range per stack level): automaton
+    steps (tiles of 16 and 32) and the write test give the oracle's arrays."""
+    mp = sx.simplex_map_create(3, n, 2, 2, block, side=side, layout=1)
+    assert mp.info.layout == 1
+    if block >= 16:
+        thr = inputs.bernoulli_threshold(0.3)
+        steps = 2 if n > 500 else 5
+        fin, live = _gpu_run(mp, n, steps, inputs.B5S45, 23, thr, sx.SIMPLEX_MODE_H)
+        got, rest = _logical(fin, mp, n)
+        ref, ref_live = oracle.ca_run(3, n, steps, *inputs.B5S45, oracle.ca_init(3, n, 23, thr))
+        np.testing.assert_array_equal(got, ref)
+        assert not rest.any()
+        np.testing.assert_array_equal(live, ref_live)
+    if n <= 255:
+        out = torch.zeros(mp.numel, dtype=torch.int32, device=DEV)
+        sx.simplex_write(mp, out, 5)
+        got, rest = _logical(out, mp, n)
+        np.testing.assert_array_equal(got.view(np.uint32), oracle.write(3, n, 5))
+        assert not rest.any()

@@ -218,3 +218,38 @@ def test_launch_form_choice():
     with pytest.raises(sx.SimplexError) as ei:
         sx.simplex_map_create(2, 1023, 2, 2, 128, launch=2)
     assert ei.value.code == sx.SIMPLEX_EUNSUPPORTED
+
+
+# ---------------------------------------------------------------- fully efficient H3 (layout 1)
+@pytest.mark.parametrize("n,rho", [(0, 4), (3, 4), (4, 4), (7, 4), (15, 4), (31, 4), (63, 4), (100, 4),
+                                   (127, 4), (255, 4), (200, 8)])
+def test_h3_levels_cover_each_simplex_block_exactly_once(n, rho):
+    mp = sx.simplex_map_create(3, n, 2, 2, rho, layout=1)
+    assert mp.info.layout == 1
+    got = _covered(mp, sx.SIMPLEX_MODE_H)
+    ind = oracle.block_indicator(3, n, rho)
+    want = {tuple(int(i) for i in x) for x in np.argwhere(ind)}
+    assert set(got) == want
+    assert all(c == 1 for c in got.values())
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 16, 32, 64, 1024])
+def test_h3_levels_launch_exactly_the_block_simplex(N):
+    # no packing waste: (N^3 - N)/6 blocks below the plane (Eq. m3) plus the
+    # plane's H2 cover; every one of them maps to a block of Delta_{N-1}
+    rho = 4
+    mp = sx.simplex_map_create(3, N * rho - 1, 2, 2, rho, layout=1)
+    plane = (N // 2) * (N - 1) + N
+    assert mp.info.h_blocks == (N ** 3 - N) // 6 + plane
+    if N <= 64:
+        main = mp.info.h_blocks - plane
+        assert all(sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)[1] for v in range(main))
+
+
+def test_layout_rejected_outside_m3_beta2():
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_create(2, 63, 2, 2, 4, layout=1)
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_create(3, 63, 2, 3, 4, layout=1)
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_create(3, 63, 2, 2, 4, layout=2)

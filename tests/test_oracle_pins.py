@@ -314,3 +314,45 @@ def test_ca_cells_agrees_with_whole_step():
         coords = np.argwhere(np.indices(g.shape).sum(0) <= n)
         got = oracle.ca_cells(m, n, rule[0], rule[1], g, coords)
         np.testing.assert_array_equal(got, ref[tuple(coords.T)])
+
+
+# ---------------------------------------------------------------- EDM (Table 1 test 3)
+def test_edm_pythagorean_points():
+    """Hand-worked example: points with integer distances (3-4-5, 5-12-13 and
+    the 1-2-2 triple); cell (x1, x2) holds d(p[x1], p[n - x2])."""
+    pts = np.array([[0, 0, 0], [3, 4, 0], [0, 0, 12], [1, 2, 2]], dtype=np.float32)
+    d = oracle.edm(3, pts)
+    want = {(0, 0): 3.0, (0, 1): 12.0, (0, 2): 5.0, (0, 3): 0.0,
+            (1, 0): math.sqrt(12.0), (1, 1): 13.0, (1, 2): 0.0,
+            (2, 0): math.sqrt(1 + 4 + 100), (2, 1): 0.0,
+            (3, 0): 0.0}
+    for (x1, x2), v in want.items():
+        assert d[x1, x2] == pytest.approx(v, rel=1e-15)
+    # outside the simplex nothing is written
+    assert d[1, 3] == 0 and d[3, 3] == 0 and d[2, 2] == 0
+
+
+@pytest.mark.parametrize("n,dim", [(0, 1), (1, 3), (30, 3), (57, 16), (40, 1)])
+def test_edm_matches_scipy_cdist(n, dim):
+    """The oracle's triangle is the upper triangle (diagonal included) of
+    scipy's distance matrix, read with j = n - x2."""
+    spatial = pytest.importorskip("scipy.spatial")
+    pts = np.random.default_rng(n * 31 + dim).random((n + 1, dim), dtype=np.float32)
+    ref = spatial.distance.cdist(pts.astype(np.float64), pts.astype(np.float64))
+    d = oracle.edm(n, pts)
+    x1, x2 = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    inside = x1 + x2 <= n
+    np.testing.assert_allclose(d[inside], ref[x1[inside], n - x2[inside]], rtol=1e-14, atol=0)
+    assert not d[~inside].any()
+    # the anti-diagonal x1 + x2 = n is the matrix diagonal i = j: exactly zero
+    assert not d[x1 + x2 == n].any()
+
+
+def test_edm_cells_agree_with_whole_matrix():
+    pts = inputs.edm_points(50, 5, seed=3)
+    full = oracle.edm(50, pts)
+    rng = np.random.default_rng(4)
+    x1 = rng.integers(0, 51, 200)
+    x2 = (rng.random(200) * (51 - x1)).astype(np.int64)
+    c = np.stack([x1, x2], 1)
+    np.testing.assert_array_equal(oracle.edm_cells(50, pts, c), full[x1, x2])
