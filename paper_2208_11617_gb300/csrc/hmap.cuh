@@ -127,6 +127,21 @@ SX_HD bool h2_cover(uint64_t v, int32_t N, int32_t logN, int32_t *X)
     return true;
 }
 
+// The plan with the single Eq. map2d grid (plus its diagonal row) on the
+// power-of-two side N for m = 2, whatever its band: the kernels without a
+// stencil (write, MAP, EDM) have no halo to keep in L2, so they take the
+// paper's map and its clz-only decode instead of the trapezoid form's search.
+SX_HD Plan single_grid(const Plan &p)
+{
+    Plan q = p;
+    if (q.m == 2 && q.band) {
+        q.band = 0;
+        q.log_band = 0;
+        q.h_blocks = h2_cover_blocks(q.N);
+    }
+    return q;
+}
+
 // x-stream form (m = 3).  Work unit w names a run of at most seg_len tiles
 // along the fastest axis X3 in one tile column (X1, X2): the column comes from
 // H2 plus its diagonal over the triangle X1 + X2 <= N - 1 (kMapH, the 2-D map
@@ -273,11 +288,17 @@ SX_HD bool h3_exact(const Plan &p, uint64_t v, int32_t *X)
     }
     v -= p.h3_cube;
     if (v < p.h3_layer) {
+        // level k holds N (N >> k)^2 / 2 = N^3 / 2^(2k+1) blocks
+        const uint64_t c = (uint64_t)N * (uint64_t)N * (uint64_t)N;
+        uint64_t u = v;
         int k = 2;
-        while (k < logN && h3_level_prefix(N, k + 1) <= v) ++k;
+        for (; k < logN; ++k) {
+            const uint64_t sz = c >> (2 * k + 1);
+            if (u < sz) break;
+            u -= sz;
+        }
         const int lb = logN - k;
         const int32_t b = 1 << lb;
-        const uint64_t u = v - h3_level_prefix(N, k);
         const int32_t q = (int32_t)(u >> (3 * lb));
         const uint32_t l = (uint32_t)(u & ((1ull << (3 * lb)) - 1ull));
         const int32_t l3 = (int32_t)(l & (uint32_t)(b - 1));

@@ -14,9 +14,8 @@
 // EDM (m = 2).  Cell x = (x1, x2) of the 2-simplex stands for the pair of
 // points (i, j) = (x1, n - x2), i <= j, and receives d(p_i, p_j) as float32:
 // the upper triangle of the distance matrix of n + 1 points, diagonal
-// included.  One block per tile of rho x rho cells: the block stages the
-// tile's rho points of each index range in shared memory (one thread decodes
-// the block and shares it; 3-D points get an unrolled kernel), every thread
+// included.  One block per tile of rho x rho cells; every thread reads its
+// points straight from global memory (3-D points get an unrolled kernel),
 // computes 4 consecutive cells along x2 and writes them with one 16-byte
 // store (4-byte stores where rows are not 16-byte aligned or on the
 // diagonal).  Arithmetic is fp32 in a fixed order without contraction
@@ -63,8 +62,9 @@ static cudaError_t launch_map_t(const Plan &p, int kind, unsigned long long *cel
     return cudaGetLastError();
 }
 
-cudaError_t launch_map_test(const Plan &p, int kind, unsigned long long *cells, cudaStream_t st)
+cudaError_t launch_map_test(const Plan &plan, int kind, unsigned long long *cells, cudaStream_t st)
 {
+    const Plan p = single_grid(plan);
     switch (p.m) {
     case 2: return launch_map_t<2>(p, kind, cells, st);
     case 3: return launch_map_t<3>(p, kind, cells, st);
@@ -79,42 +79,30 @@ template <int RHO, int DIM>
 __global__ void __launch_bounds__(RHO * RHO / 4)
     edm_kernel(const Plan p, int kind, const float *__restrict__ pts, int dim_rt, float *__restrict__ out, int vec)
 {
-    __shared__ float pi[RHO * kEdmMaxDim], pj[RHO * kEdmMaxDim];
-    __shared__ int32_t sX[3];
     const int dim = DIM > 0 ? DIM : dim_rt;
-    if (threadIdx.x == 0) {  // one decode per block, shared with the block
-        int32_t X[2];
-        sX[2] = decode<2>(p, kind, blockIdx.x, X) ? 1 : 0;
-        sX[0] = X[0];
-        sX[1] = X[1];
-    }
-    __syncthreads();
-    if (!sX[2]) return;
-    const int64_t x1_0 = (int64_t)sX[0] * RHO, x2_0 = (int64_t)sX[1] * RHO;
+    int32_t X[2];
+    if (!decode<2>(p, kind, blockIdx.x, X)) return;
+    const int64_t x1_0 = (int64_t)X[0] * RHO, x2_0 = (int64_t)X[1] * RHO;
     if (x1_0 + x2_0 > p.n) return;
     const bool partial = x1_0 + x2_0 + 2 * (RHO - 1) > p.n;
-    // points i = x1_0 + r and j = n - x2_0 - r (r < RHO) that exist
-    for (int e = threadIdx.x; e < RHO * dim; e += blockDim.x) {
-        const int r = e / dim, k = e - r * dim;
-        const int64_t i = x1_0 + r, j = p.n - x2_0 - r;
-        pi[r * kEdmMaxDim + k] = i <= p.n ? pts[i * dim + k] : 0.f;
-        pj[r * kEdmMaxDim + k] = j >= 0 ? pts[j * dim + k] : 0.f;
-    }
-    __syncthreads();
     constexpr int kChunks = RHO / 4;
     const int row = threadIdx.x / kChunks, ch = threadIdx.x - row * kChunks;
     const int64_t x1 = x1_0 + row, x2 = x2_0 + 4 * ch;
     const int64_t valid = p.n - x1 - x2 + 1;  // cells of the chunk inside the simplex
     if (partial && valid <= 0) return;
+    // point i = x1 and points j = n - x2 - c, read straight from global memory
+    // (the points are a few hundred KB: L1 and L2 hits after the first touch)
+    const float *a = pts + x1 * dim;
     float d[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float *a = pi + row * kEdmMaxDim, *b = pj + (4 * ch + c) * kEdmMaxDim;
+        const int64_t j = p.n - x2 - c;
+        const float *b = pts + (j >= 0 ? j : 0) * dim;
         float acc = 0.f;
 #pragma unroll
         for (int k = 0; k < (DIM > 0 ? DIM : kEdmMaxDim); ++k) {
             if (DIM == 0 && k >= dim) break;
-            const float df = __fsub_rn(a[k], b[k]);
+            const float df = __fsub_rn(__ldg(a + k), __ldg(b + k));
             acc = __fadd_rn(acc, __fmul_rn(df, df));
         }
         d[c] = __fsqrt_rn(acc);
@@ -131,8 +119,9 @@ __global__ void __launch_bounds__(RHO * RHO / 4)
 
 bool edm_supports(int rho) { return rho == 16 || rho == 32 || rho == 64; }
 
-cudaError_t launch_edm(const Plan &p, const float *pts, int dim, float *out, int kind, bool vec, cudaStream_t st)
+cudaError_t launch_edm(const Plan &plan, const float *pts, int dim, float *out, int kind, bool vec, cudaStream_t st)
 {
+    const Plan p = single_grid(plan);
     if (dim < 1 || dim > kEdmMaxDim) return cudaErrorInvalidValue;
     const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
     if (nb > 0x7fffffffull) return cudaErrorInvalidConfiguration;

@@ -90,8 +90,9 @@ static unsigned threads_for(const Plan &p, int lw)
     return (unsigned)(nchunks < 256 ? nchunks : 256);
 }
 
-cudaError_t launch_write(const Plan &p, uint32_t *out, uint32_t seed, int kind, bool vec, cudaStream_t st)
+cudaError_t launch_write(const Plan &plan, uint32_t *out, uint32_t seed, int kind, bool vec, cudaStream_t st)
 {
+    const Plan p = single_grid(plan);
     const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
     const unsigned g = grid_for(nb), t = threads_for(p, 2);
     switch (p.m) {
