@@ -38,18 +38,24 @@ UNIT = "cell-updates/s"
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the full-size default workload, keyed by a fingerprint of the
-# kernel's sources; a changed kernel reports null until it is measured again.
-_KERNEL_SOURCES = ["paper_2208_11617_gb300/csrc/k_ca2.cu", "paper_2208_11617_gb300/csrc/common.cuh",
-                   "paper_2208_11617_gb300/csrc/hmap.cuh", "paper_2208_11617_gb300/csrc/rule.h"]
-_KERNEL_TRAFFIC = {("c368e3dbf874d600", "ca2_step_kernel<128>", 32767): 1_037_270_000}
+# ncu captures of the full-size workloads (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch, mean of 3 launches), keyed by a fingerprint
+# of the sources the kernel's traffic depends on: a changed kernel reports null
+# until it is measured again.
+_CSRC = "paper_2208_11617_gb300/csrc/"
+_KERNEL_SOURCES = {
+    "ca2_step_kernel<128>": ["k_ca2.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp"],
+    "ca3_step_kernel<32>": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp"],
+}
+_KERNEL_TRAFFIC = {("11dbc53541d5e6e8", "ca2_step_kernel<128>", 32767): 1_032_728_661,
+                   ("8d6544fa857a5d59", "ca3_step_kernel<32>", 1023): 521_173_930}
 
 
-def _kernel_fingerprint():
+def _kernel_fingerprint(kname):
     import hashlib
     h = hashlib.sha1()
-    for f in _KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
+    for f in _KERNEL_SOURCES.get(kname, []):
+        with open(os.path.join(ROOT, _CSRC + f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -472,7 +478,7 @@ def run_ours(args, rank, world, local):
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                       "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                       "kernel": kname, "alg_bytes_per_launch": alg_bytes,
-                      "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint(), kname, wl.n)),
+                      "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint(kname), kname, wl.n)),
                       "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
             clocks=clk,
             gpu_launches=args.steps * (wl.steps + 1),

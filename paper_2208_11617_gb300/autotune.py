@@ -89,3 +89,53 @@ def tune(instances, steps: int = 4, reps: int = 3, max_per_class: int = 256, cac
             json.dump({json.dumps(list(k)): v for k, v in table.items()}, f, indent=1)
     tune.last_seconds = table_meta
     return table
+
+
+# ---------------------------------------------------------------------------
+# The (r, beta) question of Thm. 3 (Sec. 6), on the host.
+#
+# A self-similar set S of orthotopes with scale factor r = 1/k and replication
+# beta has volume (Eq. generic-m)
+#     V(S_n^m) = (n^m - beta^(log_k n)) / (k^m - beta),
+# against V(Delta) = C(n + m - 1, m) (the paper's side-length count).  Its
+# extra volume tends to alpha = m! / (k^m - beta) - 1 (Lemma 5 gives it for
+# k = beta = 2: 5/7 at m = 4, 3 at m = 5, 39 at m = 7).  Thm. 3 asks for the
+# (k, beta) minimising |V(S) - V(Delta)| subject to beta > 1 and k, beta
+# integers; a set can only cover the simplex if V(S) >= V(Delta).  The paper
+# states the bound 1/r > beta, which its own r = 1/2, beta = 2 sets break, so
+# the search uses beta < k^m (the series converges) and reports the paper's
+# bound beside each candidate.  Volume alone does not say whether a set
+# covers Delta geometrically: the maps built here are r = 1/2 with beta = 2
+# (m = 2, 3) and beta = m (m = 3, 4), and their cover is checked block by
+# block by the tests.
+
+def set_volume(m: int, n: int, k: int, beta: int) -> float:
+    """V(S_n^m) of Eq. generic-m for r = 1/k (n a power of k)."""
+    levels = round(math.log(n, k))
+    return (n ** m - beta ** levels) / (k ** m - beta)
+
+
+def simplex_volume(m: int, n: int) -> int:
+    """V(Delta_n^m) with n the side length, as Sec. 6 counts it: C(n + m - 1, m)."""
+    return math.comb(n + m - 1, m)
+
+
+def extra_volume_limit(m: int, k: int, beta: int) -> float:
+    """alpha(S, Delta) as n -> infinity: m! / (k^m - beta) - 1 (Lemma 5 for k = beta = 2)."""
+    return math.factorial(m) / (k ** m - beta) - 1.0
+
+
+def search_r_beta(m: int, n: int, k_max: int = 8):
+    """Candidates (k = 1/r, beta) of Thm. 3 for the m-simplex of side n (a
+    power of k is not required: the volume formula is evaluated at n), sorted
+    by |V(S) - V(Delta)|; each entry says whether V(S) >= V(Delta) at this n
+    and whether the paper's bound 1/r > beta holds."""
+    out = []
+    vd = simplex_volume(m, n)
+    for k in range(2, k_max + 1):
+        for beta in range(2, k ** m):
+            vs = (n ** m - beta ** math.log(n, k)) / (k ** m - beta)
+            out.append(dict(k=k, beta=beta, volume=vs, extra=vs / vd - 1.0, covers_volume=vs >= vd,
+                            paper_bound=k > beta, alpha=extra_volume_limit(m, k, beta)))
+    out.sort(key=lambda c: abs(c["volume"] - vd))
+    return out

@@ -253,3 +253,42 @@ def test_layout_rejected_outside_m3_beta2():
         sx.simplex_map_create(3, 63, 2, 3, 4, layout=1)
     with pytest.raises(sx.SimplexError):
         sx.simplex_map_create(3, 63, 2, 2, 4, layout=2)
+
+
+# ---------------------------------------------------------------- Thm. 3 / Lemma 5 (host analysis)
+def test_extra_volume_limits_match_lemma_5():
+    from paper_2208_11617_gb300 import autotune
+    # the paper's values for r = 1/2, beta = 2: 5/7 (m = 4), 3x (m = 5), 39x (m = 7)
+    assert autotune.extra_volume_limit(4, 2, 2) == pytest.approx(5 / 7)
+    assert autotune.extra_volume_limit(5, 2, 2) == pytest.approx(3.0)
+    assert autotune.extra_volume_limit(7, 2, 2) == pytest.approx(39.0)
+    # m = 2, 3: the efficient cases (alpha -> 0)
+    assert autotune.extra_volume_limit(2, 2, 2) == pytest.approx(0.0)
+    assert autotune.extra_volume_limit(3, 2, 2) == pytest.approx(0.0)
+
+
+def test_generic_m_volume_reduces_to_eq_m2_m3():
+    from paper_2208_11617_gb300 import autotune
+    for n in (2, 4, 64, 1024):
+        assert autotune.set_volume(2, n, 2, 2) == pytest.approx((n * n - n) / 2)      # Eq. m2
+        assert autotune.set_volume(3, n, 2, 2) == pytest.approx((n ** 3 - n) / 6)     # Eq. m3
+        # the maps' block counts agree: H2 grid N/2 x (N-1) and H3 (N^3 - N)/6 cells of S
+    mp = sx.simplex_map_create(4, 2 ** 10 - 1, 2, 4, 4)
+    N = mp.info.N
+    # beta = m = 4: (N^4 - 4^log2 N) / (16 - 4) blocks in the cube set (Eq. generic-m)
+    assert mp.info.h_set_blocks == (N ** 4 - 4 ** int(math.log2(N))) // 12
+
+
+def test_search_r_beta_orders_by_volume_gap():
+    from paper_2208_11617_gb300 import autotune
+    c = autotune.search_r_beta(4, 1024, k_max=4)
+    gaps = [abs(x["volume"] - autotune.simplex_volume(4, 1024)) for x in c]
+    assert gaps == sorted(gaps)
+    # the volume optimum makes k^4 - beta close to 4! = 24 (k = 3, beta near 57
+    # in the limit; the finite-n term beta^(log_k n) moves it at n = 1024)
+    best = c[0]
+    assert best["k"] == 3 and abs(best["extra"]) < 0.01
+    # under the paper's stated bound 1/r > beta no set even reaches the volume
+    # of the 4-simplex: k = 2 leaves no beta >= 2, and k >= 3 with beta < k
+    # has k^4 - beta >= 79 > 24
+    assert not any(x["paper_bound"] and x["covers_volume"] for x in c)
