@@ -305,7 +305,7 @@ typedef struct simplex_batch *simplex_batch_t;
 
 typedef struct simplex_instance {
     int32_t m;          /* 2 or 3 */
-    int32_t block;      /* tile side: m = 2: 64 or 128; m = 3: 16 */
+    int32_t block;      /* tile side: m = 2: 64 or 128; m = 3: 16 or 32 (32^3 tiles run in a second launch per step) */
     int32_t beta;       /* m = 3: 2 (hinge) or 3; m = 2: 2 */
     int32_t band;       /* m = 2 trapezoid band (power of two); 0: automatic */
     int64_t n;          /* simplex size, >= 0 */

@@ -37,7 +37,8 @@ struct RunGraph {
 struct simplex_batch {
     std::vector<simplex_instance_t> spec;
     std::vector<sx::BatchInst> insts;
-    std::vector<sx::BatchItem> items;
+    std::vector<sx::BatchItem> items;  // set 0 items, then set 1 items
+    size_t nitems0 = 0;
     std::vector<uint64_t> grid_bytes;
     uint64_t blocks = 0, cells = 0;
     // arena layout (byte offsets)
@@ -65,27 +66,45 @@ int enqueue_batch_run(simplex_batch_t b, int steps, unsigned long long *live, in
     const sx::BatchItem *items = reinterpret_cast<const sx::BatchItem *>(b->arena + b->off_items);
     const CUtensorMap *tmaps = reinterpret_cast<const CUtensorMap *>(b->arena + b->off_tmaps);
     unsigned int *queue = reinterpret_cast<unsigned int *>(b->arena + b->off_queue);
-    const uint32_t nitems = (uint32_t)b->items.size();
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * (size_t)(steps + 1), st);
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * 2 * (size_t)(steps + 1), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(queue)");
     if (live) {
         e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * b->insts.size() * (size_t)(steps + 1), st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(live)");
-        e = sx::launch_batch_pass(insts, items, nitems, tmaps, b->arena, parity, queue, live, steps + 1, 0, true, st);
-        if (e != cudaSuccess) return cuda_fail(e, "batch count launch");
     }
-    for (int s = 1; s <= steps; ++s) {
-        const int in = (parity + s - 1) & 1;
-        e = sx::launch_batch_pass(insts, items, nitems, tmaps, b->arena, in, queue + s, live, steps + 1, s, false,
-                                  st);
-        if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
-    }
-    return SIMPLEX_OK;
+    return enqueue_batch_passes(insts, items, b->items.size(), b->nitems0, tmaps, b->arena, queue,
+                                queue + steps + 1, steps, live, parity, st);
 }
 
 }  // namespace
 
 namespace sxh {
+
+int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items, size_t nitems, size_t nitems0,
+                         const CUtensorMap *tmaps, uint8_t *arena, unsigned int *q0, unsigned int *q1, int steps,
+                         unsigned long long *live, int parity, cudaStream_t st)
+{
+    cudaError_t e;
+    if (live) {
+        e = sx::launch_batch_pass(insts, items, (uint32_t)nitems, tmaps, arena, parity, q0, live, steps + 1, 0, true,
+                                  st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch count launch");
+    }
+    for (int s = 1; s <= steps; ++s) {
+        const int in = (parity + s - 1) & 1;
+        if (nitems0) {
+            e = sx::launch_batch_pass(insts, items, (uint32_t)nitems0, tmaps, arena, in, q0 + s, live, steps + 1, s,
+                                      false, st, nullptr, nullptr, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
+        }
+        if (nitems > nitems0) {
+            e = sx::launch_batch_pass(insts, items + nitems0, (uint32_t)(nitems - nitems0), tmaps, arena, in, q1 + s,
+                                      live, steps + 1, s, false, st, nullptr, nullptr, 1);
+            if (e != cudaSuccess) return cuda_fail(e, "batch step launch (32^3 tiles)");
+        }
+    }
+    return SIMPLEX_OK;
+}
 
 int batch_view(simplex_batch_t b, BatchView *out)
 {
@@ -94,6 +113,7 @@ int batch_view(simplex_batch_t b, BatchView *out)
     out->count = b->insts.size();
     out->items = b->items.data();
     out->nitems = b->items.size();
+    out->nitems0 = b->nitems0;
     out->grids_offset = b->off_grids;
     out->grids_bytes = b->bytes - b->off_grids;
     return SIMPLEX_OK;
@@ -120,6 +140,7 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         return fail(SIMPLEX_ENOMEM, "host allocation failed");
     }
     uint64_t grid_off = 0;
+    std::vector<sx::BatchItem> items1;  // items of launch set 1, appended after set 0's
     for (int i = 0; i < count; ++i) {
         const simplex_instance_t &in = instances[i];
         sx::BatchInst &bi = b->insts[i];
@@ -128,10 +149,11 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         if (in.m == 2 && in.block == 64) body = sx::kBody2x64;
         if (in.m == 2 && in.block == 128) body = sx::kBody2x128;
         if (in.m == 3 && in.block == 16) body = sx::kBody3x16;
+        if (in.m == 3 && in.block == 32) body = sx::kBody3x32;
         if (body < 0) {
             delete b;
             return fail(SIMPLEX_EINVAL, "instance %d: the batched engine runs m = 2 with block 64 or 128 and m = 3 "
-                                        "with block 16 (got m = %d, block = %d)", i, in.m, in.block);
+                                        "with block 16 or 32 (got m = %d, block = %d)", i, in.m, in.block);
         }
         const int64_t side = (in.n + 16) / 16 * 16;  // round_up(n + 1, 16)
         int band = 0;
@@ -164,9 +186,12 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += sx::kBatchChunk) {
             const uint64_t cnt = bi.plan.h_blocks - v0 < (uint64_t)sx::kBatchChunk ? bi.plan.h_blocks - v0
                                                                                     : (uint64_t)sx::kBatchChunk;
-            b->items.push_back(sx::BatchItem{(uint32_t)i, (uint32_t)v0, (uint32_t)cnt, 0u});
+            (body == sx::kBody3x32 ? items1 : b->items).push_back(
+                sx::BatchItem{(uint32_t)i, (uint32_t)v0, (uint32_t)cnt, 0u});
         }
     }
+    b->nitems0 = b->items.size();
+    b->items.insert(b->items.end(), items1.begin(), items1.end());
     if (b->items.size() >= 0xffffff00ull) {
         delete b;
         return fail(SIMPLEX_EINVAL, "too many work items (%zu)", b->items.size());
@@ -180,7 +205,7 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
     b->off_tmaps = off;
     off = align_up(off + sizeof(CUtensorMap) * 2ull * (uint64_t)count, 256);
     b->off_queue = off;
-    off = align_up(off + sizeof(unsigned int) * (uint64_t)(sx::kBatchMaxSteps + 1), 256);
+    off = align_up(off + sizeof(unsigned int) * 2ull * (uint64_t)(sx::kBatchMaxSteps + 1), 256);
     b->off_grids = off;
     for (auto &bi : b->insts) {
         bi.grid[0] += off;

@@ -3,7 +3,9 @@
 //   BatchInst[count]        each instance's map, rule and grid offsets
 //   BatchItem[nitems]       the work items (runs of blocks of one instance)
 //   CUtensorMap[2 * count]  TMA maps of each instance's two grids
-//   queue[kBatchMaxSteps+1] work-queue counters, one per pass of a run
+//   queue[2 (kBatchMaxSteps+1)] work-queue counters, one per pass of a run
+//                           and launch (32^3 tiles of m = 3 run in a second
+//                           launch per step)
 //   grids                   two side^m uint8 grids per instance
 #pragma once
 
@@ -20,6 +22,7 @@ enum BatchBody : int32_t {
     kBody2x64 = 0,   // m = 2, 64 x 64 tiles
     kBody2x128 = 1,  // m = 2, 128 x 128 tiles
     kBody3x16 = 2,   // m = 3, 16^3 tiles
+    kBody3x32 = 3,   // m = 3, 32^3 tiles (a launch of its own: 74 KB stage)
 };
 
 constexpr int kBatchThreads = 128;

@@ -23,11 +23,23 @@ namespace sx {
 
 static __device__ uint32_t g_batch_status;
 
-constexpr int kBatchStageBytes = 160 * 130;  // largest box: m = 2, 128 x 128 tiles
+// Launch sets: set 0 runs the m = 2 bodies and the 16^3 body in 20.8 KB of
+// stage (8 CTAs per SM), set 1 the 32^3 body of m = 3 in a 74 KB stage with the
+// 64-byte swizzle (3 CTAs per SM).
+// Set 0 double-buffers its stage: the TMA load of an item's next tile is in
+// flight while the CTA computes the current one.
+constexpr int kBatchStageBytes = 160 * 130;  // largest box of set 0: m = 2, 128 x 128 tiles
+constexpr int kBatchStage3x32 = 64 * 34 * 34;
+__host__ __device__ constexpr int batch_stages(int set) { return set ? 1 : 2; }
+__host__ __device__ constexpr int batch_stage_pitch(int set) { return set ? (kBatchStage3x32 + 511) / 512 * 512 : (kBatchStageBytes + 127) / 128 * 128; }
+__host__ __device__ constexpr int batch_smem(int set) { return batch_stages(set) * batch_stage_pitch(set) + (set ? 512 : 128); }
 
 __device__ __forceinline__ uint32_t body_box_bytes(int body)
 {
-    return body == kBody2x64 ? 96u * 66u : body == kBody2x128 ? 160u * 130u : 48u * 18u * 18u;
+    return body == kBody2x64    ? 96u * 66u
+           : body == kBody2x128 ? 160u * 130u
+           : body == kBody3x16  ? 48u * 18u * 18u
+                                : (uint32_t)kBatchStage3x32;
 }
 
 // Live cells of one tile of grid `g`, read straight from global memory in
@@ -59,25 +71,30 @@ __device__ __forceinline__ uint32_t count_tile(const Plan &p, const int32_t *X, 
     return c_live;
 }
 
-__global__ void __launch_bounds__(kBatchThreads)
+template <int SET>
+__global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
     batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items, uint32_t nitems,
                  const CUtensorMap *__restrict__ tmaps, uint8_t *__restrict__ arena, int in_parity,
                  unsigned int *__restrict__ queue, unsigned long long *__restrict__ live, int live_stride,
                  int live_index, int count_only, unsigned long long *__restrict__ digest,
                  unsigned int *__restrict__ zero_next)
 {
+    constexpr int NST = batch_stages(SET), kPitch = batch_stage_pitch(SET);
     extern __shared__ uint8_t dsmem[];
     __shared__ BatchInst si;
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[NST];
     __shared__ uint32_t red[32];
     __shared__ uint32_t s_item, s_next;
-    __shared__ int s_cur;
-    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
+    __shared__ int s_cur, s_ntiles;
+    __shared__ int4 s_tiles[kBatchChunk];  // the item's tiles with cells: X[0..2], partial
+    constexpr uintptr_t kAlign = SET ? 512 : 128;
+    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + kAlign - 1) & ~(kAlign - 1));
+    // stage s at tile + s * kPitch
     const int tid = threadIdx.x;
-    uint32_t phase = 0;
+    uint32_t phase = 0;  // bit s: parity of stage s's next completion
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        for (int k = 0; k < NST; ++k) mbar_init(&bar[k], 1);
         fence_mbar_init();
         s_cur = -1;
         s_next = atomicAdd(queue, 1u);
@@ -114,61 +131,103 @@ __global__ void __launch_bounds__(kBatchThreads)
         uint8_t *gout = arena + si.grid[par ^ 1];
         uint32_t my_live = 0;
         unsigned long long my_dig = 0;
-        for (uint32_t j = 0; j < item.cnt; ++j) {
-            const uint64_t v = (uint64_t)item.v0 + j;
-            int32_t X[3] = {0, 0, 0};
-            const bool ok = p.m == 2 ? decode<2>(p, kMapH, v, X) : decode<3>(p, kMapH, v, X);
-            if (!ok) continue;
-            const int64_t s0 = tile_base_sum<3>(p, X);  // X[2] = 0 for m = 2
-            if (s0 > p.n) continue;
-            const bool partial = s0 + (int64_t)p.m * (p.rho - 1) > p.n;
-            if (count_only) {
+        if (count_only) {
+            for (uint32_t j = 0; j < item.cnt; ++j) {
+                int32_t X[3] = {0, 0, 0};
+                const uint64_t v = (uint64_t)item.v0 + j;
+                if (!(p.m == 2 ? decode<2>(p, kMapH, v, X) : decode<3>(p, kMapH, v, X))) continue;
+                const int64_t s0 = tile_base_sum<3>(p, X);  // X[2] = 0 for m = 2
+                if (s0 > p.n) continue;
+                const bool partial = s0 + (int64_t)p.m * (p.rho - 1) > p.n;
                 unsigned long long *acc = digest ? &my_dig : nullptr;
                 my_live += p.m == 2 ? count_tile<2>(p, X, gin, partial, acc) : count_tile<3>(p, X, gin, partial, acc);
-                continue;
             }
+        } else if ((si.body == kBody3x32) != (SET == 1)) {  // an item of the other launch set: not run here
+            if (tid == 0) atomicOr(&g_batch_status, 2u);
+        } else {
+            // the item's tiles that hold cells, then a pipelined walk over them
             if (tid == 0) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bar, body_box_bytes(si.body));
-                const CUtensorMap *tm = tmaps + si.tmap + par;
-                if (p.m == 2)
-                    tma_load_2d(tile, tm, X[1] * p.rho - 16, X[0] * p.rho - 1, &bar);
-                else
-                    tma_load_3d(tile, tm, X[2] * p.rho - 16, X[1] * p.rho - 1, X[0] * p.rho - 1, &bar);
-            }
-            const bool done = mbar_wait_bounded(&bar, phase, kWaitLimitNs);
-            phase ^= 1u;
-            if (__syncthreads_or(!done)) {
-                if (tid == 0) {
-                    atomicOr(&g_batch_status, 1u);
-                    mbar_wait_bounded(&bar, phase ^ 1u, kWaitLimitNs);
+                int nt = 0;
+                for (uint32_t j = 0; j < item.cnt; ++j) {
+                    int32_t X[3] = {0, 0, 0};
+                    const uint64_t v = (uint64_t)item.v0 + j;
+                    if (!(p.m == 2 ? decode<2>(p, kMapH, v, X) : decode<3>(p, kMapH, v, X))) continue;
+                    const int64_t s0 = tile_base_sum<3>(p, X);
+                    if (s0 > p.n) continue;
+                    s_tiles[nt++] = make_int4(X[0], X[1], X[2], s0 + (int64_t)p.m * (p.rho - 1) > p.n ? 1 : 0);
                 }
-                return;
+                s_ntiles = nt;
             }
-            const bool ork = si.rule.or_k != 0;
-            switch (si.body) {
-            case kBody2x64:
-                my_live += ork ? ca2_tile<64, 2, true>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 64,
-                                                       (int64_t)X[0] * 64, partial, tid & 3, tid >> 2)
-                               : ca2_tile<64, 2, false>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 64,
-                                                        (int64_t)X[0] * 64, partial, tid & 3, tid >> 2);
-                break;
-            case kBody2x128:
-                my_live += ork ? ca2_tile<128, 8, true>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 128,
-                                                        (int64_t)X[0] * 128, partial, tid & 7, tid >> 3)
-                               : ca2_tile<128, 8, false>(tile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 128,
-                                                         (int64_t)X[0] * 128, partial, tid & 7, tid >> 3);
-                break;
-            default:
-                my_live += ork ? ca3_tile<16, 2, true>(tile, p.n, p.side, si.rule, gout, (int64_t)X[2] * 16,
-                                                       (int64_t)X[1] * 16, (int64_t)X[0] * 16, partial, 0,
-                                                       tid & 15, tid >> 4)
-                               : ca3_tile<16, 2, false>(tile, p.n, p.side, si.rule, gout, (int64_t)X[2] * 16,
-                                                        (int64_t)X[1] * 16, (int64_t)X[0] * 16, partial, 0,
-                                                        tid & 15, tid >> 4);
-                break;
+            __syncthreads();
+            const int nt = s_ntiles;
+            const uint32_t box = body_box_bytes(si.body);
+            const CUtensorMap *tm = tmaps + si.tmap + par;
+            auto issue = [&](int k) {  // thread 0: load tile k into stage k % NST
+                const int st = k % NST;
+                const int4 t = s_tiles[k];
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar[st], box);
+                if (p.m == 2)
+                    tma_load_2d(tile + st * kPitch, tm, t.y * p.rho - 16, t.x * p.rho - 1, &bar[st]);
+                else
+                    tma_load_3d(tile + st * kPitch, tm, t.z * p.rho - 16, t.y * p.rho - 1, t.x * p.rho - 1, &bar[st]);
+            };
+            if (tid == 0)
+                for (int k = 0; k < NST && k < nt; ++k) issue(k);
+            for (int k = 0; k < nt; ++k) {
+                const int st = k % NST;
+                const bool done = mbar_wait_bounded(&bar[st], (phase >> st) & 1u, kWaitLimitNs);
+                phase ^= 1u << st;
+                if (__syncthreads_or(!done)) {
+                    if (tid == 0) {
+                        atomicOr(&g_batch_status, 1u);
+                        // every load still in flight must land before the CTA exits
+                        mbar_wait_bounded(&bar[st], ((phase >> st) & 1u) ^ 1u, kWaitLimitNs);
+                        for (int k2 = k + 1; k2 < nt && k2 < k + NST; ++k2)
+                            mbar_wait_bounded(&bar[k2 % NST], (phase >> (k2 % NST)) & 1u, kWaitLimitNs);
+                    }
+                    return;
+                }
+                const int4 t = s_tiles[k];
+                const int32_t X[3] = {t.x, t.y, t.z};
+                const bool partial = t.w != 0;
+                const uint8_t *stile = tile + st * kPitch;
+                const bool ork = si.rule.or_k != 0;
+                if constexpr (SET == 1) {
+                    const int64_t z0 = (int64_t)X[0] * 32, y0 = (int64_t)X[1] * 32, x0 = (int64_t)X[2] * 32;
+                    my_live += ork ? ca3_tile32<8, true>(stile, p.n, p.side, si.rule, gout, x0, y0, z0, partial,
+                                                         tid & 1, (tid >> 1) & 15, tid >> 5)
+                                   : ca3_tile32<8, false>(stile, p.n, p.side, si.rule, gout, x0, y0, z0, partial,
+                                                          tid & 1, (tid >> 1) & 15, tid >> 5);
+                } else {
+                    switch (si.body) {
+                    case kBody2x64:
+                        my_live += ork ? ca2_tile<64, 2, true>(stile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 64,
+                                                               (int64_t)X[0] * 64, partial, tid & 3, tid >> 2)
+                                       : ca2_tile<64, 2, false>(stile, p.n, p.side, si.rule, gout, (int64_t)X[1] * 64,
+                                                                (int64_t)X[0] * 64, partial, tid & 3, tid >> 2);
+                        break;
+                    case kBody2x128:
+                        my_live += ork ? ca2_tile<128, 8, true>(stile, p.n, p.side, si.rule, gout,
+                                                                (int64_t)X[1] * 128, (int64_t)X[0] * 128, partial,
+                                                                tid & 7, tid >> 3)
+                                       : ca2_tile<128, 8, false>(stile, p.n, p.side, si.rule, gout,
+                                                                 (int64_t)X[1] * 128, (int64_t)X[0] * 128, partial,
+                                                                 tid & 7, tid >> 3);
+                        break;
+                    default:
+                        my_live += ork ? ca3_tile<16, 2, true>(stile, p.n, p.side, si.rule, gout, (int64_t)X[2] * 16,
+                                                               (int64_t)X[1] * 16, (int64_t)X[0] * 16, partial, 0,
+                                                               tid & 15, tid >> 4)
+                                       : ca3_tile<16, 2, false>(stile, p.n, p.side, si.rule, gout,
+                                                                (int64_t)X[2] * 16, (int64_t)X[1] * 16,
+                                                                (int64_t)X[0] * 16, partial, 0, tid & 15, tid >> 4);
+                        break;
+                    }
+                }
+                __syncthreads();  // stage st fully read before it is loaded again
+                if (tid == 0 && k + NST < nt) issue(k + NST);
             }
-            __syncthreads();  // the staged box is fully read before the next load
         }
         if (live)
             block_add_u64(live + (uint64_t)item.inst * live_stride + live_index + (item.tag >> 1), my_live, red);
@@ -189,46 +248,54 @@ cudaError_t batch_prepare()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchStageBytes + 128);
+    e = cudaFuncSetAttribute(batch_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem(0));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem(1));
     if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
     return e;
 }
 
-// Resident CTAs of the persistent launch on the current device (SM count x
-// occupancy), looked up once per device.
-cudaError_t batch_resident_ctas(uint64_t *out)
+// Resident CTAs of the persistent launch of set `set` on the current device
+// (SM count x occupancy), looked up once per device.
+cudaError_t batch_resident_ctas(uint64_t *out, int set)
 {
-    static uint64_t cached[64] = {};
+    static uint64_t cached[2][64] = {};
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64 && cached[dev]) {
-        *out = cached[dev];
+    set = set ? 1 : 0;
+    if (dev >= 0 && dev < 64 && cached[set][dev]) {
+        *out = cached[set][dev];
         return cudaSuccess;
     }
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads,
-                                                           kBatchStageBytes + 128)) != cudaSuccess)
-        return e;
+    e = set ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<1>, kBatchThreads, batch_smem(1))
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<0>, kBatchThreads, batch_smem(0));
+    if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     *out = (uint64_t)sms * (uint64_t)per_sm;
-    if (dev >= 0 && dev < 64) cached[dev] = *out;
+    if (dev >= 0 && dev < 64) cached[set][dev] = *out;
     return cudaSuccess;
 }
 
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
-                              cudaStream_t st, unsigned long long *digest, unsigned int *zero_next)
+                              cudaStream_t st, unsigned long long *digest, unsigned int *zero_next, int set)
 {
     cudaError_t e = batch_prepare();
     if (e != cudaSuccess) return e;
+    set = (set && !count_only) ? 1 : 0;
     uint64_t g = 0;
-    if ((e = batch_resident_ctas(&g)) != cudaSuccess) return e;  // persistent: every CTA resident
+    if ((e = batch_resident_ctas(&g, set)) != cudaSuccess) return e;  // persistent: every CTA resident
     if (g > nitems) g = nitems ? nitems : 1;
-    batch_kernel<<<(unsigned)g, kBatchThreads, kBatchStageBytes + 128, st>>>(
-        insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0,
-        digest, zero_next);
+    if (set)
+        batch_kernel<1><<<(unsigned)g, kBatchThreads, batch_smem(1), st>>>(
+            insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, 0, digest, zero_next);
+    else
+        batch_kernel<0><<<(unsigned)g, kBatchThreads, batch_smem(0), st>>>(
+            insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0,
+            digest, zero_next);
     return cudaGetLastError();
 }
 
@@ -303,7 +370,7 @@ extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, u
     const uint64_t off_items = up(sizeof(sx::BatchInst) * bv.count);
     const uint64_t off_tmaps = up(off_items + sizeof(sx::BatchItem) * bv.nitems);
     const uint64_t off_queue = up(off_tmaps + sizeof(CUtensorMap) * 2 * bv.count);
-    const uint64_t need = off_queue + sizeof(unsigned int) * (uint64_t)(steps + 1);
+    const uint64_t need = off_queue + sizeof(unsigned int) * 2 * (uint64_t)(steps + 1);
     if (need > sx::kStaticScratchBytes)
         return fail(SIMPLEX_EINVAL,
                     "batch too large for the fixed scratch: needs %llu bytes of descriptors, work items and "
@@ -322,7 +389,7 @@ extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, u
             cudaSuccess ||
         (e = cudaMemcpyAsync(scratch + off_items, bv.items, sizeof(sx::BatchItem) * bv.nitems,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * (size_t)(steps + 1), st)) != cudaSuccess)
+        (e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * 2 * (size_t)(steps + 1), st)) != cudaSuccess)
         return cuda_fail(e, "filling the static batch scratch");
     // TMA maps of the caller's grids, encoded in a fixed host buffer and copied
     // in pieces (a copy from pageable memory has read its source on return)
@@ -340,19 +407,11 @@ extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, u
     const sx::BatchInst *insts = reinterpret_cast<const sx::BatchInst *>(scratch);
     const sx::BatchItem *items = reinterpret_cast<const sx::BatchItem *>(scratch + off_items);
     const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(scratch + off_tmaps);
-    const uint32_t nitems = (uint32_t)bv.nitems;
-    if (live) {
-        if ((e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * bv.count * (size_t)(steps + 1), st)) !=
-            cudaSuccess)
-            return cuda_fail(e, "cudaMemsetAsync(live)");
-        if ((e = sx::launch_batch_pass(insts, items, nitems, tm, base, parity, queue, live, steps + 1, 0, true,
-                                       st)) != cudaSuccess)
-            return cuda_fail(e, "batch count launch");
-    }
-    for (int s = 1; s <= steps; ++s) {
-        if ((e = sx::launch_batch_pass(insts, items, nitems, tm, base, (parity + s - 1) & 1, queue + s, live,
-                                       steps + 1, s, false, st)) != cudaSuccess)
-            return cuda_fail(e, "batch step launch");
-    }
+    if (live &&
+        (e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * bv.count * (size_t)(steps + 1), st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync(live)");
+    rc = enqueue_batch_passes(insts, items, bv.nitems, bv.nitems0, tm, base, queue, queue + steps + 1, steps, live,
+                              parity, st);
+    if (rc) return rc;
     return SIMPLEX_OK;
 }

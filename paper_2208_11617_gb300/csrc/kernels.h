@@ -57,14 +57,16 @@ cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
 // work-queue counters of a later round that this pass sets to zero (they must
 // not be in use).
 cudaError_t batch_prepare();
+// `set` 1 runs the items of 32^3 tiles of m = 3 (kBody3x32), set 0 every other
+// body; a count pass (count_only) runs any item in set 0.
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
                               cudaStream_t st, unsigned long long *digest = nullptr,
-                              unsigned int *zero_next = nullptr);
+                              unsigned int *zero_next = nullptr, int set = 0);
 cudaError_t batch_read_status(uint32_t *out);
-// CTAs of the batched kernel resident at once on the current device (SMs x occupancy).
-cudaError_t batch_resident_ctas(uint64_t *out);
+// CTAs of the batched kernel's launch set resident at once on the current device (SMs x occupancy).
+cudaError_t batch_resident_ctas(uint64_t *out, int set = 0);
 
 // Device error words of the TMA kernels (bounded waits that gave up).
 // Reads and clears; synchronous.

@@ -34,7 +34,7 @@ def test_batch_counts_and_layout():
     assert info["arena_bytes"] >= grids
 
 
-@pytest.mark.parametrize("bad", [_inst(2, 100, 32), _inst(3, 63, 32), _inst(4, 31, 16), _inst(2, -1, 64),
+@pytest.mark.parametrize("bad", [_inst(2, 100, 32), _inst(3, 63, 64), _inst(3, 63, 8), _inst(4, 31, 16), _inst(2, -1, 64),
                                  _inst(3, 63, 16, beta=4)])
 def test_batch_rejects_unsupported_instances(bad):
     with pytest.raises(sx.SimplexError) as ei:

@@ -25,7 +25,11 @@ MIXED = [
     _inst(3, 0, 16, seed=9), _inst(3, 20, 16, seed=10, p=0.3), _inst(3, 63, 16, seed=11, p=0.3),
     _inst(3, 100, 16, beta=3, seed=12, p=0.3), _inst(3, 150, 16, rule=(1 << 4, 1 << 2 | 1 << 3 | 1 << 4), seed=13),
     _inst(2, 4095, 128, seed=14), _inst(3, 255, 16, seed=15, p=0.3),
+    _inst(3, 0, 32, seed=16), _inst(3, 31, 32, seed=17, p=0.3), _inst(3, 100, 32, beta=3, seed=18, p=0.3),
+    _inst(3, 200, 32, seed=19, p=0.3), _inst(3, 150, 32, rule=(1 << 4, 1 << 2 | 1 << 3 | 1 << 4), seed=20),
 ]
+
+ONLY32 = [_inst(3, 64, 32, seed=21, p=0.3), _inst(3, 255, 32, seed=22, p=0.3), _inst(3, 17, 32, seed=23)]
 
 
 def _logical(t, n):
@@ -49,6 +53,24 @@ def test_mixed_batch_matches_oracle(use_graph):
             np.testing.assert_array_equal(_logical(g, d["n"]), ref, err_msg=f"instance {i}")
             np.testing.assert_array_equal(live[i], ref_live, err_msg=f"instance {i} live")
             refs[i] = ref
+    assert sx.simplex_device_status() == 0
+
+
+def test_batch_of_32_cubed_tiles_only_matches_oracle():
+    """A batch whose every instance runs in the second launch set (32^3 tiles)."""
+    b = sx.simplex_batch_create(ONLY32)
+    sx.simplex_batch_bind(b)
+    sx.simplex_batch_init(b)
+    steps = 4
+    live = torch.zeros(len(ONLY32) * (steps + 1), dtype=torch.int64, device="cuda")
+    sx.simplex_batch_run(b, steps, live)
+    torch.cuda.synchronize()
+    live = live.view(len(ONLY32), steps + 1).cpu().numpy().astype(np.uint64)
+    for i, d in enumerate(ONLY32):
+        ref, ref_live = oracle.ca_run(d["m"], d["n"], steps, d["birth"], d["survive"],
+                                      oracle.ca_init(d["m"], d["n"], d["seed"], d["threshold"]))
+        np.testing.assert_array_equal(_logical(sx.simplex_batch_grid(b, i, d["m"]), d["n"]), ref)
+        np.testing.assert_array_equal(live[i], ref_live)
     assert sx.simplex_device_status() == 0
 
 

@@ -29,7 +29,8 @@ def _inst(m, n, block, beta=2, seed=0, p=0.5, rule=None):
 
 INSTANCES = [_inst(2, 1000, 64, seed=1), _inst(2, 2047, 128, seed=2), _inst(2, 37, 64, seed=3),
              _inst(3, 120, 16, seed=4, p=0.3), _inst(3, 63, 16, beta=3, seed=5, p=0.3),
-             _inst(2, 300, 64, seed=6, rule=(1 << 3 | 1 << 6, 1 << 2 | 1 << 3))]
+             _inst(2, 300, 64, seed=6, rule=(1 << 3 | 1 << 6, 1 << 2 | 1 << 3)),
+             _inst(3, 150, 32, seed=7, p=0.3)]
 
 
 def test_static_scratch_run_matches_arena_run_twice():
