@@ -107,19 +107,28 @@ __global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
 // once per run instead of each tile reading a box with 16-byte x halos on both
 // sides (3 sectors of 32 bytes per 32-byte row).
 //
-// Warp 8 (one lane) is the producer: it fetches units, and TMA-loads their
-// columns in order into a ring of kStreamSlots stages, writing the run into
-// the stage's meta entry first (full[s] counts the bytes; empty[s] takes one
-// arrival per consumer warp when the stage may be refilled).  After the last
-// unit it publishes an end marker (a > b) with a plain arrival.  Warps 0-7
-// are the consumers: column c of the sequence is the centre of one tile, with
-// c - 1 and c + 1 its neighbours; after a tile they release its left column,
-// after a run's last tile the last two.  Every wait is bounded; a timeout sets
-// the status word and an abort flag that stops both sides, and the producer
-// then waits (bounded) for the loads it issued before the CTA exits.  The
-// last CTA to finish puts the work counter back to zero for the next launch.
+// The last warp (one lane) is the producer.  Per run it first publishes a
+// header (the run and the sequence number of its first column) in a ring of
+// kStreamHeaders entries (hfull: one plain arrival; hempty: one arrival per
+// consumer warp once it has read the header), then TMA-loads the run's columns
+// in order into a ring of kStreamSlots stages (full: the bytes; empty: see
+// below).  After the last unit it publishes an end header (a > b).
+// The consumers form kStreamGroups groups of 4 warps; group g takes the tiles
+// g, g + G, ... of the CTA's tile sequence, so G tiles are computed at once,
+// each by 4 warps walking 8 planes per thread.  Column c of a run is the
+// centre of tile c and a neighbour of tiles c - 1 and c + 1: every column has
+// exactly three uses (a tile at a run's end also performs the uses of the
+// tiles missing beyond it), so empty completes after 3 x 4 warp arrivals,
+// when every tile reading the column is done; a column is never refilled while
+// a group that has not reached its tile still needs it.  Every wait is
+// bounded; a timeout sets the status word and an abort flag that stops both
+// sides, and the producer then waits (bounded) for the loads it issued before
+// the CTA exits.  The last CTA to finish puts the work counter back to zero.
 constexpr int kStreamSlots = 6;
-constexpr int kStreamConsumers = 256;  // 2 chunks x 16 row pairs x 8 runs of 4 planes
+constexpr int kStreamHeaders = 8;
+constexpr int kStreamGroups = 2;
+constexpr int kStreamGroupWarps = 4;  // 2 chunks x 16 row pairs x 4 runs of 8 planes
+constexpr int kStreamConsumers = kStreamGroups * kStreamGroupWarps * 32;
 constexpr int kStreamThreads = kStreamConsumers + 32;
 constexpr uint32_t kColBytes = 32u * 34u * 34u;  // 36,992 = 289 x 128
 constexpr int kStreamSmem = kStreamSlots * (int)kColBytes + 128;
@@ -130,10 +139,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     const Rule rule, int kind, uint64_t units, unsigned long long *__restrict__ live,
                     unsigned long long *__restrict__ queue)
 {
-    constexpr int S = kStreamSlots;
+    constexpr int S = kStreamSlots, HN = kStreamHeaders, G = kStreamGroups;
     extern __shared__ uint8_t dsmem[];
-    __shared__ __align__(8) uint64_t full[S], empty[S];
-    __shared__ int4 meta[S];  // run of the staged column: X1, X2, a, b (a > b: no more work)
+    __shared__ __align__(8) uint64_t full[S], empty[S], hfull[HN], hempty[HN];
+    __shared__ int4 hdr[HN];             // X1, X2, a, b of the run (a > b: no more work)
+    __shared__ unsigned long long hseq[HN];  // sequence number of the run's first column
     __shared__ uint32_t red[32];
     __shared__ volatile int abort_flag;
     uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
@@ -144,7 +154,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         prefetch_tmap(&tcol);
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kStreamConsumers / 32);
+            mbar_init(&empty[s], 3 * kStreamGroupWarps);
+        }
+        for (int h = 0; h < HN; ++h) {
+            mbar_init(&hfull[h], 1);
+            mbar_init(&hempty[h], G * kStreamGroupWarps);
         }
         fence_mbar_init();
         abort_flag = 0;
@@ -154,74 +168,83 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     if (warp == kStreamConsumers / 32) {
         // producer
         if (lane == 0) {
-            uint64_t seq = 0;
-            // stage for sequence number seq, once the consumers released its last use
-            auto acquire = [&](int &s) {
-                s = (int)(seq % S);
-                if (seq < (uint64_t)S) return true;
-                return mbar_wait_bounded(&empty[s], (uint32_t)((seq / S - 1) & 1), kWaitLimitNs);
-            };
+            uint64_t seq = 0, nh = 0;
             bool ok = true;
+            auto header = [&](int4 r) {  // publish header nh
+                const int h = (int)(nh % HN);
+                if (nh >= (uint64_t)HN &&
+                    !mbar_wait_bounded(&hempty[h], (uint32_t)((nh / HN - 1) & 1), kWaitLimitNs))
+                    return false;
+                hdr[h] = r;
+                hseq[h] = seq;
+                ++nh;
+                mbar_arrive(&hfull[h]);
+                return true;
+            };
             while (ok) {
                 const uint64_t w = atomicAdd(&queue[0], 1ull);
                 if (w >= units) break;
                 XRun r;
                 if (!xrun_decode(p, kind, w, r)) continue;
+                if (!(ok = header(make_int4(r.X1, r.X2, r.a, r.b)))) break;
                 for (int32_t c = r.a - 1; c <= r.b + 1; ++c, ++seq) {
-                    int s;
-                    if (!(ok = acquire(s))) break;
-                    meta[s] = make_int4(r.X1, r.X2, r.a, r.b);
+                    const int s = (int)(seq % S);
+                    if (seq >= (uint64_t)S &&
+                        !(ok = mbar_wait_bounded(&empty[s], (uint32_t)((seq / S - 1) & 1), kWaitLimitNs)))
+                        break;
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(&full[s], kColBytes);
                     tma_load_3d(ring + s * kColBytes, &tcol, c * 32, r.X2 * 32 - 1, r.X1 * 32 - 1, &full[s]);
                 }
             }
             issued = seq;
-            int s;
-            if (ok && (ok = acquire(s))) {
-                meta[s] = make_int4(0, 0, 1, 0);
-                mbar_arrive(&full[s]);
-            }
+            if (ok) ok = header(make_int4(0, 0, 1, 0));
             if (!ok) abort_flag = 1;
         }
     } else {
         // consumers
-        const int tx = lane & 1, pr = lane >> 1, tz = warp;
-        uint64_t seq = 0;  // sequence number of the next run's first column
+        const int grp = warp / kStreamGroupWarps, tz = warp % kStreamGroupWarps;
+        const int tx = lane & 1, pr = lane >> 1;
+        uint64_t nh = 0;
+        uint32_t t0 = 0;  // tiles of the sequence before the current run
         for (;;) {
-            if (abort_flag || !mbar_wait_bounded(&full[seq % S], (uint32_t)((seq / S) & 1), kWaitLimitNs)) {
+            const int h = (int)(nh % HN);
+            if (abort_flag || !mbar_wait_bounded(&hfull[h], (uint32_t)((nh / HN) & 1), kWaitLimitNs)) {
                 abort_flag = 1;
                 break;
             }
-            const int4 r = meta[seq % S];
-            if (r.z > r.w) break;  // end marker
+            const int4 r = hdr[h];
+            const uint64_t seq = hseq[h];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&hempty[h]);
+            ++nh;
+            if (r.z > r.w) break;  // end header
             const int64_t z0 = (int64_t)r.x * 32, y0 = (int64_t)r.y * 32;
             bool ok = true;
-            for (int32_t x3 = r.z; x3 <= r.w; ++x3) {
-                const uint64_t c = seq + (uint64_t)(x3 - r.z) + 1;
-                // column c - 1 (and c) were awaited already: by the run start or the previous tile
-                for (uint64_t q = (x3 == r.z ? c : c + 1); q <= c + 1 && ok; ++q)
+            const int32_t first = r.z + (int32_t)((uint32_t)(grp - (int)(t0 % G) + G) % G);
+            for (int32_t x3 = first; x3 <= r.w && ok; x3 += G) {
+                const uint64_t c = seq + (uint64_t)(x3 - r.z) + 1;  // centre column of this tile
+                for (uint64_t q = c - 1; q <= c + 1 && ok; ++q)
                     ok = !abort_flag && mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
                 if (!ok) break;
                 const int64_t x0 = (int64_t)x3 * 32;
                 const bool partial = z0 + y0 + x0 + 3 * 31 > p.n;
-                my_live += ca3_tile32c<4, ORK>(ring + (c % S) * kColBytes, ring + ((c - 1) % S) * kColBytes,
+                my_live += ca3_tile32c<8, ORK>(ring + (c % S) * kColBytes, ring + ((c - 1) % S) * kColBytes,
                                                ring + ((c + 1) % S) * kColBytes, x3 > 0, x0 + 32 <= p.n, p.n, p.side,
                                                rule, out, x0, y0, z0, partial, tx, pr, tz);
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[(c - 1) % S]);
+                if (lane == 0) {
+                    const bool fst = x3 == r.z, lst = x3 == r.w;
+                    mbar_arrive_n(&empty[(c - 1) % S], fst ? 3u : 1u);
+                    mbar_arrive_n(&empty[c % S], 1u + (fst ? 1u : 0u) + (lst ? 1u : 0u));
+                    mbar_arrive_n(&empty[(c + 1) % S], lst ? 3u : 1u);
+                }
             }
             if (!ok) {
                 abort_flag = 1;
                 break;
             }
-            const uint64_t last = seq + (uint64_t)(r.w - r.z) + 1;
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&empty[last % S]);
-                mbar_arrive(&empty[(last + 1) % S]);
-            }
-            seq = last + 2;
+            t0 += (uint32_t)(r.w - r.z + 1);
         }
     }
     __syncthreads();
