@@ -94,18 +94,36 @@ __global__ void __launch_bounds__(RHO * RHO / 4)
     // (the points are a few hundred KB: L1 and L2 hits after the first touch)
     const float *a = pts + x1 * dim;
     float d[4];
+    if (DIM > 0 && (!partial || valid >= 4)) {
+        // all four j exist: point j0 - c sits c * DIM floats below point j0
+        float ai[DIM > 0 ? DIM : 1];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int64_t j = p.n - x2 - c;
-        const float *b = pts + (j >= 0 ? j : 0) * dim;
-        float acc = 0.f;
+        for (int k = 0; k < DIM; ++k) ai[k] = __ldg(a + k);
+        const float *b0 = pts + (p.n - x2) * DIM;
 #pragma unroll
-        for (int k = 0; k < (DIM > 0 ? DIM : kEdmMaxDim); ++k) {
-            if (DIM == 0 && k >= dim) break;
-            const float df = __fsub_rn(__ldg(a + k), __ldg(b + k));
-            acc = __fadd_rn(acc, __fmul_rn(df, df));
+        for (int c = 0; c < 4; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                const float df = __fsub_rn(ai[k], __ldg(b0 - c * DIM + k));
+                acc = __fadd_rn(acc, __fmul_rn(df, df));
+            }
+            d[c] = __fsqrt_rn(acc);
         }
-        d[c] = __fsqrt_rn(acc);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t j = p.n - x2 - c;
+            const float *b = pts + (j >= 0 ? j : 0) * dim;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < (DIM > 0 ? DIM : kEdmMaxDim); ++k) {
+                if (DIM == 0 && k >= dim) break;
+                const float df = __fsub_rn(__ldg(a + k), __ldg(b + k));
+                acc = __fadd_rn(acc, __fmul_rn(df, df));
+            }
+            d[c] = __fsqrt_rn(acc);
+        }
     }
     float *dst = out + x1 * p.side + x2;
     if (vec && (!partial || valid >= 4)) {
