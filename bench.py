@@ -762,7 +762,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override n (smaller case of the workload)")
     ap.add_argument("--block", type=int, default=None, help="override the tile side")
     ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
-    ap.add_argument("--launch", type=int, default=0, help="automaton step form: 0 auto, 1 grid, 2 persistent")
+    ap.add_argument("--launch", type=int, default=0, help="automaton step form: 0 auto, 1 grid, 2 x-stream (m = 3)")
     ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")
     ap.add_argument("--layout", type=int, default=0,
                     help="m = 3 H3 layout: 0 packed grid (Sec. 4.3), 1 one block range per stack level")

@@ -67,7 +67,7 @@ typedef struct simplex_map_info {
     int32_t log2N;
     int32_t band;           /* m = 2 trapezoid band height in tiles; 0 = single H2 grid */
     int32_t Ne;             /* m = 2 trapezoid form: block-triangle side (multiple of band) */
-    int32_t launch;         /* automaton step form: 1 grid, 2 persistent */
+    int32_t launch;         /* automaton step form: 1 grid, 2 x-stream (persistent) */
     int32_t layout;         /* m = 3, beta = 2: 0 packed grid, 1 one block range per level */
     uint64_t cells;         /* C(n+m, m), Eq. 1 */
     uint64_t useful_blocks; /* tiles holding at least one cell: C(floor(n/rho)+m, m) */
@@ -107,7 +107,7 @@ typedef struct simplex_map_params {
     int64_t n;
     int64_t side;                  /* array side, >= n + 1; 0 means n + 1 */
     int32_t band;                  /* m = 2 only, see below; must be 0 or -1 for m > 2 */
-    int32_t launch;                /* automaton step: 0 automatic, 1 grid, 2 persistent (see below) */
+    int32_t launch;                /* automaton step: 0 automatic, 1 grid, 2 x-stream (see below) */
     int32_t layout;                /* m = 3, beta = 2: 0 packed grid, 1 one range per level (see below) */
 } simplex_map_params_t;
 
@@ -127,11 +127,16 @@ typedef struct simplex_map_params {
  * `launch` selects how simplex_ca_step runs the map's blocks:
  *   1 (grid): one CUDA block per block of the map, the paper's execution
  *     model (Sec. 2): the grid of a launch is the map's parallel space;
- *   2 (persistent): one CTA per SM walks the map's blocks in the same order
- *     through a ring of shared-memory stages, with TMA loads for the next
- *     tiles in flight while it computes the current one (m = 3, block 32);
- *   0 (automatic): grid (the faster form on GB300 for every tile size
- *     implemented so far).
+ *   2 (x-stream, m = 3 with block 32): one persistent CTA per SM takes runs
+ *     of up to 16 tiles along x3 from a device work counter; the tile columns
+ *     (x1, x2) of the runs are enumerated by Eq. map2d over the triangle
+ *     x1 + x2 <= N - 1 (the bounding box: the N x N square).  The CTA streams
+ *     each run's 32-byte-wide x-columns through a ring of TMA stages, so a
+ *     column is read once per run; the map's per-tile blocks of modes H and
+ *     BB become per-run work units.  The map keeps a 16-byte work counter in
+ *     device memory, allocated on first use: steps of one map must not run
+ *     concurrently on different streams.
+ *   0 (automatic): grid.
  * `layout` (m = 3, beta = 2 only) selects how H3 lays out its cubes:
  *   0: the single packed grid of Sec. 4.3: the big cube (N/2)^3 and one layer
  *     of height N/4 holding every smaller cube, whose blocks past the cube's

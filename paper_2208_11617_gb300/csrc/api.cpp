@@ -308,7 +308,7 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
     if (!params || !out) return fail(SIMPLEX_EINVAL, "params and out must not be NULL");
     *out = nullptr;
     if (params->launch < 0 || params->launch > 2)
-        return fail(SIMPLEX_EINVAL, "params->launch must be 0 (automatic), 1 (grid) or 2 (persistent), got %d",
+        return fail(SIMPLEX_EINVAL, "params->launch must be 0 (automatic), 1 (grid) or 2 (x-stream), got %d",
                     params->launch);
     const int64_t side = params->side ? params->side : params->n + 1;
     int band = params->band;
@@ -321,11 +321,11 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
     int rc = build_plan(params->m, params->n, params->r_inv, params->beta, params->block, side, band, &p,
                         params->layout);
     if (rc == SIMPLEX_OK) {
-        // automatic: the grid form (measured faster on GB300 for every tile
-        // size implemented); the persistent form on request (m = 3, block 32)
+        // automatic: the grid form (one CTA per block of the map, the paper's
+        // model); the x-stream form on request (m = 3, block 32)
         const bool can_persist = p.m == 3 && p.rho == 32;
         if (params->launch == 2 && !can_persist)
-            return fail(SIMPLEX_EUNSUPPORTED, "the persistent automaton step exists for m = 3, block 32");
+            return fail(SIMPLEX_EUNSUPPORTED, "the x-stream automaton step exists for m = 3, block 32");
         p.persistent = params->launch == 2 ? 1 : 0;
     }
     if (rc) return rc;

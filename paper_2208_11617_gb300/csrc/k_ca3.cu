@@ -13,7 +13,9 @@
 // For RHO = 32 the staged rows are 64 bytes and the tensor map uses the 64-byte
 // swizzle (16-byte unit u of staged row R sits at u ^ ((R >> 1) & 3)); each
 // thread owns two output rows (ca3_tile32) and the lanes of one 16-byte load
-// instruction spread over all shared-memory banks.
+// instruction spread over all shared-memory banks.  The file also holds the
+// x-stream form (ca3_step_stream, launch 2): persistent CTAs that stream runs
+// of tiles along x3 through a ring of 32-byte-wide x-columns.
 #include "ca_tiles.cuh"
 #include "common.cuh"
 #include "hmap.cuh"

@@ -234,8 +234,8 @@ def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, 
     """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4).
 
     band (m = 2): None/0 automatic trapezoid bands, > 0 band height, -1 the
-    single grid of Eq. map2d.  launch: 0 automatic, 1 grid, 2 persistent
-    automaton step.  layout (m = 3, beta = 2): 0 packed grid, 1 one block
+    single grid of Eq. map2d.  launch: 0 automatic, 1 grid, 2 x-stream
+    (persistent) automaton step for m = 3, block 32.  layout (m = 3, beta = 2): 0 packed grid, 1 one block
     range per stack level."""
     if beta is None:
         beta = 2 if m <= 3 else m

@@ -211,7 +211,8 @@ def test_write_h2_forms_match_oracle(band):
 @pytest.mark.parametrize("n,side,beta", [(255, None, 2), (200, 208, 2), (255, None, 3), (31, 32, 2), (1, 16, 2)])
 def test_ca3_grid_and_persistent_forms_match_oracle(launch, mode, n, side, beta):
     """The m = 3 step in both launch forms (one CTA per block of the map, and
-    persistent CTAs with a TMA stage ring) gives the oracle's grid."""
+    the x-stream form: persistent CTAs streaming runs of tiles along x3
+    through a ring of x-columns) gives the oracle's grid."""
     mp = sx.simplex_map_create(3, n, 2, beta, 32, side=side, launch=launch)
     assert mp.info.launch == launch
     thr = inputs.bernoulli_threshold(0.3)
