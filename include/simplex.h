@@ -403,8 +403,9 @@ int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t gri
  * Jobs -- an automaton on an m-simplex of size n for a number of steps --
  * arrive over time.  The server keeps each admitted job's two grids resident
  * in a device pool capped by an HBM budget and works in rounds: one round is
- * ONE launch of the batched persistent kernel that advances every resident
- * job by one step, whatever step each is at.  Between rounds it admits
+ * round_steps launches of the batched persistent kernel, each advancing every
+ * resident job that still has steps left by one step, whatever step each is
+ * at.  Between rounds it admits
  * arrived jobs first come first served as soon as a job slot, pool memory and
  * room in the round's work list (max_items) are free, and retires finished jobs: their live count after every step and
  * a digest of their final grid are copied to host memory and their memory
@@ -420,6 +421,7 @@ typedef struct simplex_server_params {
     int32_t max_items;       /* map blocks of all resident jobs together, >= 1024 (a round's
                                 work items hold 1..8 blocks: fewer when the round is light) */
     int32_t max_inflight;    /* rounds the host may queue ahead of the GPU (1..64) */
+    int32_t round_steps;     /* automaton steps per round, 1..16; 0 means 8 */
 } simplex_server_params_t;
 
 typedef struct simplex_job {

@@ -94,12 +94,12 @@ int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items,
         const int in = (parity + s - 1) & 1;
         if (nitems0) {
             e = sx::launch_batch_pass(insts, items, (uint32_t)nitems0, tmaps, arena, in, q0 + s, live, steps + 1, s,
-                                      false, st, nullptr, nullptr, 0);
+                                      false, st, nullptr, 0);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
         }
         if (nitems > nitems0) {
             e = sx::launch_batch_pass(insts, items + nitems0, (uint32_t)(nitems - nitems0), tmaps, arena, in, q1 + s,
-                                      live, steps + 1, s, false, st, nullptr, nullptr, 1);
+                                      live, steps + 1, s, false, st, nullptr, 1);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch (32^3 tiles)");
         }
     }

@@ -76,8 +76,7 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
     batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items, uint32_t nitems,
                  const CUtensorMap *__restrict__ tmaps, uint8_t *__restrict__ arena, int in_parity,
                  unsigned int *__restrict__ queue, unsigned long long *__restrict__ live, int live_stride,
-                 int live_index, int count_only, unsigned long long *__restrict__ digest,
-                 unsigned int *__restrict__ zero_next)
+                 int live_index, int count_only, unsigned long long *__restrict__ digest, int pass)
 {
     constexpr int NST = batch_stages(SET), kPitch = batch_stage_pitch(SET);
     extern __shared__ uint8_t dsmem[];
@@ -98,10 +97,6 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
         fence_mbar_init();
         s_cur = -1;
         s_next = atomicAdd(queue, 1u);
-        if (zero_next && blockIdx.x == 0) {  // a later round's pair of counters, idle now
-            zero_next[0] = 0u;
-            zero_next[1] = 0u;
-        }
     }
     __syncthreads();
 
@@ -114,6 +109,13 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
         const uint32_t it = s_item;
         if (it >= nitems) break;
         const BatchItem item = items[it];
+        // item.tag: bit 0 flips the input grid, bits 1..12 offset the live-count
+        // index, bits 13..16 + 1 = passes the item takes part in (pass p of a
+        // multi-step launch sequence reads grid parity ^ p and counts at index + p)
+        if ((uint32_t)pass > ((item.tag >> 13) & 15u)) {  // uniform: the job has no step left in this pass
+            __syncthreads();  // s_item is read by every thread before thread 0 pops the next item
+            continue;
+        }
         if ((int)item.inst != s_cur) {
             // load the instance description into shared memory (all threads)
             const uint32_t *src = reinterpret_cast<const uint32_t *>(insts + item.inst);
@@ -122,11 +124,11 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
             __syncthreads();
             if (tid == 0) {
                 s_cur = (int)item.inst;
-                if (!count_only) prefetch_tmap(tmaps + si.tmap + (in_parity ^ (int)(item.tag & 1u)));
+                if (!count_only) prefetch_tmap(tmaps + si.tmap + (in_parity ^ (int)((item.tag ^ (uint32_t)pass) & 1u)));
             }
         }
         const Plan &p = si.plan;
-        const int par = in_parity ^ (int)(item.tag & 1u);
+        const int par = in_parity ^ (int)((item.tag ^ (uint32_t)pass) & 1u);
         const uint8_t *gin = arena + si.grid[par];
         uint8_t *gout = arena + si.grid[par ^ 1];
         uint32_t my_live = 0;
@@ -230,7 +232,8 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
             }
         }
         if (live)
-            block_add_u64(live + (uint64_t)item.inst * live_stride + live_index + (item.tag >> 1), my_live, red);
+            block_add_u64(live + (uint64_t)item.inst * live_stride + live_index + ((item.tag >> 1) & 0xfffu) + pass,
+                          my_live, red);
         if (digest) {
             unsigned long long w = my_dig;
 #pragma unroll
@@ -281,7 +284,7 @@ cudaError_t batch_resident_ctas(uint64_t *out, int set)
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
-                              cudaStream_t st, unsigned long long *digest, unsigned int *zero_next, int set)
+                              cudaStream_t st, unsigned long long *digest, int set, int pass)
 {
     cudaError_t e = batch_prepare();
     if (e != cudaSuccess) return e;
@@ -291,11 +294,11 @@ cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, ui
     if (g > nitems) g = nitems ? nitems : 1;
     if (set)
         batch_kernel<1><<<(unsigned)g, kBatchThreads, batch_smem(1), st>>>(
-            insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, 0, digest, zero_next);
+            insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, 0, digest, pass);
     else
         batch_kernel<0><<<(unsigned)g, kBatchThreads, batch_smem(0), st>>>(
             insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0,
-            digest, zero_next);
+            digest, pass);
     return cudaGetLastError();
 }
 

@@ -53,17 +53,16 @@ cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
 
 // Batched engine: one persistent pass (count_only: live counts of the input
 // grids, plus a result digest when `digest` is given; else one automaton step
-// in -> out) over every work item.  `zero_next`, when given, points to two
-// work-queue counters of a later round that this pass sets to zero (they must
-// not be in use).
+// in -> out) over every work item.  `set` 1 runs the items of 32^3 tiles of
+// m = 3 (kBody3x32), set 0 every other body; a count pass runs any item in set
+// 0.  `pass` p > 0 is step p of a sequence launched over the same items: an
+// item takes part while p < its pass count (tag bits 13..16, plus 1), reading
+// grid parity ^ p and counting at its live index + p.
 cudaError_t batch_prepare();
-// `set` 1 runs the items of 32^3 tiles of m = 3 (kBody3x32), set 0 every other
-// body; a count pass (count_only) runs any item in set 0.
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
-                              cudaStream_t st, unsigned long long *digest = nullptr,
-                              unsigned int *zero_next = nullptr, int set = 0);
+                              cudaStream_t st, unsigned long long *digest = nullptr, int set = 0, int pass = 0);
 cudaError_t batch_read_status(uint32_t *out);
 // CTAs of the batched kernel's launch set resident at once on the current device (SMs x occupancy).
 cudaError_t batch_resident_ctas(uint64_t *out, int set = 0);

@@ -4,9 +4,12 @@
 // Jobs (an m-simplex automaton of size n run for a number of steps) arrive
 // over time.  The server keeps every admitted job's two grids resident in a
 // device arena whose grid pool is capped by an HBM budget, and works in
-// rounds: each round is ONE launch of the batched persistent kernel that
-// advances every resident job by one step, whatever step each job is at
-// (per-item tags select each job's input grid and live-count slot).  Between
+// rounds: each round is round_steps launches of the batched persistent
+// kernel, launch k advancing every resident job that still has steps left by
+// one step, whatever step each job is at (per-item tags select each job's
+// input grid and live-count slot).  Several steps per round keep the
+// per-round costs (item upload, digest pass, result copies, event) off most
+// steps, so a job's latency approaches its run time alone.  Between
 // rounds the host loop admits jobs that have arrived (first come, first
 // served) as soon as a slot and enough pool memory are free, and retires jobs
 // whose last step has completed (their results -- live counts of every step
@@ -118,10 +121,14 @@ struct Round {
 
 int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
 
-// Work-queue counters: round r uses counters 2 (r % kQueueRing/2) (its step
-// pass) and the next one (its digest pass); each round's step pass zeroes the
-// pair that round r + 2 will use, so no round needs a memset of its own.
-constexpr int kQueueRing = 16;
+// Work-queue counters: round r uses group r % (max_inflight + 1) of
+// round_steps + 1 counters (its step passes, then its digest pass), zeroed by
+// a memset at the start of the round: the groups of the rounds still in
+// flight are not touched.
+constexpr int kDefaultRoundSteps = 8;
+constexpr int kMaxRoundSteps = 16;
+
+int round_steps(const simplex_server_params_t &p) { return p.round_steps ? p.round_steps : kDefaultRoundSteps; }
 
 }  // namespace
 
@@ -167,9 +174,10 @@ uint64_t layout(const simplex_server_params_t &p, simplex_server *s)
     if (s) s->off_tmaps = off;
     off = align_up(off + sizeof(CUtensorMap) * 2 * slots, 256);
     if (s) s->off_items = off;
+    const uint64_t K = (uint64_t)round_steps(p);
     off = align_up(off + sizeof(sx::BatchItem) * max_items * 2, 256);  // round items + finishing items
     if (s) s->off_queue = off;
-    off = align_up(off + sizeof(unsigned int) * kQueueRing, 256);
+    off = align_up(off + sizeof(unsigned int) * (K + 1) * (uint64_t)(p.max_inflight + 1), 256);
     if (s) s->off_live = off;
     off = align_up(off + sizeof(unsigned long long) * slots * (uint64_t)(p.max_steps + 1), 256);
     if (s) s->off_digest = off;
@@ -189,6 +197,8 @@ int check_params(const simplex_server_params_t *p)
     if (p->max_steps < 1 || p->max_steps > 4095) return fail(SIMPLEX_EINVAL, "max_steps must be in [1, 4095]");
     if (p->max_items < 1024 || p->max_items > (1 << 26)) return fail(SIMPLEX_EINVAL, "max_items must be in [1024, 2^26]");
     if (p->max_inflight < 1 || p->max_inflight > 64) return fail(SIMPLEX_EINVAL, "max_inflight must be in [1, 64]");
+    if (p->round_steps < 0 || p->round_steps > kMaxRoundSteps)
+        return fail(SIMPLEX_EINVAL, "round_steps must be in [0, %d]", kMaxRoundSteps);
     return SIMPLEX_OK;
 }
 
@@ -282,27 +292,34 @@ int launch_round(simplex_server *s, cudaStream_t st)
 
 int launch_round_impl(simplex_server *s, cudaStream_t st)
 {
+    const int K = round_steps(s->prm);
     s->items.clear();
     s->fin_items.clear();
     Round r;
-    // blocks per work item: 8 when the round has work for every resident CTA
+    // blocks per work item: 8 when a pass has work for every resident CTA
     // several times over, fewer (down to 1) when it has not, so that a light
-    // round is spread over more CTAs instead of queueing blocks behind each other
+    // pass is spread over more CTAs instead of queueing blocks behind each other
     uint64_t blocks = 0;
     for (int64_t j : s->active) blocks += s->slot_inst[s->jobs[j].slot].plan.h_blocks;
     uint64_t chunk = blocks / (2 * s->ctas + 1);
     chunk = chunk < 1 ? 1 : (chunk > (uint64_t)sx::kBatchChunk ? (uint64_t)sx::kBatchChunk : chunk);
+    // one item list for the round's passes: a job with r steps left takes part
+    // in the first min(r, K) passes (tag bits 13..16); pass k reads parity ^ k
+    // and counts at step index + k
+    int passes = 0;
     for (int64_t j : s->active) {
         ServerJob &job = s->jobs[j];
         const sx::BatchInst &bi = s->slot_inst[job.slot];
-        const uint32_t tag = (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1);
+        const int np = std::min(K, job.spec.steps - job.step);
+        passes = std::max(passes, np);
+        const uint32_t tag = (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1) | ((uint32_t)(np - 1) << 13);
         for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += chunk) {
             const uint64_t cnt = std::min<uint64_t>(chunk, bi.plan.h_blocks - v0);
             s->items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt, tag});
         }
-        job.step += 1;
-        job.parity ^= 1;
-        s->cell_updates += job.cells;
+        job.step += np;
+        job.parity ^= np & 1;
+        s->cell_updates += job.cells * (uint64_t)np;
         if (job.step == job.spec.steps) {
             r.finishing.push_back(j);
             for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += sx::kBatchChunk) {
@@ -324,25 +341,26 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     unsigned long long *live = reinterpret_cast<unsigned long long *>(s->arena + s->off_live);
     unsigned long long *dig = reinterpret_cast<unsigned long long *>(s->arena + s->off_digest);
     cudaError_t e;
-    const int pair = (int)(s->round_no % (kQueueRing / 2));
-    unsigned int *q = queue + 2 * pair;
-    unsigned int *q_next = queue + 2 * (int)((s->round_no + 2) % (kQueueRing / 2));
-    // stage in pinned memory so the copy runs asynchronously; a ring slot is
+    const uint64_t ring = (uint64_t)(s->prm.max_inflight + 1);
+    unsigned int *q = queue + (size_t)(K + 1) * (s->round_no % ring);
+    // stage in pinned memory so the copies run asynchronously; a ring slot is
     // rewritten max_inflight + 1 rounds later, when the round that read it has
     // completed (the run loop never keeps more than max_inflight in flight)
-    sx::BatchItem *stage =
-        s->stage + (s->round_no % (uint64_t)(s->prm.max_inflight + 1)) * 2 * s->max_items;
+    sx::BatchItem *stage = s->stage + (s->round_no % ring) * 2 * s->max_items;
     std::memcpy(stage, s->items.data(), sizeof(sx::BatchItem) * s->items.size());
-    if ((e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice, st)) !=
-            cudaSuccess ||
-        (e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q, live,
-                                   s->prm.max_steps + 1, 0, false, st, nullptr, q_next)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(q, 0, sizeof(unsigned int) * (size_t)(K + 1), st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
         return cuda_fail(e, "launching a serving round");
+    for (int k = 0; k < passes; ++k)
+        if ((e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q + k, live,
+                                       s->prm.max_steps + 1, 0, false, st, nullptr, 0, k)) != cudaSuccess)
+            return cuda_fail(e, "launching a serving round");
     if (!s->fin_items.empty()) {
         std::memcpy(stage + s->max_items, s->fin_items.data(), sizeof(sx::BatchItem) * s->fin_items.size());
         if ((e = cudaMemcpyAsync(fitems, stage + s->max_items, sizeof(sx::BatchItem) * s->fin_items.size(),
                                  cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = sx::launch_batch_pass(insts, fitems, (uint32_t)s->fin_items.size(), tmaps, s->arena, 0, q + 1,
+            (e = sx::launch_batch_pass(insts, fitems, (uint32_t)s->fin_items.size(), tmaps, s->arena, 0, q + K,
                                        nullptr, 0, 0, true, st, dig)) != cudaSuccess)
             return cuda_fail(e, "launching the digest pass");
         for (int64_t j : r.finishing) {
@@ -515,9 +533,7 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
     s->pool.reset(s->prm.hbm_budget);
     cudaError_t e = sx::batch_prepare();
     if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
-    if ((e = cudaMemsetAsync(s->arena + s->off_queue, 0, sizeof(unsigned int) * kQueueRing, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_fail(e, "resetting the work queue");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronising before a trace");
     s->round_no = 0;
     if ((e = sx::batch_resident_ctas(&s->ctas)) != cudaSuccess) return cuda_fail(e, "occupancy query");
     if ((e = cudaEventRecord(s->t0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
