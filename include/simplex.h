@@ -48,7 +48,10 @@ extern "C" {
 
 /* ---- map modes ----------------------------------------------------------- */
 #define SIMPLEX_MODE_H 0  /* block-space map H (Sec. 4)                         */
-#define SIMPLEX_MODE_BB 1 /* bounding box f(x) = x over N^m tiles (Sec. 2, Eq. 3) */
+#define SIMPLEX_MODE_BB 1 /* bounding box f(x) = x over N^m tiles (Sec. 2, Eq. 3)   */
+#define SIMPLEX_MODE_BB_THREAD 2 /* the same bounding box with only a per-thread filter (the
+                                    paper's baseline): blocks wholly outside the domain run
+                                    too and their threads find no cell; identical results */
 
 /* ---- visit-count levels ---------------------------------------------------- */
 #define SIMPLEX_LEVEL_BLOCK 0
@@ -177,7 +180,8 @@ int simplex_map_block(simplex_map_t map, int mode, uint64_t v, int32_t *coord, i
  *   out   device, uint32, side^m elements; 16-byte aligned rows (side % 4 == 0
  *         and a 16-byte aligned base) take the 16-byte store path, anything
  *         else the 4-byte path.
- *   mode  SIMPLEX_MODE_H or SIMPLEX_MODE_BB (identical results).
+ *   mode  SIMPLEX_MODE_H, SIMPLEX_MODE_BB or SIMPLEX_MODE_BB_THREAD (identical
+ *         results).
  */
 int simplex_write(simplex_map_t map, uint32_t *out, uint32_t seed, int mode, void *stream);
 
@@ -210,7 +214,8 @@ int simplex_ca_init(simplex_map_t map, uint8_t *grid, uint32_t seed, uint32_t th
  *   birth, survive  rule masks, bits 0..3^m-1.  B3/S23: 0x8, 0xC.
  *   live     device uint64 or NULL: the number of live cells after the step
  *            is ADDED to *live.
- *   mode     SIMPLEX_MODE_H or SIMPLEX_MODE_BB (identical results).
+ *   mode     SIMPLEX_MODE_H, SIMPLEX_MODE_BB or SIMPLEX_MODE_BB_THREAD
+ *            (identical results; the x-stream form runs BB_THREAD as BB).
  * m = 2 supports block 32, 64, 128; m = 3 supports block 16, 32.
  * A device-side wait that exceeds its bound is reported by a later
  * simplex_device_status() call (SIMPLEX_ETIMEOUT); the kernel never hangs.

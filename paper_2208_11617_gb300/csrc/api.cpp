@@ -212,8 +212,9 @@ int check_map(simplex_map_t map)
 
 int check_mode(int mode)
 {
-    if (mode != SIMPLEX_MODE_H && mode != SIMPLEX_MODE_BB)
-        return fail(SIMPLEX_EINVAL, "mode must be SIMPLEX_MODE_H or SIMPLEX_MODE_BB (got %d)", mode);
+    if (mode != SIMPLEX_MODE_H && mode != SIMPLEX_MODE_BB && mode != SIMPLEX_MODE_BB_THREAD)
+        return fail(SIMPLEX_EINVAL, "mode must be SIMPLEX_MODE_H, SIMPLEX_MODE_BB or SIMPLEX_MODE_BB_THREAD (got %d)",
+                    mode);
     return SIMPLEX_OK;
 }
 
@@ -393,7 +394,7 @@ int simplex_map_block(simplex_map_t map, int mode, uint64_t v, int32_t *coord, i
     if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
     if (!coord || !valid) return fail(SIMPLEX_EINVAL, "coord and valid must not be NULL");
     const sx::Plan &p = map->plan;
-    const uint64_t nb = mode == SIMPLEX_MODE_BB ? p.bb_blocks : p.h_blocks;
+    const uint64_t nb = sx::is_bb(mode) ? p.bb_blocks : p.h_blocks;
     if (v >= nb) return fail(SIMPLEX_EINVAL, "block index %llu out of range (%llu blocks)",
                              (unsigned long long)v, (unsigned long long)nb);
     int32_t X[sx::kMaxM] = {0, 0, 0, 0};

@@ -48,7 +48,12 @@ namespace sx {
 constexpr int kMaxM = 4;
 constexpr int kMaxLevels = 16;  // log2 N <= 15 keeps every count well inside 64 bits
 
-enum MapKind : int { kMapH = 0, kMapBB = 1 };
+// kMapBBThread: the bounding box with only a per-thread filter (the paper's
+// baseline): blocks wholly outside the domain run too, their threads find no
+// cell.  kMapBB exits such blocks as a whole.
+enum MapKind : int { kMapH = 0, kMapBB = 1, kMapBBThread = 2 };
+
+SX_HD bool is_bb(int kind) { return kind != kMapH; }
 
 // Launch plan, passed by value to every kernel.
 struct Plan {
@@ -154,7 +159,7 @@ struct XRun {
 
 SX_HD uint64_t xrun_units(const Plan &p, int kind)
 {
-    const uint64_t cols = kind == kMapBB ? (uint64_t)p.N * (uint64_t)p.N : h2_cover_blocks(p.N);
+    const uint64_t cols = is_bb(kind) ? (uint64_t)p.N * (uint64_t)p.N : h2_cover_blocks(p.N);
     return cols * (uint64_t)(p.N / p.seg_len);
 }
 
@@ -164,7 +169,7 @@ SX_HD bool xrun_decode(const Plan &p, int kind, uint64_t w, XRun &r)
     const uint64_t col = w / segs;
     const int32_t s = (int32_t)(w - col * segs);
     int32_t Y[2];
-    if (kind == kMapBB) {
+    if (is_bb(kind)) {
         Y[0] = (int32_t)(col >> p.logN);
         Y[1] = (int32_t)(col & (uint64_t)(p.N - 1));
     } else {
@@ -376,7 +381,7 @@ struct Cover<2> {
 template <int M>
 SX_HD bool decode(const Plan &p, int kind, uint64_t v, int32_t *X)
 {
-    if (kind == kMapBB) {
+    if (is_bb(kind)) {
         // bounding box, f(x) = x (Eq. 3), on the N^m lattice linearised to 1-D
 #pragma unroll
         for (int i = 0; i < M; ++i)

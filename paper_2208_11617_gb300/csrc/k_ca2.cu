@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R), ca2_min_blocks<RHO>())
         int32_t X[2];
         if (!decode<2>(p, kind, v, X)) continue;
         const int64_t y0 = (int64_t)X[0] * RHO, x0 = (int64_t)X[1] * RHO;
-        if (y0 + x0 > p.n) continue;  // tile past the domain
+        if (y0 + x0 > p.n && kind != kMapBBThread) continue;  // tile past the domain
         const bool partial = y0 + x0 + 2 * (RHO - 1) > p.n;
         if (tid == 0) {
             fence_proxy_async_smem();
@@ -132,7 +132,7 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     constexpr int smem = (RHO + 32) * (RHO + 2) + 128;
     cudaError_t e = prepare_t<RHO, R>();
     if (e != cudaSuccess) return e;
-    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const unsigned g = (unsigned)(nb < 0x7fffffffull ? (nb ? nb : 1) : 0x7fffffffull);
     if (rule.or_k)
         ca2_step_kernel<RHO, R, true><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);

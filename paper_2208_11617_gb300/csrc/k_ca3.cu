@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
         int32_t X[3];
         if (!decode<3>(p, kind, v, X)) continue;
         const int64_t z0 = (int64_t)X[0] * RHO, y0 = (int64_t)X[1] * RHO, x0 = (int64_t)X[2] * RHO;
-        if (z0 + y0 + x0 > p.n) continue;
+        if (z0 + y0 + x0 > p.n && kind != kMapBBThread) continue;
         const bool partial = z0 + y0 + x0 + 3 * (RHO - 1) > p.n;
         if (tid == 0) {
             fence_proxy_async_smem();
@@ -304,7 +304,7 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     constexpr int smem = ca3_box_bytes<RHO>() + ca3_box_align<RHO>();
     cudaError_t e = prepare_t<RHO, RZ>();
     if (e != cudaSuccess) return e;
-    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const unsigned g = (unsigned)(nb < 0x7fffffffull ? (nb ? nb : 1) : 0x7fffffffull);
     if (rule.or_k)
         ca3_step_kernel<RHO, RZ, true><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);

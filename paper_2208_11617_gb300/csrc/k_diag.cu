@@ -55,7 +55,7 @@ __global__ void map_kernel(const Plan p, int kind, uint64_t nblocks, unsigned lo
 template <int M>
 static cudaError_t launch_map_t(const Plan &p, int kind, unsigned long long *cells, cudaStream_t st)
 {
-    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const uint32_t threads = 1u << (M * p.log_rho);
     if (nb > 0x7fffffffull || threads > 1024) return cudaErrorInvalidConfiguration;
     map_kernel<M><<<(unsigned)(nb ? nb : 1), threads, 0, st>>>(p, kind, nb, cells);
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(RHO * RHO / 4)
     int32_t X[2];
     if (!decode<2>(p, kind, blockIdx.x, X)) return;
     const int64_t x1_0 = (int64_t)X[0] * RHO, x2_0 = (int64_t)X[1] * RHO;
-    if (x1_0 + x2_0 > p.n) return;
+    if (x1_0 + x2_0 > p.n && kind != kMapBBThread) return;
     const bool partial = x1_0 + x2_0 + 2 * (RHO - 1) > p.n;
     constexpr int kChunks = RHO / 4;
     const int row = threadIdx.x / kChunks, ch = threadIdx.x - row * kChunks;
@@ -141,7 +141,7 @@ cudaError_t launch_edm(const Plan &plan, const float *pts, int dim, float *out, 
 {
     const Plan p = single_grid(plan);
     if (dim < 1 || dim > kEdmMaxDim) return cudaErrorInvalidValue;
-    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     if (nb > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     const unsigned g = (unsigned)(nb ? nb : 1);
     const int v = vec ? 1 : 0;

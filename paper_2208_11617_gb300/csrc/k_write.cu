@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__re
         int32_t X[M];
         if (!decode<M>(p, kind, v, X)) continue;
         const int64_t s0 = tile_base_sum<M>(p, X);
-        if (s0 > p.n) continue;  // tile past the domain
+        if (s0 > p.n && kind != kMapBBThread) continue;  // tile past the domain
         const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
         for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
             const ChunkPos<M> q = chunk_pos<M>(p, X, c, 2);
@@ -93,7 +93,7 @@ static unsigned threads_for(const Plan &p, int lw)
 cudaError_t launch_write(const Plan &plan, uint32_t *out, uint32_t seed, int kind, bool vec, cudaStream_t st)
 {
     const Plan p = single_grid(plan);
-    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const unsigned g = grid_for(nb), t = threads_for(p, 2);
     switch (p.m) {
     case 2: write_kernel<2><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
@@ -106,7 +106,7 @@ cudaError_t launch_write(const Plan &plan, uint32_t *out, uint32_t seed, int kin
 
 cudaError_t launch_visit(const Plan &p, uint32_t *counts, int level, int kind, cudaStream_t st)
 {
-    const uint64_t nb = kind == kMapBB ? p.bb_blocks : p.h_blocks;
+    const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const unsigned g = grid_for(nb), t = threads_for(p, 2);
     switch (p.m) {
     case 2: visit_kernel<2><<<g, t, 0, st>>>(p, counts, level, kind, nb); break;

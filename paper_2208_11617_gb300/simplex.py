@@ -27,6 +27,7 @@ SIMPLEX_EUNSUPPORTED = 5
 
 SIMPLEX_MODE_H = 0
 SIMPLEX_MODE_BB = 1
+SIMPLEX_MODE_BB_THREAD = 2
 SIMPLEX_LEVEL_BLOCK = 0
 SIMPLEX_LEVEL_CELL = 1
 

@@ -19,7 +19,7 @@ from paper_2208_11617_gb300 import simplex as sx
 
 pytestmark = pytest.mark.gpu
 
-MODES = [sx.SIMPLEX_MODE_H, sx.SIMPLEX_MODE_BB]
+MODES = [sx.SIMPLEX_MODE_H, sx.SIMPLEX_MODE_BB, sx.SIMPLEX_MODE_BB_THREAD]
 DEV = "cuda"
 
 

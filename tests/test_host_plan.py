@@ -292,3 +292,12 @@ def test_search_r_beta_orders_by_volume_gap():
     # of the 4-simplex: k = 2 leaves no beta >= 2, and k >= 3 with beta < k
     # has k^4 - beta >= 79 > 24
     assert not any(x["paper_bound"] and x["covers_volume"] for x in c)
+
+
+@pytest.mark.parametrize("case", [(2, 63, 4), (3, 50, 8), (4, 31, 4)])
+def test_bb_thread_mode_decodes_like_bb(case):
+    # the per-thread-filter bounding box enumerates the same N^m lattice
+    m, n, rho = case
+    mp = sx.simplex_map_create(m, n, 2, 2 if m <= 3 else 4, rho)
+    for v in range(0, mp.info.bb_blocks, 7):
+        assert sx.simplex_map_block(mp, sx.SIMPLEX_MODE_BB_THREAD, v) == sx.simplex_map_block(mp, sx.SIMPLEX_MODE_BB, v)
