@@ -438,7 +438,7 @@ def run_ours(args, rank, world, local):
     res = {}
     if isinstance(wl, inputs.CAWorkload):
         mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, band=args.band if wl.m == 2 else None,
-                                   launch=args.launch, layout=args.layout if wl.m == 3 else 0)
+                                   launch=args.launch, layout=args.layout if wl.m == 3 else 0, side=args.side)
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
@@ -772,6 +772,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller case of the workload)")
     ap.add_argument("--block", type=int, default=None, help="override the tile side")
+    ap.add_argument("--side", type=int, default=None,
+                    help="automaton: padded array side (cells per row, a multiple of 16; default n + 1 rounded up)")
     ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
     ap.add_argument("--launch", type=int, default=0, help="automaton step form: 0 auto, 1 grid, 2 x-stream (m = 3)")
     ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")

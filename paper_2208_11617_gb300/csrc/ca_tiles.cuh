@@ -264,11 +264,13 @@ __device__ __forceinline__ uint32_t ca3_tile32(const uint8_t *tile, int64_t n, i
     return byte_sum(lacc);
 }
 
-// m = 3, 32^3 tiles of the x-stream form: the tile's own x-column M and its
-// neighbours L (x3 - 32) and R (x3 + 32) are staged separately, 32 x 34 x 34
+// m = 3, 32^3 tiles of the x-stream form: the x-column M of a slab of the
+// tile (planes z0 ... z0 + 32 / kStreamZSplit - 1) and its neighbours L
+// (x3 - 32) and R (x3 + 32) are staged separately, 32 x 34 x kStreamColPlanes
 // bytes each, unswizzled (row R = zz * 34 + yy at byte 32 R; x1 = z0 + zz - 1,
-// x2 = y0 + yy - 1, x3 = x0 ... x0 + 31 for M).  The thread layout and sums
-// are those of ca3_tile32; the halo word of lane tx = 0 is the last word of
+// x2 = y0 + yy - 1, x3 = x0 ... x0 + 31 for M); warp tz walks the planes
+// z0 + tz RZ ... z0 + tz RZ + RZ - 1.  The thread layout and sums are those
+// of ca3_tile32; the halo word of lane tx = 0 is the last word of
 // the L row, of tx = 1 the first word of the R row (0 where has_l / has_r
 // is false: the neighbour column lies before x3 = 0 or past the domain).
 // Lanes whose row-pair index p has bit 1 set read their rows in reverse

@@ -102,12 +102,16 @@ __global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
 
 // ---------------------------------------------------------------------------
 // x-stream form (32^3 tiles): one CTA per SM takes work units from a device
-// counter; unit w is a run of up to seg_len tiles along x3 in one tile column
-// (xrun_decode: H2 over the triangle of columns, or the bounding square).  A
-// run of tiles X3 = a ... b needs the x-columns a - 1 ... b + 1 (32 x 34 x 34
-// bytes each: the tile's cells plus the x1/x2 halo), so every column is read
-// once per run instead of each tile reading a box with 16-byte x halos on both
-// sides (3 sectors of 32 bytes per 32-byte row).
+// counter.  A tile column (X1, X2) (xrun_decode: H2 over the triangle of
+// columns, or the bounding square) is cut into runs of up to seg_len tiles
+// along x3, and every run into kStreamZSplit slabs of 32 / kStreamZSplit
+// planes along x1: unit w is slab w % kStreamZSplit of run w / kStreamZSplit,
+// so the slabs of one run go to different CTAs at about the same time and
+// share their halo planes in L2.  A slab run of tiles X3 = a ... b needs the
+// x-columns a - 1 ... b + 1 (32 x 34 x kStreamColPlanes bytes each: the
+// slab's cells plus the x1/x2 halo), so every column is read once per run
+// instead of each tile reading a box with 16-byte x halos on both sides (3
+// sectors of 32 bytes per 32-byte row).
 //
 // The last warp (one lane) is the producer.  Per run it first publishes a
 // header (the run and the sequence number of its first column) in a ring of
@@ -115,25 +119,28 @@ __global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
 // consumer warp once it has read the header), then TMA-loads the run's columns
 // in order into a ring of kStreamSlots stages (full: the bytes; empty: see
 // below).  After the last unit it publishes an end header (a > b).
-// The consumers form kStreamGroups groups of 4 warps; group g takes the tiles
-// g, g + G, ... of the CTA's tile sequence, so G tiles are computed at once,
-// each by 4 warps walking 8 planes per thread.  Column c of a run is the
-// centre of tile c and a neighbour of tiles c - 1 and c + 1: every column has
-// exactly three uses (a tile at a run's end also performs the uses of the
-// tiles missing beyond it), so empty completes after 3 x 4 warp arrivals,
-// when every tile reading the column is done; a column is never refilled while
-// a group that has not reached its tile still needs it.  Every wait is
-// bounded; a timeout sets the status word and an abort flag that stops both
-// sides, and the producer then waits (bounded) for the loads it issued before
-// the CTA exits.  The last CTA to finish puts the work counter back to zero.
-constexpr int kStreamSlots = 6;
+// The consumers form kStreamGroups groups of kStreamGroupWarps warps; group g
+// takes the tiles g, g + G, ... of the CTA's tile sequence, so G slab tiles
+// are computed at once, each by 2 warps walking 8 planes per thread.  Column c
+// of a run is the centre of tile c and a neighbour of tiles c - 1 and c + 1:
+// every column has exactly three uses (a tile at a run's end also performs the
+// uses of the tiles missing beyond it), so empty completes after 3 x
+// kStreamGroupWarps warp arrivals, when every tile reading the column is done;
+// a column is never refilled while a group that has not reached its tile still
+// needs it.  Every wait is bounded; a timeout sets the status word and an
+// abort flag that stops both sides, and the producer then waits (bounded) for
+// the loads it issued before the CTA exits.  The last CTA to finish puts the
+// work counter back to zero.
+constexpr int kStreamSlots = 11;
 constexpr int kStreamHeaders = 8;
-constexpr int kStreamGroups = 2;
-constexpr int kStreamGroupWarps = 4;  // 2 chunks x 16 row pairs x 4 runs of 8 planes
+constexpr int kStreamGroups = 5;
+constexpr int kStreamGroupWarps = 32 / kStreamZSplit / 8;  // 2 chunks x 16 row pairs x runs of 8 planes
 constexpr int kStreamConsumers = kStreamGroups * kStreamGroupWarps * 32;
 constexpr int kStreamThreads = kStreamConsumers + 32;
-constexpr uint32_t kColBytes = 32u * 34u * 34u;  // 36,992 = 289 x 128
+constexpr uint32_t kColBytes = 32u * 34u * (uint32_t)kStreamColPlanes;  // 19,584 = 153 x 128
 constexpr int kStreamSmem = kStreamSlots * (int)kColBytes + 128;
+static_assert(kColBytes % 128 == 0, "ring slots must stay 128-byte aligned");
+static_assert(kStreamSmem <= 227 * 1024, "ring exceeds the shared memory of one CTA");
 
 template <bool ORK>
 __global__ void __launch_bounds__(kStreamThreads, 1)
@@ -187,8 +194,14 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 const uint64_t w = atomicAdd(&queue[0], 1ull);
                 if (w >= units) break;
                 XRun r;
-                if (!xrun_decode(p, kind, w, r)) continue;
-                if (!(ok = header(make_int4(r.X1, r.X2, r.a, r.b)))) break;
+                if (!xrun_decode(p, kind, w / kStreamZSplit, r)) continue;
+                // slab zs: planes z0 ... z0 + 32 / kStreamZSplit - 1; its tiles
+                // hold cells while X3 * 32 <= n - z0 - y0
+                const int32_t zs = r.X1 * kStreamZSplit + (int32_t)(w % kStreamZSplit);
+                const int64_t reach = (p.n - (int64_t)zs * (32 / kStreamZSplit) - (int64_t)r.X2 * 32) >> 5;
+                if (reach < (int64_t)r.b) r.b = (int32_t)reach;
+                if (r.b < r.a) continue;
+                if (!(ok = header(make_int4(zs, r.X2, r.a, r.b)))) break;
                 for (int32_t c = r.a - 1; c <= r.b + 1; ++c, ++seq) {
                     const int s = (int)(seq % S);
                     if (seq >= (uint64_t)S &&
@@ -196,7 +209,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                         break;
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(&full[s], kColBytes);
-                    tma_load_3d(ring + s * kColBytes, &tcol, c * 32, r.X2 * 32 - 1, r.X1 * 32 - 1, &full[s]);
+                    tma_load_3d(ring + s * kColBytes, &tcol, c * 32, r.X2 * 32 - 1, zs * (32 / kStreamZSplit) - 1,
+                                &full[s]);
                 }
             }
             issued = seq;
@@ -221,7 +235,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             if (lane == 0) mbar_arrive(&hempty[h]);
             ++nh;
             if (r.z > r.w) break;  // end header
-            const int64_t z0 = (int64_t)r.x * 32, y0 = (int64_t)r.y * 32;
+            const int64_t z0 = (int64_t)r.x * (32 / kStreamZSplit), y0 = (int64_t)r.y * 32;
             bool ok = true;
             const int32_t first = r.z + (int32_t)((uint32_t)(grp - (int)(t0 % G) + G) % G);
             for (int32_t x3 = first; x3 <= r.w && ok; x3 += G) {
@@ -230,7 +244,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     ok = !abort_flag && mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
                 if (!ok) break;
                 const int64_t x0 = (int64_t)x3 * 32;
-                const bool partial = z0 + y0 + x0 + 3 * 31 > p.n;
+                const bool partial = z0 + y0 + x0 + (32 / kStreamZSplit - 1) + 2 * 31 > p.n;
                 my_live += ca3_tile32c<8, ORK>(ring + (c % S) * kColBytes, ring + ((c - 1) % S) * kColBytes,
                                                ring + ((c + 1) % S) * kColBytes, x3 > 0, x0 + 32 <= p.n, p.n, p.side,
                                                rule, out, x0, y0, z0, partial, tx, pr, tz);
@@ -336,7 +350,7 @@ static cudaError_t launch_stream(const Plan &p, const CUtensorMap &tcol, uint8_t
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const uint64_t units = xrun_units(p, kind);
+    const uint64_t units = xrun_units(p, kind) * kStreamZSplit;
     const uint64_t g = units < (uint64_t)sms ? (units ? units : 1) : (uint64_t)sms;  // one CTA per SM
     if (rule.or_k)
         ca3_step_stream<true><<<(unsigned)g, kStreamThreads, kStreamSmem, st>>>(tcol, out, p, rule, kind, units, live,

@@ -29,6 +29,11 @@ cudaError_t launch_ca_count(const Plan &p, const uint8_t *grid, unsigned long lo
 bool ca2_supports(int rho);
 bool ca3_supports(int rho);
 bool ca3_swizzled(int rho);  // tensor map needs CU_TENSOR_MAP_SWIZZLE_64B
+// m = 3 x-stream form: every 32^3 tile is processed as kStreamZSplit slabs
+// along x1, and its x-columns are staged as boxes of 32 x 34 x
+// kStreamColPlanes bytes (one slab plus its two halo planes).
+constexpr int kStreamZSplit = 2;
+constexpr int kStreamColPlanes = 32 / kStreamZSplit + 2;
 cudaError_t launch_ca2_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
                             int kind, unsigned long long *live, cudaStream_t st);
 // queue: two zeroed 64-bit counters (work counter, CTAs done) that the x-stream

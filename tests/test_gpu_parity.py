@@ -208,7 +208,8 @@ def test_write_h2_forms_match_oracle(band):
 
 @pytest.mark.parametrize("launch", [1, 2])
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("n,side,beta", [(255, None, 2), (200, 208, 2), (255, None, 3), (31, 32, 2), (1, 16, 2)])
+@pytest.mark.parametrize("n,side,beta", [(255, None, 2), (200, 208, 2), (255, None, 3), (31, 32, 2), (1, 16, 2),
+                                         (527, 528, 2), (600, 608, 2)])
 def test_ca3_grid_and_persistent_forms_match_oracle(launch, mode, n, side, beta):
     """The m = 3 step in both launch forms (one CTA per block of the map, and
     the x-stream form: persistent CTAs streaming runs of tiles along x3
