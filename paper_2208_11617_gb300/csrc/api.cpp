@@ -259,7 +259,7 @@ int step_once(simplex_map_t map, const uint8_t *in, uint8_t *out, const sx::Rule
     int rc = ensure_queue(map);
     if (rc) return rc;
     CUtensorMap tm;
-    rc = make_tensor_map(p, in, &tm);
+    rc = make_tensor_map(p, in, &tm, sx::ca3_box_planes(p));
     if (rc) return rc;
     cudaError_t e = p.m == 2 ? sx::launch_ca2_step(p, tm, out, rule, mode, live, st)
                              : sx::launch_ca3_step(p, tm, out, rule, mode, live, map->queue, st);

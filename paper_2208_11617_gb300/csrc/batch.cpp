@@ -256,7 +256,8 @@ int simplex_batch_bind(simplex_batch_t b, void *arena, uint64_t arena_bytes, voi
     std::vector<CUtensorMap> tmaps(2 * b->insts.size());
     for (size_t i = 0; i < b->insts.size(); ++i)
         for (int g = 0; g < 2; ++g) {
-            rc = make_tensor_map(b->insts[i].plan, base + b->insts[i].grid[g], &tmaps[2 * i + g]);
+            rc = make_tensor_map(b->insts[i].plan, base + b->insts[i].grid[g], &tmaps[2 * i + g],
+                                 b->insts[i].plan.rho + 2);
             if (rc) return rc;
         }
     cudaError_t e;

@@ -29,7 +29,8 @@ sx::Rule make_rule(int m, uint32_t birth, uint32_t survive);
 
 // TMA tensor map over a uint8 grid of the plan's layout (extent n + 1 per
 // axis, pitch side), box = tile + halo; SIMPLEX_OK or an error code.
-int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm);
+// box_planes: depth along x1 of an m = 3 box (ignored for m = 2).
+int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm, int box_planes);
 
 // Read-only view of a batch's host-side plans and work items; grid offsets in
 // the BatchInst records count from the start of the arena, and the grids

@@ -400,7 +400,8 @@ extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, u
     for (size_t k0 = 0; k0 < 2 * bv.count; k0 += 32) {
         const size_t k1 = k0 + 32 < 2 * bv.count ? k0 + 32 : 2 * bv.count;
         for (size_t k = k0; k < k1; ++k) {
-            rc = make_tensor_map(bv.insts[k / 2].plan, base + bv.insts[k / 2].grid[k % 2], &piece[k - k0]);
+            rc = make_tensor_map(bv.insts[k / 2].plan, base + bv.insts[k / 2].grid[k % 2], &piece[k - k0],
+                                 bv.insts[k / 2].plan.rho + 2);
             if (rc) return rc;
         }
         if ((e = cudaMemcpyAsync(scratch + off_tmaps + sizeof(CUtensorMap) * k0, piece,

@@ -34,6 +34,9 @@ bool ca3_swizzled(int rho);  // tensor map needs CU_TENSOR_MAP_SWIZZLE_64B
 // kStreamColPlanes bytes (one slab plus its two halo planes).
 constexpr int kStreamZSplit = 2;
 constexpr int kStreamColPlanes = 32 / kStreamZSplit + 2;
+// Depth along x1 of the box the single-instance m = 3 step stages: the
+// x-stream column of a slab, or the whole tile plus halo (grid form).
+int ca3_box_planes(const Plan &p);
 cudaError_t launch_ca2_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
                             int kind, unsigned long long *live, cudaStream_t st);
 // queue: two zeroed 64-bit counters (work counter, CTAs done) that the x-stream

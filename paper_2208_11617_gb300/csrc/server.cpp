@@ -246,7 +246,7 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
     bi.grid[0] = s->off_pool + off;
     bi.grid[1] = s->off_pool + off + align_up(gb, 256);
     for (int g = 0; g < 2; ++g) {
-        rc = make_tensor_map(bi.plan, s->arena + bi.grid[g], &s->slot_tmap[2 * slot + g]);
+        rc = make_tensor_map(bi.plan, s->arena + bi.grid[g], &s->slot_tmap[2 * slot + g], bi.plan.rho + 2);
         if (rc) return -1;
     }
     cudaError_t e;

@@ -31,15 +31,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 // Tensor map over a uint8 grid: extent n + 1 along every axis (cells past the
 // domain's bounding box read as zero), row pitch `side`, box of the tile plus
-// its halo: (rho + 32) x (rho + 2) [x (rho + 2)], or for the m = 3 x-stream
-// form one x-column of a slab: rho x (rho + 2) x (rho / kStreamZSplit + 2).  L2 fills are promoted to 64
+// its halo: (rho + 32) x (rho + 2) [x box_planes], or for the m = 3 x-stream
+// form one x-column of a slab: rho x (rho + 2) x box_planes.  L2 fills are promoted to 64
 // bytes for m = 2 and 128 bytes for m = 3: wider fills fetched bytes of rows
 // that no box in flight reads (the 128 x 128 step was 4 % slower and noisier
 // at 256 bytes, the 32^3 step 9 % slower).
-int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
+int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm, int box_planes)
 {
     auto fn = encode_fn();
     if (!fn) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (p.m == 3 && (box_planes < 3 || box_planes > p.rho + 2))
+        return fail(SIMPLEX_EINVAL, "m = 3 box depth %d outside 3 ... rho + 2", box_planes);
     cuuint64_t dims[3], strides[2];
     cuuint32_t box[3], estr[3] = {1, 1, 1};
     for (int i = 0; i < p.m; ++i) dims[i] = (cuuint64_t)(p.n + 1);
@@ -49,7 +51,7 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm)
     const bool xcols = p.m == 3 && p.persistent;
     box[0] = (cuuint32_t)(xcols ? p.rho : p.rho + 32);
     box[1] = (cuuint32_t)(p.rho + 2);
-    box[2] = (cuuint32_t)(xcols ? sx::kStreamColPlanes : p.rho + 2);
+    box[2] = (cuuint32_t)box_planes;
     const CUtensorMapSwizzle swz = (p.m == 3 && !xcols && sx::ca3_swizzled(p.rho)) ? CU_TENSOR_MAP_SWIZZLE_64B
                                                                                   : CU_TENSOR_MAP_SWIZZLE_NONE;
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, (cuuint32_t)p.m, const_cast<void *>(base), dims, strides, box,
