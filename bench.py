@@ -325,6 +325,32 @@ def _fifo_latency(arrivals_s, service_s):
     return out
 
 
+def _serve_classes(srv, jobs):
+    """Latency by job class (m, and n above or below the class median) and the
+    make-up of the jobs at or above the trace's p99 latency."""
+    lat = np.array([srv.result(i)["done_ms"] - srv.result(i)["arrival_ms"] for i in range(len(jobs))])
+    ms = np.array([d["m"] for d in jobs])
+    ns = np.array([d["n"] for d in jobs])
+    steps = np.array([d["steps"] for d in jobs])
+    out = {}
+    for m in (2, 3):
+        sel = ms == m
+        if not sel.any():
+            continue
+        med = float(np.median(ns[sel]))
+        for part, cond in (("small", ns <= med), ("large", ns > med)):
+            l = lat[sel & cond]
+            if len(l):
+                out[f"m{m}_{part}"] = {"jobs": int(len(l)), "n_range": [int(ns[sel & cond].min()), int(ns[sel & cond].max())],
+                                       "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99))}
+    tail = lat >= np.percentile(lat, 99)
+    out["tail_p99"] = {"jobs": int(tail.sum()), "m3_share": float((ms[tail] == 3).mean()),
+                       "mean_n_m2": float(ns[tail & (ms == 2)].mean()) if (tail & (ms == 2)).any() else None,
+                       "mean_n_m3": float(ns[tail & (ms == 3)].mean()) if (tail & (ms == 3)).any() else None,
+                       "mean_steps": float(steps[tail].mean())}
+    return out
+
+
 def run_serve(args, rank, world):
     """Serving workload: Poisson arrivals at 2000 jobs/s, continuous batching
     under a 64 GiB grid budget; p50/p99 latency and cell-updates/s, against
@@ -347,6 +373,7 @@ def run_serve(args, rank, world):
     clk = clocks.stop()
     st = srv.stats()
     value = st["cell_updates"] / wall
+    by_class = _serve_classes(srv, jobs)
     # serial per-job execution: service time of each job alone (a sample), then a FIFO queue
     rng = np.random.default_rng(7)
     sample = sorted(rng.choice(len(jobs), size=min(args.serve_sample, len(jobs)), replace=False).tolist())
@@ -405,10 +432,13 @@ def run_serve(args, rank, world):
                "rounds": st["rounds"], "mean_resident_jobs": st["mean_active"],
                "peak_pool_gib": st["peak_pool_bytes"] / 2 ** 30, "offered_cell_updates_per_s":
                    st["cell_updates"] / seconds},
+        serve_by_class=by_class,
         serial={"cell_updates_per_s": serial_rate, "mean_service_ms": mean_svc * 1e3,
                 "utilisation_at_this_rate": inputs.SERVE_RATE * mean_svc, "p50_ms": q(0.5), "p99_ms": q(0.99),
                 "sample_jobs": len(sample), "digest_mismatches": mismatches},
         host_issue_ms_per_round=st["host_issue_ms"] / max(1, st["rounds"]),
+        gpu_ms_per_round=st["gpu_round_ms"],
+        gpu_busy_fraction=st["gpu_round_ms"] * st["rounds"] / (wall * 1e3),
         capacity={"jobs": len(cap_jobs), "server_cell_updates_per_s": cap["cell_updates"] / cap_wall,
                   "serial_cell_updates_per_s": serial_cap_rate, "server_over_serial":
                       (cap["cell_updates"] / cap_wall) / serial_cap_rate, "mean_resident_jobs": cap["mean_active"]},

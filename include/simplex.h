@@ -455,6 +455,7 @@ typedef struct simplex_server_stats {
     double mean_active;      /* resident jobs per round */
     double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* latency: done - arrival */
     double host_issue_ms;    /* host time spent building and issuing rounds */
+    double gpu_round_ms;     /* mean device time of a round: its first operation to its last */
 } simplex_server_stats_t;
 
 /* Device bytes the server's arena needs for these parameters (tables + pool). */

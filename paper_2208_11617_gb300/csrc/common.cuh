@@ -119,6 +119,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Programmatic dependent launch (sm_90 and later).  A grid launched with
+// programmatic stream serialization may start while the kernel before it in
+// the stream is still running: grid_dep_wait() blocks until that kernel has
+// completed and its writes are visible, and grid_dep_trigger() lets the next
+// such grid start once every CTA of this one has called it or exited.  Both
+// return at once for a grid launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");

@@ -8,6 +8,13 @@
 // issued while the current item runs), loads the item's instance description
 // into shared memory when it changes, decodes each block with that instance's
 // map and runs the same per-tile body as the single-instance kernels.
+//
+// Consecutive passes are launched with programmatic stream serialization: a
+// pass starts while the one before it drains, pops its first item, loads the
+// instance description and decodes the item's blocks (none of which the
+// previous pass writes), and waits for the previous pass to complete only
+// before its first access to a grid.  A CTA lets the next pass start once it
+// holds its last item.
 #include <mutex>
 
 #include "../../include/simplex.h"
@@ -91,6 +98,7 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
     // stage s at tile + s * kPitch
     const int tid = threadIdx.x;
     uint32_t phase = 0;  // bit s: parity of stage s's next completion
+    bool waited = false, triggered = false;  // CTA-uniform
 
     if (tid == 0) {
         for (int k = 0; k < NST; ++k) mbar_init(&bar[k], 1);
@@ -107,6 +115,10 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
         }
         __syncthreads();
         const uint32_t it = s_item;
+        if (!triggered && s_next >= nitems) {  // this is the CTA's last item: the next pass may start
+            grid_dep_trigger();
+            triggered = true;
+        }
         if (it >= nitems) break;
         const BatchItem item = items[it];
         // item.tag: bit 0 flips the input grid, bits 1..12 offset the live-count
@@ -134,6 +146,10 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
         uint32_t my_live = 0;
         unsigned long long my_dig = 0;
         if (count_only) {
+            if (!waited) {  // the grid may still be written by the previous pass
+                grid_dep_wait();
+                waited = true;
+            }
             for (uint32_t j = 0; j < item.cnt; ++j) {
                 int32_t X[3] = {0, 0, 0};
                 const uint64_t v = (uint64_t)item.v0 + j;
@@ -161,6 +177,10 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
                 s_ntiles = nt;
             }
             __syncthreads();
+            if (!waited) {  // the previous pass writes this pass's input and reads its output
+                grid_dep_wait();
+                waited = true;
+            }
             const int nt = s_ntiles;
             const uint32_t box = body_box_bytes(si.body);
             const CUtensorMap *tm = tmaps + si.tmap + par;
@@ -292,14 +312,26 @@ cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, ui
     uint64_t g = 0;
     if ((e = batch_resident_ctas(&g, set)) != cudaSuccess) return e;  // persistent: every CTA resident
     if (g > nitems) g = nitems ? nitems : 1;
+    // programmatic stream serialization: the pass may start while the kernel
+    // before it drains (the kernel waits before it touches a grid)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = (size_t)batch_smem(set);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int co = count_only ? 1 : 0;
     if (set)
-        batch_kernel<1><<<(unsigned)g, kBatchThreads, batch_smem(1), st>>>(
-            insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, 0, digest, pass);
+        e = cudaLaunchKernelEx(&cfg, batch_kernel<1>, insts, items, nitems, tmaps, arena, in_parity, queue, live,
+                               live_stride, live_index, 0, digest, pass);
     else
-        batch_kernel<0><<<(unsigned)g, kBatchThreads, batch_smem(0), st>>>(
-            insts, items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, count_only ? 1 : 0,
-            digest, pass);
-    return cudaGetLastError();
+        e = cudaLaunchKernelEx(&cfg, batch_kernel<0>, insts, items, nitems, tmaps, arena, in_parity, queue, live,
+                               live_stride, live_index, co, digest, pass);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t batch_read_status(uint32_t *out)

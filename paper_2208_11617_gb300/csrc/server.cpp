@@ -115,7 +115,7 @@ struct ServerJob {
 };
 
 struct Round {
-    cudaEvent_t ev;
+    cudaEvent_t ev0 = nullptr, ev = nullptr;  // before its first operation, after its last
     std::vector<int64_t> finishing;
 };
 
@@ -160,6 +160,7 @@ struct simplex_server {
     // stats
     uint64_t rounds = 0, cell_updates = 0, active_sum = 0;
     double wall_ms = 0;
+    double gpu_round_ms = 0;                     // device time of the retired rounds
 };
 
 namespace {
@@ -282,6 +283,20 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
 // count get a digest pass and their results queued for copy to the host.
 int launch_round_impl(simplex_server *s, cudaStream_t st);
 
+// An event from the pool (created when the pool is empty).
+cudaError_t take_event(simplex_server *s, cudaEvent_t *ev)
+{
+    if (s->spare_events.empty()) {
+        cudaEvent_t e0;
+        const cudaError_t e = cudaEventCreate(&e0);
+        if (e != cudaSuccess) return e;
+        s->spare_events.push_back(e0);
+    }
+    *ev = s->spare_events.back();
+    s->spare_events.pop_back();
+    return cudaSuccess;
+}
+
 int launch_round(simplex_server *s, cudaStream_t st)
 {
     const auto t = std::chrono::steady_clock::now();
@@ -348,6 +363,20 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     // completed (the run loop never keeps more than max_inflight in flight)
     sx::BatchItem *stage = s->stage + (s->round_no % ring) * 2 * s->max_items;
     std::memcpy(stage, s->items.data(), sizeof(sx::BatchItem) * s->items.size());
+    // the round's events go back to the pool on every early return
+    struct Guard {
+        simplex_server *s;
+        Round *r;
+        bool armed;
+        ~Guard()
+        {
+            if (!armed) return;
+            if (r->ev0) s->spare_events.push_back(r->ev0);
+            if (r->ev) s->spare_events.push_back(r->ev);
+        }
+    } guard{s, &r, true};
+    if ((e = take_event(s, &r.ev0)) != cudaSuccess || (e = cudaEventRecord(r.ev0, st)) != cudaSuccess)
+        return cuda_fail(e, "recording the start of a serving round");
     if ((e = cudaMemsetAsync(q, 0, sizeof(unsigned int) * (size_t)(K + 1), st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
@@ -382,14 +411,9 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
         }
         s->active.swap(still);
     }
-    if (s->spare_events.empty()) {
-        cudaEvent_t ev;
-        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-        s->spare_events.push_back(ev);
-    }
-    r.ev = s->spare_events.back();
-    s->spare_events.pop_back();
-    if ((e = cudaEventRecord(r.ev, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = take_event(s, &r.ev)) != cudaSuccess || (e = cudaEventRecord(r.ev, st)) != cudaSuccess)
+        return cuda_fail(e, "recording the end of a serving round");
+    guard.armed = false;
     s->inflight.push_back(std::move(r));
     s->rounds += 1;
     s->round_no += 1;
@@ -407,8 +431,11 @@ int retire(simplex_server *s, bool wait)
         cudaError_t e = wait && n == 0 ? cudaEventSynchronize(r.ev) : cudaEventQuery(r.ev);
         if (e == cudaErrorNotReady) break;
         if (e != cudaSuccess) return cuda_fail(e, "waiting for a serving round");
-        float ms = 0;
-        if ((e = cudaEventElapsedTime(&ms, s->t0, r.ev)) != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        float ms = 0, dur = 0;
+        if ((e = cudaEventElapsedTime(&ms, s->t0, r.ev)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&dur, r.ev0, r.ev)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventElapsedTime");
+        s->gpu_round_ms += dur;
         for (int64_t j : r.finishing) {
             ServerJob &job = s->jobs[j];
             const size_t row = (size_t)(s->prm.max_steps + 1);
@@ -422,6 +449,7 @@ int retire(simplex_server *s, bool wait)
             ++finished;
         }
         s->spare_events.push_back(r.ev);
+        s->spare_events.push_back(r.ev0);
         s->inflight.pop_front();
         ++n;
     }
@@ -493,6 +521,7 @@ int simplex_server_destroy(simplex_server_t s)
     for (auto &r : s->inflight) {
         cudaEventSynchronize(r.ev);
         cudaEventDestroy(r.ev);
+        cudaEventDestroy(r.ev0);
     }
     for (auto ev : s->spare_events) cudaEventDestroy(ev);
     if (s->t0) cudaEventDestroy(s->t0);
@@ -530,6 +559,7 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
     s->rounds = s->cell_updates = s->active_sum = 0;
     s->active_items = 0;
     s->host_round_ms = 0;
+    s->gpu_round_ms = 0;
     s->pool.reset(s->prm.hbm_budget);
     cudaError_t e = sx::batch_prepare();
     if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
@@ -614,6 +644,7 @@ int simplex_server_stats(simplex_server_t s, simplex_server_stats_t *out)
     out->mean_active = s->rounds ? (double)s->active_sum / (double)s->rounds : 0.0;
     out->peak_pool_bytes = s->pool.peak();
     out->host_issue_ms = s->host_round_ms;
+    out->gpu_round_ms = s->rounds ? s->gpu_round_ms / (double)s->rounds : 0.0;
     if (!lat.empty()) {
         std::sort(lat.begin(), lat.end());
         auto q = [&](double f) { return lat[std::min(lat.size() - 1, (size_t)(f * (double)(lat.size() - 1) + 0.5))]; };
