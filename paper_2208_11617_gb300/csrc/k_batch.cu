@@ -14,7 +14,8 @@
 // instance description and decodes the item's blocks (none of which the
 // previous pass writes), and waits for the previous pass to complete only
 // before its first access to a grid.  A CTA lets the next pass start once it
-// holds its last item.
+// has got past that wait and holds its last item, so at most one pass runs
+// ahead.
 #include <mutex>
 
 #include "../../include/simplex.h"
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
         }
         __syncthreads();
         const uint32_t it = s_item;
-        if (!triggered && s_next >= nitems) {  // this is the CTA's last item: the next pass may start
+        if (!triggered && waited && s_next >= nitems) {  // the CTA's last item: the next pass may start
             grid_dep_trigger();
             triggered = true;
         }
@@ -149,6 +150,10 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
             if (!waited) {  // the grid may still be written by the previous pass
                 grid_dep_wait();
                 waited = true;
+                if (s_next >= nitems) {  // the CTA's last item: the next pass may start
+                    grid_dep_trigger();
+                    triggered = true;
+                }
             }
             for (uint32_t j = 0; j < item.cnt; ++j) {
                 int32_t X[3] = {0, 0, 0};
@@ -180,6 +185,10 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
             if (!waited) {  // the previous pass writes this pass's input and reads its output
                 grid_dep_wait();
                 waited = true;
+                if (s_next >= nitems) {  // the CTA's last item: the next pass may start
+                    grid_dep_trigger();
+                    triggered = true;
+                }
             }
             const int nt = s_ntiles;
             const uint32_t box = body_box_bytes(si.body);
@@ -314,24 +323,13 @@ cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, ui
     if (g > nitems) g = nitems ? nitems : 1;
     // programmatic stream serialization: the pass may start while the kernel
     // before it drains (the kernel waits before it touches a grid)
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)g);
-    cfg.blockDim = dim3(kBatchThreads);
-    cfg.dynamicSmemBytes = (size_t)batch_smem(set);
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
     const int co = count_only ? 1 : 0;
     if (set)
-        e = cudaLaunchKernelEx(&cfg, batch_kernel<1>, insts, items, nitems, tmaps, arena, in_parity, queue, live,
-                               live_stride, live_index, 0, digest, pass);
-    else
-        e = cudaLaunchKernelEx(&cfg, batch_kernel<0>, insts, items, nitems, tmaps, arena, in_parity, queue, live,
-                               live_stride, live_index, co, digest, pass);
-    return e != cudaSuccess ? e : cudaGetLastError();
+        return launch_pdl(batch_kernel<1>, dim3((unsigned)g), dim3(kBatchThreads), (size_t)batch_smem(1), st, insts,
+                          items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, 0, digest,
+                          pass);
+    return launch_pdl(batch_kernel<0>, dim3((unsigned)g), dim3(kBatchThreads), (size_t)batch_smem(0), st, insts,
+                      items, nitems, tmaps, arena, in_parity, queue, live, live_stride, live_index, co, digest, pass);
 }
 
 cudaError_t batch_read_status(uint32_t *out)

@@ -15,7 +15,11 @@
 //   5. adds its live cells to the step's counter: new states (0/1 bytes) are
 //      summed byte-wise per thread, folded once per tile, reduced per CTA and
 //      added with one atomic per CTA.
-// Only tiles on the diagonal band mask cells past x1 + x2 = n.
+// Only tiles on the diagonal band mask cells past x1 + x2 = n.  Steps are
+// launched with programmatic stream serialization: once every CTA of a step
+// has got past its own wait for the step before, the next step's CTAs may
+// start, decode their tiles and wait for the step to complete before their
+// first load.
 #include "ca_tiles.cuh"
 #include "common.cuh"
 #include "hmap.cuh"
@@ -53,6 +57,7 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R), ca2_min_blocks<RHO>())
         fence_mbar_init();
     }
     __syncthreads();
+    bool waited = false;  // CTA-uniform
 
     for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
         int32_t X[2];
@@ -60,6 +65,11 @@ __global__ void __launch_bounds__(RHO * RHO / (16 * R), ca2_min_blocks<RHO>())
         const int64_t y0 = (int64_t)X[0] * RHO, x0 = (int64_t)X[1] * RHO;
         if (y0 + x0 > p.n && kind != kMapBBThread) continue;  // tile past the domain
         const bool partial = y0 + x0 + 2 * (RHO - 1) > p.n;
+        if (!waited) {  // the previous step writes this step's input and reads its output
+            grid_dep_wait();
+            grid_dep_trigger();  // the next step may start (at most one step ahead)
+            waited = true;
+        }
         if (tid == 0) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar, kBoxBytes);
@@ -135,10 +145,10 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const unsigned g = (unsigned)(nb < 0x7fffffffull ? (nb ? nb : 1) : 0x7fffffffull);
     if (rule.or_k)
-        ca2_step_kernel<RHO, R, true><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
-    else
-        ca2_step_kernel<RHO, R, false><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
-    return cudaGetLastError();
+        return launch_pdl(ca2_step_kernel<RHO, R, true>, dim3(g), dim3(T), (size_t)smem, st, tin, out, p, rule, kind,
+                          nb, live);
+    return launch_pdl(ca2_step_kernel<RHO, R, false>, dim3(g), dim3(T), (size_t)smem, st, tin, out, p, rule, kind, nb,
+                      live);
 }
 
 cudaError_t launch_ca2_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,

@@ -13,7 +13,10 @@
 // For RHO = 32 the staged rows are 64 bytes and the tensor map uses the 64-byte
 // swizzle (16-byte unit u of staged row R sits at u ^ ((R >> 1) & 3)); each
 // thread owns two output rows (ca3_tile32) and the lanes of one 16-byte load
-// instruction spread over all shared-memory banks.  The file also holds the
+// instruction spread over all shared-memory banks.  Grid-form steps are
+// launched with programmatic stream serialization (the next step's CTAs may
+// start and decode their tiles once every CTA of this one has got past its
+// own wait, and wait for it to complete before their first load).  The file also holds the
 // x-stream form (ca3_step_stream, launch 2): persistent CTAs that stream runs
 // of tiles along x3 through a ring of 32-byte-wide x-columns.
 #include "ca_tiles.cuh"
@@ -69,6 +72,7 @@ __global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
         fence_mbar_init();
     }
     __syncthreads();
+    bool waited = false;  // CTA-uniform
 
     for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
         int32_t X[3];
@@ -76,6 +80,11 @@ __global__ void __launch_bounds__(ca3_threads<RHO, RZ>(), ca3_min_blocks<RHO>())
         const int64_t z0 = (int64_t)X[0] * RHO, y0 = (int64_t)X[1] * RHO, x0 = (int64_t)X[2] * RHO;
         if (z0 + y0 + x0 > p.n && kind != kMapBBThread) continue;
         const bool partial = z0 + y0 + x0 + 3 * (RHO - 1) > p.n;
+        if (!waited) {  // the previous step writes this step's input and reads its output
+            grid_dep_wait();
+            grid_dep_trigger();  // the next step may start (at most one step ahead)
+            waited = true;
+        }
         if (tid == 0) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar, kBoxBytes);
@@ -327,10 +336,10 @@ static cudaError_t launch_t(const Plan &p, const CUtensorMap &tin, uint8_t *out,
     const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const unsigned g = (unsigned)(nb < 0x7fffffffull ? (nb ? nb : 1) : 0x7fffffffull);
     if (rule.or_k)
-        ca3_step_kernel<RHO, RZ, true><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
-    else
-        ca3_step_kernel<RHO, RZ, false><<<g, T, smem, st>>>(tin, out, p, rule, kind, nb, live);
-    return cudaGetLastError();
+        return launch_pdl(ca3_step_kernel<RHO, RZ, true>, dim3(g), dim3(T), (size_t)smem, st, tin, out, p, rule, kind,
+                          nb, live);
+    return launch_pdl(ca3_step_kernel<RHO, RZ, false>, dim3(g), dim3(T), (size_t)smem, st, tin, out, p, rule, kind,
+                      nb, live);
 }
 
 template <bool ORK>
