@@ -7,7 +7,7 @@
 // the domain (rho * sum(X) + m (rho - 1) <= n) take the predicate-free path;
 // only tiles on the diagonal band test each cell (Sec. 4.1: extra threads only
 // at the diagonal).  (Programmatic dependent launch, which the automaton steps
-// use, made the back-to-back 2.1 MB writes slower: 2.4 -> 2.9 us a launch.)
+// use, made the back-to-back 2.1 MB writes 20 to 40 % slower.)
 #include "common.cuh"
 #include "hmap.cuh"
 #include "kernels.h"
