@@ -538,8 +538,10 @@ def run_ours(args, rank, world, local):
                 sx.simplex_ca_run_host(mp, h_in, h_out, a, b, wl.steps, birth, survive, live, h_live)
             t1 = time.perf_counter()
             e2e_val = aggregate(cells * wl.steps * e2e_steps, t1 - t0, world)[0]
-        res["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": mp.numel,
-                      "d2h_bytes_per_step": mp.numel + 8 * (wl.steps + 1)}
+        # the call moves the domain's row prefixes only (host_copy_bytes each way)
+        res["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": info["host_copy_bytes"],
+                      "d2h_bytes_per_step": info["host_copy_bytes"] + 8 * (wl.steps + 1),
+                      "array_bytes": mp.numel}
         assert sx.simplex_device_status() == 0
     else:
         beta = 2 if wl.m <= 3 else wl.m

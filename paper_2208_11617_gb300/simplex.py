@@ -59,7 +59,8 @@ class SimplexMapInfo(ctypes.Structure):
                 ("Ne", ctypes.c_int32), ("launch", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("cells", ctypes.c_uint64),
                 ("useful_blocks", ctypes.c_uint64), ("h_blocks", ctypes.c_uint64),
-                ("bb_blocks", ctypes.c_uint64), ("h_set_blocks", ctypes.c_uint64)]
+                ("bb_blocks", ctypes.c_uint64), ("h_set_blocks", ctypes.c_uint64),
+                ("host_copy_bytes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

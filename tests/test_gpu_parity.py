@@ -255,20 +255,32 @@ def test_ca_step_api_single_steps():
         a, b = b, a
 
 
-def test_ca_run_host_end_to_end():
-    m, n, steps = 2, 1023, 12
-    mp = sx.simplex_map_create(m, n, 2, 2, 128)
+@pytest.mark.parametrize("m,n,block,side,steps", [(2, 1023, 128, None, 12), (2, 100, 32, 112, 5), (2, 0, 32, 16, 3),
+                                                  (3, 200, 16, 208, 7), (3, 63, 32, None, 4)])
+def test_ca_run_host_end_to_end(m, n, block, side, steps):
+    """Host buffers in and out; only the domain moves, so host_out keeps a
+    sentinel or gets 0 outside the domain and the oracle's grid inside."""
+    mp = sx.simplex_map_create(m, n, 2, 2, block, side=side)
+    rule = inputs.B3S23 if m == 2 else inputs.B5S45
     thr = inputs.bernoulli_threshold(0.5)
     init = oracle.ca_init(m, n, 7, thr)
-    h_in = torch.from_numpy(init.reshape(-1).copy()).pin_memory()
-    h_out = torch.zeros(mp.numel, dtype=torch.uint8).pin_memory()
+    full = np.zeros(mp.shape, dtype=np.uint8)
+    full[tuple(slice(0, n + 1) for _ in range(m))] = init
+    h_in = torch.from_numpy(full.reshape(-1).copy()).pin_memory()
+    h_out = torch.full((mp.numel,), 0xAB, dtype=torch.uint8).pin_memory()
     h_live = torch.zeros(steps + 1, dtype=torch.int64)
     a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
     b = torch.zeros_like(a)
     d_live = torch.zeros(steps + 1, dtype=torch.int64, device=DEV)
-    sx.simplex_ca_run_host(mp, h_in, h_out, a, b, steps, *inputs.B3S23, d_live, h_live)
-    ref, ref_live = oracle.ca_run(m, n, steps, *inputs.B3S23, init)
-    np.testing.assert_array_equal(h_out.numpy().reshape(mp.shape), ref)
+    sx.simplex_ca_run_host(mp, h_in, h_out, a, b, steps, *rule, d_live, h_live)
+    ref, ref_live = oracle.ca_run(m, n, steps, *rule, init)
+    got = h_out.numpy().reshape(mp.shape)
+    idx = np.indices(mp.shape).sum(axis=0)
+    inside = idx <= n
+    refg = np.zeros(mp.shape, dtype=np.uint8)
+    refg[tuple(slice(0, n + 1) for _ in range(m))] = ref
+    np.testing.assert_array_equal(got[inside], refg[inside])
+    assert np.isin(got[~inside], [0, 0xAB]).all()
     np.testing.assert_array_equal(h_live.numpy().astype(np.uint64), ref_live)
 
 

@@ -294,6 +294,20 @@ def test_search_r_beta_orders_by_volume_gap():
     assert not any(x["paper_bound"] and x["covers_volume"] for x in c)
 
 
+@pytest.mark.parametrize("m,n,block", [(2, 0, 32), (2, 1, 32), (2, 100, 32), (2, 1023, 128), (2, 32767, 128),
+                                       (3, 0, 16), (3, 5, 16), (3, 200, 16), (3, 1023, 32)])
+def test_host_copy_covers_the_domain_and_less_than_the_array(m, n, block):
+    # simplex_ca_run_host moves every domain row prefix: at least the domain's
+    # C(n + m, m) cells, at most the (n + 1)^m box; for the large cases close
+    # to the domain (a few percent of staircase for m = 2, under 30 % for m = 3)
+    mp = sx.simplex_map_create(m, n, 2, 2, block)
+    info = sx.simplex_map_info(mp)
+    cells = math.comb(n + m, m)
+    assert cells <= info["host_copy_bytes"] <= (n + 1) ** m
+    if n >= 1023:
+        assert info["host_copy_bytes"] <= cells * (1.05 if m == 2 else 1.30)
+
+
 @pytest.mark.parametrize("case", [(2, 63, 4), (3, 50, 8), (4, 31, 4)])
 def test_bb_thread_mode_decodes_like_bb(case):
     # the per-thread-filter bounding box enumerates the same N^m lattice
