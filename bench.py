@@ -45,10 +45,14 @@ UNIT = "cell-updates/s"
 _CSRC = "paper_2208_11617_gb300/csrc/"
 _KERNEL_SOURCES = {
     "ca2_step_kernel<128>": ["k_ca2.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp"],
-    "ca3_step_kernel<32>": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp"],
+    "ca3_step_kernel<32>": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
+    "ca3_step_stream": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
 }
-_KERNEL_TRAFFIC = {("11dbc53541d5e6e8", "ca2_step_kernel<128>", 32767): 1_032_728_661,
-                   ("8d6544fa857a5d59", "ca3_step_kernel<32>", 1023): 521_173_930}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (mean of 3 launches
+# at full size), for the kernel sources with the given fingerprint
+_KERNEL_TRAFFIC = {("dd4f335cea150870", "ca2_step_kernel<128>", 32767): 1_032_842_837,
+                   ("c37e9ab828aa4255", "ca3_step_kernel<32>", 1023): 521_809_152,
+                   ("c37e9ab828aa4255", "ca3_step_stream", 1023): 407_859_712}
 
 
 def _kernel_fingerprint(kname):
