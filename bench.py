@@ -365,7 +365,7 @@ def run_serve(args, rank, world):
     seconds = args.serve_seconds
     jobs, t = inputs.serve_trace(seconds=seconds)
     srv = sx.SimplexServer(hbm_budget=inputs.SERVE_BUDGET, max_jobs=8192, max_steps=64, max_items=1 << 18,
-                           max_inflight=2, round_steps=args.round_steps)
+                           max_inflight=2, round_steps=args.round_steps, direct_jobs=args.direct_jobs)
     warm, wt = inputs.serve_trace(seconds=0.05, seed=5)
     srv.run(warm, wt, realtime=True)                  # warm-up trace (not timed)
     torch.cuda.synchronize()
@@ -799,6 +799,9 @@ def main():
     ap.add_argument("--serve-high-rate", type=float, default=8000.0, help="serve: arrival rate of the heavy-load run")
     ap.add_argument("--serve-high-seconds", type=float, default=5.0, help="serve: length of the heavy-load run")
     ap.add_argument("--round-steps", type=int, default=0, help="serve: automaton steps per round (0: the default, 8)")
+    ap.add_argument("--direct-jobs", type=int, default=0,
+                    help="serve: rounds with at most this many resident jobs launch each job's steps directly "
+                         "(0: the default, 3; -1: never)")
     ap.add_argument("--no-tune", action="store_true", help="batch: untuned tile choices")
     ap.add_argument("--no-loop", action="store_true", help="batch: skip the single-instance loop baseline")
     ap.add_argument("--batch-m2", type=int, default=2048, help="batch: number of m = 2 instances")

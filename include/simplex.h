@@ -425,6 +425,9 @@ int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t gri
  * a digest of their final grid are copied to host memory and their memory
  * returns to the pool.  A job's result is identical whether it runs alone or
  * among others.  Tiles: m = 2: 128 from n = 1024 up, else 64; m = 3: 16.
+ * Light rounds (at most direct_jobs resident jobs) launch each job's steps
+ * with the single-instance step kernels on its own grids instead: a batched
+ * pass costs more than a few jobs' own step launches.
  */
 typedef struct simplex_server *simplex_server_t;
 
@@ -436,6 +439,9 @@ typedef struct simplex_server_params {
                                 work items hold 1..8 blocks: fewer when the round is light) */
     int32_t max_inflight;    /* rounds the host may queue ahead of the GPU (1..64) */
     int32_t round_steps;     /* automaton steps per round, 1..16; 0 means 8 */
+    int32_t direct_jobs;     /* a round with at most this many resident jobs runs each job's
+                                steps as single-instance step launches instead of batched
+                                passes; 0 means 3, -1 never, at most 64 */
 } simplex_server_params_t;
 
 typedef struct simplex_job {

@@ -9,7 +9,10 @@
 // one step, whatever step each job is at (per-item tags select each job's
 // input grid and live-count slot).  Several steps per round keep the
 // per-round costs (item upload, digest pass, result copies, event) off most
-// steps, so a job's latency approaches its run time alone.  Between
+// steps, so a job's latency approaches its run time alone.  A light round
+// (at most direct_jobs resident jobs) launches each job's steps with the
+// single-instance step kernels on its own grids and tensor maps instead: a
+// persistent batched pass costs more than a few jobs' own launches.  Between
 // rounds the host loop admits jobs that have arrived (first come, first
 // served) as soon as a slot and enough pool memory are free, and retires jobs
 // whose last step has completed (their results -- live counts of every step
@@ -130,6 +133,9 @@ constexpr int kMaxRoundSteps = 16;
 
 int round_steps(const simplex_server_params_t &p) { return p.round_steps ? p.round_steps : kDefaultRoundSteps; }
 
+constexpr int kDefaultDirectJobs = 3, kMaxDirectJobs = 64;
+int direct_jobs(const simplex_server_params_t &p) { return p.direct_jobs ? p.direct_jobs : kDefaultDirectJobs; }
+
 }  // namespace
 
 struct simplex_server {
@@ -200,6 +206,8 @@ int check_params(const simplex_server_params_t *p)
     if (p->max_inflight < 1 || p->max_inflight > 64) return fail(SIMPLEX_EINVAL, "max_inflight must be in [1, 64]");
     if (p->round_steps < 0 || p->round_steps > kMaxRoundSteps)
         return fail(SIMPLEX_EINVAL, "round_steps must be in [0, %d]", kMaxRoundSteps);
+    if (p->direct_jobs < -1 || p->direct_jobs > kMaxDirectJobs)
+        return fail(SIMPLEX_EINVAL, "direct_jobs must be in [-1, %d]", kMaxDirectJobs);
     return SIMPLEX_OK;
 }
 
@@ -311,6 +319,27 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     s->items.clear();
     s->fin_items.clear();
     Round r;
+    cudaError_t e;
+    // the round's events go back to the pool on every early return
+    struct Guard {
+        simplex_server *s;
+        Round *r;
+        bool armed;
+        ~Guard()
+        {
+            if (!armed) return;
+            if (r->ev0) s->spare_events.push_back(r->ev0);
+            if (r->ev) s->spare_events.push_back(r->ev);
+        }
+    } guard{s, &r, true};
+    if ((e = take_event(s, &r.ev0)) != cudaSuccess || (e = cudaEventRecord(r.ev0, st)) != cudaSuccess)
+        return cuda_fail(e, "recording the start of a serving round");
+    // a light round runs each job's steps with the single-instance step
+    // kernels (one launch per job and step) instead of batched passes
+    const int dj = direct_jobs(s->prm);
+    const bool direct = dj > 0 && s->active.size() <= (size_t)dj;
+    unsigned long long *live_all = reinterpret_cast<unsigned long long *>(s->arena + s->off_live);
+    const size_t live_row = (size_t)(s->prm.max_steps + 1);
     // blocks per work item: 8 when a pass has work for every resident CTA
     // several times over, fewer (down to 1) when it has not, so that a light
     // pass is spread over more CTAs instead of queueing blocks behind each other
@@ -327,10 +356,24 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
         const sx::BatchInst &bi = s->slot_inst[job.slot];
         const int np = std::min(K, job.spec.steps - job.step);
         passes = std::max(passes, np);
-        const uint32_t tag = (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1) | ((uint32_t)(np - 1) << 13);
-        for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += chunk) {
-            const uint64_t cnt = std::min<uint64_t>(chunk, bi.plan.h_blocks - v0);
-            s->items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt, tag});
+        if (direct) {
+            // step k reads grid parity ^ k and counts at step index + k, as a pass does
+            for (int k = 0; k < np; ++k) {
+                const int par = job.parity ^ (k & 1);
+                uint8_t *out = s->arena + bi.grid[par ^ 1];
+                unsigned long long *lv = live_all + (size_t)job.slot * live_row + (size_t)(job.step + 1 + k);
+                const CUtensorMap &tm = s->slot_tmap[2 * job.slot + par];
+                e = bi.plan.m == 2 ? sx::launch_ca2_step(bi.plan, tm, out, bi.rule, sx::kMapH, lv, st)
+                                   : sx::launch_ca3_step(bi.plan, tm, out, bi.rule, sx::kMapH, lv, nullptr, st);
+                if (e != cudaSuccess) return cuda_fail(e, "launching a job's step");
+            }
+        } else {
+            const uint32_t tag =
+                (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1) | ((uint32_t)(np - 1) << 13);
+            for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += chunk) {
+                const uint64_t cnt = std::min<uint64_t>(chunk, bi.plan.h_blocks - v0);
+                s->items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt, tag});
+            }
         }
         job.step += np;
         job.parity ^= np & 1;
@@ -355,36 +398,26 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     unsigned int *queue = reinterpret_cast<unsigned int *>(s->arena + s->off_queue);
     unsigned long long *live = reinterpret_cast<unsigned long long *>(s->arena + s->off_live);
     unsigned long long *dig = reinterpret_cast<unsigned long long *>(s->arena + s->off_digest);
-    cudaError_t e;
     const uint64_t ring = (uint64_t)(s->prm.max_inflight + 1);
     unsigned int *q = queue + (size_t)(K + 1) * (s->round_no % ring);
     // stage in pinned memory so the copies run asynchronously; a ring slot is
     // rewritten max_inflight + 1 rounds later, when the round that read it has
     // completed (the run loop never keeps more than max_inflight in flight)
     sx::BatchItem *stage = s->stage + (s->round_no % ring) * 2 * s->max_items;
-    std::memcpy(stage, s->items.data(), sizeof(sx::BatchItem) * s->items.size());
-    // the round's events go back to the pool on every early return
-    struct Guard {
-        simplex_server *s;
-        Round *r;
-        bool armed;
-        ~Guard()
-        {
-            if (!armed) return;
-            if (r->ev0) s->spare_events.push_back(r->ev0);
-            if (r->ev) s->spare_events.push_back(r->ev);
-        }
-    } guard{s, &r, true};
-    if ((e = take_event(s, &r.ev0)) != cudaSuccess || (e = cudaEventRecord(r.ev0, st)) != cudaSuccess)
-        return cuda_fail(e, "recording the start of a serving round");
-    if ((e = cudaMemsetAsync(q, 0, sizeof(unsigned int) * (size_t)(K + 1), st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice, st)) !=
-            cudaSuccess)
-        return cuda_fail(e, "launching a serving round");
-    for (int k = 0; k < passes; ++k)
-        if ((e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q + k, live,
-                                       s->prm.max_steps + 1, 0, false, st, nullptr, 0, k)) != cudaSuccess)
+    if (!direct) {
+        std::memcpy(stage, s->items.data(), sizeof(sx::BatchItem) * s->items.size());
+        if ((e = cudaMemsetAsync(q, 0, sizeof(unsigned int) * (size_t)(K + 1), st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice,
+                                 st)) != cudaSuccess)
             return cuda_fail(e, "launching a serving round");
+        for (int k = 0; k < passes; ++k)
+            if ((e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q + k, live,
+                                           s->prm.max_steps + 1, 0, false, st, nullptr, 0, k)) != cudaSuccess)
+                return cuda_fail(e, "launching a serving round");
+    } else if (!s->fin_items.empty() &&
+               (e = cudaMemsetAsync(q + K, 0, sizeof(unsigned int), st)) != cudaSuccess) {  // the digest pass's counter
+        return cuda_fail(e, "launching a serving round");
+    }
     if (!s->fin_items.empty()) {
         std::memcpy(stage + s->max_items, s->fin_items.data(), sizeof(sx::BatchItem) * s->fin_items.size());
         if ((e = cudaMemcpyAsync(fitems, stage + s->max_items, sizeof(sx::BatchItem) * s->fin_items.size(),

@@ -89,7 +89,8 @@ class SimplexBatchInfo(ctypes.Structure):
 
 class SimplexServerParams(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_jobs", ctypes.c_int32), ("max_steps", ctypes.c_int32),
-                ("max_items", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("round_steps", ctypes.c_int32)]
+                ("max_items", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("round_steps", ctypes.c_int32),
+                ("direct_jobs", ctypes.c_int32)]
 
 
 class SimplexJob(ctypes.Structure):
@@ -442,8 +443,9 @@ class SimplexServer:
     """A serving engine over a torch-allocated arena (owns the C handle)."""
 
     def __init__(self, hbm_budget: int, max_jobs: int = 4096, max_steps: int = 64, max_items: int = 1 << 18,
-                 max_inflight: int = 2, round_steps: int = 0):
-        self.params = SimplexServerParams(hbm_budget, max_jobs, max_steps, max_items, max_inflight, round_steps)
+                 max_inflight: int = 2, round_steps: int = 0, direct_jobs: int = 0):
+        self.params = SimplexServerParams(hbm_budget, max_jobs, max_steps, max_items, max_inflight, round_steps,
+                                          direct_jobs)
         need = _u64()
         _check(_lib.simplex_server_arena_bytes(ctypes.byref(self.params), ctypes.byref(need)),
                "simplex_server_arena_bytes")

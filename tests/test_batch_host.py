@@ -51,3 +51,19 @@ def test_batch_workload_generator():
     assert len(n3) == 256 and min(n3) >= 32 and max(n3) < 256
     assert insts == inputs.batch_instances()          # seeded
     assert [d["seed"] for d in insts] == list(range(2304))
+
+
+@pytest.mark.parametrize("field,bad", [("round_steps", 17), ("round_steps", -1), ("direct_jobs", -2),
+                                       ("direct_jobs", 65), ("max_inflight", 0)])
+def test_server_params_are_validated(field, bad):
+    import ctypes
+    good = dict(hbm_budget=1 << 30, max_jobs=16, max_steps=8, max_items=1 << 12, max_inflight=2, round_steps=0,
+                direct_jobs=0)
+    need = ctypes.c_uint64()
+    p = sx.SimplexServerParams(**good)
+    assert sx._lib.simplex_server_arena_bytes(ctypes.byref(p), ctypes.byref(need)) == 0 and need.value > 0
+    for ok in ({"direct_jobs": -1}, {"direct_jobs": 64}, {"round_steps": 16}):
+        p = sx.SimplexServerParams(**(good | ok))
+        assert sx._lib.simplex_server_arena_bytes(ctypes.byref(p), ctypes.byref(need)) == 0
+    p = sx.SimplexServerParams(**(good | {field: bad}))
+    assert sx._lib.simplex_server_arena_bytes(ctypes.byref(p), ctypes.byref(need)) == sx.SIMPLEX_EINVAL

@@ -74,6 +74,26 @@ def test_jobs_equal_alone_and_in_the_mix():
             assert _oracle_digest(ref, job["n"]) == res["digest"]
 
 
+def test_direct_and_batched_rounds_agree():
+    """Rounds with few resident jobs launch each job's steps on its own grids
+    (direct_jobs); the results equal those of batched passes only."""
+    jobs, _ = inputs.serve_trace(rate=4000, seconds=0.05, seed=13, n2=(16, 1500), n3=(8, 200), max_steps=12)
+    assert len(jobs) > 100
+    res = []
+    for dj in (-1, 64):
+        srv = sx.SimplexServer(hbm_budget=2 << 30, max_jobs=512, max_steps=12, direct_jobs=dj)
+        srv.run(jobs, None, realtime=False)   # all at once: batched rounds first, direct ones as jobs finish
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["rejected"] == 0
+        res.append([srv.result(i, job["steps"]) for i, job in enumerate(jobs)])
+    strip = lambda r: {k: v for k, v in r.items() if not k.endswith("_ms")}
+    for i, (a, b) in enumerate(zip(*res)):
+        assert strip(a) == strip(b), f"job {i}"
+    for i in (0, len(jobs) // 2, len(jobs) - 1):
+        dig, live, _, _ = _alone(jobs[i])
+        assert res[1][i]["digest"] == dig and res[1][i]["live"] == live
+
+
 def test_budget_limits_resident_memory_and_rejects_oversized_jobs():
     rule = inputs.B3S23
     thr = inputs.bernoulli_threshold(0.5)
