@@ -365,7 +365,7 @@ def run_serve(args, rank, world):
     seconds = args.serve_seconds
     jobs, t = inputs.serve_trace(seconds=seconds)
     srv = sx.SimplexServer(hbm_budget=inputs.SERVE_BUDGET, max_jobs=8192, max_steps=64, max_items=1 << 18,
-                           max_inflight=2, round_steps=args.round_steps, direct_jobs=args.direct_jobs)
+                           max_inflight=args.max_inflight, round_steps=args.round_steps, direct_jobs=args.direct_jobs)
     warm, wt = inputs.serve_trace(seconds=0.05, seed=5)
     srv.run(warm, wt, realtime=True)                  # warm-up trace (not timed)
     torch.cuda.synchronize()
@@ -798,7 +798,8 @@ def main():
     ap.add_argument("--serve-capacity-jobs", type=int, default=4000, help="serve: jobs of the offline capacity run")
     ap.add_argument("--serve-high-rate", type=float, default=8000.0, help="serve: arrival rate of the heavy-load run")
     ap.add_argument("--serve-high-seconds", type=float, default=5.0, help="serve: length of the heavy-load run")
-    ap.add_argument("--round-steps", type=int, default=0, help="serve: automaton steps per round (0: the default, 8)")
+    ap.add_argument("--round-steps", type=int, default=0, help="serve: automaton steps per batched round (0: the default, 16)")
+    ap.add_argument("--max-inflight", type=int, default=2, help="serve: rounds the host may queue ahead of the GPU")
     ap.add_argument("--direct-jobs", type=int, default=0,
                     help="serve: rounds with at most this many resident jobs launch each job's steps directly "
                          "(0: the default, 3; -1: never)")

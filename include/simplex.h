@@ -438,7 +438,8 @@ typedef struct simplex_server_params {
     int32_t max_items;       /* map blocks of all resident jobs together, >= 1024 (a round's
                                 work items hold 1..8 blocks: fewer when the round is light) */
     int32_t max_inflight;    /* rounds the host may queue ahead of the GPU (1..64) */
-    int32_t round_steps;     /* automaton steps per round, 1..16; 0 means 8 */
+    int32_t round_steps;     /* automaton steps per batched round, 1..64; 0 means 16 (a
+                                direct round takes up to 4x as many, at most 64) */
     int32_t direct_jobs;     /* a round with at most this many resident jobs runs each job's
                                 steps as single-instance step launches instead of batched
                                 passes; 0 means 3, -1 never, at most 64 */

@@ -33,7 +33,7 @@ constexpr int kBatchMaxSteps = 4096;   // steps per simplex_batch_run call
 // blocks v0 .. v0 + cnt - 1 of instance `inst`'s map.  `tag` lets instances
 // that are at different steps share one launch: bit 0 flips the grid the
 // instance reads, bits 1..12 add to the live-count index of the pass, bits
-// 13..16 + 1 = how many passes of a multi-step sequence the item takes part in.
+// 13..18 + 1 = how many passes of a multi-step sequence the item takes part in.
 struct BatchItem {
     uint32_t inst, v0, cnt, tag;
 };

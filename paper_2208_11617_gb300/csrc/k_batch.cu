@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
         if (it >= nitems) break;
         const BatchItem item = items[it];
         // item.tag: bit 0 flips the input grid, bits 1..12 offset the live-count
-        // index, bits 13..16 + 1 = passes the item takes part in (pass p of a
+        // index, bits 13..18 + 1 = passes the item takes part in (pass p of a
         // multi-step launch sequence reads grid parity ^ p and counts at index + p)
-        if ((uint32_t)pass > ((item.tag >> 13) & 15u)) {  // uniform: the job has no step left in this pass
+        if ((uint32_t)pass > ((item.tag >> 13) & 63u)) {  // uniform: the job has no step left in this pass
             __syncthreads();  // s_item is read by every thread before thread 0 pops the next item
             continue;
         }

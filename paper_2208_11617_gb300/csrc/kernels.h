@@ -64,7 +64,7 @@ cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t st);
 // in -> out) over every work item.  `set` 1 runs the items of 32^3 tiles of
 // m = 3 (kBody3x32), set 0 every other body; a count pass runs any item in set
 // 0.  `pass` p > 0 is step p of a sequence launched over the same items: an
-// item takes part while p < its pass count (tag bits 13..16, plus 1), reading
+// item takes part while p < its pass count (tag bits 13..18, plus 1), reading
 // grid parity ^ p and counting at its live index + p.
 cudaError_t batch_prepare();
 cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, uint32_t nitems,

@@ -128,8 +128,8 @@ int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
 // round_steps + 1 counters (its step passes, then its digest pass), zeroed by
 // a memset at the start of the round: the groups of the rounds still in
 // flight are not touched.
-constexpr int kDefaultRoundSteps = 8;
-constexpr int kMaxRoundSteps = 16;
+constexpr int kDefaultRoundSteps = 16;
+constexpr int kMaxRoundSteps = 64;
 
 int round_steps(const simplex_server_params_t &p) { return p.round_steps ? p.round_steps : kDefaultRoundSteps; }
 
@@ -338,6 +338,9 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     // kernels (one launch per job and step) instead of batched passes
     const int dj = direct_jobs(s->prm);
     const bool direct = dj > 0 && s->active.size() <= (size_t)dj;
+    // a direct round takes up to 4 K steps: with few jobs resident a new
+    // arrival waits little for it, and fewer rounds mean fewer round costs
+    const int Kr = direct ? std::min(kMaxRoundSteps, 4 * K) : K;
     unsigned long long *live_all = reinterpret_cast<unsigned long long *>(s->arena + s->off_live);
     const size_t live_row = (size_t)(s->prm.max_steps + 1);
     // blocks per work item: 8 when a pass has work for every resident CTA
@@ -348,13 +351,13 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     uint64_t chunk = blocks / (2 * s->ctas + 1);
     chunk = chunk < 1 ? 1 : (chunk > (uint64_t)sx::kBatchChunk ? (uint64_t)sx::kBatchChunk : chunk);
     // one item list for the round's passes: a job with r steps left takes part
-    // in the first min(r, K) passes (tag bits 13..16); pass k reads parity ^ k
+    // in the first min(r, K) passes (tag bits 13..18); pass k reads parity ^ k
     // and counts at step index + k
     int passes = 0;
     for (int64_t j : s->active) {
         ServerJob &job = s->jobs[j];
         const sx::BatchInst &bi = s->slot_inst[job.slot];
-        const int np = std::min(K, job.spec.steps - job.step);
+        const int np = std::min(Kr, job.spec.steps - job.step);
         passes = std::max(passes, np);
         if (direct) {
             // step k reads grid parity ^ k and counts at step index + k, as a pass does
@@ -634,8 +637,11 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
         if (r < 0) return SIMPLEX_ECUDA;
         done += r;
         if (s->active.empty() && s->inflight.empty() && !s->pending.empty() && realtime) {
+            // sleep until 0.2 ms before the next arrival, then spin: a sleep can
+            // overshoot by tens of microseconds, which would add to that job's latency
             const double wait_ms = s->jobs[s->pending.front()].arrival_ms - host_ms(s);
-            if (wait_ms > 0.05) std::this_thread::sleep_for(std::chrono::microseconds((int64_t)(wait_ms * 900)));
+            if (wait_ms > 0.3)
+                std::this_thread::sleep_for(std::chrono::microseconds((int64_t)((wait_ms - 0.2) * 1000)));
         }
     }
     s->wall_ms = host_ms(s);

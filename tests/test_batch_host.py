@@ -53,7 +53,7 @@ def test_batch_workload_generator():
     assert [d["seed"] for d in insts] == list(range(2304))
 
 
-@pytest.mark.parametrize("field,bad", [("round_steps", 17), ("round_steps", -1), ("direct_jobs", -2),
+@pytest.mark.parametrize("field,bad", [("round_steps", 65), ("round_steps", -1), ("direct_jobs", -2),
                                        ("direct_jobs", 65), ("max_inflight", 0)])
 def test_server_params_are_validated(field, bad):
     import ctypes
@@ -62,7 +62,7 @@ def test_server_params_are_validated(field, bad):
     need = ctypes.c_uint64()
     p = sx.SimplexServerParams(**good)
     assert sx._lib.simplex_server_arena_bytes(ctypes.byref(p), ctypes.byref(need)) == 0 and need.value > 0
-    for ok in ({"direct_jobs": -1}, {"direct_jobs": 64}, {"round_steps": 16}):
+    for ok in ({"direct_jobs": -1}, {"direct_jobs": 64}, {"round_steps": 64}):
         p = sx.SimplexServerParams(**(good | ok))
         assert sx._lib.simplex_server_arena_bytes(ctypes.byref(p), ctypes.byref(need)) == 0
     p = sx.SimplexServerParams(**(good | {field: bad}))
