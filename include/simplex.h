@@ -94,7 +94,7 @@ typedef struct simplex_map_info {
  *   block  tile side rho in cells, a power of two in [4, 256].
  *   out    receives the new map.
  * Allocates host memory only.  The lattice side N is the power of two at or
- * above ceil((n+1)/rho) ("approach n from above", Sec. 4.2); tiles past the
+ * above ceil((n+1)/rho) (n padded from above, Sec. 4.2); tiles past the
  * domain exit at once.  Errors: SIMPLEX_EINVAL for a bad argument,
  * SIMPLEX_EUNSUPPORTED for r_inv != 2 or a beta this build does not map,
  * SIMPLEX_ENOMEM.

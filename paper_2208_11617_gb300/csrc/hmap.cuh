@@ -14,7 +14,7 @@
 // Map summary (one linear CUDA block index v per launch):
 //   m = 2  H2 (Sec. 4.1, Thm. 1, Eq. map2d) on the N/2 x (N-1) grid covers the
 //          blocks with sum <= N-2; a row of N blocks covers the diagonal
-//          sum = N-1 ("extra threads at the diagonal", Sec. 4.1).
+//          sum = N-1 (the diagonal gets its own threads, Sec. 4.1).
 //          Trapezoid form (Sec. 4.2, concurrent trapezoids, in one launch):
 //          the block triangle of side Ne (any multiple of the band height h)
 //          is cut into bands of h tile rows; band k is a trapezoid made of a
