@@ -526,6 +526,17 @@ def run_ours(args, rank, world, local):
                     "wasted_frac_h": 1 - info["useful_blocks"] / info["h_blocks"],
                     "wasted_frac_bb": 1 - info["useful_blocks"] / info["bb_blocks"]},
         )
+        if wl.m == 3 and wl.block == 32 and info["launch"] != 2:
+            # the other m = 3 step form on the same grids: persistent CTAs streaming
+            # slab columns along x3 (H2 over the tile columns)
+            mpx = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, launch=2, side=args.side)
+            mx_ms = _per_launch_ms(lambda: sx.simplex_ca_step(mpx, a, nxt, birth, survive, None), 20)[0]
+            ach_x = alg_bytes / (mx_ms * 1e-3) / 1e9
+            res["x_stream"] = {"kernel": "ca3_step_stream", "launch_ms_mean": mx_ms, "achieved": ach_x,
+                               "frac": ach_x / hbm_peak,
+                               "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint("ca3_step_stream"),
+                                                               "ca3_step_stream", wl.n)),
+                               "note": "same step, x-stream form (launch 2)"}
         # end to end through the C ABI from pinned host memory
         e2e_steps = 0 if args.no_e2e else max(1, min(3, args.steps))
         e2e_val = None
