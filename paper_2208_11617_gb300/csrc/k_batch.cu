@@ -30,6 +30,7 @@
 namespace sx {
 
 static __device__ uint32_t g_batch_status;
+static_assert(kBatchChunk <= 32, "one lane of warp 0 decodes each block of an item");
 
 // Launch sets: set 0 runs the m = 2 bodies and the 16^3 body in 20.8 KB of
 // stage (8 CTAs per SM), set 1 the 32^3 body of m = 3 in a 74 KB stage with the
@@ -168,18 +169,24 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
         } else if ((si.body == kBody3x32) != (SET == 1)) {  // an item of the other launch set: not run here
             if (tid == 0) atomicOr(&g_batch_status, 2u);
         } else {
-            // the item's tiles that hold cells, then a pipelined walk over them
-            if (tid == 0) {
-                int nt = 0;
-                for (uint32_t j = 0; j < item.cnt; ++j) {
+            // the item's tiles that hold cells (lane j of warp 0 decodes block
+            // v0 + j; a ballot keeps them in block order), then a pipelined
+            // walk over them
+            if (tid < 32) {
+                int4 t = make_int4(0, 0, 0, 0);
+                bool hold = false;
+                if ((uint32_t)tid < item.cnt && tid < kBatchChunk) {
                     int32_t X[3] = {0, 0, 0};
-                    const uint64_t v = (uint64_t)item.v0 + j;
-                    if (!(p.m == 2 ? decode<2>(p, kMapH, v, X) : decode<3>(p, kMapH, v, X))) continue;
-                    const int64_t s0 = tile_base_sum<3>(p, X);
-                    if (s0 > p.n) continue;
-                    s_tiles[nt++] = make_int4(X[0], X[1], X[2], s0 + (int64_t)p.m * (p.rho - 1) > p.n ? 1 : 0);
+                    const uint64_t v = (uint64_t)item.v0 + (uint64_t)tid;
+                    if (p.m == 2 ? decode<2>(p, kMapH, v, X) : decode<3>(p, kMapH, v, X)) {
+                        const int64_t s0 = tile_base_sum<3>(p, X);
+                        hold = s0 <= p.n;
+                        t = make_int4(X[0], X[1], X[2], s0 + (int64_t)p.m * (p.rho - 1) > p.n ? 1 : 0);
+                    }
                 }
-                s_ntiles = nt;
+                const uint32_t held = __ballot_sync(0xffffffffu, hold);
+                if (hold) s_tiles[__popc(held & ((1u << tid) - 1u))] = t;
+                if (tid == 0) s_ntiles = __popc(held);
             }
             __syncthreads();
             if (!waited) {  // the previous pass writes this pass's input and reads its output
