@@ -75,6 +75,44 @@ def _peaks():
 
 
 # ---------------------------------------------------------------- clocks
+class EnergyMeter:
+    """Board energy of the GPU over a region: NVML's total-energy counter
+    (millijoules since the driver loaded), read through the driver's
+    libnvidia-ml with read-only queries.  read() returns joules, or None where
+    NVML or the counter is not available."""
+
+    def __init__(self, torch_index: int):
+        import ctypes
+        self.dev = None
+        try:
+            import torch
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            dev = ctypes.c_void_p()
+            pr = torch.cuda.get_device_properties(torch_index)
+            bus = getattr(pr, "pci_bus_id", None)
+            ok = False
+            if bus is not None:
+                busid = "%08X:%02X:%02X.0" % (getattr(pr, "pci_domain_id", 0), bus, getattr(pr, "pci_device_id", 0))
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(busid.encode(), ctypes.byref(dev)) == 0
+            if not ok:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(torch_index), ctypes.byref(dev)) == 0
+            if ok:
+                self.lib, self.dev = lib, dev
+        except Exception:
+            self.dev = None
+
+    def read(self):
+        import ctypes
+        if self.dev is None:
+            return None
+        mj = ctypes.c_ulonglong()
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.dev, ctypes.byref(mj)) != 0:
+            return None
+        return mj.value * 1e-3
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
@@ -235,6 +273,27 @@ def _time_region(fn, steps, warmup, world):
     torch.cuda.synchronize()
     _barrier(world)
     return s.elapsed_time(e) / 1e3
+
+
+def _energy_region(meter, fn, per_call_s, units_per_call, seconds=1.5):
+    """Board energy of fn: NVML's counter is coarse, so fn runs back to back for
+    about `seconds` (apart from the timed region) and the energy is divided
+    over the calls.  Returns joules per call, average watts and units per joule."""
+    import torch
+    if meter is None or meter.dev is None:
+        return {"joules_per_step": None, "note": "NVML energy counter unavailable"}
+    calls = max(1, int(seconds / max(per_call_s, 1e-6)))
+    torch.cuda.synchronize()
+    t0, j0 = time.perf_counter(), meter.read()
+    for _ in range(calls):
+        fn()
+    torch.cuda.synchronize()
+    t1, j1 = time.perf_counter(), meter.read()
+    if j0 is None or j1 is None or j1 <= j0:
+        return {"joules_per_step": None, "note": "NVML energy counter did not advance"}
+    joules = j1 - j0
+    return {"joules_per_step": joules / calls, "avg_watts": joules / (t1 - t0),
+            "units_per_joule": units_per_call * calls / joules, "calls": calls}
 
 
 def _per_launch_ms(launch, reps):
@@ -488,7 +547,8 @@ def run_ours(args, rank, world, local):
         clocks.start()
         secs = _time_region(step(sx.SIMPLEX_MODE_H), args.steps, args.warmup, world)
         clk = clocks.stop()
-        secs_bb = secs if args.no_bb else _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
+        secs_bb = secs if args.no_bb else _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup),
+                                                       world)
         units = cells * wl.steps * args.steps
         value, tmax = aggregate(units, secs, world)
         value_bb, _ = aggregate(units, secs_bb, world)
@@ -526,6 +586,12 @@ def run_ours(args, rank, world, local):
                     "wasted_frac_h": 1 - info["useful_blocks"] / info["h_blocks"],
                     "wasted_frac_bb": 1 - info["useful_blocks"] / info["bb_blocks"]},
         )
+        meter = EnergyMeter(torch.cuda.current_device())
+        res["energy"] = {
+            "h": _energy_region(meter, step(sx.SIMPLEX_MODE_H), secs / args.steps, cells * wl.steps),
+            "bb": None if args.no_bb else _energy_region(meter, step(sx.SIMPLEX_MODE_BB), secs_bb / args.steps,
+                                                          cells * wl.steps),
+            "unit": "cell-updates per joule (board energy, NVML, a separate ~1.5 s run per map)"}
         if wl.m == 3 and wl.block == 32 and info["launch"] != 2:
             # the other m = 3 step form on the same grids: persistent CTAs streaming
             # slab columns along x3 (H2 over the tile columns)
@@ -586,7 +652,8 @@ def run_ours(args, rank, world, local):
         clocks.start()
         secs = _time_region(step(sx.SIMPLEX_MODE_H), args.steps, args.warmup, world)
         clk = clocks.stop()
-        secs_bb = secs if args.no_bb else _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup), world)
+        secs_bb = secs if args.no_bb else _time_region(step(sx.SIMPLEX_MODE_BB), args.steps, max(1, args.warmup),
+                                                       world)
         units = cells * reps * args.steps
         value, tmax = aggregate(units, secs, world)
         value_bb, _ = aggregate(units, secs_bb, world)
@@ -616,6 +683,12 @@ def run_ours(args, rank, world, local):
                        "note": "bounding box with a per-thread filter only (the paper's baseline)"},
             blocks={"h": info["h_blocks"], "bb": info["bb_blocks"], "useful": info["useful_blocks"]},
         )
+        meter = EnergyMeter(torch.cuda.current_device())
+        res["energy"] = {
+            "h": _energy_region(meter, step(sx.SIMPLEX_MODE_H), secs / args.steps, cells * reps),
+            "bb": None if args.no_bb else _energy_region(meter, step(sx.SIMPLEX_MODE_BB), secs_bb / args.steps,
+                                                          cells * reps),
+            "unit": "cells per joule (board energy, NVML, a separate ~1.5 s run per map)"}
         # end to end: write on the device, read the array back to pinned host memory
         h_out = torch.empty(mp.numel, dtype=torch.int32).pin_memory()
         torch.cuda.synchronize()
@@ -691,6 +764,11 @@ def run_diag(args, wl, rank, world):
         blocks={"h": info["h_blocks"], "bb": info["bb_blocks"], "useful": info["useful_blocks"],
                 "bb_over_h": info["bb_blocks"] / info["h_blocks"]},
     )
+    meter = EnergyMeter(torch.cuda.current_device())
+    res["energy"] = {
+        "h": _energy_region(meter, graphs[sx.SIMPLEX_MODE_H].replay, secs / args.steps, cells * reps),
+        "bb": _energy_region(meter, graphs[sx.SIMPLEX_MODE_BB].replay, secs_bb / args.steps, cells * reps),
+        "unit": "cells per joule (board energy, NVML, a separate ~1.5 s run per map)"}
     if edm:
         alg_bytes = 4 * cells + (wl.n + 1) * inputs.EDM_DIM * 4
         achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
