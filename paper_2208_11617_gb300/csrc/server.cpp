@@ -167,6 +167,10 @@ struct simplex_server {
     uint64_t rounds = 0, cell_updates = 0, active_sum = 0;
     double wall_ms = 0;
     double gpu_round_ms = 0;                     // device time of the retired rounds
+    // the stream of the current trace or online session; online calls need
+    // simplex_server_begin first
+    cudaStream_t stream = nullptr;
+    bool stream_set = false;
 };
 
 namespace {
@@ -492,6 +496,77 @@ int retire(simplex_server *s, bool wait)
     return finished;
 }
 
+// Clears the job table and statistics and starts the server's clocks (host
+// and device) for a new trace or online session.
+int reset_session(simplex_server *s, cudaStream_t st)
+{
+    s->jobs.clear();
+    s->pending.clear();
+    s->rounds = s->cell_updates = s->active_sum = 0;
+    s->active_items = 0;
+    s->host_round_ms = 0;
+    s->gpu_round_ms = 0;
+    s->wall_ms = 0;
+    s->pool.reset(s->prm.hbm_budget);
+    cudaError_t e = sx::batch_prepare();
+    if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronising before a trace");
+    s->round_no = 0;
+    if ((e = sx::batch_resident_ctas(&s->ctas)) != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if ((e = cudaEventRecord(s->t0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    s->h0 = std::chrono::steady_clock::now();
+    s->stream = st;
+    return SIMPLEX_OK;
+}
+
+int check_job(const simplex_server *s, const simplex_job_t &sp, int64_t i)
+{
+    if ((sp.m != 2 && sp.m != 3) || sp.n < 0 || sp.steps < 1 || sp.steps > s->prm.max_steps)
+        return fail(SIMPLEX_EINVAL, "job %lld: m must be 2 or 3, n >= 0, steps in [1, %d]", (long long)i,
+                    s->prm.max_steps);
+    return SIMPLEX_OK;
+}
+
+// One turn of the serving loop: admission (jobs that have arrived, first come
+// first served, as slots and pool memory allow), one round when jobs are
+// resident and fewer than max_inflight rounds are queued, then retirement of
+// the rounds that have completed -- waiting for the oldest one when `block`
+// and nothing else can progress.  *done += the jobs that finished (done or
+// rejected).
+int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, int64_t *done)
+{
+    const double now = host_ms(s);
+    while (!s->pending.empty()) {
+        const int64_t j = s->pending.front();
+        if (realtime && s->jobs[j].arrival_ms > now) break;
+        const int a = admit(s, j, st);
+        if (a < 0) {
+            if (a == -2) {
+                s->jobs[j].status = kRejected;
+                s->pending.pop_front();
+                ++*done;
+                continue;
+            }
+            return SIMPLEX_ECUDA;
+        }
+        if (a == 0) break;
+        s->pending.pop_front();
+    }
+    if (!s->active.empty() && (int)s->inflight.size() < s->prm.max_inflight) {
+        const int rc = launch_round(s, st);
+        if (rc) return rc;
+    }
+    // keep at most max_inflight rounds queued ahead of the GPU
+    const bool must_wait = block && ((int)s->inflight.size() >= s->prm.max_inflight ||
+                                     (s->active.empty() && !s->inflight.empty() &&
+                                      (s->pending.empty() || !realtime ||
+                                       s->jobs[s->pending.front()].arrival_ms <= host_ms(s))));
+    const int r = retire(s, must_wait);
+    if (r < 0) return SIMPLEX_ECUDA;
+    *done += r;
+    return SIMPLEX_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -576,66 +651,28 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
     if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty())
         return fail(SIMPLEX_EINVAL, "the server is still running another trace");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // validate and queue every job (arrival order)
-    s->jobs.clear();
+    for (int i = 0; i < count; ++i) {
+        const int rc = check_job(s, jobs[i], i);
+        if (rc) return rc;
+    }
+    int rc = reset_session(s, st);
+    if (rc) return rc;
+    s->stream_set = false;  // a trace is not an online session
+    // queue every job in arrival order
     s->jobs.resize(count);
     std::vector<int64_t> order(count);
     for (int i = 0; i < count; ++i) {
-        const simplex_job_t &sp = jobs[i];
-        if ((sp.m != 2 && sp.m != 3) || sp.n < 0 || sp.steps < 1 || sp.steps > s->prm.max_steps)
-            return fail(SIMPLEX_EINVAL, "job %d: m must be 2 or 3, n >= 0, steps in [1, %d]", i, s->prm.max_steps);
-        s->jobs[i].spec = sp;
+        s->jobs[i].spec = jobs[i];
         s->jobs[i].arrival_ms = arrival_s ? arrival_s[i] * 1e3 : 0.0;
-        s->jobs[i].cells = binom((uint64_t)sp.n + (uint64_t)sp.m, sp.m);
+        s->jobs[i].cells = binom((uint64_t)jobs[i].n + (uint64_t)jobs[i].m, jobs[i].m);
         order[i] = i;
     }
     std::stable_sort(order.begin(), order.end(),
                      [&](int64_t a, int64_t b) { return s->jobs[a].arrival_ms < s->jobs[b].arrival_ms; });
     for (int64_t j : order) s->pending.push_back(j);
-    s->rounds = s->cell_updates = s->active_sum = 0;
-    s->active_items = 0;
-    s->host_round_ms = 0;
-    s->gpu_round_ms = 0;
-    s->pool.reset(s->prm.hbm_budget);
-    cudaError_t e = sx::batch_prepare();
-    if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronising before a trace");
-    s->round_no = 0;
-    if ((e = sx::batch_resident_ctas(&s->ctas)) != cudaSuccess) return cuda_fail(e, "occupancy query");
-    if ((e = cudaEventRecord(s->t0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    s->h0 = std::chrono::steady_clock::now();
     int64_t done = 0;
     while (done < count) {
-        // admission, first come first served, as slots and pool memory allow
-        const double now = host_ms(s);
-        while (!s->pending.empty()) {
-            const int64_t j = s->pending.front();
-            if (realtime && s->jobs[j].arrival_ms > now) break;
-            int a = admit(s, j, st);
-            if (a < 0) {
-                if (a == -2) {
-                    s->jobs[j].status = kRejected;
-                    s->pending.pop_front();
-                    ++done;
-                    continue;
-                }
-                return SIMPLEX_ECUDA;
-            }
-            if (a == 0) break;
-            s->pending.pop_front();
-        }
-        if (!s->active.empty()) {
-            int rc = launch_round(s, st);
-            if (rc) return rc;
-        }
-        // keep at most max_inflight rounds queued ahead of the GPU
-        const bool must_wait = (int)s->inflight.size() >= s->prm.max_inflight ||
-                               (s->active.empty() && !s->inflight.empty() &&
-                                (s->pending.empty() || !realtime ||
-                                 s->jobs[s->pending.front()].arrival_ms <= host_ms(s)));
-        const int r = retire(s, must_wait);
-        if (r < 0) return SIMPLEX_ECUDA;
-        done += r;
+        if ((rc = serve_turn(s, st, realtime != 0, true, &done))) return rc;
         if (s->active.empty() && s->inflight.empty() && !s->pending.empty() && realtime) {
             // sleep until 0.2 ms before the next arrival, then spin: a sleep can
             // overshoot by tens of microseconds, which would add to that job's latency
@@ -643,6 +680,64 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
             if (wait_ms > 0.3)
                 std::this_thread::sleep_for(std::chrono::microseconds((int64_t)((wait_ms - 0.2) * 1000)));
         }
+    }
+    s->wall_ms = host_ms(s);
+    return SIMPLEX_OK;
+}
+
+int simplex_server_begin(simplex_server_t s, void *stream)
+{
+    if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
+    if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty())
+        return fail(SIMPLEX_EINVAL, "the server still has jobs in progress");
+    const int rc = reset_session(s, static_cast<cudaStream_t>(stream));
+    s->stream_set = rc == SIMPLEX_OK;
+    return rc;
+}
+
+int simplex_server_submit(simplex_server_t s, const simplex_job_t *job, int64_t *id)
+{
+    if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
+    if (!job || !id) return fail(SIMPLEX_EINVAL, "job and id must not be NULL");
+    if (!s->stream_set) return fail(SIMPLEX_EINVAL, "call simplex_server_begin before submitting jobs");
+    const int64_t i = (int64_t)s->jobs.size();
+    int rc = check_job(s, *job, i);
+    if (rc) return rc;
+    ServerJob j;
+    j.spec = *job;
+    j.arrival_ms = host_ms(s);
+    j.cells = binom((uint64_t)job->n + (uint64_t)job->m, job->m);
+    s->jobs.push_back(j);
+    s->pending.push_back(i);
+    *id = i;
+    return SIMPLEX_OK;
+}
+
+int simplex_server_poll(simplex_server_t s, int *finished)
+{
+    if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
+    if (!s->stream_set) return fail(SIMPLEX_EINVAL, "call simplex_server_begin first");
+    int64_t done = 0;
+    const int rc = serve_turn(s, s->stream, true, false, &done);
+    if (rc) return rc;
+    s->wall_ms = host_ms(s);
+    if (finished) *finished = (int)done;
+    return SIMPLEX_OK;
+}
+
+int simplex_server_wait(simplex_server_t s, int64_t id)
+{
+    if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
+    if (!s->stream_set) return fail(SIMPLEX_EINVAL, "call simplex_server_begin first");
+    if (id >= (int64_t)s->jobs.size()) return fail(SIMPLEX_EINVAL, "no job %lld", (long long)id);
+    auto finished = [&]() {
+        if (id >= 0) return s->jobs[id].status == kDone || s->jobs[id].status == kRejected;
+        return s->active.empty() && s->inflight.empty() && s->pending.empty();
+    };
+    while (!finished()) {
+        int64_t done = 0;
+        const int rc = serve_turn(s, s->stream, true, true, &done);
+        if (rc) return rc;
     }
     s->wall_ms = host_ms(s);
     return SIMPLEX_OK;

@@ -38,7 +38,8 @@ EXPORTED = (
     "simplex_version", "simplex_selftest_wait_timeout", "simplex_batch_create", "simplex_batch_destroy",
     "simplex_batch_info", "simplex_batch_bind", "simplex_batch_init", "simplex_batch_run", "simplex_batch_grid",
     "simplex_batch_run_static", "simplex_server_arena_bytes", "simplex_server_create", "simplex_server_destroy",
-    "simplex_server_run", "simplex_server_result", "simplex_server_stats", "simplex_ca_digest",
+    "simplex_server_run", "simplex_server_begin", "simplex_server_submit", "simplex_server_poll",
+    "simplex_server_wait", "simplex_server_result", "simplex_server_stats", "simplex_ca_digest",
     "simplex_map_test", "simplex_edm",
 )
 
@@ -154,6 +155,10 @@ _sig("simplex_server_arena_bytes", [ctypes.POINTER(SimplexServerParams), ctypes.
 _sig("simplex_server_create", [ctypes.POINTER(SimplexServerParams), _vp, _u64, ctypes.POINTER(_vp)])
 _sig("simplex_server_destroy", [_vp])
 _sig("simplex_server_run", [_vp, ctypes.POINTER(SimplexJob), ctypes.POINTER(ctypes.c_double), _i32, _i32, _vp])
+_sig("simplex_server_begin", [_vp, _vp])
+_sig("simplex_server_submit", [_vp, ctypes.POINTER(SimplexJob), ctypes.POINTER(_i64)])
+_sig("simplex_server_poll", [_vp, ctypes.POINTER(_i32)])
+_sig("simplex_server_wait", [_vp, _i64])
 _sig("simplex_server_result", [_vp, _i64, ctypes.POINTER(SimplexJobResult), _vp])
 _sig("simplex_server_stats", [_vp, ctypes.POINTER(SimplexServerStats)])
 _sig("simplex_ca_digest", [_vp, _vp, _vp, _vp, _vp])
@@ -468,6 +473,31 @@ class SimplexServer:
         _check(_lib.simplex_server_run(self.handle, arr, times, len(jobs), 1 if realtime else 0, _stream()),
                "simplex_server_run")
         self.count = len(jobs)
+
+    def begin(self):
+        """Start an online session on the current stream (the server must be idle)."""
+        _check(_lib.simplex_server_begin(self.handle, _stream()), "simplex_server_begin")
+        self.count = 0
+
+    def submit(self, job: dict) -> int:
+        """Queue one job now; returns its id."""
+        j = SimplexJob()
+        for f, _ in SimplexJob._fields_:
+            setattr(j, f, job[f])
+        jid = _i64()
+        _check(_lib.simplex_server_submit(self.handle, ctypes.byref(j), ctypes.byref(jid)), "simplex_server_submit")
+        self.count = jid.value + 1
+        return jid.value
+
+    def poll(self) -> int:
+        """One non-blocking turn of the serving loop; returns the jobs it finished."""
+        n = _i32()
+        _check(_lib.simplex_server_poll(self.handle, ctypes.byref(n)), "simplex_server_poll")
+        return n.value
+
+    def wait(self, job: int = -1):
+        """Serve until job `job` (every submitted job when -1) has finished."""
+        _check(_lib.simplex_server_wait(self.handle, job), "simplex_server_wait")
 
     def result(self, job: int, steps: int | None = None):
         res = SimplexJobResult()

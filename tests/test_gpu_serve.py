@@ -94,6 +94,43 @@ def test_direct_and_batched_rounds_agree():
         assert res[1][i]["digest"] == dig and res[1][i]["live"] == live
 
 
+def test_online_submit_poll_wait_matches_trace_run():
+    """Jobs submitted one at a time (with polls between) give the results of
+    the same jobs run as a trace."""
+    jobs, _ = inputs.serve_trace(rate=4000, seconds=0.03, seed=17, n2=(16, 1500), n3=(8, 200), max_steps=12)
+    assert len(jobs) > 50
+    ref = sx.SimplexServer(hbm_budget=2 << 30, max_jobs=512, max_steps=12)
+    ref.run(jobs, None, realtime=False)
+    srv = sx.SimplexServer(hbm_budget=2 << 30, max_jobs=512, max_steps=12)
+    with pytest.raises(sx.SimplexError):
+        srv.submit(jobs[0])                     # no session yet
+    srv.begin()
+    ids = []
+    for k, job in enumerate(jobs):
+        ids.append(srv.submit(job))
+        if k % 3 == 0:
+            srv.poll()
+    assert ids == list(range(len(jobs)))
+    mid = ids[len(ids) // 2]
+    srv.wait(mid)
+    assert srv.result(mid)["status"] == 2
+    srv.wait()
+    strip = lambda r: {k: v for k, v in r.items() if not k.endswith("_ms")}
+    for i, job in enumerate(jobs):
+        assert strip(srv.result(i, job["steps"])) == strip(ref.result(i, job["steps"])), f"job {i}"
+    st = srv.stats()
+    assert st["completed"] == len(jobs) and st["rejected"] == 0
+    with pytest.raises(sx.SimplexError):
+        srv.wait(len(jobs) + 5)
+    with pytest.raises(sx.SimplexError):
+        srv.submit(dict(jobs[0], steps=13))     # more than max_steps
+    # a second session starts clean
+    srv.begin()
+    assert srv.submit(jobs[1]) == 0
+    srv.wait()
+    assert strip(srv.result(0, jobs[1]["steps"])) == strip(ref.result(1, jobs[1]["steps"]))
+
+
 def test_budget_limits_resident_memory_and_rejects_oversized_jobs():
     rule = inputs.B3S23
     thr = inputs.bernoulli_threshold(0.5)
