@@ -326,6 +326,21 @@ def test_ca_m3_full_size_steps_match_oracle():
     assert live_h[-1] > 0
 
 
+def test_ca_m3_full_size_x_stream_equals_grid_form():
+    """The x-stream form (launch 2, the faster m = 3 step) at n = 1023 over the
+    workload's 50 steps gives the grid form's grids and live counts bit for
+    bit (the grid form is checked against the oracle above)."""
+    w = inputs.CA_M3
+    mg = sx.simplex_map_create(w.m, w.n, 2, 2, w.block, launch=1)
+    mx = sx.simplex_map_create(w.m, w.n, 2, 2, w.block, launch=2)
+    assert mx.info.launch == 2 and mg.info.launch == 1
+    fin_g, live_g = _gpu_run(mg, w.n, w.steps, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+    fin_x, live_x = _gpu_run(mx, w.n, w.steps, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+    assert torch.equal(fin_g, fin_x)
+    np.testing.assert_array_equal(live_g, live_x)
+    assert live_x[-1] > 0
+
+
 def test_ca_m2_full_size_matches_oracle():
     """m = 2, n = 32767, B3/S23, Bernoulli(0.5) in the benchmark's launch
     configuration (128 x 128 tiles, graph-captured): two whole steps against
