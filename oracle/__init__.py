@@ -58,6 +58,8 @@ def _load():
         lib.oracle_count_cells.restype = u64
         lib.oracle_write.argtypes = [i32, i64, u32, u32p]
         lib.oracle_write.restype = u64
+        lib.oracle_accum.argtypes = [i32, i64, u32, u32p]
+        lib.oracle_accum.restype = u64
         lib.oracle_ca_init.argtypes = [i32, i64, u32, u32, u8p]
         lib.oracle_ca_init.restype = u64
         lib.oracle_ca_step.argtypes = [i32, i64, u32, u32, u8p, u8p]
@@ -103,6 +105,16 @@ def write(m: int, n: int, seed: int) -> np.ndarray:
     """Coordinate-write test: dense uint32 array, simplex cells hashed, rest 0."""
     out = np.zeros(dense_shape(m, n), dtype=np.uint32)
     c = _load().oracle_write(m, n, seed & 0xFFFFFFFF, _ptr(out, ctypes.c_uint32))
+    assert c == count_cells(m, n) or m not in (2, 3, 4)
+    return out
+
+
+def accum(m: int, n: int, data: np.ndarray, add: int) -> np.ndarray:
+    """ACCUM test (Table 1): a copy of the dense uint32 array `data` (side n + 1)
+    with `add` added (mod 2^32) to every cell of the domain."""
+    out = np.ascontiguousarray(data, dtype=np.uint32).copy()
+    assert out.shape == dense_shape(m, n)
+    c = _load().oracle_accum(m, n, add & 0xFFFFFFFF, _ptr(out, ctypes.c_uint32))
     assert c == count_cells(m, n) or m not in (2, 3, 4)
     return out
 

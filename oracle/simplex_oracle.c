@@ -86,6 +86,42 @@ uint64_t oracle_count_cells(int m, int64_t n)
     return c;
 }
 
+/* ACCUM test (Table 1): every cell of the domain in a dense D^m uint32 array,
+ * D = n + 1, receives data[x] + add (mod 2^32); the other cells are left as
+ * they are.  Returns how many cells it updated. */
+uint64_t oracle_accum(int m, int64_t n, uint32_t add, uint32_t *data)
+{
+    const int64_t D = n + 1;
+    uint64_t c = 0;
+    if (n < 0) return 0;
+    if (m == 2) {
+#pragma omp parallel for reduction(+ : c) schedule(dynamic, 8)
+        for (int64_t x1 = 0; x1 <= n; x1++)
+            for (int64_t x2 = 0; x1 + x2 <= n; x2++) {
+                data[x1 * D + x2] += add;
+                c++;
+            }
+    } else if (m == 3) {
+#pragma omp parallel for reduction(+ : c) schedule(dynamic, 1)
+        for (int64_t x1 = 0; x1 <= n; x1++)
+            for (int64_t x2 = 0; x1 + x2 <= n; x2++)
+                for (int64_t x3 = 0; x1 + x2 + x3 <= n; x3++) {
+                    data[(x1 * D + x2) * D + x3] += add;
+                    c++;
+                }
+    } else if (m == 4) {
+#pragma omp parallel for reduction(+ : c) schedule(dynamic, 1)
+        for (int64_t x1 = 0; x1 <= n; x1++)
+            for (int64_t x2 = 0; x1 + x2 <= n; x2++)
+                for (int64_t x3 = 0; x1 + x2 + x3 <= n; x3++)
+                    for (int64_t x4 = 0; x1 + x2 + x3 + x4 <= n; x4++) {
+                        data[((x1 * D + x2) * D + x3) * D + x4] += add;
+                        c++;
+                    }
+    }
+    return c;
+}
+
 /* Coordinate-write test on a dense D^m uint32 array, D = n + 1.
  * Writes exactly the cells of the domain; returns how many it wrote. */
 uint64_t oracle_write(int m, int64_t n, uint32_t seed, uint32_t *out)

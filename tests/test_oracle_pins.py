@@ -88,6 +88,29 @@ def _box_cells(m, n):
     return [x for x in itertools.product(range(n + 1), repeat=m) if sum(x) <= n]
 
 
+@pytest.mark.parametrize("m,n", [(2, 0), (2, 1), (2, 9), (3, 6), (4, 4)])
+def test_accum_adds_once_to_every_domain_cell(m, n):
+    # brute force over the bounding box: domain cells (sum <= n) gain `add`
+    # exactly once per call, wrapping mod 2^32; every other cell is unchanged
+    rng = np.random.default_rng(m * 100 + n)
+    data = rng.integers(0, 1 << 32, size=(n + 1,) * m, dtype=np.uint64).astype(np.uint32)
+    data.reshape(-1)[0] = 0xFFFFFFFF                    # wraps to add - 1
+    once = oracle.accum(m, n, data, 7)
+    twice = oracle.accum(m, n, once, 7)
+    inside = np.zeros(data.shape, dtype=bool)
+    for x in _box_cells(m, n):
+        inside[x] = True
+    assert inside.sum() == math.comb(n + m, m)
+    d64 = data.astype(np.uint64)
+    assert (once[inside] == ((d64[inside] + 7) % (1 << 32)).astype(np.uint32)).all()
+    assert (twice[inside] == ((d64[inside] + 14) % (1 << 32)).astype(np.uint32)).all()
+    assert (once[~inside] == data[~inside]).all() and (twice[~inside] == data[~inside]).all()
+    assert once.reshape(-1)[0] == 6
+    # the total grows by add x C(n + m, m) per call (mod 2^64 here: no overflow)
+    assert int(twice.astype(np.uint64).sum()) - int(once.astype(np.uint64).sum()) == \
+        7 * math.comb(n + m, m) - (1 << 32) * int(((once[inside].astype(np.uint64) + 7) >> 32).sum())
+
+
 @pytest.mark.parametrize("m,n", [(2, 0), (2, 1), (2, 7), (3, 5), (4, 4), (2, 30), (3, 11)])
 def test_write_support_and_values(m, n):
     seed = 0xDEADBEEF
