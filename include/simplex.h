@@ -187,6 +187,19 @@ int simplex_map_block(simplex_map_t map, int mode, uint64_t v, int32_t *coord, i
 int simplex_write(simplex_map_t map, uint32_t *out, uint32_t seed, int mode, void *stream);
 
 /*
+ * simplex_accum -- the ACCUM test (Table 1, Sec. 5.1): every cell x of the
+ * domain gets data[x] += add (mod 2^32), one read, one add and one write per
+ * cell; cells outside the domain are neither read nor written.
+ *   data  device, uint32, side^m elements; 16-byte aligned rows (side % 4 == 0
+ *         and a 16-byte aligned base) take the 16-byte path, anything else
+ *         4-byte accesses.
+ *   mode  SIMPLEX_MODE_H, SIMPLEX_MODE_BB or SIMPLEX_MODE_BB_THREAD (identical
+ *         results).
+ * Errors: SIMPLEX_EINVAL (NULL or misaligned data, mode), SIMPLEX_ECUDA.
+ */
+int simplex_accum(simplex_map_t map, uint32_t *data, uint32_t add, int mode, void *stream);
+
+/*
  * simplex_ca_init -- seeded Bernoulli state for the automaton: cell x of the
  * domain becomes 1 iff splitmix32(seed ^ lin(x)) < threshold, else 0 (p =
  * threshold / 2^32).  Cells outside the domain that share a 16-byte chunk with

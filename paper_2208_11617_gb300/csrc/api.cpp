@@ -503,6 +503,19 @@ int simplex_write(simplex_map_t map, uint32_t *out, uint32_t seed, int mode, voi
     return SIMPLEX_OK;
 }
 
+int simplex_accum(simplex_map_t map, uint32_t *data, uint32_t add, int mode, void *stream)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    if (!data) return fail(SIMPLEX_EINVAL, "data is NULL");
+    if ((reinterpret_cast<uintptr_t>(data) & 3u) != 0) return fail(SIMPLEX_EINVAL, "data must be 4-byte aligned");
+    const sx::Plan &p = map->plan;
+    const bool vec = aligned16(data) && (p.side % 4 == 0);
+    cudaError_t e = sx::launch_accum(p, data, add, mode, vec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "ACCUM launch");
+    return SIMPLEX_OK;
+}
+
 int simplex_map_test(simplex_map_t map, unsigned long long *cells, int mode, void *stream)
 {
     int rc;

@@ -1,5 +1,6 @@
 // k_write.cu -- the coordinate-write test fused with the map (Table 1 test 2
-// as a store-only kernel) and the coverage (visit-count) kernels.
+// as a store-only kernel), the ACCUM test (Table 1: read, add, write) and the
+// coverage (visit-count) kernels.
 //
 // One CUDA block per tile: the block decodes its tile with H (or the bounding
 // box), and its threads write the tile's cells in chunks of 4 consecutive
@@ -68,6 +69,57 @@ __global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__re
     }
 }
 
+// ACCUM (Table 1): every domain cell of `data` gains `add` (mod 2^32).  Same
+// decode and chunking as the write test; a chunk is one 16-byte load, four
+// adds and one 16-byte store (4-byte accesses where rows are not 16-byte
+// aligned, and per cell on the diagonal band).
+template <int M>
+__global__ void __launch_bounds__(256) accum_kernel(const Plan p, uint32_t *__restrict__ data, uint32_t add,
+                                                    int kind, uint64_t nblocks, int vec)
+{
+    const uint32_t nchunks = 1u << (M * p.log_rho - 2);
+    __shared__ int32_t sX[M + 1];
+    for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
+        int32_t X[M];
+        if (M >= 3) {
+            if (threadIdx.x < 32) {
+                const bool ok = decode<M>(p, kind, v, X);
+                if (threadIdx.x == 0) {
+#pragma unroll
+                    for (int i = 0; i < M; ++i) sX[i] = X[i];
+                    sX[M] = ok ? 1 : 0;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < M; ++i) X[i] = sX[i];
+            const bool ok = sX[M] != 0;
+            __syncthreads();
+            if (!ok) continue;
+        } else if (!decode<M>(p, kind, v, X)) {
+            continue;
+        }
+        const int64_t s0 = tile_base_sum<M>(p, X);
+        if (s0 > p.n && kind != kMapBBThread) continue;
+        const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
+        for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+            const ChunkPos<M> q = chunk_pos<M>(p, X, c, 2);
+            if (!partial && vec) {
+                uint4 w = *reinterpret_cast<const uint4 *>(data + q.addr);
+                w.x += add;
+                w.y += add;
+                w.z += add;
+                w.w += add;
+                *reinterpret_cast<uint4 *>(data + q.addr) = w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (!partial || q.sum + j <= p.n) data[q.addr + j] += add;
+            }
+        }
+    }
+}
+
 template <int M>
 __global__ void __launch_bounds__(256) visit_kernel(const Plan p, uint32_t *__restrict__ counts, int level,
                                                     int kind, uint64_t nblocks)
@@ -119,6 +171,21 @@ cudaError_t launch_write(const Plan &plan, uint32_t *out, uint32_t seed, int kin
     case 2: write_kernel<2><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
     case 3: write_kernel<3><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
     case 4: write_kernel<4><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accum(const Plan &plan, uint32_t *data, uint32_t add, int kind, bool vec, cudaStream_t st)
+{
+    const Plan p = single_grid(plan);
+    const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
+    const unsigned g = grid_for(nb), t = threads_for(p, 2);
+    const int vc = vec ? 1 : 0;
+    switch (p.m) {
+    case 2: accum_kernel<2><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    case 3: accum_kernel<3><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    case 4: accum_kernel<4><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

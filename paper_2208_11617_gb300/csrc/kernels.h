@@ -14,6 +14,7 @@
 namespace sx {
 
 cudaError_t launch_write(const Plan &p, uint32_t *out, uint32_t seed, int kind, bool vec, cudaStream_t st);
+cudaError_t launch_accum(const Plan &p, uint32_t *data, uint32_t add, int kind, bool vec, cudaStream_t st);
 
 cudaError_t launch_visit(const Plan &p, uint32_t *counts, int level, int kind, cudaStream_t st);
 

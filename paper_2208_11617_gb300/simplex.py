@@ -33,7 +33,7 @@ SIMPLEX_LEVEL_CELL = 1
 
 EXPORTED = (
     "simplex_map_create", "simplex_map_create_padded", "simplex_map_create_ex", "simplex_map_destroy", "simplex_map_info",
-    "simplex_map_block", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
+    "simplex_map_block", "simplex_accum", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
     "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
     "simplex_version", "simplex_selftest_wait_timeout", "simplex_batch_create", "simplex_batch_destroy",
     "simplex_batch_info", "simplex_batch_bind", "simplex_batch_init", "simplex_batch_run", "simplex_batch_grid",
@@ -134,6 +134,7 @@ _sig("simplex_map_destroy", [_vp])
 _sig("simplex_map_info", [_vp, ctypes.POINTER(SimplexMapInfo)])
 _sig("simplex_map_block", [_vp, _i32, _u64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i32)])
 _sig("simplex_write", [_vp, _vp, _u32, _i32, _vp])
+_sig("simplex_accum", [_vp, _vp, _u32, _i32, _vp])
 _sig("simplex_ca_init", [_vp, _vp, _u32, _u32, _vp, _vp])
 _sig("simplex_ca_step", [_vp, _vp, _vp, _u32, _u32, _vp, _i32, _vp])
 _sig("simplex_ca_run", [_vp, _vp, _vp, _i32, _u32, _u32, _vp, _i32, _i32, _vp])
@@ -279,6 +280,13 @@ def simplex_write(mp: SimplexMap, out: torch.Tensor, seed: int, mode: int = SIMP
     p = _dptr(out, torch.int32, "out", mp.numel) if out.dtype == torch.int32 else \
         _dptr(out, torch.uint32, "out", mp.numel)
     _check(_lib.simplex_write(mp.handle, p, seed & 0xFFFFFFFF, mode, _stream()), "simplex_write")
+
+
+def simplex_accum(mp: SimplexMap, data: torch.Tensor, add: int = 1, mode: int = SIMPLEX_MODE_H):
+    """ACCUM test: data[x] += add (mod 2^32) on every domain cell (int32 or uint32 tensor)."""
+    p = _dptr(data, torch.int32, "data", mp.numel) if data.dtype == torch.int32 else \
+        _dptr(data, torch.uint32, "data", mp.numel)
+    _check(_lib.simplex_accum(mp.handle, p, add & 0xFFFFFFFF, mode, _stream()), "simplex_accum")
 
 
 def simplex_ca_init(mp: SimplexMap, grid: torch.Tensor, seed: int, threshold: int,

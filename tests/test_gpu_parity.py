@@ -305,6 +305,32 @@ def test_ca_rejects_bad_layouts():
         sx.simplex_ca_step(mp4, a, a.clone(), *inputs.B3S23)
 
 
+# ---------------------------------------------------------------- ACCUM
+ACCUM_CASES = [(2, 1023, 16, None), (2, 1000, 16, 1004), (2, 1000, 16, 1001), (2, 0, 16, None), (2, 300, 64, None),
+               (3, 100, 8, None), (3, 63, 4, 66), (3, 200, 16, None), (4, 20, 4, None), (4, 31, 8, None)]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("m,n,block,side", ACCUM_CASES)
+def test_accum_matches_oracle(m, n, block, side, mode):
+    """Two ACCUM launches (+5, then +2^32 - 3) on random data: domain cells
+    gain 2 mod 2^32, every other cell -- outside the domain and padding -- is
+    untouched; 16-byte and 4-byte paths (side % 4), m = 2, 3, 4."""
+    mp = sx.simplex_map_create(m, n, 2, 2 if m <= 3 else m, block, side=side)
+    rng = np.random.default_rng(n * 10 + m)
+    init = rng.integers(0, 1 << 32, size=mp.shape, dtype=np.uint64).astype(np.uint32)
+    d = torch.from_numpy(init.view(np.int32).reshape(-1).copy()).to(DEV)
+    sx.simplex_accum(mp, d, 5, mode)
+    sx.simplex_accum(mp, d, (1 << 32) - 3, mode)
+    got = d.cpu().numpy().view(np.uint32).reshape(mp.shape)
+    logical = tuple(slice(0, n + 1) for _ in range(m))
+    ref = oracle.accum(m, n, oracle.accum(m, n, init[logical], 5), (1 << 32) - 3)
+    np.testing.assert_array_equal(got[logical], ref)
+    pad = np.ones(mp.shape, dtype=bool)
+    pad[logical] = False
+    np.testing.assert_array_equal(got[pad], init[pad])
+
+
 # ---------------------------------------------------------------- full workload sizes
 def test_ca_m3_full_size_steps_match_oracle():
     """m = 3, n = 1023, B5/S45, Bernoulli(0.3): first steps whole-grid against the
