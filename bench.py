@@ -218,6 +218,10 @@ def _workload(name, args=None):
         wl = inputs.WRITE_M2
     elif name == "write4":
         wl = inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
+    elif name == "accum2":
+        wl = inputs.ACCUM_M2
+    elif name == "accum3":
+        wl = inputs.ACCUM_M3
     elif name == "map2":
         wl = inputs.MAP_M2
     elif name == "map3":
@@ -634,13 +638,23 @@ def run_ours(args, rank, world, local):
         # microseconds), captured in a CUDA graph so the host is off the path
         reps = 100
 
+        accum = args.workload in ("accum2", "accum3")
+        if accum:
+            reps = 10  # the ACCUM arrays are 1 and 4 GiB: a launch moves 1.1 / 1.4 GB
+
+        def launch(mode):
+            if accum:
+                sx.simplex_accum(mp, out, 1, mode)
+            else:
+                sx.simplex_write(mp, out, wl.seed, mode)
+
         def graph_of(mode):
             g = torch.cuda.CUDAGraph()
-            sx.simplex_write(mp, out, wl.seed, mode)  # warm the launch path outside capture
+            launch(mode)  # warm the launch path outside capture
             torch.cuda.synchronize()
             with torch.cuda.graph(g):
                 for _ in range(reps):
-                    sx.simplex_write(mp, out, wl.seed, mode)
+                    launch(mode)
             return g
 
         graphs = {m: graph_of(m) for m in (sx.SIMPLEX_MODE_H, sx.SIMPLEX_MODE_BB, sx.SIMPLEX_MODE_BB_THREAD)}
@@ -662,19 +676,20 @@ def run_ours(args, rank, world, local):
         med_ms = mean_ms
         mean_bb = _per_launch_ms(graphs[sx.SIMPLEX_MODE_BB].replay, 10)[0] / reps
         mean_bbt = _per_launch_ms(graphs[sx.SIMPLEX_MODE_BB_THREAD].replay, 10)[0] / reps
-        alg_bytes = 4 * cells
+        alg_bytes = (8 if accum else 4) * cells  # ACCUM reads and writes each cell
         achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
         res.update(
             metric=METRIC, value=value, unit="cells/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="u32", data="synthetic",
             config={"workload": wl.name, "m": wl.m, "n": wl.n, "array": f"{mp.side}^{wl.m} uint32",
-                    "tile": f"{wl.block}^{wl.m}", "writes_per_step": reps, "cells": cells, "map": _map_name(info),
-                    "parallelism": "replicas" if world > 1 else "single",
-                    "l2": "array re-written back to back (L2-resident when it fits)"},
+                    "tile": f"{wl.block}^{wl.m}", "launches_per_step": reps, "cells": cells,
+                    "map": _map_name(info), "parallelism": "replicas" if world > 1 else "single",
+                    "l2": ("arrays of 1 / 4 GiB >> 129 MB L2, no flush" if accum
+                           else "array re-written back to back (L2-resident when it fits)")},
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                       "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                      "kernel": f"write_kernel<{wl.m}>", "alg_bytes_per_launch": alg_bytes,
+                      "kernel": f"{'accum' if accum else 'write'}_kernel<{wl.m}>", "alg_bytes_per_launch": alg_bytes,
                       "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
             clocks=clk, gpu_launches=args.steps * reps,
             bb={"value": value_bb, "speedup_h_over_bb": value / value_bb, "launch_ms_mean": mean_bb,
@@ -689,17 +704,21 @@ def run_ours(args, rank, world, local):
             "bb": None if args.no_bb else _energy_region(meter, step(sx.SIMPLEX_MODE_BB), secs_bb / args.steps,
                                                           cells * reps),
             "unit": "cells per joule (board energy, NVML, a separate ~1.5 s run per map)"}
-        # end to end: write on the device, read the array back to pinned host memory
+        # end to end: (ACCUM: the array in from pinned host memory,) the kernel,
+        # the array back to pinned host memory
         h_out = torch.empty(mp.numel, dtype=torch.int32).pin_memory()
+        h_in = h_out.clone().pin_memory() if accum else None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(3):
-            sx.simplex_write(mp, out, wl.seed)
+            if accum:
+                out.copy_(h_in, non_blocking=True)
+            launch(sx.SIMPLEX_MODE_H)
             h_out.copy_(out, non_blocking=True)
             torch.cuda.synchronize()
         t1 = time.perf_counter()
         e2e_val, _ = aggregate(cells * 3, t1 - t0, world)
-        res["e2e"] = {"value": e2e_val, "unit": "cells/s", "h2d_bytes_per_step": 0,
+        res["e2e"] = {"value": e2e_val, "unit": "cells/s", "h2d_bytes_per_step": 4 * mp.numel if accum else 0,
                       "d2h_bytes_per_step": 4 * mp.numel}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl)
@@ -815,6 +834,17 @@ def _oracle_sample(wl, steps_sample):
         dt = time.perf_counter() - t0
         note = f"{steps_sample} automaton step(s) of the full n={wl.n} grid ({cells} cells each)"
         return cells * steps_sample / dt, note, cores, dt
+    if wl.name.startswith("accum"):
+        # ACCUM on a smaller array of the same simplex dimension (the workload's
+        # 1 / 4 GiB arrays would spend the time copying, not adding)
+        ns = min(wl.n, 4095 if wl.m == 2 else 511)
+        data = np.zeros(oracle.dense_shape(wl.m, ns), dtype=np.uint32)
+        cells = oracle.count_cells(wl.m, ns)
+        t0 = time.perf_counter()
+        for _ in range(steps_sample):
+            data = oracle.accum(wl.m, ns, data, 1)
+        dt = time.perf_counter() - t0
+        return cells * steps_sample / dt, f"{steps_sample} ACCUM pass(es) of n={ns} (array copy included)", cores, dt
     cells = oracle.count_cells(wl.m, wl.n)
     t0 = time.perf_counter()
     for _ in range(steps_sample):
@@ -848,7 +878,7 @@ def run_reference(args, rank, world):
     wl = _workload(args.workload, args)
     if wl in ("batch", "serve") or args.workload in ("map2", "map3"):
         return {"impl": "reference", "unavailable": f"the oracle arm times the single-instance workloads "
-                f"(ca2, ca3, write2, write4, edm), not {args.workload}"}
+                f"(ca2, ca3, write2, write4, accum2, accum3, edm), not {args.workload}"}
     unit = UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s"
     if args.workload == "edm":
         sample = lambda k: _oracle_edm_sample(8191)  # noqa: E731
@@ -881,7 +911,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ca2",
-                    choices=["ca2", "ca3", "write2", "write4", "map2", "map3", "edm", "batch", "serve"])
+                    choices=["ca2", "ca3", "write2", "write4", "accum2", "accum3", "map2", "map3", "edm", "batch",
+                             "serve"])
     ap.add_argument("--serve-seconds", type=float, default=inputs.SERVE_SECONDS, help="serve: trace length")
     ap.add_argument("--serve-sample", type=int, default=400, help="serve: jobs re-run alone for the serial baseline")
     ap.add_argument("--serve-capacity-jobs", type=int, default=4000, help="serve: jobs of the offline capacity run")
