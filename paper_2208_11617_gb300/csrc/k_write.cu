@@ -16,33 +16,40 @@
 
 namespace sx {
 
+// The tile of CUDA block v, the same value in every thread of the block.  For
+// m >= 3 the generic decodes are long, so warp 0 decodes once and shares the
+// result through sX (M + 1 ints of shared memory); m = 2 decodes in every
+// thread (the Eq. map2d decode is a few instructions).  Every thread of the
+// block must call it.
+template <int M>
+__device__ __forceinline__ bool block_decode(const Plan &p, int kind, uint64_t v, int32_t *X, int32_t *sX)
+{
+    if (M < 3) return decode<M>(p, kind, v, X);
+    if (threadIdx.x < 32) {
+        const bool ok = decode<M>(p, kind, v, X);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) sX[i] = X[i];
+            sX[M] = ok ? 1 : 0;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < M; ++i) X[i] = sX[i];
+    const bool ok = sX[M] != 0;
+    __syncthreads();  // sX is read by every thread before the next block rewrites it
+    return ok;
+}
+
 template <int M>
 __global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__restrict__ out, uint32_t seed,
                                                     int kind, uint64_t nblocks, int vec)
 {
     const uint32_t nchunks = 1u << (M * p.log_rho - 2);
-    __shared__ int32_t sX[M + 1];  // m >= 3: the block's tile, decoded once by warp 0
+    __shared__ int32_t sX[M + 1];  // block_decode's shared copy of the tile (m >= 3)
     for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
         int32_t X[M];
-        if (M >= 3) {
-            // the generic decodes are long: one warp decodes the block for all
-            if (threadIdx.x < 32) {
-                const bool ok = decode<M>(p, kind, v, X);
-                if (threadIdx.x == 0) {
-#pragma unroll
-                    for (int i = 0; i < M; ++i) sX[i] = X[i];
-                    sX[M] = ok ? 1 : 0;
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < M; ++i) X[i] = sX[i];
-            const bool ok = sX[M] != 0;
-            __syncthreads();  // sX is read by every thread before the next block rewrites it
-            if (!ok) continue;
-        } else if (!decode<M>(p, kind, v, X)) {
-            continue;
-        }
+        if (!block_decode<M>(p, kind, v, X, sX)) continue;
         const int64_t s0 = tile_base_sum<M>(p, X);
         if (s0 > p.n && kind != kMapBBThread) continue;  // tile past the domain
         const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
@@ -78,27 +85,10 @@ __global__ void __launch_bounds__(256) accum_kernel(const Plan p, uint32_t *__re
                                                     int kind, uint64_t nblocks, int vec)
 {
     const uint32_t nchunks = 1u << (M * p.log_rho - 2);
-    __shared__ int32_t sX[M + 1];
+    __shared__ int32_t sX[M + 1];  // block_decode's shared copy of the tile (m >= 3)
     for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
         int32_t X[M];
-        if (M >= 3) {
-            if (threadIdx.x < 32) {
-                const bool ok = decode<M>(p, kind, v, X);
-                if (threadIdx.x == 0) {
-#pragma unroll
-                    for (int i = 0; i < M; ++i) sX[i] = X[i];
-                    sX[M] = ok ? 1 : 0;
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < M; ++i) X[i] = sX[i];
-            const bool ok = sX[M] != 0;
-            __syncthreads();
-            if (!ok) continue;
-        } else if (!decode<M>(p, kind, v, X)) {
-            continue;
-        }
+        if (!block_decode<M>(p, kind, v, X, sX)) continue;
         const int64_t s0 = tile_base_sum<M>(p, X);
         if (s0 > p.n && kind != kMapBBThread) continue;
         const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
