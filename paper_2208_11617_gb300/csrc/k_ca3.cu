@@ -212,11 +212,20 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 if (reach < (int64_t)r.b) r.b = (int32_t)reach;
                 if (r.b < r.a) continue;
                 if (!(ok = header(make_int4(zs, r.X2, r.a, r.b)))) break;
+                // the slab's right-halo column past its run holds live cells only
+                // if x3 = c * 32 can be reached from the halo rows (x1 >= z0 - 1,
+                // x2 >= y0 - 1); else it is all zeros and is not loaded (the
+                // consumers see it as absent: stream_has_right)
+                const int64_t hreach = p.n - (int64_t)zs * (32 / kStreamZSplit) - (int64_t)r.X2 * 32 + 2;
                 for (int32_t c = r.a - 1; c <= r.b + 1; ++c, ++seq) {
                     const int s = (int)(seq % S);
                     if (seq >= (uint64_t)S &&
                         !(ok = mbar_wait_bounded(&empty[s], (uint32_t)((seq / S - 1) & 1), kWaitLimitNs)))
                         break;
+                    if (c == r.b + 1 && (int64_t)c * 32 > hreach) {
+                        mbar_arrive(&full[s]);  // an empty column: the phase completes with no bytes
+                        continue;
+                    }
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(&full[s], kColBytes);
                     tma_load_3d(ring + s * kColBytes, &tcol, c * 32, r.X2 * 32 - 1, zs * (32 / kStreamZSplit) - 1,
@@ -256,7 +265,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 const int64_t x0 = (int64_t)x3 * 32;
                 const bool partial = z0 + y0 + x0 + (32 / kStreamZSplit - 1) + 2 * 31 > p.n;
                 my_live += ca3_tile32c<8, ORK>(ring + (c % S) * kColBytes, ring + ((c - 1) % S) * kColBytes,
-                                               ring + ((c + 1) % S) * kColBytes, x3 > 0, x0 + 32 <= p.n, p.n, p.side,
+                                               ring + ((c + 1) % S) * kColBytes, x3 > 0,
+                                               x0 + 32 <= p.n - z0 - y0 + 2, p.n, p.side,
                                                rule, out, x0, y0, z0, partial, tx, pr, tz);
                 __syncwarp();
                 if (lane == 0) {
