@@ -50,17 +50,23 @@ _KERNEL_SOURCES = {
 }
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (mean of 3 launches
 # at full size), for the kernel sources with the given fingerprint
-_KERNEL_TRAFFIC = {("dd4f335cea150870", "ca2_step_kernel<128>", 32767): 1_032_842_837,
-                   ("c37e9ab828aa4255", "ca3_step_kernel<32>", 1023): 521_809_152,
-                   ("c37e9ab828aa4255", "ca3_step_stream", 1023): 407_859_712}
+_KERNEL_TRAFFIC = {("aec6365a50ef8a26", "ca2_step_kernel<128>", 32767): 1_032_545_877,
+                   ("464ecdb6afbca9f1", "ca3_step_kernel<32>", 1023): 521_488_810,
+                   ("464ecdb6afbca9f1", "ca3_step_stream", 1023): 399_034_453}
 
 
 def _kernel_fingerprint(kname):
+    """Hash of the kernel's sources with comments and whitespace removed: a
+    change to the code (not to its comments) drops the recorded traffic."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in _KERNEL_SOURCES.get(kname, []):
-        with open(os.path.join(ROOT, _CSRC + f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, _CSRC + f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)   # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                # line comments
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
