@@ -520,7 +520,7 @@ def run_serve(args, rank, world):
                    "server_cell_updates_per_s": hl["cell_updates"] / (hl["wall_ms"] * 1e-3),
                    "mean_resident_jobs": hl["mean_active"], "serial_utilisation": hl_rate * mean_svc,
                    "serial_fifo_p50_ms": hq(0.5), "serial_fifo_p99_ms": hq(0.99)},
-        roofline=None, clocks=clk, gpu_launches=None,
+        roofline=None, clocks=clk, gpu_launches=st["launches"],
         e2e={"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     )
 

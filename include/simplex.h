@@ -485,6 +485,7 @@ typedef struct simplex_server_stats {
     double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* latency: done - arrival */
     double host_issue_ms;    /* host time spent building and issuing rounds */
     double gpu_round_ms;     /* mean device time of a round: its first operation to its last */
+    uint64_t launches;       /* kernels launched: admission inits, direct steps, passes, digests */
 } simplex_server_stats_t;
 
 /* Device bytes the server's arena needs for these parameters (tables + pool). */

@@ -167,6 +167,7 @@ struct simplex_server {
     uint64_t rounds = 0, cell_updates = 0, active_sum = 0;
     double wall_ms = 0;
     double gpu_round_ms = 0;                     // device time of the retired rounds
+    uint64_t launches = 0;                       // kernels launched (init, steps, passes, digests)
     // the stream of the current trace or online session; online calls need
     // simplex_server_begin first
     cudaStream_t stream = nullptr;
@@ -278,6 +279,7 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
         cuda_fail(e, "admitting a job");
         return -1;
     }
+    s->launches += 1;
     job.status = kActive;
     job.slot = slot;
     job.off = off;
@@ -373,6 +375,7 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
                 e = bi.plan.m == 2 ? sx::launch_ca2_step(bi.plan, tm, out, bi.rule, sx::kMapH, lv, st)
                                    : sx::launch_ca3_step(bi.plan, tm, out, bi.rule, sx::kMapH, lv, nullptr, st);
                 if (e != cudaSuccess) return cuda_fail(e, "launching a job's step");
+                s->launches += 1;
             }
         } else {
             const uint32_t tag =
@@ -421,6 +424,8 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
             if ((e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q + k, live,
                                            s->prm.max_steps + 1, 0, false, st, nullptr, 0, k)) != cudaSuccess)
                 return cuda_fail(e, "launching a serving round");
+            else
+                s->launches += 1;
     } else if (!s->fin_items.empty() &&
                (e = cudaMemsetAsync(q + K, 0, sizeof(unsigned int), st)) != cudaSuccess) {  // the digest pass's counter
         return cuda_fail(e, "launching a serving round");
@@ -432,6 +437,7 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
             (e = sx::launch_batch_pass(insts, fitems, (uint32_t)s->fin_items.size(), tmaps, s->arena, 0, q + K,
                                        nullptr, 0, 0, true, st, dig)) != cudaSuccess)
             return cuda_fail(e, "launching the digest pass");
+        s->launches += 1;
         for (int64_t j : r.finishing) {
             const int slot = s->jobs[j].slot;
             const size_t row = (size_t)(s->prm.max_steps + 1);
@@ -506,6 +512,7 @@ int reset_session(simplex_server *s, cudaStream_t st)
     s->active_items = 0;
     s->host_round_ms = 0;
     s->gpu_round_ms = 0;
+    s->launches = 0;
     s->wall_ms = 0;
     s->pool.reset(s->prm.hbm_budget);
     cudaError_t e = sx::batch_prepare();
@@ -779,6 +786,7 @@ int simplex_server_stats(simplex_server_t s, simplex_server_stats_t *out)
     out->peak_pool_bytes = s->pool.peak();
     out->host_issue_ms = s->host_round_ms;
     out->gpu_round_ms = s->rounds ? s->gpu_round_ms / (double)s->rounds : 0.0;
+    out->launches = s->launches;
     if (!lat.empty()) {
         std::sort(lat.begin(), lat.end());
         auto q = [&](double f) { return lat[std::min(lat.size() - 1, (size_t)(f * (double)(lat.size() - 1) + 0.5))]; };

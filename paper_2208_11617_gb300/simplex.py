@@ -114,7 +114,8 @@ class SimplexServerStats(ctypes.Structure):
                 ("rounds", ctypes.c_uint64), ("cell_updates", ctypes.c_uint64), ("peak_pool_bytes", ctypes.c_uint64),
                 ("wall_ms", ctypes.c_double), ("mean_active", ctypes.c_double), ("p50_ms", ctypes.c_double),
                 ("p90_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("mean_ms", ctypes.c_double), ("host_issue_ms", ctypes.c_double), ("gpu_round_ms", ctypes.c_double)]
+                ("mean_ms", ctypes.c_double), ("host_issue_ms", ctypes.c_double), ("gpu_round_ms", ctypes.c_double),
+                ("launches", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -49,6 +49,7 @@ def test_jobs_equal_alone_and_in_the_mix():
     st = srv.stats()
     assert st["completed"] == len(jobs) and st["rejected"] == 0
     assert st["mean_active"] > 1.0, st          # resident jobs shared rounds
+    assert st["launches"] >= len(jobs) + st["rounds"]   # an init per job and at least one launch per round
     # the same jobs all at once: many resident per round, same results
     burst = sx.SimplexServer(hbm_budget=2 << 30, max_jobs=512, max_steps=12)
     burst.run(jobs, None, realtime=False)
