@@ -438,9 +438,10 @@ int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t gri
  * a digest of their final grid are copied to host memory and their memory
  * returns to the pool.  A job's result is identical whether it runs alone or
  * among others.  Tiles: m = 2: 128 from n = 1024 up, else 64; m = 3: 16.
- * Light rounds (at most direct_jobs resident jobs) launch each job's steps
- * with the single-instance step kernels on its own grids instead: a batched
- * pass costs more than a few jobs' own step launches.
+ * With at most direct_jobs jobs resident, each job's next steps (up to 4x
+ * round_steps) go out as single-instance step launches on its own grids and
+ * on a side stream of its own, so light jobs run concurrently: a batched pass
+ * costs more than a few jobs' own step launches.
  */
 typedef struct simplex_server *simplex_server_t;
 
@@ -453,9 +454,9 @@ typedef struct simplex_server_params {
     int32_t max_inflight;    /* rounds the host may queue ahead of the GPU (1..64) */
     int32_t round_steps;     /* automaton steps per batched round, 1..64; 0 means 16 (a
                                 direct round takes up to 4x as many, at most 64) */
-    int32_t direct_jobs;     /* a round with at most this many resident jobs runs each job's
-                                steps as single-instance step launches instead of batched
-                                passes; 0 means 3, -1 never, at most 64 */
+    int32_t direct_jobs;     /* with at most this many resident jobs, each job's steps run as
+                                single-instance step launches on a side stream of its own
+                                instead of batched passes; 0 means 3, -1 never, at most 64 */
 } simplex_server_params_t;
 
 typedef struct simplex_job {
@@ -481,7 +482,7 @@ typedef struct simplex_server_stats {
     uint64_t cell_updates;   /* sum over completed work of cells x steps */
     uint64_t peak_pool_bytes;
     double wall_ms;          /* from the start of the trace to the last completion seen */
-    double mean_active;      /* resident jobs per round */
+    double mean_active;      /* resident jobs per round or direct chunk launch */
     double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* latency: done - arrival */
     double host_issue_ms;    /* host time spent building and issuing rounds */
     double gpu_round_ms;     /* mean device time of a round: its first operation to its last */

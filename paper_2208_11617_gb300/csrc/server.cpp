@@ -9,10 +9,12 @@
 // one step, whatever step each job is at (per-item tags select each job's
 // input grid and live-count slot).  Several steps per round keep the
 // per-round costs (item upload, digest pass, result copies, event) off most
-// steps, so a job's latency approaches its run time alone.  A light round
-// (at most direct_jobs resident jobs) launches each job's steps with the
-// single-instance step kernels on its own grids and tensor maps instead: a
-// persistent batched pass costs more than a few jobs' own launches.  Between
+// steps, so a job's latency approaches its run time alone.  With at most
+// direct_jobs jobs resident the server works in direct chunks instead: each
+// job's next steps go out as single-instance step launches on its own grids
+// and tensor maps, on a side stream of its own, so light jobs run
+// concurrently and a new arrival does not queue behind another job's chunk
+// (a persistent batched pass costs more than a few jobs' own launches).  Between
 // rounds the host loop admits jobs that have arrived (first come, first
 // served) as soon as a slot and enough pool memory are free, and retires jobs
 // whose last step has completed (their results -- live counts of every step
@@ -115,12 +117,25 @@ struct ServerJob {
     std::vector<uint64_t> live;
     uint64_t cells = 0;
     uint64_t items = 0;  // work items per round
+    bool busy = false;   // a direct chunk of its steps is in flight on a side stream
 };
 
 struct Round {
     cudaEvent_t ev0 = nullptr, ev = nullptr;  // before its first operation, after its last
     std::vector<int64_t> finishing;
 };
+
+// A direct chunk: the next steps of one job (and, when they are its last,
+// its digest and result copies) on a side stream of its own.
+struct Chunk {
+    int64_t job = -1;
+    cudaEvent_t ev0 = nullptr, ev = nullptr;
+    bool finishing = false;
+};
+
+// Side streams of the direct chunks: job slot s uses side[s % kSideStreams],
+// so the chunks of different light jobs run concurrently.
+constexpr int kSideStreams = 4;
 
 int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
 
@@ -168,6 +183,9 @@ struct simplex_server {
     double wall_ms = 0;
     double gpu_round_ms = 0;                     // device time of the retired rounds
     uint64_t launches = 0;                       // kernels launched (init, steps, passes, digests)
+    std::vector<Chunk> chunks;                   // direct chunks in flight
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t main_ev = nullptr;               // orders a chunk after the main stream's work
     // the stream of the current trace or online session; online calls need
     // simplex_server_begin first
     cudaStream_t stream = nullptr;
@@ -311,6 +329,67 @@ cudaError_t take_event(simplex_server *s, cudaEvent_t *ev)
     return cudaSuccess;
 }
 
+// Launches a direct chunk for active job j on its side stream: its next
+// min(r, 4 K) steps as single-instance step launches (the same kernels and
+// results as simplex_ca_step), and after its last step the digest of the
+// final grid and the copies of its results.  The side stream first waits for
+// everything already queued on the main stream (the job's admission, and the
+// batched rounds it took part in).
+int launch_chunk(simplex_server *s, int64_t j, cudaStream_t st)
+{
+    ServerJob &job = s->jobs[j];
+    const sx::BatchInst &bi = s->slot_inst[job.slot];
+    cudaStream_t cs = s->side[job.slot % kSideStreams];
+    const int np = std::min(std::min(kMaxRoundSteps, 4 * round_steps(s->prm)), job.spec.steps - job.step);
+    unsigned long long *live_row =
+        reinterpret_cast<unsigned long long *>(s->arena + s->off_live) + (size_t)job.slot * (size_t)(s->prm.max_steps + 1);
+    unsigned long long *dig = reinterpret_cast<unsigned long long *>(s->arena + s->off_digest) + job.slot;
+    Chunk c;
+    c.job = j;
+    cudaError_t e;
+    if ((e = cudaEventRecord(s->main_ev, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, s->main_ev, 0)) != cudaSuccess ||
+        (e = take_event(s, &c.ev0)) != cudaSuccess || (e = cudaEventRecord(c.ev0, cs)) != cudaSuccess)
+        return cuda_fail(e, "starting a direct chunk");
+    // step k reads grid parity ^ k and counts at step index + k, as a batched pass does
+    for (int k = 0; k < np; ++k) {
+        const int par = job.parity ^ (k & 1);
+        uint8_t *out = s->arena + bi.grid[par ^ 1];
+        const CUtensorMap &tm = s->slot_tmap[2 * job.slot + par];
+        e = bi.plan.m == 2 ? sx::launch_ca2_step(bi.plan, tm, out, bi.rule, sx::kMapH, live_row + job.step + 1 + k, cs)
+                           : sx::launch_ca3_step(bi.plan, tm, out, bi.rule, sx::kMapH, live_row + job.step + 1 + k,
+                                                 nullptr, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "launching a job's step");
+        s->launches += 1;
+    }
+    job.step += np;
+    job.parity ^= np & 1;
+    s->cell_updates += job.cells * (uint64_t)np;
+    c.finishing = job.step == job.spec.steps;
+    if (c.finishing) {
+        const size_t row = (size_t)(s->prm.max_steps + 1);
+        if ((e = sx::launch_ca_count(bi.plan, s->arena + bi.grid[job.parity], nullptr, cs, dig)) != cudaSuccess)
+            return cuda_fail(e, "launching a job's digest");
+        s->launches += 1;
+        if ((e = cudaMemcpyAsync(s->host_live + job.slot * row, live_row,
+                                 sizeof(unsigned long long) * (size_t)(job.spec.steps + 1), cudaMemcpyDeviceToHost,
+                                 cs)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(s->host_digest + job.slot, dig, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 cs)) != cudaSuccess)
+            return cuda_fail(e, "copying job results");
+    }
+    if ((e = take_event(s, &c.ev)) != cudaSuccess || (e = cudaEventRecord(c.ev, cs)) != cudaSuccess)
+        return cuda_fail(e, "recording the end of a direct chunk");
+    job.busy = true;
+    s->active_sum += s->active.size();  // resident jobs sharing the GPU at this launch
+    if (c.finishing) {  // the job leaves the active set now; its memory is released at retirement
+        s->active.erase(std::find(s->active.begin(), s->active.end(), j));
+        s->active_items -= job.items;
+    }
+    s->chunks.push_back(c);
+    s->rounds += 1;
+    return SIMPLEX_OK;
+}
+
 int launch_round(simplex_server *s, cudaStream_t st)
 {
     const auto t = std::chrono::steady_clock::now();
@@ -340,20 +419,16 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     } guard{s, &r, true};
     if ((e = take_event(s, &r.ev0)) != cudaSuccess || (e = cudaEventRecord(r.ev0, st)) != cudaSuccess)
         return cuda_fail(e, "recording the start of a serving round");
-    // a light round runs each job's steps with the single-instance step
-    // kernels (one launch per job and step) instead of batched passes
-    const int dj = direct_jobs(s->prm);
-    const bool direct = dj > 0 && s->active.size() <= (size_t)dj;
-    // a direct round takes up to 4 K steps: with few jobs resident a new
-    // arrival waits little for it, and fewer rounds mean fewer round costs
-    const int Kr = direct ? std::min(kMaxRoundSteps, 4 * K) : K;
-    unsigned long long *live_all = reinterpret_cast<unsigned long long *>(s->arena + s->off_live);
-    const size_t live_row = (size_t)(s->prm.max_steps + 1);
     // blocks per work item: 8 when a pass has work for every resident CTA
     // several times over, fewer (down to 1) when it has not, so that a light
     // pass is spread over more CTAs instead of queueing blocks behind each other
-    uint64_t blocks = 0;
-    for (int64_t j : s->active) blocks += s->slot_inst[s->jobs[j].slot].plan.h_blocks;
+    // (jobs with a direct chunk in flight sit this round out)
+    uint64_t blocks = 0, members = 0;
+    for (int64_t j : s->active)
+        if (!s->jobs[j].busy) {
+            blocks += s->slot_inst[s->jobs[j].slot].plan.h_blocks;
+            ++members;
+        }
     uint64_t chunk = blocks / (2 * s->ctas + 1);
     chunk = chunk < 1 ? 1 : (chunk > (uint64_t)sx::kBatchChunk ? (uint64_t)sx::kBatchChunk : chunk);
     // one item list for the round's passes: a job with r steps left takes part
@@ -362,28 +437,14 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     int passes = 0;
     for (int64_t j : s->active) {
         ServerJob &job = s->jobs[j];
+        if (job.busy) continue;
         const sx::BatchInst &bi = s->slot_inst[job.slot];
-        const int np = std::min(Kr, job.spec.steps - job.step);
+        const int np = std::min(K, job.spec.steps - job.step);
         passes = std::max(passes, np);
-        if (direct) {
-            // step k reads grid parity ^ k and counts at step index + k, as a pass does
-            for (int k = 0; k < np; ++k) {
-                const int par = job.parity ^ (k & 1);
-                uint8_t *out = s->arena + bi.grid[par ^ 1];
-                unsigned long long *lv = live_all + (size_t)job.slot * live_row + (size_t)(job.step + 1 + k);
-                const CUtensorMap &tm = s->slot_tmap[2 * job.slot + par];
-                e = bi.plan.m == 2 ? sx::launch_ca2_step(bi.plan, tm, out, bi.rule, sx::kMapH, lv, st)
-                                   : sx::launch_ca3_step(bi.plan, tm, out, bi.rule, sx::kMapH, lv, nullptr, st);
-                if (e != cudaSuccess) return cuda_fail(e, "launching a job's step");
-                s->launches += 1;
-            }
-        } else {
-            const uint32_t tag =
-                (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1) | ((uint32_t)(np - 1) << 13);
-            for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += chunk) {
-                const uint64_t cnt = std::min<uint64_t>(chunk, bi.plan.h_blocks - v0);
-                s->items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt, tag});
-            }
+        const uint32_t tag = (uint32_t)job.parity | ((uint32_t)(job.step + 1) << 1) | ((uint32_t)(np - 1) << 13);
+        for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += chunk) {
+            const uint64_t cnt = std::min<uint64_t>(chunk, bi.plan.h_blocks - v0);
+            s->items.push_back(sx::BatchItem{(uint32_t)job.slot, (uint32_t)v0, (uint32_t)cnt, tag});
         }
         job.step += np;
         job.parity ^= np & 1;
@@ -400,7 +461,7 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     if (s->items.size() > s->max_items || s->fin_items.size() > s->max_items)
         return fail(SIMPLEX_ENOMEM, "a round needs %zu work items, max_items is %llu", s->items.size(),
                     (unsigned long long)s->max_items);
-    s->active_sum += s->active.size();
+    s->active_sum += members;
     const sx::BatchInst *insts = reinterpret_cast<const sx::BatchInst *>(s->arena + s->off_insts);
     const CUtensorMap *tmaps = reinterpret_cast<const CUtensorMap *>(s->arena + s->off_tmaps);
     sx::BatchItem *items = reinterpret_cast<sx::BatchItem *>(s->arena + s->off_items);
@@ -414,21 +475,16 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     // rewritten max_inflight + 1 rounds later, when the round that read it has
     // completed (the run loop never keeps more than max_inflight in flight)
     sx::BatchItem *stage = s->stage + (s->round_no % ring) * 2 * s->max_items;
-    if (!direct) {
-        std::memcpy(stage, s->items.data(), sizeof(sx::BatchItem) * s->items.size());
-        if ((e = cudaMemsetAsync(q, 0, sizeof(unsigned int) * (size_t)(K + 1), st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice,
-                                 st)) != cudaSuccess)
-            return cuda_fail(e, "launching a serving round");
-        for (int k = 0; k < passes; ++k)
-            if ((e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q + k, live,
-                                           s->prm.max_steps + 1, 0, false, st, nullptr, 0, k)) != cudaSuccess)
-                return cuda_fail(e, "launching a serving round");
-            else
-                s->launches += 1;
-    } else if (!s->fin_items.empty() &&
-               (e = cudaMemsetAsync(q + K, 0, sizeof(unsigned int), st)) != cudaSuccess) {  // the digest pass's counter
+    std::memcpy(stage, s->items.data(), sizeof(sx::BatchItem) * s->items.size());
+    if ((e = cudaMemsetAsync(q, 0, sizeof(unsigned int) * (size_t)(K + 1), st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(items, stage, sizeof(sx::BatchItem) * s->items.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
         return cuda_fail(e, "launching a serving round");
+    for (int k = 0; k < passes; ++k) {
+        if ((e = sx::launch_batch_pass(insts, items, (uint32_t)s->items.size(), tmaps, s->arena, 0, q + k, live,
+                                       s->prm.max_steps + 1, 0, false, st, nullptr, 0, k)) != cudaSuccess)
+            return cuda_fail(e, "launching a serving round");
+        s->launches += 1;
     }
     if (!s->fin_items.empty()) {
         std::memcpy(stage + s->max_items, s->fin_items.data(), sizeof(sx::BatchItem) * s->fin_items.size());
@@ -466,10 +522,59 @@ int launch_round_impl(simplex_server *s, cudaStream_t st)
     return SIMPLEX_OK;
 }
 
+// A job whose last step has completed: results from the pinned copies, its
+// memory and slot back to the pool.
+void finish_job(simplex_server *s, int64_t j, float done_ms)
+{
+    ServerJob &job = s->jobs[j];
+    const size_t row = (size_t)(s->prm.max_steps + 1);
+    job.live.assign(s->host_live + job.slot * row, s->host_live + job.slot * row + job.spec.steps + 1);
+    job.digest = s->host_digest[job.slot];
+    job.done_ms = done_ms;
+    job.status = kDone;
+    job.busy = false;
+    s->pool.release(job.off, job.bytes);
+    s->free_slots.push_back(job.slot);
+    job.slot = -1;
+}
+
+// Retires the direct chunks that have completed.  Returns the number of jobs
+// that finished (or <0); *completed += the chunks retired.
+int retire_chunks(simplex_server *s, int *completed)
+{
+    int finished = 0;
+    for (size_t i = 0; i < s->chunks.size();) {
+        Chunk &c = s->chunks[i];
+        cudaError_t e = cudaEventQuery(c.ev);
+        if (e == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "waiting for a direct chunk");
+        float ms = 0, dur = 0;
+        if ((e = cudaEventElapsedTime(&ms, s->t0, c.ev)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&dur, c.ev0, c.ev)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventElapsedTime");
+        s->gpu_round_ms += dur;
+        if (c.finishing) {
+            finish_job(s, c.job, ms);
+            ++finished;
+        } else {
+            s->jobs[c.job].busy = false;
+        }
+        s->spare_events.push_back(c.ev);
+        s->spare_events.push_back(c.ev0);
+        c = s->chunks.back();
+        s->chunks.pop_back();
+        ++*completed;
+    }
+    return finished;
+}
+
 // Retires the oldest in-flight rounds whose event has completed (or, with
 // `wait`, the oldest one regardless).  Returns the number of jobs that
-// finished, or <0.
-int retire(simplex_server *s, bool wait)
+// finished, or <0; *completed += the rounds retired.
+int retire(simplex_server *s, bool wait, int *completed)
 {
     int n = 0, finished = 0;
     while (!s->inflight.empty()) {
@@ -483,15 +588,7 @@ int retire(simplex_server *s, bool wait)
             return cuda_fail(e, "cudaEventElapsedTime");
         s->gpu_round_ms += dur;
         for (int64_t j : r.finishing) {
-            ServerJob &job = s->jobs[j];
-            const size_t row = (size_t)(s->prm.max_steps + 1);
-            job.live.assign(s->host_live + job.slot * row, s->host_live + job.slot * row + job.spec.steps + 1);
-            job.digest = s->host_digest[job.slot];
-            job.done_ms = ms;
-            job.status = kDone;
-            s->pool.release(job.off, job.bytes);
-            s->free_slots.push_back(job.slot);
-            job.slot = -1;
+            finish_job(s, j, ms);
             ++finished;
         }
         s->spare_events.push_back(r.ev);
@@ -499,6 +596,7 @@ int retire(simplex_server *s, bool wait)
         s->inflight.pop_front();
         ++n;
     }
+    *completed += n;
     return finished;
 }
 
@@ -534,12 +632,13 @@ int check_job(const simplex_server *s, const simplex_job_t &sp, int64_t i)
     return SIMPLEX_OK;
 }
 
-// One turn of the serving loop: admission (jobs that have arrived, first come
-// first served, as slots and pool memory allow), one round when jobs are
-// resident and fewer than max_inflight rounds are queued, then retirement of
-// the rounds that have completed -- waiting for the oldest one when `block`
-// and nothing else can progress.  *done += the jobs that finished (done or
-// rejected).
+// One turn of the serving loop.  Admission: jobs that have arrived, first
+// come first served, as slots and pool memory allow.  Work: with at most
+// direct_jobs jobs resident, a direct chunk for every resident job that has
+// none in flight; otherwise one batched round over those jobs when fewer than
+// max_inflight rounds are queued.  Retirement of the rounds and chunks that
+// have completed -- with `block`, waiting for one to complete when nothing
+// else can progress.  *done += the jobs that finished (done or rejected).
 int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, int64_t *done)
 {
     const double now = host_ms(s);
@@ -559,18 +658,47 @@ int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, in
         if (a == 0) break;
         s->pending.pop_front();
     }
-    if (!s->active.empty() && (int)s->inflight.size() < s->prm.max_inflight) {
+    const int dj = direct_jobs(s->prm);
+    const bool direct = dj > 0 && s->active.size() <= (size_t)dj;
+    bool idle_job = false;  // a resident job with nothing in flight
+    for (int64_t j : s->active) idle_job |= !s->jobs[j].busy;
+    if (direct) {
+        const std::vector<int64_t> act = s->active;  // launch_chunk may shrink the active set
+        for (int64_t j : act)
+            if (!s->jobs[j].busy) {
+                const int rc = launch_chunk(s, j, st);
+                if (rc) return rc;
+            }
+        idle_job = false;
+    } else if (idle_job && (int)s->inflight.size() < s->prm.max_inflight) {
         const int rc = launch_round(s, st);
         if (rc) return rc;
+        idle_job = false;
+        for (int64_t j : s->active) idle_job |= !s->jobs[j].busy;
+        idle_job = idle_job && (int)s->inflight.size() < s->prm.max_inflight;
     }
-    // keep at most max_inflight rounds queued ahead of the GPU
-    const bool must_wait = block && ((int)s->inflight.size() >= s->prm.max_inflight ||
-                                     (s->active.empty() && !s->inflight.empty() &&
-                                      (s->pending.empty() || !realtime ||
-                                       s->jobs[s->pending.front()].arrival_ms <= host_ms(s))));
-    const int r = retire(s, must_wait);
+    int completed = 0;
+    int r = retire(s, false, &completed);
     if (r < 0) return SIMPLEX_ECUDA;
     *done += r;
+    if ((r = retire_chunks(s, &completed)) < 0) return SIMPLEX_ECUDA;
+    *done += r;
+    // nothing can be launched until something completes: wait for one
+    const bool busy_gpu = !s->inflight.empty() || !s->chunks.empty();
+    const bool arrived = !s->pending.empty() && (!realtime || s->jobs[s->pending.front()].arrival_ms <= host_ms(s));
+    if (block && completed == 0 && busy_gpu && !idle_job &&
+        ((int)s->inflight.size() >= s->prm.max_inflight || !arrived || s->free_slots.empty())) {
+        while (completed == 0) {
+            if ((r = retire(s, false, &completed)) < 0) return SIMPLEX_ECUDA;
+            *done += r;
+            if ((r = retire_chunks(s, &completed)) < 0) return SIMPLEX_ECUDA;
+            *done += r;
+            if (completed == 0 && s->chunks.empty() && !s->inflight.empty()) {
+                if ((r = retire(s, true, &completed)) < 0) return SIMPLEX_ECUDA;  // only rounds: block on the oldest
+                *done += r;
+            }
+        }
+    }
     return SIMPLEX_OK;
 }
 
@@ -622,13 +750,20 @@ int simplex_server_create(const simplex_server_params_t *params, void *arena, ui
         (e = cudaMallocHost(&s->host_digest, sizeof(unsigned long long) * params->max_jobs)) != cudaSuccess ||
         (e = cudaMallocHost(&s->stage, sizeof(sx::BatchItem) * 2 * (size_t)params->max_items *
                                            (size_t)(params->max_inflight + 1))) != cudaSuccess ||
-        (e = cudaEventCreate(&s->t0)) != cudaSuccess) {
+        (e = cudaEventCreate(&s->t0)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->main_ev, cudaEventDisableTiming)) != cudaSuccess) {
         if (s->host_live) cudaFreeHost(s->host_live);
         if (s->host_digest) cudaFreeHost(s->host_digest);
         if (s->stage) cudaFreeHost(s->stage);
+        if (s->t0) cudaEventDestroy(s->t0);
         delete s;
         return cuda_fail(e, "allocating the server's pinned result buffers");
     }
+    for (auto &cs : s->side)
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+            simplex_server_destroy(s);
+            return cuda_fail(e, "creating the server's side streams");
+        }
     *out = s;
     return SIMPLEX_OK;
 }
@@ -641,7 +776,15 @@ int simplex_server_destroy(simplex_server_t s)
         cudaEventDestroy(r.ev);
         cudaEventDestroy(r.ev0);
     }
+    for (auto &c : s->chunks) {
+        cudaEventSynchronize(c.ev);
+        cudaEventDestroy(c.ev);
+        cudaEventDestroy(c.ev0);
+    }
     for (auto ev : s->spare_events) cudaEventDestroy(ev);
+    for (auto cs : s->side)
+        if (cs) cudaStreamDestroy(cs);
+    if (s->main_ev) cudaEventDestroy(s->main_ev);
     if (s->t0) cudaEventDestroy(s->t0);
     if (s->host_live) cudaFreeHost(s->host_live);
     if (s->host_digest) cudaFreeHost(s->host_digest);
@@ -655,7 +798,7 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
 {
     if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
     if (!jobs || count < 0) return fail(SIMPLEX_EINVAL, "jobs is NULL");
-    if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty())
+    if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty() || !s->chunks.empty())
         return fail(SIMPLEX_EINVAL, "the server is still running another trace");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (int i = 0; i < count; ++i) {
@@ -695,7 +838,7 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
 int simplex_server_begin(simplex_server_t s, void *stream)
 {
     if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
-    if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty())
+    if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty() || !s->chunks.empty())
         return fail(SIMPLEX_EINVAL, "the server still has jobs in progress");
     const int rc = reset_session(s, static_cast<cudaStream_t>(stream));
     s->stream_set = rc == SIMPLEX_OK;
@@ -739,7 +882,7 @@ int simplex_server_wait(simplex_server_t s, int64_t id)
     if (id >= (int64_t)s->jobs.size()) return fail(SIMPLEX_EINVAL, "no job %lld", (long long)id);
     auto finished = [&]() {
         if (id >= 0) return s->jobs[id].status == kDone || s->jobs[id].status == kRejected;
-        return s->active.empty() && s->inflight.empty() && s->pending.empty();
+        return s->active.empty() && s->inflight.empty() && s->pending.empty() && s->chunks.empty();
     };
     while (!finished()) {
         int64_t done = 0;
