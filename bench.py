@@ -928,7 +928,7 @@ def main():
     ap.add_argument("--max-inflight", type=int, default=2, help="serve: rounds the host may queue ahead of the GPU")
     ap.add_argument("--direct-jobs", type=int, default=0,
                     help="serve: rounds with at most this many resident jobs launch each job's steps directly "
-                         "(0: the default, 3; -1: never)")
+                         "(0: the default, 24; -1: never)")
     ap.add_argument("--no-tune", action="store_true", help="batch: untuned tile choices")
     ap.add_argument("--no-loop", action="store_true", help="batch: skip the single-instance loop baseline")
     ap.add_argument("--batch-m2", type=int, default=2048, help="batch: number of m = 2 instances")

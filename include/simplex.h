@@ -456,7 +456,7 @@ typedef struct simplex_server_params {
                                 direct round takes up to 4x as many, at most 64) */
     int32_t direct_jobs;     /* with at most this many resident jobs, each job's steps run as
                                 single-instance step launches on a side stream of its own
-                                instead of batched passes; 0 means 3, -1 never, at most 64 */
+                                instead of batched passes; 0 means 24, -1 never, at most 64 */
 } simplex_server_params_t;
 
 typedef struct simplex_job {

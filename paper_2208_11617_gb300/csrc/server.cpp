@@ -135,7 +135,7 @@ struct Chunk {
 
 // Side streams of the direct chunks: job slot s uses side[s % kSideStreams],
 // so the chunks of different light jobs run concurrently.
-constexpr int kSideStreams = 4;
+constexpr int kSideStreams = 8;
 
 int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
 
@@ -148,7 +148,7 @@ constexpr int kMaxRoundSteps = 64;
 
 int round_steps(const simplex_server_params_t &p) { return p.round_steps ? p.round_steps : kDefaultRoundSteps; }
 
-constexpr int kDefaultDirectJobs = 3, kMaxDirectJobs = 64;
+constexpr int kDefaultDirectJobs = 24, kMaxDirectJobs = 64;
 int direct_jobs(const simplex_server_params_t &p) { return p.direct_jobs ? p.direct_jobs : kDefaultDirectJobs; }
 
 }  // namespace
