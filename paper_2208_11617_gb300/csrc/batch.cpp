@@ -183,11 +183,31 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         grid_off += align_up(gb, 256);
         b->blocks += bi.plan.h_blocks;
         b->cells += binom((uint64_t)in.n + (uint64_t)in.m, in.m);
-        for (uint64_t v0 = 0; v0 < bi.plan.h_blocks; v0 += sx::kBatchChunk) {
-            const uint64_t cnt = bi.plan.h_blocks - v0 < (uint64_t)sx::kBatchChunk ? bi.plan.h_blocks - v0
-                                                                                    : (uint64_t)sx::kBatchChunk;
-            (body == sx::kBody3x32 ? items1 : b->items).push_back(
-                sx::BatchItem{(uint32_t)i, (uint32_t)v0, (uint32_t)cnt, 0u});
+        // work items: runs of up to kBatchChunk consecutive blocks whose tiles
+        // hold cells (the host evaluates the kernels' own decode; blocks that
+        // exit -- packing waste, overhang, tiles past the padded lattice's
+        // domain -- get no item, and the kernel still decodes every block)
+        auto holds_cells = [&](uint64_t v) {
+            int32_t X[sx::kMaxM] = {0, 0, 0, 0};
+            bool ok = false;
+            switch (bi.plan.m) {
+            case 2: ok = sx::decode<2>(bi.plan, sx::kMapH, v, X); break;
+            case 3: ok = sx::decode<3>(bi.plan, sx::kMapH, v, X); break;
+            default: ok = sx::decode<4>(bi.plan, sx::kMapH, v, X); break;
+            }
+            int64_t sum = 0;
+            for (int d = 0; d < bi.plan.m; ++d) sum += X[d];
+            return ok && sum * bi.plan.rho <= bi.plan.n;
+        };
+        std::vector<sx::BatchItem> &dst = body == sx::kBody3x32 ? items1 : b->items;
+        for (uint64_t v = 0; v < bi.plan.h_blocks;) {
+            if (!holds_cells(v)) {
+                ++v;
+                continue;
+            }
+            const uint64_t v0 = v;
+            while (v < bi.plan.h_blocks && v - v0 < (uint64_t)sx::kBatchChunk && holds_cells(v)) ++v;
+            dst.push_back(sx::BatchItem{(uint32_t)i, (uint32_t)v0, (uint32_t)(v - v0), 0u});
         }
     }
     b->nitems0 = b->items.size();

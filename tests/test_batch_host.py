@@ -27,7 +27,17 @@ def test_batch_counts_and_layout():
                                    band=(min(8, 1 << ((d["n"] + d["block"]) // d["block"]).bit_length() - 1)
                                          if d["m"] == 2 else None))
         blocks += mp.info.h_blocks
-        items += -(-mp.info.h_blocks // 8)
+        # one work item per run of up to 8 consecutive blocks whose tiles hold
+        # cells (blocks that exit in the kernel get no item)
+        run = 0
+        for v in range(mp.info.h_blocks):
+            if sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)[1]:
+                run += 1
+                if run == 8:
+                    items, run = items + 1, 0
+            elif run:
+                items, run = items + 1, 0
+        items += 1 if run else 0
     assert info["blocks"] == blocks
     assert info["items"] == items
     grids = sum(2 * (-(-((d["n"] + 16) // 16 * 16) ** d["m"] // 256) * 256) for d in insts)
