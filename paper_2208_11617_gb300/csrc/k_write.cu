@@ -79,8 +79,11 @@ __global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__re
 // ACCUM (Table 1): every domain cell of `data` gains `add` (mod 2^32).  Same
 // decode and chunking as the write test; a chunk is one 16-byte load, four
 // adds and one 16-byte store (4-byte accesses where rows are not 16-byte
-// aligned, and per cell on the diagonal band).
-template <int M>
+// aligned, and per cell on the diagonal band).  With G = 4 a thread issues
+// the loads of four of its chunks before their stores (used when every thread
+// has at least four chunks; with one chunk per thread the extra registers
+// cost more occupancy than the loads in flight gain).
+template <int M, int G>
 __global__ void __launch_bounds__(256) accum_kernel(const Plan p, uint32_t *__restrict__ data, uint32_t add,
                                                     int kind, uint64_t nblocks, int vec)
 {
@@ -92,6 +95,26 @@ __global__ void __launch_bounds__(256) accum_kernel(const Plan p, uint32_t *__re
         const int64_t s0 = tile_base_sum<M>(p, X);
         if (s0 > p.n && kind != kMapBBThread) continue;
         const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
+        if (G > 1 && !partial && vec) {
+            // G chunks per thread at a time: their loads are all in flight
+            // before the first store
+            for (uint32_t c0 = threadIdx.x; c0 < nchunks; c0 += G * blockDim.x) {
+                uint4 w[G];
+                int64_t a[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const uint32_t c = c0 + (uint32_t)g * blockDim.x;
+                    a[g] = c < nchunks ? chunk_pos<M>(p, X, c, 2).addr : -1;
+                    if (a[g] >= 0) w[g] = *reinterpret_cast<const uint4 *>(data + a[g]);
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (a[g] >= 0)
+                        *reinterpret_cast<uint4 *>(data + a[g]) =
+                            make_uint4(w[g].x + add, w[g].y + add, w[g].z + add, w[g].w + add);
+            }
+            continue;
+        }
         for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
             const ChunkPos<M> q = chunk_pos<M>(p, X, c, 2);
             if (!partial && vec) {
@@ -172,10 +195,14 @@ cudaError_t launch_accum(const Plan &plan, uint32_t *data, uint32_t add, int kin
     const uint64_t nb = is_bb(kind) ? p.bb_blocks : p.h_blocks;
     const unsigned g = grid_for(nb), t = threads_for(p, 2);
     const int vc = vec ? 1 : 0;
-    switch (p.m) {
-    case 2: accum_kernel<2><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
-    case 3: accum_kernel<3><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
-    case 4: accum_kernel<4><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    const bool grouped = (1ull << (p.m * p.log_rho - 2)) >= 4ull * t;  // >= 4 chunks per thread
+    switch (p.m * 10 + (grouped ? 4 : 1)) {
+    case 21: accum_kernel<2, 1><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    case 24: accum_kernel<2, 4><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    case 31: accum_kernel<3, 1><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    case 34: accum_kernel<3, 4><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    case 41: accum_kernel<4, 1><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
+    case 44: accum_kernel<4, 4><<<g, t, 0, st>>>(p, data, add, kind, nb, vc); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -60,9 +60,9 @@ WRITE_M2 = WriteWorkload("write m=2 n=1023 rho=16", m=2, n=1023, block=16)
 WRITE_M4 = WriteWorkload("write m=4 n=127 rho=4", m=4, n=127, block=4)
 # ACCUM test (Table 1, read-add-write of one uint32 per cell) at sizes well
 # past the L2: the 2-simplex n = 16383 (134,225,920 cells, 16384^2 array) in
-# 32 x 32 tiles and the 3-simplex n = 1023 (179,481,600 cells, 1024^3 array)
+# 64 x 64 tiles and the 3-simplex n = 1023 (179,481,600 cells, 1024^3 array)
 # in 16^3 tiles.
-ACCUM_M2 = WriteWorkload("accum m=2 n=16383 rho=32", m=2, n=16383, block=32)
+ACCUM_M2 = WriteWorkload("accum m=2 n=16383 rho=64", m=2, n=16383, block=64)
 ACCUM_M3 = WriteWorkload("accum m=3 n=1023 rho=16", m=3, n=1023, block=16)
 # Automaton on the 2-simplex: n = 32767 in a 32768^2 uint8 array, Bernoulli(0.5),
 # B3/S23, 100 steps; the same run at n = 4095 is the size the oracle finishes in
