@@ -437,11 +437,13 @@ int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t gri
  * room in the round's work list (max_items) are free, and retires finished jobs: their live count after every step and
  * a digest of their final grid are copied to host memory and their memory
  * returns to the pool.  A job's result is identical whether it runs alone or
- * among others.  Tiles: m = 2: 128 from n = 1024 up, else 64; m = 3: 16.
- * With at most direct_jobs jobs resident, each job's next steps (up to 4x
- * round_steps) go out as single-instance step launches on its own grids and
- * on a side stream of its own, so light jobs run concurrently: a batched pass
- * costs more than a few jobs' own step launches.
+ * among others.  Tiles of the batched passes: m = 2: 128 from n = 1024 up,
+ * else 64; m = 3: 16.  With at most direct_jobs jobs resident, each job's next
+ * steps (up to 4x round_steps) go out as single-instance step launches on its
+ * own grids and on a side stream of its own, so light jobs run concurrently: a
+ * batched pass costs more than a few jobs' own step launches.  These direct
+ * launches use the tiles on which single-instance steps run fastest: m = 2:
+ * 128 from n = 2560 up, else 64; m = 3: 32 from n = 352 up, else 16.
  */
 typedef struct simplex_server *simplex_server_t;
 

@@ -137,7 +137,28 @@ struct Chunk {
 // so the chunks of different light jobs run concurrently.
 constexpr int kSideStreams = 8;
 
+// Tile side of a job's plan for the batched passes (the sides the batched
+// kernel's bodies cover).
 int tile_for(int m, int64_t n) { return m == 2 ? (n >= 1024 ? 128 : 64) : 16; }
+
+// Tile side of a job's direct chunks (single-instance step launches), from
+// per-step times of 64 such launches on GB300: m = 2 runs fastest on 64 x 64
+// tiles up to n ~ 2500 (n = 1500: 3.0 us a step, 3.7 us on 128 x 128) and on
+// 128 x 128 beyond; m = 3 on 16^3 tiles up to n ~ 350 and on 32^3 beyond
+// (n = 511: 18.6 us a step, 22.8 us on 16^3).  Both plans address the same
+// grids: a job may take batched passes and direct chunks in any order.
+int direct_tile_for(int m, int64_t n) { return m == 2 ? (n >= 2560 ? 128 : 64) : (n >= 352 ? 32 : 16); }
+
+// Trapezoid band height of an m = 2 plan: 8 tiles, fewer when the triangle
+// is smaller than two bands; 0 (no bands) for m = 3.
+int band_for(int m, int64_t n, int block)
+{
+    if (m != 2) return 0;
+    const int64_t nb = (n + block) / block;
+    int band = 1;
+    while (band < 8 && band * 2 <= nb) band *= 2;
+    return band;
+}
 
 // Work-queue counters: round r uses group r % (max_inflight + 1) of
 // round_steps + 1 counters (its step passes, then its digest pass), zeroed by
@@ -163,6 +184,8 @@ struct simplex_server {
     std::vector<int> free_slots;
     std::vector<sx::BatchInst> slot_inst;        // host copies uploaded at admission
     std::vector<CUtensorMap> slot_tmap;          // 2 per slot
+    std::vector<sx::Plan> slot_dplan;            // plan of the direct chunks (direct_tile_for)
+    std::vector<CUtensorMap> slot_dtmap;         // its tensor maps, 2 per slot
     std::vector<ServerJob> jobs;
     std::deque<int64_t> pending;
     std::vector<int64_t> active;
@@ -253,14 +276,11 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
     const uint64_t bytes = 2 * align_up(gb, 256);
     if (bytes > s->prm.hbm_budget) return -2;  // can never fit
     // work items per round: plan first (host only), then check the round budget
-    sx::Plan plan;
-    int band = 0;
-    if (sp.m == 2) {
-        const int64_t nb = (sp.n + block) / block;
-        band = 1;
-        while (band < 8 && band * 2 <= nb) band *= 2;
-    }
-    if (build_plan(sp.m, sp.n, 2, 2, block, side, band, &plan)) return -1;
+    sx::Plan plan, dplan;
+    const int dblock = direct_tile_for(sp.m, sp.n);
+    if (build_plan(sp.m, sp.n, 2, 2, block, side, band_for(sp.m, sp.n, block), &plan)) return -1;
+    if (dblock == block) dplan = plan;
+    else if (build_plan(sp.m, sp.n, 2, 2, dblock, side, band_for(sp.m, sp.n, dblock), &dplan)) return -1;
     const uint64_t nitems = plan.h_blocks;  // work items at the finest chunk (one block each)
     if (nitems > s->max_items) return -2;                   // can never fit in a round
     if (s->active_items + nitems > s->max_items) return 0;  // wait for the round to shrink
@@ -277,9 +297,17 @@ int admit(simplex_server *s, int64_t j, cudaStream_t st)
     bi.tmap = 2 * slot;
     bi.grid[0] = s->off_pool + off;
     bi.grid[1] = s->off_pool + off + align_up(gb, 256);
+    s->slot_dplan[slot] = dplan;
     for (int g = 0; g < 2; ++g) {
         rc = make_tensor_map(bi.plan, s->arena + bi.grid[g], &s->slot_tmap[2 * slot + g], bi.plan.rho + 2);
-        if (rc) return -1;
+        if (rc == SIMPLEX_OK)
+            rc = make_tensor_map(dplan, s->arena + bi.grid[g], &s->slot_dtmap[2 * slot + g], dplan.rho + 2);
+        if (rc) {
+            // the slot and pool memory go back: the job is not admitted
+            s->free_slots.push_back(slot);
+            s->pool.release(off, bytes);
+            return -1;
+        }
     }
     cudaError_t e;
     unsigned long long *live = reinterpret_cast<unsigned long long *>(s->arena + s->off_live) +
@@ -339,6 +367,7 @@ int launch_chunk(simplex_server *s, int64_t j, cudaStream_t st)
 {
     ServerJob &job = s->jobs[j];
     const sx::BatchInst &bi = s->slot_inst[job.slot];
+    const sx::Plan &dp = s->slot_dplan[job.slot];
     cudaStream_t cs = s->side[job.slot % kSideStreams];
     const int np = std::min(std::min(kMaxRoundSteps, 4 * round_steps(s->prm)), job.spec.steps - job.step);
     unsigned long long *live_row =
@@ -354,10 +383,9 @@ int launch_chunk(simplex_server *s, int64_t j, cudaStream_t st)
     for (int k = 0; k < np; ++k) {
         const int par = job.parity ^ (k & 1);
         uint8_t *out = s->arena + bi.grid[par ^ 1];
-        const CUtensorMap &tm = s->slot_tmap[2 * job.slot + par];
-        e = bi.plan.m == 2 ? sx::launch_ca2_step(bi.plan, tm, out, bi.rule, sx::kMapH, live_row + job.step + 1 + k, cs)
-                           : sx::launch_ca3_step(bi.plan, tm, out, bi.rule, sx::kMapH, live_row + job.step + 1 + k,
-                                                 nullptr, cs);
+        const CUtensorMap &tm = s->slot_dtmap[2 * job.slot + par];
+        e = dp.m == 2 ? sx::launch_ca2_step(dp, tm, out, bi.rule, sx::kMapH, live_row + job.step + 1 + k, cs)
+                      : sx::launch_ca3_step(dp, tm, out, bi.rule, sx::kMapH, live_row + job.step + 1 + k, nullptr, cs);
         if (e != cudaSuccess) return cuda_fail(e, "launching a job's step");
         s->launches += 1;
     }
@@ -686,6 +714,9 @@ int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, in
     // nothing can be launched until something completes: wait for one
     const bool busy_gpu = !s->inflight.empty() || !s->chunks.empty();
     const bool arrived = !s->pending.empty() && (!realtime || s->jobs[s->pending.front()].arrival_ms <= host_ms(s));
+    // (in real time the wait also ends when a job arrives that can take a
+    // free slot: it is admitted, and in direct mode started, without waiting
+    // for another job's chunk or round to end)
     if (block && completed == 0 && busy_gpu && !idle_job &&
         ((int)s->inflight.size() >= s->prm.max_inflight || !arrived || s->free_slots.empty())) {
         while (completed == 0) {
@@ -693,7 +724,12 @@ int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, in
             *done += r;
             if ((r = retire_chunks(s, &completed)) < 0) return SIMPLEX_ECUDA;
             *done += r;
-            if (completed == 0 && s->chunks.empty() && !s->inflight.empty()) {
+            if (completed) break;
+            if (realtime) {
+                if (!s->pending.empty() && !s->free_slots.empty() &&
+                    s->jobs[s->pending.front()].arrival_ms <= host_ms(s))
+                    break;
+            } else if (s->chunks.empty() && !s->inflight.empty()) {
                 if ((r = retire(s, true, &completed)) < 0) return SIMPLEX_ECUDA;  // only rounds: block on the oldest
                 *done += r;
             }
@@ -739,6 +775,8 @@ int simplex_server_create(const simplex_server_params_t *params, void *arena, ui
     try {
         s->slot_inst.resize(params->max_jobs);
         s->slot_tmap.resize(2 * (size_t)params->max_jobs);
+        s->slot_dplan.resize(params->max_jobs);
+        s->slot_dtmap.resize(2 * (size_t)params->max_jobs);
         for (int i = params->max_jobs - 1; i >= 0; --i) s->free_slots.push_back(i);
     } catch (...) {
         delete s;

@@ -95,6 +95,38 @@ def test_direct_and_batched_rounds_agree():
         assert res[1][i]["digest"] == dig and res[1][i]["live"] == live
 
 
+def test_direct_chunks_on_their_own_tiles_match_batched_passes():
+    """Direct chunks run m = 3 jobs with n >= 352 on 32^3 tiles and m = 2 jobs
+    with 1024 <= n < 2560 on 64 x 64 tiles, while batched passes keep 16^3 and
+    128 x 128 tiles on the same grids.  All-batched, all-direct and a mix (a
+    job takes batched passes while many are resident, direct chunks as the
+    rest drain) give the same results, equal to the single-instance path's."""
+    thr = inputs.bernoulli_threshold(0.5)
+    rng = np.random.default_rng(21)
+    jobs = []
+    for k in range(36):
+        if k % 3 == 0:
+            m, n, rule = 3, int(rng.integers(352, 512)), inputs.B5S45
+        else:
+            m, rule = 2, inputs.B3S23
+            n = int(rng.integers(1024, 2560)) if k % 3 == 1 else int(rng.integers(100, 4000))
+        jobs.append(dict(m=m, n=n, steps=int(rng.integers(17, 41)), birth=rule[0], survive=rule[1], seed=k,
+                         threshold=thr))
+    res = []
+    for dj in (-1, 64, 6):
+        srv = sx.SimplexServer(hbm_budget=4 << 30, max_jobs=64, max_steps=40, direct_jobs=dj)
+        srv.run(jobs, None, realtime=False)
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["rejected"] == 0
+        res.append([srv.result(i, job["steps"]) for i, job in enumerate(jobs)])
+    strip = lambda r: {k: v for k, v in r.items() if not k.endswith("_ms")}
+    for i in range(len(jobs)):
+        assert strip(res[0][i]) == strip(res[1][i]) == strip(res[2][i]), f"job {i}"
+    for i in (0, 1, 3, 4, len(jobs) - 3):
+        dig, live, _, _ = _alone(jobs[i])
+        assert res[1][i]["digest"] == dig and res[1][i]["live"] == live, f"job {i}"
+
+
 def test_online_submit_poll_wait_matches_trace_run():
     """Jobs submitted one at a time (with polls between) give the results of
     the same jobs run as a trace."""
