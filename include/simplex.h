@@ -513,9 +513,6 @@ int simplex_server_destroy(simplex_server_t server);
 int simplex_server_run(simplex_server_t server, const simplex_job_t *jobs, const double *arrival_s, int count,
                        int realtime, void *stream);
 
-/* Result of job `job` (index into the last trace); `live` (nullable, host,
- * steps + 1 entries) receives the live count before the first and after
- * every step. */
 /*
  * Online use, one job at a time (single-threaded: call these from one host
  * thread).  simplex_server_begin starts a session on `stream` (the server must
@@ -523,20 +520,26 @@ int simplex_server_run(simplex_server_t server, const simplex_job_t *jobs, const
  * queues one job with arrival = now and returns its id (0, 1, ... in submit
  * order); it does no GPU work.  simplex_server_poll runs one turn of the
  * serving loop without waiting on the GPU: it admits queued jobs as slots and
- * pool memory allow, launches a round when jobs are resident and fewer than
- * max_inflight rounds are queued, and retires the rounds that have completed;
+ * pool memory allow, launches work (a direct chunk for every resident job
+ * without one in flight while at most direct_jobs are resident, else a batched
+ * round when fewer than max_inflight rounds are queued), and retires the
+ * rounds and chunks that have completed;
  * *finished (nullable) receives how many jobs finished in that turn (done or
  * rejected).  simplex_server_wait turns the loop, waiting on the GPU when
  * nothing else can progress, until job `id` has finished, or with id < 0
  * until every submitted job has.  Results and statistics are read as after
  * simplex_server_run.  Errors: SIMPLEX_EINVAL (no session, bad job or id,
- * begin while jobs are in progress), SIMPLEX_ECUDA.
+ * begin while jobs are in progress), SIMPLEX_ECUDA.  After SIMPLEX_ECUDA from
+ * any serving call the server's job state is undefined: destroy it.
  */
 int simplex_server_begin(simplex_server_t server, void *stream);
 int simplex_server_submit(simplex_server_t server, const simplex_job_t *job, int64_t *id);
 int simplex_server_poll(simplex_server_t server, int *finished);
 int simplex_server_wait(simplex_server_t server, int64_t id);
 
+/* Result of job `job` (index into the last trace or session); `live`
+ * (nullable, host, steps + 1 entries) receives the live count before the
+ * first and after every step. */
 int simplex_server_result(simplex_server_t server, int64_t job, simplex_job_result_t *out, unsigned long long *live);
 
 int simplex_server_stats(simplex_server_t server, simplex_server_stats_t *out);
