@@ -413,6 +413,43 @@ def test_ca_m2_full_size_matches_oracle():
     assert int(fin_b.sum(dtype=torch.int64).item()) == int(live_b[-1])
 
 
+def test_ca_m2_past_2_32_offsets_matches_oracle():
+    """Size limit of 32-bit indexing: m = 2, n = 70000 on side 70016 (4.9 GB
+    grids), so byte offsets and row-major indices pass 2^32 (the initial state
+    hashes lin mod 2^32 on both sides).  The initial state and one step on the
+    benchmark's 128 x 128 tiles equal the oracle's whole grids, the padding
+    rows and columns stay zero, and the live counts agree."""
+    n, side, w = 70000, 70016, inputs.CA_M2
+    assert n * (n + 1) + n >= 1 << 32 and side * side > 1 << 32
+    mp = sx.simplex_map_create(2, n, 2, 2, w.block, side=side)
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    b = torch.zeros_like(a)
+    live = torch.zeros(2, dtype=torch.int64, device=DEV)
+    sx.simplex_ca_init(mp, a, w.seed, w.threshold, live[0:1])
+    sx.simplex_ca_step(mp, a, b, w.rule[0], w.rule[1], live[1:2])
+    torch.cuda.synchronize()
+    live = live.cpu().tolist()
+
+    def same(t, ref):
+        g = t.view(side, side)
+        assert not g[n + 1:].any() and not g[:, n + 1:].any()  # padding untouched
+        for r0 in range(0, n + 1, 8192):
+            r1 = min(n + 1, r0 + 8192)
+            got = g[r0:r1, : n + 1].cpu().numpy()
+            if not np.array_equal(got, ref[r0:r1]):
+                bad = np.argwhere(got != ref[r0:r1])[:5]
+                raise AssertionError(f"rows {r0}..{r1}: first mismatches {(bad + [r0, 0]).tolist()}")
+
+    ref0 = oracle.ca_init(2, n, w.seed, w.threshold)
+    same(a, ref0)
+    assert live[0] == int(np.count_nonzero(ref0))
+    del a
+    ref1, live1 = oracle.ca_step(2, n, w.rule[0], w.rule[1], ref0)
+    del ref0
+    same(b, ref1)
+    assert live[1] == live1
+
+
 @pytest.mark.parametrize("n,block,side", [(255, 32, None), (200, 32, 208), (127, 16, None), (1023, 32, None),
                                           (63, 8, None)])
 def test_h3_level_layout_matches_oracle(n, block, side):
