@@ -450,6 +450,48 @@ def test_ca_m2_past_2_32_offsets_matches_oracle():
     assert live[1] == live1
 
 
+def test_ca_m3_past_2_32_offsets_matches_oracle():
+    """The same limit for m = 3: n = 1700 on side 1712 (5.0 GB grids, offsets
+    and row-major indices past 2^32; tile columns N = 64).  The initial state
+    and one step of the grid form equal the oracle's whole grids with the
+    padding zero; the x-stream form's step equals the grid form's."""
+    n, side, w = 1700, 1712, inputs.CA_M3
+    assert (n + 1) ** 3 > 1 << 32 and side ** 3 > 1 << 32
+    mg = sx.simplex_map_create(3, n, 2, 2, 32, side=side, launch=1)
+    mx = sx.simplex_map_create(3, n, 2, 2, 32, side=side, launch=2)
+    a = torch.zeros(mg.numel, dtype=torch.uint8, device=DEV)
+    b = torch.zeros_like(a)
+    c = torch.zeros_like(a)
+    live = torch.zeros(3, dtype=torch.int64, device=DEV)
+    sx.simplex_ca_init(mg, a, w.seed, w.threshold, live[0:1])
+    sx.simplex_ca_step(mg, a, b, w.rule[0], w.rule[1], live[1:2])
+    sx.simplex_ca_step(mx, a, c, w.rule[0], w.rule[1], live[2:3])
+    torch.cuda.synchronize()
+    assert torch.equal(b, c)
+    del c
+    live = live.cpu().tolist()
+    assert live[1] == live[2]
+
+    def same(t, ref):
+        g = t.view(side, side, side)
+        assert not g[n + 1:].any() and not g[:, n + 1:].any() and not g[:, :, n + 1:].any()
+        for r0 in range(0, n + 1, 64):
+            r1 = min(n + 1, r0 + 64)
+            got = g[r0:r1, : n + 1, : n + 1].cpu().numpy()
+            if not np.array_equal(got, ref[r0:r1]):
+                bad = np.argwhere(got != ref[r0:r1])[:5]
+                raise AssertionError(f"planes {r0}..{r1}: first mismatches {(bad + [r0, 0, 0]).tolist()}")
+
+    ref0 = oracle.ca_init(3, n, w.seed, w.threshold)
+    same(a, ref0)
+    assert live[0] == int(np.count_nonzero(ref0))
+    del a
+    ref1, live1 = oracle.ca_step(3, n, w.rule[0], w.rule[1], ref0)
+    del ref0
+    same(b, ref1)
+    assert live[1] == live1
+
+
 @pytest.mark.parametrize("n,block,side", [(255, 32, None), (200, 32, 208), (127, 16, None), (1023, 32, None),
                                           (63, 8, None)])
 def test_h3_level_layout_matches_oracle(n, block, side):
