@@ -24,59 +24,68 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile simplex_oracle.c into liboracle.so (OpenMP if gcc supports it)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+def compile_source(src: str, out: str) -> str:
+    """gcc a C source file into the shared library `out` (OpenMP if gcc supports it)."""
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", src, "-o", out, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True, text=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True, text=True)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile simplex_oracle.c into liboracle.so."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    compile_source(_SRC, tmp)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def configure(lib):
+    """Declares the C signatures of the oracle's entry points on a loaded library."""
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    i64, u32, i32, u64 = ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint64
+    lib.oracle_splitmix32.argtypes = [u32]
+    lib.oracle_splitmix32.restype = u32
+    lib.oracle_num_threads.argtypes = []
+    lib.oracle_num_threads.restype = i32
+    lib.oracle_count_cells.argtypes = [i32, i64]
+    lib.oracle_count_cells.restype = u64
+    lib.oracle_write.argtypes = [i32, i64, u32, u32p]
+    lib.oracle_write.restype = u64
+    lib.oracle_accum.argtypes = [i32, i64, u32, u32p]
+    lib.oracle_accum.restype = u64
+    lib.oracle_ca_init.argtypes = [i32, i64, u32, u32, u8p]
+    lib.oracle_ca_init.restype = u64
+    lib.oracle_ca_step.argtypes = [i32, i64, u32, u32, u8p, u8p]
+    lib.oracle_ca_step.restype = u64
+    lib.oracle_ca_run.argtypes = [i32, i64, i32, u32, u32, u8p, u8p, u64p]
+    lib.oracle_ca_run.restype = None
+    lib.oracle_ca_cells.argtypes = [i32, i64, u32, u32, u8p, ctypes.POINTER(ctypes.c_int64), i64, u8p]
+    lib.oracle_ca_cells.restype = None
+    lib.oracle_block_indicator.argtypes = [i32, i64, i32, u32p]
+    lib.oracle_block_indicator.restype = None
+    lib.oracle_edm.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)]
+    lib.oracle_edm.restype = None
+    lib.oracle_edm_cells.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64), i64,
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.oracle_edm_cells.restype = None
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        build()
-        lib = ctypes.CDLL(_LIB)
-        u8p = ctypes.POINTER(ctypes.c_uint8)
-        u32p = ctypes.POINTER(ctypes.c_uint32)
-        u64p = ctypes.POINTER(ctypes.c_uint64)
-        i64, u32, i32, u64 = ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint64
-        lib.oracle_splitmix32.argtypes = [u32]
-        lib.oracle_splitmix32.restype = u32
-        lib.oracle_num_threads.argtypes = []
-        lib.oracle_num_threads.restype = i32
-        lib.oracle_count_cells.argtypes = [i32, i64]
-        lib.oracle_count_cells.restype = u64
-        lib.oracle_write.argtypes = [i32, i64, u32, u32p]
-        lib.oracle_write.restype = u64
-        lib.oracle_accum.argtypes = [i32, i64, u32, u32p]
-        lib.oracle_accum.restype = u64
-        lib.oracle_ca_init.argtypes = [i32, i64, u32, u32, u8p]
-        lib.oracle_ca_init.restype = u64
-        lib.oracle_ca_step.argtypes = [i32, i64, u32, u32, u8p, u8p]
-        lib.oracle_ca_step.restype = u64
-        lib.oracle_ca_run.argtypes = [i32, i64, i32, u32, u32, u8p, u8p, u64p]
-        lib.oracle_ca_run.restype = None
-        lib.oracle_ca_cells.argtypes = [i32, i64, u32, u32, u8p, ctypes.POINTER(ctypes.c_int64), i64, u8p]
-        lib.oracle_ca_cells.restype = None
-        lib.oracle_block_indicator.argtypes = [i32, i64, i32, u32p]
-        lib.oracle_block_indicator.restype = None
-        lib.oracle_edm.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)]
-        lib.oracle_edm.restype = None
-        lib.oracle_edm_cells.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64), i64,
-                                         ctypes.POINTER(ctypes.c_double)]
-        lib.oracle_edm_cells.restype = None
-        _lib = lib
-        return lib
+        if _lib is None:
+            build()
+            _lib = configure(ctypes.CDLL(_LIB))
+        return _lib
 
 
 def _ptr(a: np.ndarray, ctype):

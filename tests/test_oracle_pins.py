@@ -151,6 +151,19 @@ def test_init_matches_threshold_rule_and_rate():
                 assert g[x1, x2] == 0
 
 
+def test_init_threshold_is_strict():
+    """A cell is alive iff its hash is strictly below the threshold: with the
+    threshold equal to one cell's hash that cell is dead, one above it alive."""
+    seed, n = 77, 20
+    for m, (x1, x2, x3) in ((2, (3, 5, 0)), (3, (2, 4, 6))):
+        D = n + 1
+        lin = x1 * D + x2 if m == 2 else (x1 * D + x2) * D + x3
+        cell = (x1, x2) if m == 2 else (x1, x2, x3)
+        h = oracle.splitmix32(seed ^ lin)
+        assert oracle.ca_init(m, n, seed, h)[cell] == 0
+        assert oracle.ca_init(m, n, seed, h + 1)[cell] == 1
+
+
 def test_bernoulli_thresholds():
     assert inputs.bernoulli_threshold(0.4) == 1717986918
     assert inputs.bernoulli_threshold(0.3) == 1288490188
@@ -320,7 +333,8 @@ def test_ca_run_live_counts_are_popcounts():
 
 # ---------------------------------------------------------------- block indicator
 @pytest.mark.parametrize("m,n,rho", [(2, 63, 16), (2, 100, 16), (2, 1023, 16), (3, 63, 8),
-                                     (3, 40, 8), (4, 31, 4), (4, 30, 8), (2, 5, 4)])
+                                     (3, 40, 8), (4, 31, 4), (4, 30, 8), (2, 5, 4),
+                                     (2, 64, 16), (3, 48, 8), (4, 32, 8)])  # tiles holding one cell
 def test_block_indicator_closed_form(m, n, rho):
     ind = oracle.block_indicator(m, n, rho)
     X = np.indices(ind.shape).sum(0)
