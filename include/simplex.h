@@ -507,8 +507,9 @@ int simplex_server_destroy(simplex_server_t server);
  * realtime = 0 or arrival_s = NULL every job is available at once).  Work is
  * issued on `stream`.  Results and statistics stay queryable until the next
  * run.  A job whose grids exceed the budget, or whose work list exceeds
- * max_items, is rejected (status 3) and the others still run.  Errors:
- * SIMPLEX_EINVAL (a job's parameters), SIMPLEX_ECUDA.
+ * max_items, is rejected (status 3) and the others still run.  count = 0
+ * (jobs may then be NULL) runs an empty trace.  Errors: SIMPLEX_EINVAL (a
+ * job's parameters, count < 0), SIMPLEX_ECUDA.
  */
 int simplex_server_run(simplex_server_t server, const simplex_job_t *jobs, const double *arrival_s, int count,
                        int realtime, void *stream);

@@ -835,7 +835,7 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
                        int realtime, void *stream)
 {
     if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
-    if (!jobs || count < 0) return fail(SIMPLEX_EINVAL, "jobs is NULL");
+    if (count < 0 || (!jobs && count > 0)) return fail(SIMPLEX_EINVAL, "jobs is NULL or count < 0");
     if (!s->active.empty() || !s->inflight.empty() || !s->pending.empty() || !s->chunks.empty())
         return fail(SIMPLEX_EINVAL, "the server is still running another trace");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

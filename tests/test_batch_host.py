@@ -52,6 +52,12 @@ def test_batch_rejects_unsupported_instances(bad):
     assert "instance 1" in str(ei.value)
 
 
+def test_batch_rejects_an_empty_list():
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_batch_create([])
+    assert ei.value.code == sx.SIMPLEX_EINVAL
+
+
 def test_batch_workload_generator():
     insts = inputs.batch_instances()
     assert len(insts) == 2304

@@ -195,4 +195,10 @@ def test_server_is_reusable_and_rejects_bad_jobs():
         srv.run([dict(good[0], steps=9)], None, realtime=False)
     with pytest.raises(sx.SimplexError):
         srv.run([dict(good[0], m=4)], None, realtime=False)
+    # empty: a trace without jobs, and a session that waits with nothing submitted
+    srv.run([], None, realtime=False)
+    assert srv.stats()["submitted"] == 0 and srv.stats()["completed"] == 0
+    srv.begin()
+    srv.wait()
+    assert srv.poll() == 0
     assert sx.simplex_device_status() == 0
