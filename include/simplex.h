@@ -44,7 +44,7 @@ extern "C" {
 #define SIMPLEX_ENOMEM 2       /* host or device allocation failed */
 #define SIMPLEX_ECUDA 3        /* a CUDA runtime or driver call failed */
 #define SIMPLEX_ETIMEOUT 4     /* a bounded device-side wait gave up */
-#define SIMPLEX_EUNSUPPORTED 5 /* valid request this build does not implement */
+#define SIMPLEX_EUNSUPPORTED 5 /* valid request the library does not implement */
 
 /* ---- map modes ----------------------------------------------------------- */
 #define SIMPLEX_MODE_H 0  /* block-space map H (Sec. 4)                         */
@@ -96,7 +96,7 @@ typedef struct simplex_map_info {
  * Allocates host memory only.  The lattice side N is the power of two at or
  * above ceil((n+1)/rho) (n padded from above, Sec. 4.2); tiles past the
  * domain exit at once.  Errors: SIMPLEX_EINVAL for a bad argument,
- * SIMPLEX_EUNSUPPORTED for r_inv != 2 or a beta this build does not map,
+ * SIMPLEX_EUNSUPPORTED for r_inv != 2 or a beta the library does not map,
  * SIMPLEX_ENOMEM.
  */
 int simplex_map_create(int m, int64_t n, int r_inv, int beta, int block, simplex_map_t *out);
