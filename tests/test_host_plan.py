@@ -30,6 +30,38 @@ def test_library_exports_every_declared_symbol():
     assert "sm_103a" in sx.simplex_version()
 
 
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """A copy of the binding next to no libsimplex.so refuses to import: the
+    product path has no CPU fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "pkg_copy"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2208_11617_gb300", "simplex.py"), pkg / "simplex.py")
+    (pkg / "__init__.py").write_text("")
+    r = subprocess.run([sys.executable, "-c", "import pkg_copy.simplex"], cwd=tmp_path, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "no CPU fallback" in r.stderr
+
+
+def test_product_package_never_touches_the_oracle():
+    """Only tests, the smoke check and the bench's CPU legs may use oracle/:
+    no file of the package imports it, loads its library or calls its C entry
+    points (comments may mention it)."""
+    pkg = os.path.join(ROOT, "paper_2208_11617_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                use = re.search(r"^\s*(import|from)\s+oracle\b|\boracle\.\w|liboracle|simplex_oracle|\boracle_\w+\s*\(",
+                                text, flags=re.M)
+                assert not use, (os.path.join(dirpath, f), use.group(0) if use else None)
+
+
 # ------------------------------------------------------------------ plan sizes
 @pytest.mark.parametrize("m,n,block", [(2, 1023, 16), (2, 32767, 128), (2, 4095, 128), (3, 1023, 32),
                                        (3, 1023, 16), (4, 127, 4), (4, 127, 8), (2, 1000, 16), (3, 200, 16),
