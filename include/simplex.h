@@ -499,6 +499,9 @@ int simplex_server_arena_bytes(const simplex_server_params_t *params, uint64_t *
 int simplex_server_create(const simplex_server_params_t *params, void *arena, uint64_t arena_bytes,
                           simplex_server_t *out);
 
+/* Waits for the server's rounds and chunks still in flight, then frees its
+ * streams, events and pinned host buffers (the arena stays the caller's).
+ * NULL is a no-op. */
 int simplex_server_destroy(simplex_server_t server);
 
 /*
@@ -543,6 +546,10 @@ int simplex_server_wait(simplex_server_t server, int64_t id);
  * first and after every step. */
 int simplex_server_result(simplex_server_t server, int64_t job, simplex_job_result_t *out, unsigned long long *live);
 
+/* Statistics of the last trace or session (the fields of
+ * simplex_server_stats_t): latency quantiles over the completed jobs, counts
+ * of submitted, completed and rejected jobs, rounds, cell updates, launches
+ * and timings.  Errors: SIMPLEX_EINVAL (NULL arguments). */
 int simplex_server_stats(simplex_server_t server, simplex_server_stats_t *out);
 
 /* The result digest of one grid: *digest += sum over live cells x of
