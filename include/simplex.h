@@ -363,8 +363,13 @@ typedef struct simplex_batch_info {
  * message names it), SIMPLEX_ENOMEM. */
 int simplex_batch_create(const simplex_instance_t *instances, int count, simplex_batch_t *out);
 
+/* Frees the batch's host plan, its cached CUDA graphs and capture stream
+ * (the bound arena stays the caller's; finish the batch's stream work
+ * first).  NULL is a no-op. */
 int simplex_batch_destroy(simplex_batch_t batch);
 
+/* Sizes of the batch (host only): the fields of simplex_batch_info_t.
+ * Errors: SIMPLEX_EINVAL (NULL arguments). */
 int simplex_batch_info(simplex_batch_t batch, simplex_batch_info_t *out);
 
 /* Binds the batch to `arena` (device, 256-byte aligned, >= arena_bytes,
