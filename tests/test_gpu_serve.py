@@ -127,6 +127,31 @@ def test_direct_chunks_on_their_own_tiles_match_batched_passes():
         assert res[1][i]["digest"] == dig and res[1][i]["live"] == live, f"job {i}"
 
 
+def test_round_length_and_queue_depth_do_not_change_results():
+    """Batched rounds of 1, 5 and 64 passes (the largest pass count the item
+    tags hold), with 1 or 3 rounds queued ahead, give every job the same
+    result: a job's steps are split over rounds differently, its grids and
+    live counts are not."""
+    jobs, _ = inputs.serve_trace(rate=4000, seconds=0.02, seed=19, n2=(16, 1500), n3=(8, 200), max_steps=70)
+    assert len(jobs) > 40 and max(j["steps"] for j in jobs) > 64
+    strip = lambda r: {k: v for k, v in r.items() if not k.endswith("_ms")}
+    ref = None
+    for k, depth in ((1, 1), (5, 3), (64, 1), (64, 3), (0, 2)):
+        srv = sx.SimplexServer(hbm_budget=2 << 30, max_jobs=512, max_steps=70, round_steps=k, max_inflight=depth,
+                               direct_jobs=-1)
+        srv.run(jobs, None, realtime=False)
+        st = srv.stats()
+        assert st["completed"] == len(jobs) and st["rejected"] == 0
+        res = [strip(srv.result(i, job["steps"])) for i, job in enumerate(jobs)]
+        if ref is None:
+            ref = res
+        else:
+            assert res == ref, (k, depth)
+    for i in (0, len(jobs) - 1):
+        dig, live, _, _ = _alone(jobs[i])
+        assert ref[i]["digest"] == dig and ref[i]["live"] == live
+
+
 def test_online_submit_poll_wait_matches_trace_run():
     """Jobs submitted one at a time (with polls between) give the results of
     the same jobs run as a trace."""
