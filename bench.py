@@ -285,11 +285,16 @@ def _time_region(fn, steps, warmup, world):
     return s.elapsed_time(e) / 1e3
 
 
+_ENERGY = True  # --no-energy clears it (e.g. for a profiler run of a few launches)
+
+
 def _energy_region(meter, fn, per_call_s, units_per_call, seconds=1.5):
     """Board energy of fn: NVML's counter is coarse, so fn runs back to back for
     about `seconds` (apart from the timed region) and the energy is divided
     over the calls.  Returns joules per call, average watts and units per joule."""
     import torch
+    if not _ENERGY:
+        return {"joules_per_step": None, "note": "not measured (--no-energy)"}
     if meter is None or meter.dev is None:
         return {"joules_per_step": None, "note": "NVML energy counter unavailable"}
     calls = max(1, int(seconds / max(per_call_s, 1e-6)))
@@ -712,18 +717,20 @@ def run_ours(args, rank, world, local):
             "unit": "cells per joule (board energy, NVML, a separate ~1.5 s run per map)"}
         # end to end: (ACCUM: the array in from pinned host memory,) the kernel,
         # the array back to pinned host memory
-        h_out = torch.empty(mp.numel, dtype=torch.int32).pin_memory()
-        h_in = h_out.clone().pin_memory() if accum else None
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(3):
-            if accum:
-                out.copy_(h_in, non_blocking=True)
-            launch(sx.SIMPLEX_MODE_H)
-            h_out.copy_(out, non_blocking=True)
+        e2e_val = None
+        if not args.no_e2e:
+            h_out = torch.empty(mp.numel, dtype=torch.int32).pin_memory()
+            h_in = h_out.clone().pin_memory() if accum else None
             torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        e2e_val, _ = aggregate(cells * 3, t1 - t0, world)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                if accum:
+                    out.copy_(h_in, non_blocking=True)
+                launch(sx.SIMPLEX_MODE_H)
+                h_out.copy_(out, non_blocking=True)
+                torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e2e_val, _ = aggregate(cells * 3, t1 - t0, world)
         res["e2e"] = {"value": e2e_val, "unit": "cells/s", "h2d_bytes_per_step": 4 * mp.numel if accum else 0,
                       "d2h_bytes_per_step": 4 * mp.numel}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -936,6 +943,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--no-energy", action="store_true", help="skip the NVML energy runs")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller case of the workload)")
     ap.add_argument("--block", type=int, default=None, help="override the tile side")
     ap.add_argument("--side", type=int, default=None,
@@ -946,6 +954,8 @@ def main():
     ap.add_argument("--layout", type=int, default=0,
                     help="m = 3 H3 layout: 0 packed grid (Sec. 4.3), 1 one block range per stack level")
     args = ap.parse_args()
+    global _ENERGY
+    _ENERGY = not args.no_energy
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank, world, local = _dist_init()
