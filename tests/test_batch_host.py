@@ -83,3 +83,31 @@ def test_server_params_are_validated(field, bad):
         assert sx._lib.simplex_server_arena_bytes(ctypes.byref(p), ctypes.byref(need)) == 0
     p = sx.SimplexServerParams(**(good | {field: bad}))
     assert sx._lib.simplex_server_arena_bytes(ctypes.byref(p), ctypes.byref(need)) == sx.SIMPLEX_EINVAL
+
+
+def test_serve_trace_generator():
+    """The serving workload: Poisson arrivals at the stated rate (count within
+    5 sigma, exponential gaps with the right mean), 80/20 m = 2/m = 3, n
+    log-uniform in its range (the median near the geometric mean), steps
+    uniform in 1..64, the rules of each m and Bernoulli(0.5) initial states."""
+    import numpy as np
+    rate, secs = 2000.0, 5.0
+    jobs, t = inputs.serve_trace(rate=rate, seconds=secs)
+    k = len(jobs)
+    assert len(t) == k and abs(k - rate * secs) < 5 * math.sqrt(rate * secs)
+    assert (np.diff(t) > 0).all() and t[0] >= 0 and t[-1] < secs
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / rate) < 5 / rate / math.sqrt(k)
+    m3 = np.array([d["m"] == 3 for d in jobs])
+    assert abs(m3.mean() - 0.2) < 5 * math.sqrt(0.2 * 0.8 / k)
+    for m, (lo, hi), rule in ((2, (128, 8192), inputs.B3S23), (3, (32, 512), inputs.B5S45)):
+        ns = np.array([d["n"] for d in jobs if d["m"] == m])
+        assert ns.min() >= lo and ns.max() < hi
+        assert abs(np.log(np.median(ns)) - 0.5 * (np.log(lo) + np.log(hi))) < 0.15
+        assert all((d["birth"], d["survive"]) == rule for d in jobs if d["m"] == m)
+    steps = np.array([d["steps"] for d in jobs])
+    assert steps.min() == 1 and steps.max() == 64 and abs(steps.mean() - 32.5) < 1.0
+    assert all(d["threshold"] == inputs.bernoulli_threshold(0.5) for d in jobs)
+    assert [d["seed"] for d in jobs] == list(range(k))
+    again, t2 = inputs.serve_trace(rate=rate, seconds=secs)
+    assert again == jobs and (t2 == t).all()        # seeded
