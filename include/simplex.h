@@ -515,7 +515,10 @@ int simplex_server_destroy(simplex_server_t server);
  * realtime = 0 or arrival_s = NULL every job is available at once).  Work is
  * issued on `stream`.  Results and statistics stay queryable until the next
  * run.  A job whose grids exceed the budget, or whose work list exceeds
- * max_items, is rejected (status 3) and the others still run.  count = 0
+ * max_items, is rejected (status 3) and the others still run.  In real time
+ * the calling thread polls the GPU's events while work is in flight (it
+ * sleeps only when nothing is resident, until 0.2 ms before the next
+ * arrival), so one host core is busy for the length of the trace.  count = 0
  * (jobs may then be NULL) runs an empty trace.  Errors: SIMPLEX_EINVAL (a
  * job's parameters, count < 0), SIMPLEX_ECUDA.
  */
