@@ -37,6 +37,7 @@
 #include "batch.h"
 #include "host.h"
 #include "kernels.h"
+#include "pool.h"
 
 using namespace sxh;
 
@@ -50,59 +51,6 @@ uint64_t binom(uint64_t n, int k)
     for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
     return (uint64_t)r;
 }
-
-// First-fit allocator over the grid pool [0, size), 256-byte granules; free
-// ranges are coalesced on release.
-class FreeList {
-  public:
-    void reset(uint64_t size)
-    {
-        free_.clear();
-        if (size) free_[0] = size;
-        size_ = size;
-        used_ = 0;
-        peak_ = 0;
-    }
-    bool alloc(uint64_t bytes, uint64_t *off)
-    {
-        bytes = align_up(bytes, 256);
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second >= bytes) {
-                *off = it->first;
-                const uint64_t rest = it->second - bytes, start = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[start] = rest;
-                used_ += bytes;
-                peak_ = std::max(peak_, used_);
-                return true;
-            }
-        return false;
-    }
-    void release(uint64_t off, uint64_t bytes)
-    {
-        bytes = align_up(bytes, 256);
-        used_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto next = std::next(it);
-        if (next != free_.end() && it->first + it->second == next->first) {
-            it->second += next->second;
-            free_.erase(next);
-        }
-        if (it != free_.begin()) {
-            auto prev = std::prev(it);
-            if (prev->first + prev->second == it->first) {
-                prev->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    uint64_t used() const { return used_; }
-    uint64_t peak() const { return peak_; }
-
-  private:
-    std::map<uint64_t, uint64_t> free_;
-    uint64_t size_ = 0, used_ = 0, peak_ = 0;
-};
 
 enum JobStatus : int32_t { kPending = 0, kActive = 1, kDone = 2, kRejected = 3 };
 
