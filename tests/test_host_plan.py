@@ -347,3 +347,44 @@ def test_bb_thread_mode_decodes_like_bb(case):
     mp = sx.simplex_map_create(m, n, 2, 2 if m <= 3 else 4, rho)
     for v in range(0, mp.info.bb_blocks, 7):
         assert sx.simplex_map_block(mp, sx.SIMPLEX_MODE_BB_THREAD, v) == sx.simplex_map_block(mp, sx.SIMPLEX_MODE_BB, v)
+
+
+_NULL_PROBE = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2208_11617_gb300 import simplex as sx
+L, N = sx._lib, None
+calls = {
+    "simplex_map_info": (N, N), "simplex_map_block": (N, 0, 0, N, N), "simplex_write": (N, N, 0, 0, N),
+    "simplex_accum": (N, N, 0, 0, N), "simplex_ca_init": (N, N, 0, 0, N, N),
+    "simplex_ca_step": (N, N, N, 0, 0, N, 0, N), "simplex_ca_run": (N, N, N, 1, 0, 0, N, 1, 0, N),
+    "simplex_ca_run_host": (N, N, N, N, N, 1, 0, 0, N, N, 1, 0, N), "simplex_visit_count": (N, N, 0, 0, N),
+    "simplex_map_test": (N, N, 0, N), "simplex_edm": (N, N, 3, N, 0, N), "simplex_ca_digest": (N, N, N, N, N),
+    "simplex_batch_info": (N, N), "simplex_batch_bind": (N, N, 0, N), "simplex_batch_init": (N, N),
+    "simplex_batch_run": (N, 1, N, 1, N), "simplex_batch_grid": (N, 0, N, N),
+    "simplex_batch_run_static": (N, N, 0, 0, 1, N, N), "simplex_server_run": (N, N, N, 0, 0, N),
+    "simplex_server_begin": (N, N), "simplex_server_submit": (N, N, N), "simplex_server_poll": (N, N),
+    "simplex_server_wait": (N, -1), "simplex_server_result": (N, 0, N, N), "simplex_server_stats": (N, N),
+    "simplex_server_arena_bytes": (N, N), "simplex_server_create": (N, N, 0, N), "simplex_map_create_ex": (N, N),
+    "simplex_map_create": (2, 10, 2, 2, 16, N), "simplex_batch_create": (N, 0, N),
+    "simplex_map_destroy": (N,), "simplex_batch_destroy": (N,), "simplex_server_destroy": (N,),
+}
+print(json.dumps({name: getattr(L, name)(*args) for name, args in calls.items()}))
+'''
+
+
+def test_null_handles_and_outputs_are_rejected():
+    """Every entry point given a NULL handle (or NULL output) returns
+    SIMPLEX_EINVAL before touching the GPU; destroying NULL is a no-op.  Run in
+    a child process so that a crash would fail this test, not the suite."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _NULL_PROBE, ROOT], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    assert set(got) >= set(sx.EXPORTED) - {"simplex_device_status", "simplex_last_error", "simplex_version",
+                                             "simplex_selftest_wait_timeout", "simplex_map_create_padded"}
+    for name, rc in got.items():
+        want = sx.SIMPLEX_OK if name.endswith("_destroy") else sx.SIMPLEX_EINVAL
+        assert rc == want, (name, rc)
