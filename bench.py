@@ -47,6 +47,7 @@ _KERNEL_SOURCES = {
     "ca2_step_kernel<128>": ["k_ca2.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp"],
     "ca3_step_kernel<32>": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
     "ca3_step_stream": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
+    "ca3_step_planes": ["k_ca3p.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
 }
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (mean of 3 launches
 # at full size), for the kernel sources with the given fingerprint
@@ -265,6 +266,9 @@ def _map_name(info):
         return "H3, one block range per stack level (fully efficient, r=1/2, beta=2)"
     if info.get("launch") == 2:
         return "x-stream: H2 (Eq. map2d) over the tile columns, runs of up to 16 tiles along x3"
+    if info.get("launch") == 3:
+        return ("plane stream: slabs of planes x1 cut into 32 x 128 bricks, numbered slab by slab, "
+                "each brick streamed along x1")
     return f"H (r=1/{info['r_inv']}, beta={info['beta']})"
 
 
@@ -506,7 +510,9 @@ def run_serve(args, rank, world):
                             "n log-U[128,8192]/[32,512], steps U{1..64}, Bernoulli(0.5), 64 GiB grid budget",
                 "jobs": len(jobs), "parallelism": "replicas" if world > 1 else "single"},
         serve={"p50_ms": st["p50_ms"], "p90_ms": st["p90_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-               "mean_ms": st["mean_ms"], "completed": st["completed"], "rejected": st["rejected"],
+               "mean_ms": st["mean_ms"], "host_p50_ms": st["host_p50_ms"], "host_p99_ms": st["host_p99_ms"],
+               "latency_note": "p*_ms: arrival to the device event after the job's result copies; host_p*_ms: "
+                               "arrival to the serving loop finding the job complete", "completed": st["completed"], "rejected": st["rejected"],
                "rounds": st["rounds"], "mean_resident_jobs": st["mean_active"],
                "peak_pool_gib": st["peak_pool_bytes"] / 2 ** 30, "offered_cell_updates_per_s":
                    st["cell_updates"] / seconds},
@@ -522,6 +528,7 @@ def run_serve(args, rank, world):
                       (cap["cell_updates"] / cap_wall) / serial_cap_rate, "mean_resident_jobs": cap["mean_active"]},
         high_load={"rate_jobs_per_s": hl_rate, "seconds": args.serve_high_seconds, "jobs": len(hjobs),
                    "server_p50_ms": hl["p50_ms"], "server_p99_ms": hl["p99_ms"],
+                   "server_host_p50_ms": hl["host_p50_ms"], "server_host_p99_ms": hl["host_p99_ms"],
                    "server_cell_updates_per_s": hl["cell_updates"] / (hl["wall_ms"] * 1e-3),
                    "mean_resident_jobs": hl["mean_active"], "serial_utilisation": hl_rate * mean_svc,
                    "serial_fifo_p50_ms": hq(0.5), "serial_fifo_p99_ms": hq(0.99)},
@@ -576,7 +583,7 @@ def run_ours(args, rank, world, local):
             lambda: sx.simplex_ca_step(mp, a, nxt, birth, survive, None, sx.SIMPLEX_MODE_BB_THREAD), 10)[0]
         alg_bytes = 2 * cells
         achieved = alg_bytes / (mean_ms * 1e-3) / 1e9
-        kname = ("ca3_step_stream" if info["launch"] == 2 else f"ca{wl.m}_step_kernel<{wl.block}>")
+        kname = {2: "ca3_step_stream", 3: "ca3_step_planes"}.get(info["launch"], f"ca{wl.m}_step_kernel<{wl.block}>")
         res.update(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -607,6 +614,16 @@ def run_ours(args, rank, world, local):
             "bb": None if args.no_bb else _energy_region(meter, step(sx.SIMPLEX_MODE_BB), secs_bb / args.steps,
                                                           cells * wl.steps),
             "unit": "cell-updates per joule (board energy, NVML, a separate ~1.5 s run per map)"}
+        if wl.m == 3 and info["launch"] != 3:
+            # the plane-stream form on the same grids
+            mpq = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, launch=3, side=args.side)
+            mq_ms = _per_launch_ms(lambda: sx.simplex_ca_step(mpq, a, nxt, birth, survive, None), 20)[0]
+            ach_q = alg_bytes / (mq_ms * 1e-3) / 1e9
+            res["plane_stream"] = {"kernel": "ca3_step_planes", "launch_ms_mean": mq_ms, "achieved": ach_q,
+                                   "frac": ach_q / hbm_peak,
+                                   "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint("ca3_step_planes"),
+                                                                   "ca3_step_planes", wl.n)),
+                                   "note": "same step, plane-stream form (launch 3)"}
         if wl.m == 3 and wl.block == 32 and info["launch"] != 2:
             # the other m = 3 step form on the same grids: persistent CTAs streaming
             # slab columns along x3 (H2 over the tile columns)
@@ -734,7 +751,7 @@ def run_ours(args, rank, world, local):
         res["e2e"] = {"value": e2e_val, "unit": "cells/s", "h2d_bytes_per_step": 4 * mp.numel if accum else 0,
                       "d2h_bytes_per_step": 4 * mp.numel}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(wl)
+        res["cpu_baseline"] = cpu_baseline(wl, workload=args.workload, n=args.n)
     return res
 
 
@@ -829,7 +846,7 @@ def run_diag(args, wl, rank, world):
         res["theory_speedup"] = {2: 2.0, 3: 6.0}.get(wl.m)
         res["e2e"] = {"value": None, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and edm:
-        res["cpu_baseline"] = cpu_baseline(wl, edm=True)
+        res["cpu_baseline"] = cpu_baseline(wl, edm=True, workload="edm")
     return res
 
 
@@ -876,13 +893,73 @@ def _oracle_edm_sample(n_sample):
     return oracle.count_cells(2, n_sample) / dt, f"the whole EDM triangle at n={n_sample}", oracle.num_threads(), dt
 
 
-def cpu_baseline(wl, edm=False):
+def _cpu_model() -> str:
+    """The host CPU's model string (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# One bounded oracle sample in a child process with OpenMP limited to one
+# thread (the oracle's parallel loops then run serially); prints JSON.
+_SINGLE_THREAD_PROBE = r"""
+import dataclasses, json, sys
+sys.path.insert(0, sys.argv[1])
+import bench
+wl = bench._workload(sys.argv[2])
+if sys.argv[3] != "-":
+    wl = dataclasses.replace(wl, n=int(sys.argv[3]))
+if sys.argv[4] == "edm":
+    v, note, cores, dt = bench._oracle_edm_sample(int(sys.argv[5]))
+else:
+    v, note, cores, dt = bench._oracle_sample(wl, int(sys.argv[5]))
+print(json.dumps({"value": v, "sample": note, "cores": cores, "seconds": dt}))
+"""
+
+
+def _oracle_single_thread(workload, n, edm, sample):
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", _SINGLE_THREAD_PROBE, ROOT, workload, str(n) if n is not None else "-",
+                            "edm" if edm else "-", str(sample)], capture_output=True, text=True, timeout=600,
+                           env=env)
+        if r.returncode == 0:
+            return json.loads(r.stdout.strip().splitlines()[-1])
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else f"exit {r.returncode}"}
+    except (OSError, subprocess.SubprocessError, ValueError) as exc:
+        return {"error": str(exc)}
+
+
+def cpu_baseline(wl, edm=False, workload=None, n=None):
+    """The oracle on all host cores (OpenMP) on a bounded sample, plus the same
+    oracle on one thread (a smaller sample) and the CPU model string."""
     if edm:
         v, note, cores, dt = _oracle_edm_sample(8191)
-        return {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": note, "seconds": dt}
-    v, note, cores, dt = _oracle_sample(wl, 2 if isinstance(wl, inputs.CAWorkload) else 5)
-    return {"value": v, "unit": UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s", "cores": cores,
-            "kind": "oracle", "sample": note, "seconds": dt}
+        res = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": note, "seconds": dt}
+        one = _oracle_single_thread("edm", None, True, 4095)
+    else:
+        ca = isinstance(wl, inputs.CAWorkload)
+        v, note, cores, dt = _oracle_sample(wl, 2 if ca else 5)
+        res = {"value": v, "unit": UNIT if ca else "cells/s", "cores": cores,
+               "kind": "oracle", "sample": note, "seconds": dt}
+        one = _oracle_single_thread(workload, n, False, 1) if workload else {"error": "no workload name"}
+    res["cpu_model"] = _cpu_model()
+    res["single_thread"] = one if "error" in one else {"value": one["value"], "unit": res["unit"], "cores": 1,
+                                                       "sample": one["sample"], "seconds": one["seconds"]}
+    return res
 
 
 def run_reference(args, rank, world):
@@ -949,7 +1026,8 @@ def main():
     ap.add_argument("--side", type=int, default=None,
                     help="automaton: padded array side (cells per row, a multiple of 16; default n + 1 rounded up)")
     ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
-    ap.add_argument("--launch", type=int, default=0, help="automaton step form: 0 auto, 1 grid, 2 x-stream (m = 3)")
+    ap.add_argument("--launch", type=int, default=0,
+                    help="automaton step form: 0 auto, 1 grid, 2 x-stream, 3 plane stream (m = 3)")
     ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")
     ap.add_argument("--layout", type=int, default=0,
                     help="m = 3 H3 layout: 0 packed grid (Sec. 4.3), 1 one block range per stack level")

@@ -70,7 +70,7 @@ typedef struct simplex_map_info {
     int32_t log2N;
     int32_t band;           /* m = 2 trapezoid band height in tiles; 0 = single H2 grid */
     int32_t Ne;             /* m = 2 trapezoid form: block-triangle side (multiple of band) */
-    int32_t launch;         /* automaton step form: 1 grid, 2 x-stream (persistent) */
+    int32_t launch;         /* automaton step form: 1 grid, 2 x-stream, 3 plane stream */
     int32_t layout;         /* m = 3, beta = 2: 0 packed grid, 1 one block range per level */
     uint64_t cells;         /* C(n+m, m), Eq. 1 */
     uint64_t useful_blocks; /* tiles holding at least one cell: C(floor(n/rho)+m, m) */
@@ -78,6 +78,8 @@ typedef struct simplex_map_info {
     uint64_t bb_blocks;     /* CUDA blocks one bounding-box launch starts (N^m) */
     uint64_t h_set_blocks;  /* blocks of the self-similar set S (Eq. generic-m) */
     uint64_t host_copy_bytes; /* bytes simplex_ca_run_host moves each way (m = 2, 3) */
+    uint64_t plane_units;     /* launch 3: work units of one step in mode H (else 0) */
+    uint64_t plane_units_bb;  /* launch 3: work units of one step in the bounding-box modes */
 } simplex_map_info_t;
 
 /*
@@ -111,7 +113,7 @@ typedef struct simplex_map_params {
     int64_t n;
     int64_t side;                  /* array side, >= n + 1; 0 means n + 1 */
     int32_t band;                  /* m = 2 only, see below; must be 0 or -1 for m > 2 */
-    int32_t launch;                /* automaton step: 0 automatic, 1 grid, 2 x-stream (see below) */
+    int32_t launch;                /* automaton step: 0 automatic, 1 grid, 2 x-stream, 3 plane stream (see below) */
     int32_t layout;                /* m = 3, beta = 2: 0 packed grid, 1 one range per level (see below) */
 } simplex_map_params_t;
 
@@ -140,6 +142,24 @@ typedef struct simplex_map_params {
  *     BB become per-run work units.  The map keeps a 16-byte work counter in
  *     device memory, allocated on first use: steps of one map must not run
  *     concurrently on different streams.
+ *   3 (plane stream, m = 3 with block 16 or 32; the block size does not
+ *     enter the step): persistent CTAs, several per SM, take work units from
+ *     a device work counter.  The tetrahedron is cut into slabs of
+ *     consecutive planes x1 and each slab's cross-section x2 + x3 <= n - x1
+ *     into bricks of 32 rows x2 by 128 cells x3; a unit is one brick of one
+ *     slab (simplex_map_unit), numbered slab by slab so that bricks in
+ *     flight are neighbours.  The CTA streams the brick along x1, staging
+ *     each plane (the brick plus its one-cell halo, a box only as wide as
+ *     the plane's domain cells reach) by one TMA load into a ring of stages,
+ *     and reads every staged byte once.  Slabs hold 64 planes at most and
+ *     shrink towards the apex (x1 = n) to 4, so the last units of a step are
+ *     short.  Mode H numbers only bricks holding cells of their slab;
+ *     SIMPLEX_MODE_BB numbers every brick of the (n+1)^2 square in every slab
+ *     and the empty ones are skipped by the CTA that takes them;
+ *     SIMPLEX_MODE_BB_THREAD stages and computes them too, every store
+ *     masked.  The same 16-byte work counter as launch 2 applies.  Plans
+ *     that would need more than 320 slabs (n above about 7000) are refused
+ *     with SIMPLEX_EUNSUPPORTED.
  *   0 (automatic): grid.
  * `layout` (m = 3, beta = 2 only) selects how H3 lays out its cubes:
  *   0: the single packed grid of Sec. 4.3: the big cube (N/2)^3 and one layer
@@ -171,6 +191,19 @@ int simplex_map_info(simplex_map_t map, simplex_map_info_t *out);
  * No GPU needed.
  */
 int simplex_map_block(simplex_map_t map, int mode, uint64_t v, int32_t *coord, int *valid);
+
+/*
+ * simplex_map_unit -- host-side evaluation of the plane-stream work unit
+ * numbering (launch 3) for unit index `w` of a step in `mode`: unit[0] = y0
+ * (first row x2 of the brick, a multiple of 32), unit[1] = x0 (first cell x3,
+ * a multiple of 128), unit[2] = first and unit[3] = last plane x1 the unit
+ * writes.  *valid = 0 iff the unit's brick holds no cell of its slab
+ * (SIMPLEX_MODE_BB; the step skips it).  The kernels run the same decode.
+ * SIMPLEX_EINVAL if the map is not a plane-stream map or w is not below
+ * plane_units (mode H) or plane_units_bb (the bounding-box modes).  No GPU
+ * needed.
+ */
+int simplex_map_unit(simplex_map_t map, int mode, uint64_t w, int32_t *unit, int *valid);
 
 /*
  * simplex_write -- coordinate-write test (Table 1 test 2 as a store-only
@@ -417,15 +450,23 @@ int simplex_batch_grid(simplex_batch_t batch, int i, uint8_t **grid, int64_t *si
  *                grid (parity + steps) % 2; grids must be zero outside each
  *                domain.  The batch need not be bound.
  *   steps, live  as simplex_batch_run (live is zeroed, then filled).
- * Runs `steps` launches on `stream`, asynchronously.  The first call on a
- * device looks up the fixed array's address there (cudaGetSymbolAddress);
- * make that first call before any stream capture on that device.  Every call
- * overwrites the fixed array (its work-queue counters are zeroed each call), so
- * calls whose work overlaps on the GPU -- other streams, other host threads --
- * race and give wrong results: serialise them.  A batch whose descriptors,
- * work items and counters exceed 8 MiB (about 1.2 KB per instance: several
- * thousand instances; the 2,304-instance batched workload needs 2.8 MB) is
- * rejected with SIMPLEX_EINVAL.
+ * Runs `steps` launches on `stream`.  The first call on a device looks up
+ * the fixed array's address there (cudaGetSymbolAddress) and keeps it for the
+ * life of the process: make that first call before any stream capture on
+ * that device (this concerns the look-up only), and do not reset the device
+ * (cudaDeviceReset) after it, since the array may then move.
+ * Host cost: when the array does not already hold this batch's descriptors,
+ * work items and tensor maps for these grids (the previous call on the device
+ * was for another batch or another grids address), the call encodes the
+ * tensor maps and copies all of it from ordinary (pageable) host memory, so it
+ * may block the host until those copies are done; a repeated call with the
+ * same batch and grids only zeroes the work-queue counters and launches.
+ * Every call rewrites part of the fixed array (at least its work-queue
+ * counters), so calls whose work overlaps on the GPU -- other streams, other
+ * host threads -- race and give wrong results: serialise them.  A batch whose
+ * descriptors, work items and counters exceed 8 MiB (about 1.2 KB per
+ * instance: several thousand instances; the 2,304-instance batched workload
+ * needs 2.8 MB) is rejected with SIMPLEX_EINVAL.
  */
 int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t grids_bytes, int parity, int steps,
                              unsigned long long *live, void *stream);
@@ -479,9 +520,13 @@ typedef struct simplex_job_result {
     int32_t steps;
     double arrival_ms;       /* from the trace */
     double admit_ms;         /* host time of admission */
-    double done_ms;          /* device time at which its last step had completed */
+    double done_ms;          /* device time at which its last step and its result copies had completed
+                                (a CUDA event on the serving stream, against one recorded at the start) */
     uint64_t digest;         /* sum over live cells x of splitmix32(0x00D16E57 ^ lin(x)), mod 2^64 */
     uint64_t live_final;     /* live cells after the last step */
+    double seen_ms;          /* host time at which the serving loop found the job complete and its
+                                results became readable (simplex_server_result): done_ms plus the
+                                loop's detection delay */
 } simplex_job_result_t;
 
 typedef struct simplex_server_stats {
@@ -490,10 +535,11 @@ typedef struct simplex_server_stats {
     uint64_t peak_pool_bytes;
     double wall_ms;          /* from the start of the trace to the last completion seen */
     double mean_active;      /* resident jobs per round or direct chunk launch */
-    double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* latency: done - arrival */
+    double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;   /* latency: done_ms - arrival (device clock) */
     double host_issue_ms;    /* host time spent building and issuing rounds */
     double gpu_round_ms;     /* mean device time of a round: its first operation to its last */
     uint64_t launches;       /* kernels launched: admission inits, direct steps, passes, digests */
+    double host_p50_ms, host_p99_ms; /* latency as the host sees it: seen_ms - arrival */
 } simplex_server_stats_t;
 
 /* Device bytes the server's arena needs for these parameters (tables + pool). */

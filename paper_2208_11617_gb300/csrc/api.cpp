@@ -92,9 +92,12 @@ struct simplex_map {
     int device = -1;
     cudaStream_t capture = nullptr;
     std::vector<GraphEntry> graphs;
-    // m = 3 x-stream form: work counter and CTAs-done counter (zero between launches)
+    // m = 3 x-stream and plane-stream forms: work counter and CTAs-done
+    // counter (zero between launches)
     unsigned long long *queue = nullptr;
     int queue_device = -1;
+    // m = 3 plane-stream form: the unit schedule of each mode (built on first use)
+    sx::PlaneSched *sched[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace sxh {
@@ -234,6 +237,19 @@ int check_ca_layout(const sx::Plan &p, const void *grid, const char *name)
 int ensure_queue(simplex_map_t map)
 {
     if (!(map->plan.m == 3 && map->plan.persistent)) return SIMPLEX_OK;
+    if (map->plan.persistent == 2) {
+        for (int k = 0; k < 3; ++k) {
+            if (map->sched[k]) continue;
+            sx::PlaneSched *s = new (std::nothrow) sx::PlaneSched();
+            if (!s) return fail(SIMPLEX_ENOMEM, "host allocation failed");
+            if (!sx::plane_sched_build(map->plan.n, k, s)) {
+                delete s;
+                return fail(SIMPLEX_EUNSUPPORTED, "n = %lld needs more plane-stream segments or units than supported",
+                            (long long)map->plan.n);
+            }
+            map->sched[k] = s;
+        }
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -259,6 +275,13 @@ int step_once(simplex_map_t map, const uint8_t *in, uint8_t *out, const sx::Rule
     const sx::Plan &p = map->plan;
     int rc = ensure_queue(map);
     if (rc) return rc;
+    if (p.m == 3 && p.persistent == 2) {
+        sx::PlaneMaps maps;
+        if ((rc = make_plane_maps(p, in, &maps))) return rc;
+        cudaError_t e = sx::launch_ca3_planes(*map->sched[mode], maps, p.n, p.side, out, rule, live, map->queue, st);
+        if (e != cudaSuccess) return cuda_fail(e, "automaton step launch");
+        return SIMPLEX_OK;
+    }
     CUtensorMap tm;
     rc = make_tensor_map(p, in, &tm, sx::ca3_box_planes(p));
     if (rc) return rc;
@@ -383,8 +406,9 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
 {
     if (!params || !out) return fail(SIMPLEX_EINVAL, "params and out must not be NULL");
     *out = nullptr;
-    if (params->launch < 0 || params->launch > 2)
-        return fail(SIMPLEX_EINVAL, "params->launch must be 0 (automatic), 1 (grid) or 2 (x-stream), got %d",
+    if (params->launch < 0 || params->launch > 3)
+        return fail(SIMPLEX_EINVAL,
+                    "params->launch must be 0 (automatic), 1 (grid), 2 (x-stream) or 3 (plane stream), got %d",
                     params->launch);
     const int64_t side = params->side ? params->side : params->n + 1;
     int band = params->band;
@@ -402,7 +426,14 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
         const bool can_persist = p.m == 3 && p.rho == 32;
         if (params->launch == 2 && !can_persist)
             return fail(SIMPLEX_EUNSUPPORTED, "the x-stream automaton step exists for m = 3, block 32");
-        p.persistent = params->launch == 2 ? 1 : 0;
+        if (params->launch == 3) {
+            if (p.m != 3) return fail(SIMPLEX_EUNSUPPORTED, "the plane-stream automaton step exists for m = 3");
+            sx::PlaneSched probe;
+            if (!sx::plane_sched_build(p.n, sx::kMapBB, &probe))
+                return fail(SIMPLEX_EUNSUPPORTED, "n = %lld needs more plane-stream segments or units than supported",
+                            (long long)p.n);
+        }
+        p.persistent = params->launch == 2 ? 1 : (params->launch == 3 ? 2 : 0);
     }
     if (rc) return rc;
     simplex_map *map = new (std::nothrow) simplex_map();
@@ -430,6 +461,7 @@ int simplex_map_destroy(simplex_map_t map)
     for (auto &g : map->graphs) cudaGraphExecDestroy(g.exec);
     if (map->capture) cudaStreamDestroy(map->capture);
     if (map->queue) cudaFree(map->queue);
+    for (auto *s : map->sched) delete s;
     delete map;
     return SIMPLEX_OK;
 }
@@ -451,11 +483,16 @@ int simplex_map_info(simplex_map_t map, simplex_map_info_t *out)
     out->log2N = p.logN;
     out->band = p.band;
     out->Ne = p.Ne;
-    out->launch = p.persistent ? 2 : 1;
+    out->launch = p.persistent == 2 ? 3 : (p.persistent ? 2 : 1);
     out->layout = p.h3_exact;
     out->cells = binom((uint64_t)p.n + (uint64_t)p.m, p.m);
     out->useful_blocks = binom((uint64_t)(p.n / p.rho) + (uint64_t)p.m, p.m);
     out->host_copy_bytes = (p.m == 2 || p.m == 3) ? domain_copy_bytes(p) : 0;
+    if (p.m == 3 && p.persistent == 2) {
+        sx::PlaneSched sh, sb;
+        if (sx::plane_sched_build(p.n, sx::kMapH, &sh)) out->plane_units = sh.units;
+        if (sx::plane_sched_build(p.n, sx::kMapBB, &sb)) out->plane_units_bb = sb.units;
+    }
     out->h_blocks = p.h_blocks;
     out->bb_blocks = p.bb_blocks;
     // Eq. generic-m with r = 1/2: (N^m - beta^log2 N) / (2^m - beta)
@@ -486,6 +523,28 @@ int simplex_map_block(simplex_map_t map, int mode, uint64_t v, int32_t *coord, i
         for (int i = 0; i < p.m; ++i) s += X[i];
         ok = s * p.rho <= p.n;
     }
+    *valid = ok ? 1 : 0;
+    return SIMPLEX_OK;
+}
+
+int simplex_map_unit(simplex_map_t map, int mode, uint64_t w, int32_t *unit, int *valid)
+{
+    int rc;
+    if ((rc = check_map(map)) || (rc = check_mode(mode))) return rc;
+    if (!unit || !valid) return fail(SIMPLEX_EINVAL, "unit and valid must not be NULL");
+    const sx::Plan &p = map->plan;
+    if (!(p.m == 3 && p.persistent == 2)) return fail(SIMPLEX_EINVAL, "the map is not a plane-stream (launch 3) map");
+    sx::PlaneSched s;
+    if (!sx::plane_sched_build(p.n, mode, &s)) return fail(SIMPLEX_EUNSUPPORTED, "plane-stream schedule too large");
+    if (w >= s.units)
+        return fail(SIMPLEX_EINVAL, "unit index %llu out of range (%llu units)", (unsigned long long)w,
+                    (unsigned long long)s.units);
+    sx::PlaneUnit u;
+    const bool ok = sx::plane_unit_decode(s, w, u);
+    unit[0] = u.y0;
+    unit[1] = u.x0;
+    unit[2] = u.b;
+    unit[3] = u.e;
     *valid = ok ? 1 : 0;
     return SIMPLEX_OK;
 }
@@ -586,6 +645,7 @@ int simplex_ca_run(simplex_map_t map, uint8_t *a, uint8_t *b, int steps, uint32_
         map->device = dev;
     }
     e = map->plan.m == 2 ? sx::ca2_prepare(map->plan.rho) : sx::ca3_prepare(map->plan.rho);
+    if (e == cudaSuccess && map->plan.m == 3 && map->plan.persistent == 2) e = sx::ca3_planes_prepare();
     if (e != cudaSuccess) return cuda_fail(e, "setting the kernel shared-memory limit");
     if ((rc = ensure_queue(map))) return rc;
     cudaGraphExec_t exec = nullptr;
@@ -677,6 +737,10 @@ int simplex_device_status(uint32_t *out)
     if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
     e = sx::ca3_read_status(&s3);
     if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+    uint32_t s3p = 0;
+    e = sx::ca3p_read_status(&s3p);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+    s3 |= s3p;
     uint32_t sb = 0;
     e = sx::batch_read_status(&sb);
     if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");

@@ -70,7 +70,9 @@ struct Plan {
     int32_t Ne, nbands;
     // automaton launch form: 0 = one CTA per block of the map (the paper's
     // execution model), 1 = persistent CTAs streaming runs of tiles along the
-    // fastest axis (m = 3, see xrun_decode); seg_len = tiles per run
+    // fastest axis (m = 3, see xrun_decode; seg_len = tiles per run), 2 =
+    // persistent CTAs streaming bricks along the slowest axis (m = 3, see
+    // plane_unit_decode)
     int32_t persistent, seg_len;
     // m = 3, beta = 2: 0 = the single packed grid of Sec. 4.3 (the layer of
     // height N/4 with per-level exits), 1 = one block range per stack level
@@ -181,6 +183,124 @@ SX_HD bool xrun_decode(const Plan &p, int kind, uint64_t w, XRun &r)
     r.a = s * p.seg_len;
     r.b = (int32_t)(last < (int64_t)(r.a + p.seg_len - 1) ? last : (int64_t)(r.a + p.seg_len - 1));
     return last >= (int64_t)r.a;
+}
+
+// Plane-stream form (m = 3, launch 3).  The tetrahedron is cut into slabs of
+// consecutive planes x1 (segments) and each slab's cross-section, the
+// triangle x2 + x3 <= n - x1, into bricks of kPlaneTY rows x2 by kPlaneTX
+// cells x3.  A work unit is one brick of one segment: the CTA streams the
+// brick's planes along x1 (see k_ca3p.cu).  Units are numbered segment by
+// segment (the whole cross-section of one slab before the next, so the
+// bricks processed at the same time are neighbours and their halos meet in
+// L2); within a segment brick column X (x3 = 128 X ...) comes before X + 1,
+// and inside a column the rows Y = 0, 1, ... (a compact numbering: every
+// unit index names a brick that holds cells of the segment's first plane,
+// found from prefix counts instead of a map with padding).  The bounding box
+// numbers every brick of the (n+1) x (n+1) square in every segment; bricks
+// past the domain exit (kMapBB) or run with every store masked
+// (kMapBBThread).  Segments shrink towards the apex so that the last units
+// of a launch are short: a segment starting at plane b has
+// clamp(2^floor(log2((n + 1 - b) / 32)), 4, 64) planes.
+constexpr int kPlaneTY = 32, kPlaneTX = 128;
+constexpr int kPlaneMaxSegs = 320;
+
+struct PlaneSched {
+    int32_t nseg;        // segments
+    int32_t nty, ntx;    // bricks per axis of the square: ceil((n+1)/TY), ceil((n+1)/TX)
+    int32_t kind;        // map kind the units were counted for
+    int64_t n;
+    uint64_t units;      // work units of one step
+    int32_t seg_b[kPlaneMaxSegs + 1];   // first plane of segment s; seg_b[nseg] = n + 1
+    uint32_t seg_u[kPlaneMaxSegs + 1];  // first unit of segment s; seg_u[nseg] = units
+};
+
+// Planes of the segment that starts at plane b.
+SX_HD int32_t plane_seg_len(int64_t n, int64_t b)
+{
+    const int64_t q = (n + 1 - b) / 32;
+    int32_t s = 4;
+    while (s < 64 && (int64_t)(2 * s) <= q) s *= 2;
+    return s;
+}
+
+// Bricks of the cross-section x2 + x3 <= K that hold a cell (K >= 0):
+// column X has floor((K - TX X) / TY) + 1 rows.
+SX_HD uint64_t plane_tri_bricks(int64_t K)
+{
+    uint64_t c = 0;
+    for (int64_t x0 = 0; x0 <= K; x0 += kPlaneTX) c += (uint64_t)((K - x0) / kPlaneTY + 1);
+    return c;
+}
+
+// Fills s for a map of side n; false if n needs more than kPlaneMaxSegs
+// segments or more than 2^32 units.
+inline bool plane_sched_build(int64_t n, int kind, PlaneSched *s)
+{
+    s->n = n;
+    s->kind = kind;
+    s->nty = (int32_t)((n + kPlaneTY) / kPlaneTY);
+    s->ntx = (int32_t)((n + kPlaneTX) / kPlaneTX);
+    uint64_t u = 0;
+    int32_t k = 0;
+    for (int64_t b = 0; b <= n; b += plane_seg_len(n, b)) {
+        if (k >= kPlaneMaxSegs) return false;
+        s->seg_b[k] = (int32_t)b;
+        s->seg_u[k] = (uint32_t)u;
+        u += is_bb(kind) ? (uint64_t)s->nty * (uint64_t)s->ntx : plane_tri_bricks(n - b);
+        if (u >= (1ull << 32)) return false;
+        ++k;
+    }
+    s->nseg = k;
+    s->seg_b[k] = (int32_t)(n + 1);
+    s->seg_u[k] = (uint32_t)u;
+    s->units = u;
+    return true;
+}
+
+// One work unit: brick rows y0 ... y0 + TY - 1, cells x0 ... x0 + TX - 1,
+// output planes b ... e (inclusive).
+struct PlaneUnit {
+    int32_t y0, x0, b, e;
+};
+
+// Unit w -> its brick and planes.  False when the brick has no cell in the
+// segment (bounding box only; kMapBBThread keeps such bricks, with e the
+// segment's last plane, and their stores are all masked).
+SX_HD bool plane_unit_decode(const PlaneSched &s, uint64_t w, PlaneUnit &u)
+{
+    // segment: the last s with seg_u[s] <= w
+    int32_t lo = 0, hi = s.nseg - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if ((uint64_t)s.seg_u[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const int64_t b = s.seg_b[lo], e = (int64_t)s.seg_b[lo + 1] - 1;
+    uint64_t r = w - (uint64_t)s.seg_u[lo];
+    int64_t Y, X;
+    if (is_bb(s.kind)) {
+        X = (int64_t)(r / (uint64_t)s.nty);
+        Y = (int64_t)(r - (uint64_t)X * (uint64_t)s.nty);
+    } else {
+        const int64_t K = s.n - b;
+        X = 0;
+        for (;;) {
+            const uint64_t rows = (uint64_t)((K - X * kPlaneTX) / kPlaneTY + 1);
+            if (r < rows) break;
+            r -= rows;
+            ++X;
+        }
+        Y = (int64_t)r;
+    }
+    u.y0 = (int32_t)(Y * kPlaneTY);
+    u.x0 = (int32_t)(X * kPlaneTX);
+    u.b = (int32_t)b;
+    const int64_t last = s.n - Y * kPlaneTY - X * kPlaneTX;  // last plane with a cell of the brick
+    if (s.kind == kMapBBThread) {
+        u.e = (int32_t)e;
+        return true;
+    }
+    u.e = (int32_t)(last < e ? last : e);
+    return last >= b;
 }
 
 // Blocks before band k of the trapezoid form: sum over j < k of

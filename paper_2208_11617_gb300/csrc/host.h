@@ -10,6 +10,7 @@
 
 #include "batch.h"
 #include "hmap.cuh"
+#include "kernels.h"
 #include "rule.h"
 
 namespace sxh {
@@ -32,6 +33,9 @@ sx::Rule make_rule(int m, uint32_t birth, uint32_t survive);
 // box_planes: depth along x1 of an m = 3 box (ignored for m = 2).
 int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm, int box_planes);
 
+// The tensor maps of the m = 3 plane-stream step (one per box width).
+int make_plane_maps(const sx::Plan &p, const void *base, sx::PlaneMaps *maps);
+
 // Read-only view of a batch's host-side plans and work items; grid offsets in
 // the BatchInst records count from the start of the arena, and the grids
 // occupy [grids_offset, grids_offset + grids_bytes).
@@ -42,6 +46,7 @@ struct BatchView {
     size_t nitems;
     size_t nitems0;  // items of launch set 0 come first, then those of set 1 (32^3 tiles of m = 3)
     uint64_t grids_offset, grids_bytes;
+    uint64_t serial;  // unique per batch of this process: equal serials mean equal plans and items
 };
 
 // The step passes of a run: per step, launch set 0 over items [0, nitems0)

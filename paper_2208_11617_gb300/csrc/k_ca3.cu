@@ -308,7 +308,7 @@ bool ca3_supports(int rho) { return rho == 16 || rho == 32; }
 
 int ca3_box_planes(const Plan &p)
 {
-    return p.persistent ? kStreamColPlanes : p.rho + 2;
+    return p.persistent == 1 ? kStreamColPlanes : p.rho + 2;
 }
 
 // The 64-byte swizzle the tensor map must use for this tile side (see above).
@@ -389,7 +389,7 @@ static cudaError_t launch_stream(const Plan &p, const CUtensorMap &tcol, uint8_t
 cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule, int kind,
                             unsigned long long *live, unsigned long long *queue, cudaStream_t st)
 {
-    if (p.persistent && p.rho == 32) return launch_stream(p, tin, out, rule, kind, live, queue, st);
+    if (p.persistent == 1 && p.rho == 32) return launch_stream(p, tin, out, rule, kind, live, queue, st);
     switch (p.rho) {
     case 16: return launch_t<16, 4>(p, tin, out, rule, kind, live, st);
     case 32: return launch_t<32, kCa3Rz32>(p, tin, out, rule, kind, live, st);

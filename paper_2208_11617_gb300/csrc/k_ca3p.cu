@@ -1,0 +1,313 @@
+// k_ca3p.cu -- one step of the automaton on the 3-simplex (Table 1 test 4 on
+// the tetrahedron, fixed-dead boundary, Sec. 5.1), plane-stream form
+// (launch 3).
+//
+// Persistent CTAs (kPlCtasPerSm per SM, 128 threads each) take work units
+// from a device counter; a unit is one brick of kPlaneTY rows x2 by kPlaneTX
+// cells x3 over one segment of planes x1 (plane_unit_decode).  The CTA
+// streams the brick along x1: every input plane of the brick (its 32 rows and
+// 128 cells plus the one-cell halo: 34 rows of up to 160 bytes, the box
+// starting 16 bytes left of the brick because a TMA x coordinate must be
+// 16-byte aligned) comes in by one TMA tiled load into a ring of kPlSlots
+// stages, is read from shared memory once, and is reduced at once to column
+// sums over x2 that slide along x1 in registers.  So every staged byte is
+// read once, and the 3 x 3 x 3 sum of a cell is three column sums (planes
+// x1 - 1, x1, x1 + 1) plus one horizontal 3-sum, all byte-parallel in 32-bit
+// words (cells are 0/1, sums stay below 32: no carries between bytes).
+//
+// Thread (c, p) -- c = tid & 7, p = tid >> 3 -- owns the 16-byte chunk c of
+// the brick's rows 2p and 2p + 1: per plane it loads its chunk of the four
+// staged rows 2p ... 2p + 3 and one halo word (lane c = 0 the word left of
+// the brick, c = 7 the word right of it), and takes the neighbouring
+// chunks' edge words from lanes c - 1 and c + 1 by shuffle.  The register
+// sets of three consecutive planes rotate through a loop unrolled three
+// times, so nothing is copied between planes.
+//
+// Box width.  The cells of a staged plane x1 that lie in the domain have
+// x3 <= n - x1 - (y0 - 1), so the box only has to reach that far: the
+// producer picks the narrowest of kPlWidths tensor maps (box widths 48, 80,
+// 112, 144 and 160 bytes) that covers it, and the consumers treat chunks
+// past the box as zero (they are zero in the grid: outside the domain).  On
+// the bricks along the diagonal this halves the bytes read; a staged plane
+// with no domain cell in reach (before x1 = 0, past the brick's apex) is not
+// loaded at all.
+//
+// The producer is thread 0: after the CTA's barrier that ends the reads of
+// stage s it refills s with the plane kPlSlots ahead, fetching the next unit
+// from the counter one unit in advance.  A unit of output planes b ... e
+// stages planes b - 1 ... e + 1; the first two only fill the sums.  Every
+// wait is bounded: a CTA whose wait runs out sets the status word, waits
+// (bounded) for the loads it issued and leaves.  The last CTA to finish puts
+// the counter back to zero.
+#include "ca_tiles.cuh"
+#include "common.cuh"
+#include "hmap.cuh"
+#include "kernels.h"
+
+namespace sx {
+
+static __device__ uint32_t g_ca3p_status;
+
+constexpr int kPlSlots = 10;
+constexpr int kPlCtasPerSm = 4;
+constexpr int kPlThreads = (kPlaneTX / 16) * (kPlaneTY / 2);  // 8 chunks x 16 row pairs
+constexpr int kPlRows = kPlaneTY + 2;
+constexpr int kPlMaxW = kPlaneTX + 32;
+constexpr uint32_t kPlSlotBytes = ((uint32_t)(kPlRows * kPlMaxW) + 127u) / 128u * 128u;
+constexpr int kPlSmem = kPlSlots * (int)kPlSlotBytes + 128;
+static_assert(kPlThreads == 128, "the thread layout assumes 8 chunks x 16 row pairs");
+static_assert(kPlMaxW == 160 && kPlaneTY == 32, "the halo-word offsets assume 160-byte rows");
+static_assert(kPlCtasPerSm * (kPlSmem + 2048) <= 228 * 1024, "the ring of four CTAs exceeds an SM's shared memory");
+
+// Phase codes of a staged plane (meta .w bits 8..9).
+constexpr int kPhFirst = 0, kPhSecond = 1, kPhOut = 2, kPhEnd = 3;
+
+__host__ __device__ constexpr int plane_box_width(int i) { return i < kPlWidths - 1 ? 48 + 32 * i : kPlMaxW; }
+
+template <bool ORK>
+__global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
+    ca3_step_planes(const __grid_constant__ PlaneMaps maps, uint8_t *__restrict__ out, const int64_t n,
+                    const int64_t side, const Rule rule, const __grid_constant__ PlaneSched sched,
+                    unsigned long long *__restrict__ live, unsigned long long *__restrict__ queue)
+{
+    extern __shared__ uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t full[kPlSlots];
+    __shared__ int4 meta[kPlSlots];  // y0, x0, staged plane, width | phase << 8
+    __shared__ uint32_t red[32];
+    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x, c = tid & 7, p = tid >> 3;
+
+    // producer state (thread 0)
+    unsigned long long next_w = 0;
+    int32_t py0 = 0, px0 = 0, pb = 0, pe = -1, px1 = 0;
+    bool have = false, done = false;
+    auto produce = [&](int s) {
+        int4 md = make_int4(0, 0, 0, kPhEnd << 8);
+        while (!done) {
+            if (!have) {
+                const unsigned long long w = next_w;
+                if (w >= sched.units) {
+                    done = true;
+                    break;
+                }
+                next_w = atomicAdd(queue, 1ull);
+                PlaneUnit u;
+                if (!plane_unit_decode(sched, w, u)) continue;
+                py0 = u.y0;
+                px0 = u.x0;
+                pb = u.b;
+                pe = u.e;
+                px1 = pb - 1;
+                have = true;
+            }
+            const int ph = px1 == pb - 1 ? kPhFirst : (px1 == pb ? kPhSecond : kPhOut);
+            // bytes of the box that can hold domain cells: from x0 - 16 up to
+            // n - x1 - (y0 - 1) inclusive
+            const int64_t need = (n - px1 - py0 + 2) - (int64_t)(px0 - 16);
+            int wi = -1;
+            if (px1 >= 0 && px1 <= n && sched.kind == kMapBBThread) {
+                wi = kPlWidths - 1;  // the paper's bounding box: every brick staged in full
+            } else if (px1 >= 0 && px1 <= n && need > 16) {
+                wi = 0;
+                while (wi < kPlWidths - 1 && (int64_t)plane_box_width(wi) < need) ++wi;
+            }
+            const int W = wi < 0 ? 0 : plane_box_width(wi);
+            md = make_int4(py0, px0, px1, W | (ph << 8));
+            meta[s] = md;
+            if (wi < 0) {
+                mbar_arrive(&full[s]);  // nothing to load: the phase completes with no bytes
+            } else {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[s], (uint32_t)(kPlRows * W));
+                tma_load_3d(ring + s * kPlSlotBytes, &maps.m[wi], px0 - 16, py0 - 1, px1, &full[s]);
+            }
+            if (++px1 > pe + 1) have = false;
+            return;
+        }
+        meta[s] = md;
+        mbar_arrive(&full[s]);
+    };
+
+    if (tid == 0) {
+        for (int i = 0; i < kPlWidths; ++i) prefetch_tmap(&maps.m[i]);
+        for (int s = 0; s < kPlSlots; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+        next_w = atomicAdd(queue, 1ull);
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < kPlSlots; ++s) produce(s);
+
+    // column sums of the three newest staged planes (rotating): words 0..3 of
+    // row 2p (f) and of row 2p + 1 (s), [4] the halo word; and the centre rows
+    uint32_t sf[3][5], ss[3][5], af[3][4], as[3][4];
+    uint32_t lsum = 0;
+    int slot = 0;
+    uint32_t parity = 0;
+    bool ok = true;
+    for (;;) {
+        bool end = false;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            ok = mbar_wait_bounded(&full[slot], parity, kWaitLimitNs);
+            const int4 md = meta[slot];
+            const int W = md.w & 255, ph = (md.w >> 8) & 3;
+            uint32_t v[4][4], h[4];
+            {
+                const uint8_t *base = ring + slot * kPlSlotBytes + 2 * p * W;
+                const bool has_c = 16 * c + 32 <= W;
+                const bool has_h = (c == 0 && W > 0) || (c == 7 && W == kPlMaxW);
+                const int ho = c == 0 ? 12 : 16 + kPlaneTX;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                    if (ok && ph != kPhEnd && has_c) q = *reinterpret_cast<const uint4 *>(base + k * W + 16 + 16 * c);
+                    v[k][0] = q.x;
+                    v[k][1] = q.y;
+                    v[k][2] = q.z;
+                    v[k][3] = q.w;
+                    h[k] = (ok && ph != kPhEnd && has_h) ? *reinterpret_cast<const uint32_t *>(base + k * W + ho) : 0u;
+                }
+            }
+            // every thread is done with the stage (and with the meta word)
+            if (__syncthreads_or(!ok)) {
+                ok = false;
+                end = true;
+                break;
+            }
+            if (ph == kPhEnd) {
+                end = true;
+                break;
+            }
+            if (tid == 0) produce(slot);
+            // sums of this plane into set j
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                sf[j][w] = v[0][w] + v[1][w] + v[2][w];
+                ss[j][w] = v[1][w] + v[2][w] + v[3][w];
+                af[j][w] = v[1][w];
+                as[j][w] = v[2][w];
+            }
+            sf[j][4] = h[0] + h[1] + h[2];
+            ss[j][4] = h[1] + h[2] + h[3];
+            if (ph == kPhOut) {
+                // output plane md.z - 1 from the sets of planes md.z - 2 (j+1), md.z - 1 (j+2), md.z (j)
+                const int P = (j + 1) % 3, Q = (j + 2) % 3;
+                const int64_t x1 = (int64_t)md.z - 1;
+                const int64_t y = (int64_t)md.x + 2 * p;
+                const int64_t xc = (int64_t)md.y + 16 * c;
+                const bool partial = x1 + md.x + md.y + (kPlaneTY - 1) + (kPlaneTX - 1) > n;
+                uint8_t *dst = out + (x1 * side + y) * side + xc;
+                uint32_t acc = 0;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    uint32_t V[5], S[4], nw[4];
+#pragma unroll
+                    for (int w = 0; w < 5; ++w)
+                        V[w] = r == 0 ? sf[P][w] + sf[Q][w] + sf[j][w] : ss[P][w] + ss[Q][w] + ss[j][w];
+                    const uint32_t lft = __shfl_up_sync(0xffffffffu, V[3], 1, 8);
+                    const uint32_t rgt = __shfl_down_sync(0xffffffffu, V[0], 1, 8);
+                    hsum4(V, c == 0 ? V[4] : lft, c == 7 ? V[4] : rgt, S);
+                    next_state4<ORK>(S, r == 0 ? af[Q] : as[Q], rule, nw);
+                    if (partial) {
+                        const int64_t c64 = n - x1 - (y + r) - xc + 1;  // cells of the chunk in the domain
+                        const int cnt = (int)(c64 < 0 ? 0 : (c64 > 16 ? 16 : c64));
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(cnt, w);
+                        if (cnt > 0) store16(dst + r * side, nw);
+                    } else {
+                        store16(dst + r * side, nw);
+                    }
+                    acc += (nw[0] + nw[1]) + (nw[2] + nw[3]);
+                }
+                lsum += (acc * 0x01010101u) >> 24;  // bytes <= 8: their sum fits the top byte
+            }
+            if (++slot == kPlSlots) {
+                slot = 0;
+                parity ^= 1u;
+            }
+        }
+        if (end) break;
+    }
+
+    if (!ok && tid == 0) {
+        atomicOr(&g_ca3p_status, 1u);
+        // the loads issued into the stages after the one that timed out must
+        // land before the CTA exits
+        for (int k = 0; k < kPlSlots; ++k) {
+            mbar_wait_bounded(&full[slot], parity, kWaitLimitNs);
+            if (++slot == kPlSlots) {
+                slot = 0;
+                parity ^= 1u;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // the last CTA out resets the work counter (every fetch of this launch is done)
+        __threadfence();
+        if (atomicAdd(&queue[1], 1ull) == (unsigned long long)gridDim.x - 1ull) {
+            queue[0] = 0;
+            queue[1] = 0;
+            __threadfence();
+        }
+    }
+    if (live) block_add_u64(live, lsum, red);
+}
+
+template <bool ORK>
+static cudaError_t prepare_planes_one()
+{
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(ca3_step_planes<ORK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlSmem);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
+    return e;
+}
+
+cudaError_t ca3_planes_prepare()
+{
+    cudaError_t e = prepare_planes_one<false>();
+    return e != cudaSuccess ? e : prepare_planes_one<true>();
+}
+
+int plane_box_widths(int *w)
+{
+    for (int i = 0; i < kPlWidths; ++i) w[i] = plane_box_width(i);
+    return kPlWidths;
+}
+
+cudaError_t launch_ca3_planes(const PlaneSched &sched, const PlaneMaps &maps, int64_t n, int64_t side, uint8_t *out,
+                              const Rule &rule, unsigned long long *live, unsigned long long *queue, cudaStream_t st)
+{
+    if (!queue) return cudaErrorInvalidValue;
+    cudaError_t e = ca3_planes_prepare();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ca3_step_planes<true>, kPlThreads, kPlSmem)) !=
+        cudaSuccess)
+        return e;
+    if (occ < 1) occ = 1;
+    const uint64_t resident = (uint64_t)sms * (uint64_t)occ;
+    const uint64_t g = sched.units < resident ? (sched.units ? sched.units : 1) : resident;
+    if (rule.or_k)
+        ca3_step_planes<true><<<(unsigned)g, kPlThreads, kPlSmem, st>>>(maps, out, n, side, rule, sched, live, queue);
+    else
+        ca3_step_planes<false><<<(unsigned)g, kPlThreads, kPlSmem, st>>>(maps, out, n, side, rule, sched, live, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t ca3p_read_status(uint32_t *out)
+{
+    uint32_t zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_ca3p_status, sizeof(uint32_t));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(g_ca3p_status, &zero, sizeof(uint32_t));
+}
+
+}  // namespace sx

@@ -45,6 +45,21 @@ cudaError_t launch_ca2_step(const Plan &p, const CUtensorMap &tin, uint8_t *out,
 cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out, const Rule &rule,
                             int kind, unsigned long long *live, unsigned long long *queue, cudaStream_t st);
 
+// m = 3 plane-stream form (launch 3, k_ca3p.cu): bricks of kPlaneTY x
+// kPlaneTX cells streamed along x1.  Each staged plane is one TMA box of 34
+// rows by one of kPlWidths widths (plane_box_widths: 48 ... 160 bytes);
+// maps.m[i] maps the input grid with box width i.  queue: two zeroed 64-bit
+// counters, left zeroed.
+constexpr int kPlWidths = 5;
+struct PlaneMaps {
+    CUtensorMap m[kPlWidths];
+};
+int plane_box_widths(int *w);  // fills kPlWidths widths in bytes, returns kPlWidths
+cudaError_t launch_ca3_planes(const PlaneSched &sched, const PlaneMaps &maps, int64_t n, int64_t side, uint8_t *out,
+                              const Rule &rule, unsigned long long *live, unsigned long long *queue, cudaStream_t st);
+cudaError_t ca3_planes_prepare();
+cudaError_t ca3p_read_status(uint32_t *out);
+
 // Sets the kernels' shared-memory limits for the current device (before any
 // stream capture).
 cudaError_t ca2_prepare(int rho);

@@ -48,7 +48,7 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm, int bo
     strides[0] = (cuuint64_t)p.side;
     if (p.m == 3) strides[1] = (cuuint64_t)(p.side * p.side);
     // the m = 3 x-stream form stages x-columns of the tile's own width
-    const bool xcols = p.m == 3 && p.persistent;
+    const bool xcols = p.m == 3 && p.persistent == 1;
     box[0] = (cuuint32_t)(xcols ? p.rho : p.rho + 32);
     box[1] = (cuuint32_t)(p.rho + 2);
     box[2] = (cuuint32_t)box_planes;
@@ -59,6 +59,32 @@ int make_tensor_map(const sx::Plan &p, const void *base, CUtensorMap *tm, int bo
                     p.m == 3 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return SIMPLEX_OK;
+}
+
+// The tensor maps of the m = 3 plane-stream form: extent n + 1 along every
+// axis, one box of 34 rows x one plane per width of plane_box_widths, no
+// swizzle (the consumers read rows at the box's own pitch).  L2 fills are
+// promoted to 128 bytes: the bricks in flight read whole rows of the
+// cross-section, so the rest of a line is read by a neighbouring brick.
+int make_plane_maps(const sx::Plan &p, const void *base, sx::PlaneMaps *maps)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (p.m != 3) return fail(SIMPLEX_EINVAL, "the plane-stream form is an m = 3 step");
+    int widths[sx::kPlWidths];
+    sx::plane_box_widths(widths);
+    cuuint64_t dims[3] = {(cuuint64_t)(p.n + 1), (cuuint64_t)(p.n + 1), (cuuint64_t)(p.n + 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)p.side, (cuuint64_t)(p.side * p.side)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    for (int i = 0; i < sx::kPlWidths; ++i) {
+        cuuint32_t box[3] = {(cuuint32_t)widths[i], (cuuint32_t)(sx::kPlaneTY + 2), 1};
+        CUresult r = fn(&maps->m[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(SIMPLEX_ECUDA, "cuTensorMapEncodeTiled failed for box width %d (CUresult %d)", widths[i], (int)r);
+    }
     return SIMPLEX_OK;
 }
 

@@ -33,7 +33,7 @@ SIMPLEX_LEVEL_CELL = 1
 
 EXPORTED = (
     "simplex_map_create", "simplex_map_create_padded", "simplex_map_create_ex", "simplex_map_destroy", "simplex_map_info",
-    "simplex_map_block", "simplex_accum", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
+    "simplex_map_block", "simplex_map_unit", "simplex_accum", "simplex_write", "simplex_ca_init", "simplex_ca_step", "simplex_ca_run",
     "simplex_ca_run_host", "simplex_visit_count", "simplex_device_status", "simplex_last_error",
     "simplex_version", "simplex_selftest_wait_timeout", "simplex_batch_create", "simplex_batch_destroy",
     "simplex_batch_info", "simplex_batch_bind", "simplex_batch_init", "simplex_batch_run", "simplex_batch_grid",
@@ -61,7 +61,8 @@ class SimplexMapInfo(ctypes.Structure):
                 ("cells", ctypes.c_uint64),
                 ("useful_blocks", ctypes.c_uint64), ("h_blocks", ctypes.c_uint64),
                 ("bb_blocks", ctypes.c_uint64), ("h_set_blocks", ctypes.c_uint64),
-                ("host_copy_bytes", ctypes.c_uint64)]
+                ("host_copy_bytes", ctypes.c_uint64), ("plane_units", ctypes.c_uint64),
+                ("plane_units_bb", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,7 +104,7 @@ class SimplexJob(ctypes.Structure):
 class SimplexJobResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("arrival_ms", ctypes.c_double),
                 ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("digest", ctypes.c_uint64),
-                ("live_final", ctypes.c_uint64)]
+                ("live_final", ctypes.c_uint64), ("seen_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,7 +116,7 @@ class SimplexServerStats(ctypes.Structure):
                 ("wall_ms", ctypes.c_double), ("mean_active", ctypes.c_double), ("p50_ms", ctypes.c_double),
                 ("p90_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("host_issue_ms", ctypes.c_double), ("gpu_round_ms", ctypes.c_double),
-                ("launches", ctypes.c_uint64)]
+                ("launches", ctypes.c_uint64), ("host_p50_ms", ctypes.c_double), ("host_p99_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -134,6 +135,7 @@ _sig("simplex_map_create_ex", [ctypes.POINTER(SimplexMapParams), ctypes.POINTER(
 _sig("simplex_map_destroy", [_vp])
 _sig("simplex_map_info", [_vp, ctypes.POINTER(SimplexMapInfo)])
 _sig("simplex_map_block", [_vp, _i32, _u64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i32)])
+_sig("simplex_map_unit", [_vp, _i32, _u64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_i32)])
 _sig("simplex_write", [_vp, _vp, _u32, _i32, _vp])
 _sig("simplex_accum", [_vp, _vp, _u32, _i32, _vp])
 _sig("simplex_ca_init", [_vp, _vp, _u32, _u32, _vp, _vp])
@@ -245,7 +247,8 @@ def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, 
 
     band (m = 2): None/0 automatic trapezoid bands, > 0 band height, -1 the
     single grid of Eq. map2d.  launch: 0 automatic, 1 grid, 2 x-stream
-    (persistent) automaton step for m = 3, block 32.  layout (m = 3, beta = 2): 0 packed grid, 1 one block
+    (persistent) automaton step for m = 3, block 32, 3 plane stream (m = 3,
+    persistent CTAs streaming bricks along x1).  layout (m = 3, beta = 2): 0 packed grid, 1 one block
     range per stack level."""
     if beta is None:
         beta = 2 if m <= 3 else m
@@ -275,6 +278,14 @@ def simplex_map_block(mp: SimplexMap, mode: int, v: int):
     valid = _i32()
     _check(_lib.simplex_map_block(mp.handle, mode, v, coord, ctypes.byref(valid)), "simplex_map_block")
     return tuple(coord[: mp.m]), bool(valid.value)
+
+
+def simplex_map_unit(mp: SimplexMap, mode: int, w: int):
+    """Host evaluation of plane-stream work unit w: ((y0, x0, first plane, last plane), valid)."""
+    unit = (ctypes.c_int32 * 4)()
+    valid = _i32()
+    _check(_lib.simplex_map_unit(mp.handle, mode, w, unit, ctypes.byref(valid)), "simplex_map_unit")
+    return tuple(unit), bool(valid.value)
 
 
 def simplex_write(mp: SimplexMap, out: torch.Tensor, seed: int, mode: int = SIMPLEX_MODE_H):

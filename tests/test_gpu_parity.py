@@ -206,14 +206,15 @@ def test_write_h2_forms_match_oracle(band):
     np.testing.assert_array_equal(out.view(mp.shape).cpu().numpy().view(np.uint32), oracle.write(2, 1023, 77))
 
 
-@pytest.mark.parametrize("launch", [1, 2])
+@pytest.mark.parametrize("launch", [1, 2, 3])
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n,side,beta", [(255, None, 2), (200, 208, 2), (255, None, 3), (31, 32, 2), (1, 16, 2),
                                          (527, 528, 2), (600, 608, 2)])
 def test_ca3_grid_and_persistent_forms_match_oracle(launch, mode, n, side, beta):
-    """The m = 3 step in both launch forms (one CTA per block of the map, and
+    """The m = 3 step in its three launch forms (one CTA per block of the map;
     the x-stream form: persistent CTAs streaming runs of tiles along x3
-    through a ring of x-columns) gives the oracle's grid."""
+    through a ring of x-columns; the plane-stream form: persistent CTAs
+    streaming 32 x 128 bricks along x1) gives the oracle's grid."""
     mp = sx.simplex_map_create(3, n, 2, beta, 32, side=side, launch=launch)
     assert mp.info.launch == launch
     thr = inputs.bernoulli_threshold(0.3)
@@ -223,6 +224,54 @@ def test_ca3_grid_and_persistent_forms_match_oracle(launch, mode, n, side, beta)
     np.testing.assert_array_equal(got, ref)
     assert not rest.any()
     np.testing.assert_array_equal(live, ref_live)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,side,block,steps,rule,p", [
+    (0, 16, 16, 3, inputs.B5S45, 0.5),
+    (1, 16, 32, 3, (1, 1), 0.5),                      # birth on 0: every dead domain cell is born
+    (31, 32, 32, 6, inputs.B5S45, 0.5),
+    (127, None, 32, 6, (1 << 4, 1 << 5 | 1 << 6 | 1 << 7), 0.3),   # B4/S567: the general rule tables
+    (128, 144, 16, 5, inputs.B5S45, 0.3),
+    (160, 176, 32, 4, (0x7FFFFFF, 0x7FFFFFF), 0.2),   # every count turns a cell on
+    (300, 304, 32, 5, inputs.B5S45, 0.3),
+    (700, 704, 32, 2, (1 << 5 | 1 << 6, 1 << 4 | 1 << 5), 0.3),
+])
+def test_ca3_plane_stream_sizes_and_rules(mode, n, side, block, steps, rule, p):
+    """The plane-stream step (launch 3) against the oracle on ragged and padded
+    sides (n + 1 not a multiple of the 32 x 128 brick), degenerate sizes, both
+    rule paths (or-k and the general tables) and rules that light cells next
+    to the domain's faces."""
+    mp = sx.simplex_map_create(3, n, 2, 2, block, side=side, launch=3)
+    assert mp.info.launch == 3
+    thr = inputs.bernoulli_threshold(p)
+    fin, live = _gpu_run(mp, n, steps, rule, 29, thr, mode)
+    got, rest = _logical(fin, mp, n)
+    ref, ref_live = oracle.ca_run(3, n, steps, rule[0], rule[1], oracle.ca_init(3, n, 29, thr))
+    np.testing.assert_array_equal(got, ref)
+    assert not rest.any()
+    np.testing.assert_array_equal(live, ref_live)
+
+
+def test_ca3_plane_stream_single_steps_reuse_the_counter():
+    """Consecutive simplex_ca_step calls (no graph) on one map share its work
+    counter: each launch must leave it at zero for the next."""
+    n = 255
+    mp = sx.simplex_map_create(3, n, 2, 2, 32, launch=3)
+    thr = inputs.bernoulli_threshold(0.3)
+    a = torch.zeros(mp.numel, dtype=torch.uint8, device=DEV)
+    b = torch.zeros_like(a)
+    sx.simplex_ca_init(mp, a, 3, thr)
+    ref = oracle.ca_init(3, n, 3, thr)
+    for i in range(5):
+        live = torch.zeros(1, dtype=torch.int64, device=DEV)
+        mode = MODES[i % 3]
+        sx.simplex_ca_step(mp, a, b, *inputs.B5S45, live, mode)
+        ref, ref_live = oracle.ca_step(3, n, *inputs.B5S45, ref)
+        got, _ = _logical(b, mp, n)
+        np.testing.assert_array_equal(got, ref)
+        assert int(live.item()) == ref_live
+        a, b = b, a
 
 
 def test_ca_step_by_step_equals_graph_run():
@@ -352,6 +401,23 @@ def test_ca_m3_full_size_steps_match_oracle():
     assert live_h[-1] > 0
 
 
+def test_ca_m3_full_size_matches_oracle():
+    """The m = 3 automaton at the benchmark's size and length (n = 1023, 50
+    steps, B5/S45, Bernoulli(0.3)) in the launch form the benchmark times (the
+    plane stream): the final grid and all 51 live counts equal the oracle's
+    whole run."""
+    w = inputs.CA_M3
+    mp = sx.simplex_map_create(w.m, w.n, 2, 2, w.block, launch=3)
+    fin, live = _gpu_run(mp, w.n, w.steps, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+    got = fin.view(mp.shape).cpu().numpy()
+    del fin
+    ref, ref_live = oracle.ca_run(w.m, w.n, w.steps, w.rule[0], w.rule[1],
+                                  oracle.ca_init(w.m, w.n, w.seed, w.threshold))
+    assert len(ref_live) == w.steps + 1
+    np.testing.assert_array_equal(live, ref_live)
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_ca_m3_full_size_x_stream_equals_grid_form():
     """The x-stream form (launch 2, the faster m = 3 step) at n = 1023 over the
     workload's 50 steps gives the grid form's grids and live counts bit for
@@ -365,6 +431,14 @@ def test_ca_m3_full_size_x_stream_equals_grid_form():
     assert torch.equal(fin_g, fin_x)
     np.testing.assert_array_equal(live_g, live_x)
     assert live_x[-1] > 0
+    del fin_x
+    # the bounding-box modes of the plane stream
+    mp = sx.simplex_map_create(w.m, w.n, 2, 2, w.block, launch=3)
+    for mode in (sx.SIMPLEX_MODE_BB, sx.SIMPLEX_MODE_BB_THREAD):
+        fin_p, live_p = _gpu_run(mp, w.n, 4, w.rule, w.seed, w.threshold, mode)
+        fin_g4, live_g4 = _gpu_run(mg, w.n, 4, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+        assert torch.equal(fin_p, fin_g4)
+        np.testing.assert_array_equal(live_p, live_g4)
 
 
 def test_ca_m2_full_size_matches_oracle():
@@ -454,23 +528,29 @@ def test_ca_m3_past_2_32_offsets_matches_oracle():
     """The same limit for m = 3: n = 1700 on side 1712 (5.0 GB grids, offsets
     and row-major indices past 2^32; tile columns N = 64).  The initial state
     and one step of the grid form equal the oracle's whole grids with the
-    padding zero; the x-stream form's step equals the grid form's."""
+    padding zero; the x-stream and plane-stream forms' steps equal the grid
+    form's."""
     n, side, w = 1700, 1712, inputs.CA_M3
     assert (n + 1) ** 3 > 1 << 32 and side ** 3 > 1 << 32
     mg = sx.simplex_map_create(3, n, 2, 2, 32, side=side, launch=1)
     mx = sx.simplex_map_create(3, n, 2, 2, 32, side=side, launch=2)
+    mq = sx.simplex_map_create(3, n, 2, 2, 32, side=side, launch=3)
     a = torch.zeros(mg.numel, dtype=torch.uint8, device=DEV)
     b = torch.zeros_like(a)
     c = torch.zeros_like(a)
-    live = torch.zeros(3, dtype=torch.int64, device=DEV)
+    live = torch.zeros(4, dtype=torch.int64, device=DEV)
     sx.simplex_ca_init(mg, a, w.seed, w.threshold, live[0:1])
     sx.simplex_ca_step(mg, a, b, w.rule[0], w.rule[1], live[1:2])
     sx.simplex_ca_step(mx, a, c, w.rule[0], w.rule[1], live[2:3])
     torch.cuda.synchronize()
     assert torch.equal(b, c)
+    c.zero_()
+    sx.simplex_ca_step(mq, a, c, w.rule[0], w.rule[1], live[3:4])
+    torch.cuda.synchronize()
+    assert torch.equal(b, c)
     del c
     live = live.cpu().tolist()
-    assert live[1] == live[2]
+    assert live[1] == live[2] == live[3]
 
     def same(t, ref):
         g = t.view(side, side, side)

@@ -250,6 +250,68 @@ def test_launch_form_choice():
     with pytest.raises(sx.SimplexError) as ei:
         sx.simplex_map_create(2, 1023, 2, 2, 128, launch=2)
     assert ei.value.code == sx.SIMPLEX_EUNSUPPORTED
+    assert sx.simplex_map_info(sx.simplex_map_create(3, 1023, 2, 2, 32, launch=3))["launch"] == 3
+    assert sx.simplex_map_info(sx.simplex_map_create(3, 200, 2, 2, 16, side=208, launch=3))["launch"] == 3
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_map_create(2, 1023, 2, 2, 128, launch=3)
+    assert ei.value.code == sx.SIMPLEX_EUNSUPPORTED
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_map_unit(sx.simplex_map_create(3, 63, 2, 2, 32), sx.SIMPLEX_MODE_H, 0)
+    assert ei.value.code == sx.SIMPLEX_EINVAL
+
+
+# ---------------------------------------------------------------- plane-stream work units (launch 3)
+def _plane_units(mp, mode):
+    info = mp.info
+    total = info.plane_units if mode == sx.SIMPLEX_MODE_H else info.plane_units_bb
+    out = []
+    for w in range(total):
+        u, ok = sx.simplex_map_unit(mp, mode, w)
+        out.append((u, ok))
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_unit(mp, mode, total)
+    return out
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 32, 127, 128, 200, 255, 300, 527, 1023])
+def test_plane_units_cover_each_brick_plane_exactly_once(n):
+    """Every plane x1 of every 32 x 128 brick that holds a domain cell on that
+    plane (32 Y + 128 X <= n - x1) is written by exactly one unit of a step in
+    mode H, and by exactly one valid unit in mode BB; mode BB_THREAD runs every
+    brick of the square on every plane once.  Units are numbered slab by slab
+    and slabs shrink towards the apex."""
+    mp = sx.simplex_map_create(3, n, 2, 2, 32, side=((n + 16) // 16) * 16, launch=3)
+    ty, tx = 32, 128
+    nY, nX = (n + ty) // ty, (n + tx) // tx
+    want = np.zeros((n + 1, nY, nX), dtype=np.int64)
+    for x1 in range(n + 1):
+        for Y in range(nY):
+            for X in range(nX):
+                want[x1, Y, X] = 1 if ty * Y + tx * X <= n - x1 else 0
+    for mode in (sx.SIMPLEX_MODE_H, sx.SIMPLEX_MODE_BB, sx.SIMPLEX_MODE_BB_THREAD):
+        got = np.zeros_like(want)
+        last_b = -1
+        for (y0, x0, b, e), ok in _plane_units(mp, mode):
+            assert y0 % ty == 0 and x0 % tx == 0 and 0 <= b
+            assert b >= last_b  # slab by slab
+            last_b = b
+            if mode == sx.SIMPLEX_MODE_H:
+                assert ok
+            if not ok:
+                assert y0 + x0 > n - b
+                continue
+            assert b <= e <= n
+            assert e - b + 1 <= 64
+            got[b:e + 1, y0 // ty, x0 // tx] += 1
+        if mode == sx.SIMPLEX_MODE_BB_THREAD:
+            np.testing.assert_array_equal(got, np.ones_like(want))
+        else:
+            np.testing.assert_array_equal(got, want)
+    if n == 1023:
+        # slab lengths: 2^floor(log2((n + 1 - b) / 32)) clamped to [4, 64]
+        starts = sorted({u[2] for u, _ in _plane_units(mp, sx.SIMPLEX_MODE_H)})
+        lens = np.diff(starts + [n + 1])
+        assert lens[0] == 32 and lens[-1] == 4 and all(np.diff(lens) <= 0)
 
 
 # ---------------------------------------------------------------- fully efficient H3 (layout 1)
@@ -355,7 +417,8 @@ sys.path.insert(0, sys.argv[1])
 from paper_2208_11617_gb300 import simplex as sx
 L, N = sx._lib, None
 calls = {
-    "simplex_map_info": (N, N), "simplex_map_block": (N, 0, 0, N, N), "simplex_write": (N, N, 0, 0, N),
+    "simplex_map_info": (N, N), "simplex_map_block": (N, 0, 0, N, N), "simplex_map_unit": (N, 0, 0, N, N),
+    "simplex_write": (N, N, 0, 0, N),
     "simplex_accum": (N, N, 0, 0, N), "simplex_ca_init": (N, N, 0, 0, N, N),
     "simplex_ca_step": (N, N, N, 0, 0, N, 0, N), "simplex_ca_run": (N, N, N, 1, 0, 0, N, 1, 0, N),
     "simplex_ca_run_host": (N, N, N, N, N, 1, 0, 0, N, N, 1, 0, N), "simplex_visit_count": (N, N, 0, 0, N),
