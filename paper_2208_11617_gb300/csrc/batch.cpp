@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -48,6 +49,7 @@ struct simplex_batch {
     int parity = 0;
     cudaStream_t capture = nullptr;
     std::vector<RunGraph> graphs;
+    uint64_t serial = 0;  // unique per batch created in this process (never reused)
 };
 
 namespace {
@@ -116,6 +118,7 @@ int batch_view(simplex_batch_t b, BatchView *out)
     out->nitems0 = b->nitems0;
     out->grids_offset = b->off_grids;
     out->grids_bytes = b->bytes - b->off_grids;
+    out->serial = b->serial;
     return SIMPLEX_OK;
 }
 
@@ -232,6 +235,8 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         bi.grid[1] += off;
     }
     b->bytes = off + grid_off;
+    static std::atomic<uint64_t> next_serial{0};
+    b->serial = ++next_serial;
     *out = b;
     return SIMPLEX_OK;
 }

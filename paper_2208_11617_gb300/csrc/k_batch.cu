@@ -368,23 +368,26 @@ constexpr uint64_t kStaticScratchBytes = 8ull << 20;  // 8 MiB
 static __device__ __align__(256) uint8_t g_batch_static_scratch[kStaticScratchBytes];
 
 // Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
-static cudaError_t static_scratch_address(uint8_t **out)
+// per device (cudaGetSymbolAddress with that device current), and what the
+// array holds there: the batch (its serial) and grids whose descriptors, work
+// items and tensor maps the last complete upload put in.  Guarded by
+// g_static_mu, which a call holds while it fills the array and enqueues its
+// work.
+static std::mutex g_static_mu;
+static uint8_t *g_static_addr[64] = {};
+static uint64_t g_static_serial[64] = {};
+static const uint8_t *g_static_grids[64] = {};
+
+static cudaError_t static_scratch_address(int dev, uint8_t **out)
 {
-    static std::mutex mu;
-    static uint8_t *addr[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!g_static_addr[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_batch_static_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_batch_static_scratch);
         if (e != cudaSuccess) return e;
-        addr[dev] = static_cast<uint8_t *>(p);
+        g_static_addr[dev] = static_cast<uint8_t *>(p);
     }
-    *out = addr[dev];
+    *out = g_static_addr[dev];
     return cudaSuccess;
 }
 
@@ -416,8 +419,12 @@ extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, u
                     "batch too large for the fixed scratch: needs %llu bytes of descriptors, work items and "
                     "queue counters, the limit is %llu (use simplex_batch_bind / simplex_batch_run)",
                     (unsigned long long)need, (unsigned long long)sx::kStaticScratchBytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(sx::g_static_mu);
     uint8_t *scratch = nullptr;
-    cudaError_t e = sx::static_scratch_address(&scratch);
+    e = sx::static_scratch_address(dev, &scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static batch scratch)");
     // the grid offsets of the descriptors count from the arena start; the
     // caller's buffer starts at the grids, so shift the base accordingly
@@ -425,26 +432,39 @@ extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, u
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((e = sx::batch_prepare()) != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared memory");
     unsigned int *queue = reinterpret_cast<unsigned int *>(scratch + off_queue);
-    if ((e = cudaMemcpyAsync(scratch, bv.insts, sizeof(sx::BatchInst) * bv.count, cudaMemcpyHostToDevice, st)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(scratch + off_items, bv.items, sizeof(sx::BatchItem) * bv.nitems,
-                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * 2 * (size_t)(steps + 1), st)) != cudaSuccess)
-        return cuda_fail(e, "filling the static batch scratch");
-    // TMA maps of the caller's grids, encoded in a fixed host buffer and copied
-    // in pieces (a copy from pageable memory has read its source on return)
-    CUtensorMap piece[32];
-    for (size_t k0 = 0; k0 < 2 * bv.count; k0 += 32) {
-        const size_t k1 = k0 + 32 < 2 * bv.count ? k0 + 32 : 2 * bv.count;
-        for (size_t k = k0; k < k1; ++k) {
-            rc = make_tensor_map(bv.insts[k / 2].plan, base + bv.insts[k / 2].grid[k % 2], &piece[k - k0],
-                                 bv.insts[k / 2].plan.rho + 2);
-            if (rc) return rc;
-        }
-        if ((e = cudaMemcpyAsync(scratch + off_tmaps + sizeof(CUtensorMap) * k0, piece,
-                                 sizeof(CUtensorMap) * (k1 - k0), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    // descriptors, work items and tensor maps depend only on the batch and the
+    // grids' address: when the array already holds them (the last complete
+    // upload on this device was for the same batch and grids), only the queue
+    // counters are reset
+    const bool fresh = !(sx::g_static_serial[dev] == bv.serial && sx::g_static_grids[dev] == grids);
+    if (fresh) {
+        sx::g_static_serial[dev] = 0;  // the array is about to change
+        sx::g_static_grids[dev] = nullptr;
+        if ((e = cudaMemcpyAsync(scratch, bv.insts, sizeof(sx::BatchInst) * bv.count, cudaMemcpyHostToDevice,
+                                 st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(scratch + off_items, bv.items, sizeof(sx::BatchItem) * bv.nitems,
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_fail(e, "filling the static batch scratch");
+        // TMA maps of the caller's grids, encoded in a fixed host buffer and
+        // copied in pieces (a copy from pageable memory has read its source on
+        // return)
+        CUtensorMap piece[32];
+        for (size_t k0 = 0; k0 < 2 * bv.count; k0 += 32) {
+            const size_t k1 = k0 + 32 < 2 * bv.count ? k0 + 32 : 2 * bv.count;
+            for (size_t k = k0; k < k1; ++k) {
+                rc = make_tensor_map(bv.insts[k / 2].plan, base + bv.insts[k / 2].grid[k % 2], &piece[k - k0],
+                                     bv.insts[k / 2].plan.rho + 2);
+                if (rc) return rc;
+            }
+            if ((e = cudaMemcpyAsync(scratch + off_tmaps + sizeof(CUtensorMap) * k0, piece,
+                                     sizeof(CUtensorMap) * (k1 - k0), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "filling the static batch scratch");
+        }
+        sx::g_static_serial[dev] = bv.serial;
+        sx::g_static_grids[dev] = grids;
     }
+    if ((e = cudaMemsetAsync(queue, 0, sizeof(unsigned int) * 2 * (size_t)(steps + 1), st)) != cudaSuccess)
+        return cuda_fail(e, "resetting the static batch queue counters");
     const sx::BatchInst *insts = reinterpret_cast<const sx::BatchInst *>(scratch);
     const sx::BatchItem *items = reinterpret_cast<const sx::BatchItem *>(scratch + off_items);
     const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(scratch + off_tmaps);

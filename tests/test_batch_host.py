@@ -111,3 +111,21 @@ def test_serve_trace_generator():
     assert [d["seed"] for d in jobs] == list(range(k))
     again, t2 = inputs.serve_trace(rate=rate, seconds=secs)
     assert again == jobs and (t2 == t).all()        # seeded
+
+
+def test_static_run_checks_arguments_before_any_device_work():
+    """simplex_batch_run_static rejects a NULL or unaligned grids pointer, a
+    grids buffer smaller than the batch's grids, a parity other than 0 or 1
+    and a step count outside 1 ... 4096 with SIMPLEX_EINVAL before it makes any
+    CUDA call (the addresses below are never dereferenced)."""
+    import ctypes
+    b = sx.simplex_batch_create([_inst(2, 100, 64), _inst(3, 63, 16)])
+    need = sx.simplex_batch_info(b)["grids_bytes"]
+    fake = 1 << 40  # 256-byte aligned, never touched
+    cases = [(None, need, 0, 3, "NULL"), (fake + 16, need, 0, 3, "256-byte aligned"),
+             (fake, need - 1, 0, 3, "too small"), (fake, need, 2, 3, "parity"), (fake, need, 0, 0, "steps"),
+             (fake, need, 0, 4097, "steps")]
+    for ptr, nbytes, parity, steps, what in cases:
+        rc = sx._lib.simplex_batch_run_static(b.handle, ctypes.c_void_p(ptr) if ptr else None, nbytes, parity,
+                                              steps, None, None)
+        assert rc == sx.SIMPLEX_EINVAL and what in sx.simplex_last_error(), (ptr, nbytes, parity, steps)
