@@ -57,6 +57,7 @@ enum JobStatus : int32_t { kPending = 0, kActive = 1, kDone = 2, kRejected = 3 }
 struct ServerJob {
     simplex_job_t spec;
     double arrival_ms = 0, admit_ms = 0, done_ms = 0;
+    double seen_ms = 0;  // host time at which the serving loop found the job complete
     int32_t status = kPending;
     int slot = -1;
     uint64_t off = 0, bytes = 0;
@@ -507,6 +508,7 @@ void finish_job(simplex_server *s, int64_t j, float done_ms)
     job.live.assign(s->host_live + job.slot * row, s->host_live + job.slot * row + job.spec.steps + 1);
     job.digest = s->host_digest[job.slot];
     job.done_ms = done_ms;
+    job.seen_ms = host_ms(s);
     job.status = kDone;
     job.busy = false;
     s->pool.release(job.off, job.bytes);
@@ -891,6 +893,7 @@ int simplex_server_result(simplex_server_t s, int64_t job, simplex_job_result_t 
     out->arrival_ms = j.arrival_ms;
     out->admit_ms = j.admit_ms;
     out->done_ms = j.done_ms;
+    out->seen_ms = j.seen_ms;
     out->digest = j.digest;
     out->live_final = j.live.empty() ? 0 : j.live.back();
     if (live && !j.live.empty()) std::memcpy(live, j.live.data(), sizeof(unsigned long long) * j.live.size());
@@ -902,10 +905,14 @@ int simplex_server_stats(simplex_server_t s, simplex_server_stats_t *out)
     if (!s) return fail(SIMPLEX_EINVAL, "server is NULL");
     if (!out) return fail(SIMPLEX_EINVAL, "out is NULL");
     std::memset(out, 0, sizeof *out);
-    std::vector<double> lat;
+    std::vector<double> lat, seen;
     for (const auto &j : s->jobs)
-        if (j.status == kDone) lat.push_back(j.done_ms - j.arrival_ms);
-        else if (j.status == kRejected) out->rejected += 1;
+        if (j.status == kDone) {
+            lat.push_back(j.done_ms - j.arrival_ms);
+            seen.push_back(j.seen_ms - j.arrival_ms);
+        } else if (j.status == kRejected) {
+            out->rejected += 1;
+        }
     out->submitted = s->jobs.size();
     out->completed = lat.size();
     out->rounds = s->rounds;
@@ -926,6 +933,12 @@ int simplex_server_stats(simplex_server_t s, simplex_server_stats_t *out)
         double sum = 0;
         for (double x : lat) sum += x;
         out->mean_ms = sum / (double)lat.size();
+        std::sort(seen.begin(), seen.end());
+        auto qs = [&](double f) {
+            return seen[std::min(seen.size() - 1, (size_t)(f * (double)(seen.size() - 1) + 0.5))];
+        };
+        out->host_p50_ms = qs(0.50);
+        out->host_p99_ms = qs(0.99);
     }
     return SIMPLEX_OK;
 }
