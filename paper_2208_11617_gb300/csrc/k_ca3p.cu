@@ -50,12 +50,13 @@ static __device__ uint32_t g_ca3p_status;
 
 constexpr int kPlSlots = 10;
 constexpr int kPlCtasPerSm = 4;
-constexpr int kPlThreads = (kPlaneTX / 16) * (kPlaneTY / 2);  // 8 chunks x 16 row pairs
+constexpr int kPlConsumerWarps = (kPlaneTX / 16) * (kPlaneTY / 2) / 32;  // 8 chunks x 16 row pairs
+constexpr int kPlThreads = 32 * (kPlConsumerWarps + 1);                  // plus the producer warp
 constexpr int kPlRows = kPlaneTY + 2;
 constexpr int kPlMaxW = kPlaneTX + 32;
 constexpr uint32_t kPlSlotBytes = ((uint32_t)(kPlRows * kPlMaxW) + 127u) / 128u * 128u;
 constexpr int kPlSmem = kPlSlots * (int)kPlSlotBytes + 128;
-static_assert(kPlThreads == 128, "the thread layout assumes 8 chunks x 16 row pairs");
+static_assert(kPlConsumerWarps == 4, "the thread layout assumes 8 chunks x 16 row pairs");
 static_assert(kPlMaxW == 160 && kPlaneTY == 32, "the halo-word offsets assume 160-byte rows");
 static_assert(kPlCtasPerSm * (kPlSmem + 2048) <= 228 * 1024, "the ring of four CTAs exceeds an SM's shared memory");
 
@@ -71,179 +72,202 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                     unsigned long long *__restrict__ live, unsigned long long *__restrict__ queue)
 {
     extern __shared__ uint8_t dsmem[];
-    __shared__ __align__(8) uint64_t full[kPlSlots];
+    __shared__ __align__(8) uint64_t full[kPlSlots], empty[kPlSlots];
     __shared__ int4 meta[kPlSlots];  // y0, x0, staged plane, width | phase << 8
     __shared__ uint32_t red[32];
+    __shared__ volatile int abort_flag;
     uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
-    const int tid = threadIdx.x, c = tid & 7, p = tid >> 3;
-
-    // producer state (thread 0)
-    unsigned long long next_w = 0;
-    int32_t py0 = 0, px0 = 0, pb = 0, pe = -1, px1 = 0;
-    bool have = false, done = false;
-    auto produce = [&](int s) {
-        int4 md = make_int4(0, 0, 0, kPhEnd << 8);
-        while (!done) {
-            if (!have) {
-                const unsigned long long w = next_w;
-                if (w >= sched.units) {
-                    done = true;
-                    break;
-                }
-                next_w = atomicAdd(queue, 1ull);
-                PlaneUnit u;
-                if (!plane_unit_decode(sched, w, u)) continue;
-                py0 = u.y0;
-                px0 = u.x0;
-                pb = u.b;
-                pe = u.e;
-                px1 = pb - 1;
-                have = true;
-            }
-            const int ph = px1 == pb - 1 ? kPhFirst : (px1 == pb ? kPhSecond : kPhOut);
-            // bytes of the box that can hold domain cells: from x0 - 16 up to
-            // n - x1 - (y0 - 1) inclusive
-            const int64_t need = (n - px1 - py0 + 2) - (int64_t)(px0 - 16);
-            int wi = -1;
-            if (px1 >= 0 && px1 <= n && sched.kind == kMapBBThread) {
-                wi = kPlWidths - 1;  // the paper's bounding box: every brick staged in full
-            } else if (px1 >= 0 && px1 <= n && need > 16) {
-                wi = 0;
-                while (wi < kPlWidths - 1 && (int64_t)plane_box_width(wi) < need) ++wi;
-            }
-            const int W = wi < 0 ? 0 : plane_box_width(wi);
-            md = make_int4(py0, px0, px1, W | (ph << 8));
-            meta[s] = md;
-            if (wi < 0) {
-                mbar_arrive(&full[s]);  // nothing to load: the phase completes with no bytes
-            } else {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&full[s], (uint32_t)(kPlRows * W));
-                tma_load_3d(ring + s * kPlSlotBytes, &maps.m[wi], px0 - 16, py0 - 1, px1, &full[s]);
-            }
-            if (++px1 > pe + 1) have = false;
-            return;
-        }
-        meta[s] = md;
-        mbar_arrive(&full[s]);
-    };
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint32_t lsum = 0;
+    uint64_t issued = 0;  // producer: stages filled (loads and markers)
 
     if (tid == 0) {
         for (int i = 0; i < kPlWidths; ++i) prefetch_tmap(&maps.m[i]);
-        for (int s = 0; s < kPlSlots; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < kPlSlots; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kPlConsumerWarps);
+        }
         fence_mbar_init();
-        next_w = atomicAdd(queue, 1ull);
+        abort_flag = 0;
     }
     __syncthreads();
-    if (tid == 0)
-        for (int s = 0; s < kPlSlots; ++s) produce(s);
 
-    // column sums of the three newest staged planes (rotating): words 0..3 of
-    // row 2p (f) and of row 2p + 1 (s), [4] the halo word; and the centre rows
-    uint32_t sf[3][5], ss[3][5], af[3][4], as[3][4];
-    uint32_t lsum = 0;
-    int slot = 0;
-    uint32_t parity = 0;
-    bool ok = true;
-    for (;;) {
-        bool end = false;
+    if (warp == kPlConsumerWarps) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            unsigned long long next_w = atomicAdd(queue, 1ull);
+            int32_t py0 = 0, px0 = 0, pb = 0, pe = -1, px1 = 0;
+            bool have = false;
+            for (uint64_t k = 0;; ++k) {
+                const int s = (int)(k % kPlSlots);
+                if (k >= (uint64_t)kPlSlots &&
+                    !mbar_wait_bounded(&empty[s], (uint32_t)((k / kPlSlots - 1) & 1), kWaitLimitNs)) {
+                    abort_flag = 1;
+                    break;
+                }
+                while (!have) {
+                    const unsigned long long w = next_w;
+                    if (w >= sched.units) break;
+                    next_w = atomicAdd(queue, 1ull);
+                    PlaneUnit u;
+                    if (!plane_unit_decode(sched, w, u)) continue;
+                    py0 = u.y0;
+                    px0 = u.x0;
+                    pb = u.b;
+                    pe = u.e;
+                    px1 = pb - 1;
+                    have = true;
+                }
+                if (!have) {  // no more work: one end marker
+                    meta[s] = make_int4(0, 0, 0, kPhEnd << 8);
+                    mbar_arrive(&full[s]);
+                    issued = k + 1;
+                    break;
+                }
+                const int ph = px1 == pb - 1 ? kPhFirst : (px1 == pb ? kPhSecond : kPhOut);
+                // bytes of the box that can hold domain cells: from x0 - 16 up to
+                // n - x1 - (y0 - 1) inclusive
+                const int64_t need = (n - px1 - py0 + 2) - (int64_t)(px0 - 16);
+                int wi = -1;
+                if (px1 >= 0 && px1 <= n && sched.kind == kMapBBThread) {
+                    wi = kPlWidths - 1;  // the paper's bounding box: every brick staged in full
+                } else if (px1 >= 0 && px1 <= n && need > 16) {
+                    wi = 0;
+                    while (wi < kPlWidths - 1 && (int64_t)plane_box_width(wi) < need) ++wi;
+                }
+                const int W = wi < 0 ? 0 : plane_box_width(wi);
+                meta[s] = make_int4(py0, px0, px1, W | (ph << 8));
+                if (wi < 0) {
+                    mbar_arrive(&full[s]);  // nothing to load: the phase completes with no bytes
+                } else {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)(kPlRows * W));
+                    tma_load_3d(ring + s * kPlSlotBytes, &maps.m[wi], px0 - 16, py0 - 1, px1, &full[s]);
+                }
+                issued = k + 1;
+                if (++px1 > pe + 1) have = false;
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- consumers
+        const int c = tid & 7, p = tid >> 3;
+        // column sums of the three newest staged planes (rotating): words 0..3
+        // of row 2p (f) and of row 2p + 1 (s), [4] the halo word; and the
+        // centre rows (the cells' own states)
+        uint32_t sf[3][5], ss[3][5], af[3][4], as[3][4];
+        int slot = 0;
+        uint32_t parity = 0;
+        const int ho = c == 0 ? 12 : 16 + kPlaneTX;  // this lane's halo word (left or right of the brick)
+        for (;;) {
+            bool stop = false;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            ok = mbar_wait_bounded(&full[slot], parity, kWaitLimitNs);
-            const int4 md = meta[slot];
-            const int W = md.w & 255, ph = (md.w >> 8) & 3;
-            uint32_t v[4][4], h[4];
-            {
+            for (int j = 0; j < 3; ++j) {
+                if (!mbar_try_wait(&full[slot], parity) &&
+                    (abort_flag || !mbar_wait_bounded(&full[slot], parity, kWaitLimitNs))) {
+                    abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                const int4 md = meta[slot];
+                const int W = md.w & 255, ph = md.w >> 8;
+                if (ph == kPhEnd) {
+                    stop = true;
+                    break;
+                }
+                uint32_t v[4][4], h[4];
                 const uint8_t *base = ring + slot * kPlSlotBytes + 2 * p * W;
-                const bool has_c = 16 * c + 32 <= W;
-                const bool has_h = (c == 0 && W > 0) || (c == 7 && W == kPlMaxW);
-                const int ho = c == 0 ? 12 : 16 + kPlaneTX;
+                if (W == kPlMaxW) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    uint4 q = make_uint4(0u, 0u, 0u, 0u);
-                    if (ok && ph != kPhEnd && has_c) q = *reinterpret_cast<const uint4 *>(base + k * W + 16 + 16 * c);
-                    v[k][0] = q.x;
-                    v[k][1] = q.y;
-                    v[k][2] = q.z;
-                    v[k][3] = q.w;
-                    h[k] = (ok && ph != kPhEnd && has_h) ? *reinterpret_cast<const uint32_t *>(base + k * W + ho) : 0u;
-                }
-            }
-            // every thread is done with the stage (and with the meta word)
-            if (__syncthreads_or(!ok)) {
-                ok = false;
-                end = true;
-                break;
-            }
-            if (ph == kPhEnd) {
-                end = true;
-                break;
-            }
-            if (tid == 0) produce(slot);
-            // sums of this plane into set j
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                sf[j][w] = v[0][w] + v[1][w] + v[2][w];
-                ss[j][w] = v[1][w] + v[2][w] + v[3][w];
-                af[j][w] = v[1][w];
-                as[j][w] = v[2][w];
-            }
-            sf[j][4] = h[0] + h[1] + h[2];
-            ss[j][4] = h[1] + h[2] + h[3];
-            if (ph == kPhOut) {
-                // output plane md.z - 1 from the sets of planes md.z - 2 (j+1), md.z - 1 (j+2), md.z (j)
-                const int P = (j + 1) % 3, Q = (j + 2) % 3;
-                const int64_t x1 = (int64_t)md.z - 1;
-                const int64_t y = (int64_t)md.x + 2 * p;
-                const int64_t xc = (int64_t)md.y + 16 * c;
-                const bool partial = x1 + md.x + md.y + (kPlaneTY - 1) + (kPlaneTX - 1) > n;
-                uint8_t *dst = out + (x1 * side + y) * side + xc;
-                uint32_t acc = 0;
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    uint32_t V[5], S[4], nw[4];
-#pragma unroll
-                    for (int w = 0; w < 5; ++w)
-                        V[w] = r == 0 ? sf[P][w] + sf[Q][w] + sf[j][w] : ss[P][w] + ss[Q][w] + ss[j][w];
-                    const uint32_t lft = __shfl_up_sync(0xffffffffu, V[3], 1, 8);
-                    const uint32_t rgt = __shfl_down_sync(0xffffffffu, V[0], 1, 8);
-                    hsum4(V, c == 0 ? V[4] : lft, c == 7 ? V[4] : rgt, S);
-                    next_state4<ORK>(S, r == 0 ? af[Q] : as[Q], rule, nw);
-                    if (partial) {
-                        const int64_t c64 = n - x1 - (y + r) - xc + 1;  // cells of the chunk in the domain
-                        const int cnt = (int)(c64 < 0 ? 0 : (c64 > 16 ? 16 : c64));
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) nw[w] &= chunk_word_mask(cnt, w);
-                        if (cnt > 0) store16(dst + r * side, nw);
-                    } else {
-                        store16(dst + r * side, nw);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint4 q = *reinterpret_cast<const uint4 *>(base + k * kPlMaxW + 16 + 16 * c);
+                        v[k][0] = q.x;
+                        v[k][1] = q.y;
+                        v[k][2] = q.z;
+                        v[k][3] = q.w;
+                        h[k] = *reinterpret_cast<const uint32_t *>(base + k * kPlMaxW + ho);
                     }
-                    acc += (nw[0] + nw[1]) + (nw[2] + nw[3]);
+                } else {
+                    const bool has_c = 16 * c + 32 <= W, has_h = c == 0 && W > 0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                        if (has_c) q = *reinterpret_cast<const uint4 *>(base + k * W + 16 + 16 * c);
+                        v[k][0] = q.x;
+                        v[k][1] = q.y;
+                        v[k][2] = q.z;
+                        v[k][3] = q.w;
+                        h[k] = has_h ? *reinterpret_cast<const uint32_t *>(base + k * W + 12) : 0u;
+                    }
                 }
-                lsum += (acc * 0x01010101u) >> 24;  // bytes <= 8: their sum fits the top byte
+                // this warp is done with the stage
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                // sums of this plane into set j; only lanes c = 0 (left) and
+                // c = 7 (right) use their halo word
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    sf[j][w] = v[0][w] + v[1][w] + v[2][w];
+                    ss[j][w] = v[1][w] + v[2][w] + v[3][w];
+                    af[j][w] = v[1][w];
+                    as[j][w] = v[2][w];
+                }
+                sf[j][4] = h[0] + h[1] + h[2];
+                ss[j][4] = h[1] + h[2] + h[3];
+                if (ph == kPhOut) {
+                    // output plane md.z - 1 from the sets of planes md.z - 2
+                    // (j + 1), md.z - 1 (j + 2) and md.z (j)
+                    const int P = (j + 1) % 3, Q = (j + 2) % 3;
+                    const int64_t x1 = (int64_t)md.z - 1;
+                    const int yf = md.x + 2 * p, xc = md.y + 16 * c;
+                    const bool partial = x1 + md.x + md.y + (kPlaneTY - 1) + (kPlaneTX - 1) > n;
+                    const int lim = (int)(n - x1) + 1;  // a cell is in the domain iff x2 + x3 < lim
+                    uint8_t *dst = out + ((x1 * side + yf) * side + xc);
+                    uint32_t acc = 0;
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        uint32_t V[5], S[4], nw[4];
+#pragma unroll
+                        for (int w = 0; w < 5; ++w)
+                            V[w] = r == 0 ? sf[P][w] + sf[Q][w] + sf[j][w] : ss[P][w] + ss[Q][w] + ss[j][w];
+                        const uint32_t lft = __shfl_up_sync(0xffffffffu, V[3], 1, 8);
+                        const uint32_t rgt = __shfl_down_sync(0xffffffffu, V[0], 1, 8);
+                        hsum4(V, c == 0 ? V[4] : lft, c == 7 ? V[4] : rgt, S);
+                        next_state4<ORK>(S, r == 0 ? af[Q] : as[Q], rule, nw);
+                        if (partial) {
+                            const int cnt = lim - (yf + r) - xc;  // cells of the chunk in the domain
+                            if (cnt < 16) {
+                                const int c8 = 8 * cnt;
+#pragma unroll
+                                for (int w = 0; w < 4; ++w)
+                                    nw[w] &= __funnelshift_rc(0xffffffffu, 0u, (uint32_t)max(0, 32 * w + 32 - c8));
+                            }
+                            if (cnt > 0) store16(dst + r * side, nw);
+                        } else {
+                            store16(dst + r * side, nw);
+                        }
+                        acc += (nw[0] + nw[1]) + (nw[2] + nw[3]);
+                    }
+                    lsum += (acc * 0x01010101u) >> 24;  // bytes <= 8: their sum fits the top byte
+                }
+                if (++slot == kPlSlots) {
+                    slot = 0;
+                    parity ^= 1u;
+                }
             }
-            if (++slot == kPlSlots) {
-                slot = 0;
-                parity ^= 1u;
-            }
+            if (stop) break;
         }
-        if (end) break;
     }
 
-    if (!ok && tid == 0) {
-        atomicOr(&g_ca3p_status, 1u);
-        // the loads issued into the stages after the one that timed out must
-        // land before the CTA exits
-        for (int k = 0; k < kPlSlots; ++k) {
-            mbar_wait_bounded(&full[slot], parity, kWaitLimitNs);
-            if (++slot == kPlSlots) {
-                slot = 0;
-                parity ^= 1u;
+    __syncthreads();
+    if (tid == kPlConsumerWarps * 32) {
+        if (abort_flag) {
+            atomicOr(&g_ca3p_status, 1u);
+            // the last fill issued into each stage must land before the CTA exits
+            for (int j = 1; j <= kPlSlots && (uint64_t)j <= issued; ++j) {
+                const uint64_t q = issued - j;
+                mbar_wait_bounded(&full[q % kPlSlots], (uint32_t)((q / kPlSlots) & 1), kWaitLimitNs);
             }
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
         // the last CTA out resets the work counter (every fetch of this launch is done)
         __threadfence();
         if (atomicAdd(&queue[1], 1ull) == (unsigned long long)gridDim.x - 1ull) {
