@@ -330,7 +330,7 @@ def _per_launch_ms(launch, reps):
     return statistics.mean(ts), statistics.median(ts)
 
 
-def run_batch(args, rank, world):
+def run_batch(args, rank, world, compact=False):
     """Batched workload: 2048 + 256 automata, 16 steps per benchmark step, one
     persistent launch per automaton step (graph replay), against looping the
     single-instance path over the instances."""
@@ -377,6 +377,13 @@ def run_batch(args, rank, world):
     secs_loop = _time_region(loop, 1, 1, world) if maps else float("nan")
     value_loop = aggregate(cells * steps, secs_loop, world)[0] if maps else float("nan")
     assert sx.simplex_device_status() == 0
+    if compact:
+        return {"workload": "2048 m=2 (n log-U[64,2048]) + 256 m=3 (n log-U[32,256]), 16 steps, one persistent "
+                            "launch per step, graph replay", "instances": len(insts), "cells": cells,
+                "cell_updates_per_s": value, "ms_per_16_steps": tmax / args.steps * 1e3,
+                "kernel_ms_per_step": step_ms, "roofline_frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "single_instance_loop_cell_updates_per_s": value_loop, "speedup_over_loop": value / value_loop,
+                "autotuned": not args.no_tune, "tune_seconds": tune_s}
     return dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=tmax / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -433,10 +440,11 @@ def _serve_classes(srv, jobs):
     return out
 
 
-def run_serve(args, rank, world):
+def run_serve(args, rank, world, compact=False):
     """Serving workload: Poisson arrivals at 2000 jobs/s, continuous batching
     under a 64 GiB grid budget; p50/p99 latency and cell-updates/s, against
-    serial per-job execution on the single-instance path."""
+    serial per-job execution on the single-instance path.  compact: the trace
+    and the serial baseline only (no capacity or heavy-load runs)."""
     import torch
     from paper_2208_11617_gb300 import simplex as sx
 
@@ -484,6 +492,18 @@ def run_serve(args, rank, world):
     svc_all = [svc[k % len(svc)] for k in range(len(jobs))]
     lat = sorted(_fifo_latency(list(t), svc_all))
     q = lambda f: lat[min(len(lat) - 1, int(f * (len(lat) - 1) + 0.5))] * 1e3
+    assert mismatches == 0, f"{mismatches} jobs differ between the server and the single-instance path"
+    if compact:
+        return {"trace": f"Poisson {inputs.SERVE_RATE:g} jobs/s for {seconds:g} s", "jobs": len(jobs),
+                "completed": st["completed"], "cell_updates_per_s": value,
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                "host_p50_ms": st["host_p50_ms"], "host_p99_ms": st["host_p99_ms"],
+                "serial_fifo_p50_ms": q(0.5), "serial_fifo_p99_ms": q(0.99),
+                "serial_cell_updates_per_s": serial_rate, "serial_sample_jobs": len(sample),
+                "digest_mismatches": mismatches, "gpu_launches": st["launches"],
+                "note": "p*_ms: arrival to the device event after the job's result copies; host_p*_ms: arrival to "
+                        "the serving loop finding it complete; serial: FIFO queue of the same arrivals served one "
+                        "job at a time on the single-instance path"}
     # capacity: the first jobs of the trace all available at once (no arrival gaps)
     cap_jobs = jobs[: args.serve_capacity_jobs]
     t1 = time.perf_counter()
@@ -752,6 +772,16 @@ def run_ours(args, rank, world, local):
                       "d2h_bytes_per_step": 4 * mp.numel}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl, workload=args.workload, n=args.n)
+    if args.workload == "ca2" and args.n is None and world == 1 and not args.no_records:
+        # the batched engine and the server, briefly, so that the default line
+        # carries them too (their own workloads: --workload batch / serve)
+        import copy
+        ab = copy.copy(args)
+        ab.steps, ab.warmup = 3, 3
+        res["batch"] = run_batch(ab, rank, world, compact=True)
+        asv = copy.copy(args)
+        asv.serve_seconds, asv.serve_sample = 5.0, 200
+        res["serve"] = run_serve(asv, rank, world, compact=True)
     return res
 
 
@@ -1021,6 +1051,8 @@ def main():
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-energy", action="store_true", help="skip the NVML energy runs")
+    ap.add_argument("--no-records", action="store_true",
+                    help="ca2: leave out the short batched and serving records of the default line")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller case of the workload)")
     ap.add_argument("--block", type=int, default=None, help="override the tile side")
     ap.add_argument("--side", type=int, default=None,

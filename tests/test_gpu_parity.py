@@ -401,6 +401,22 @@ def test_ca_m3_full_size_steps_match_oracle():
     assert live_h[-1] > 0
 
 
+def test_ca_m2_full_length_matches_oracle():
+    """m = 2 at the benchmark's size and length (n = 32767, 100 steps, B3/S23,
+    Bernoulli(0.5), 128 x 128 tiles, graph-captured): the final grid and all
+    101 live counts equal the oracle's whole run."""
+    w = inputs.CA_M2
+    mp = sx.simplex_map_create(w.m, w.n, 2, 2, w.block)
+    fin, live = _gpu_run(mp, w.n, w.steps, w.rule, w.seed, w.threshold, sx.SIMPLEX_MODE_H)
+    got = fin.view(mp.shape).cpu().numpy()
+    del fin
+    ref, ref_live = oracle.ca_run(w.m, w.n, w.steps, w.rule[0], w.rule[1],
+                                  oracle.ca_init(w.m, w.n, w.seed, w.threshold))
+    assert len(ref_live) == w.steps + 1
+    np.testing.assert_array_equal(live, ref_live)
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_ca_m3_full_size_matches_oracle():
     """The m = 3 automaton at the benchmark's size and length (n = 1023, 50
     steps, B5/S45, Bernoulli(0.3)) in the launch form the benchmark times (the
