@@ -73,7 +73,10 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
 {
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t full[kPlSlots], empty[kPlSlots];
-    __shared__ int4 meta[kPlSlots];  // y0, x0, staged plane, width | phase << 8
+    // per stage: the output row offset (x1 - 1, y0, x0) in the grid as two 32-bit
+    // halves; n - (x1 - 1) + 1 - y0 - x0 (a cell of that plane is in the
+    // domain iff its offsets inside the brick sum below it); width | phase << 8
+    __shared__ int4 meta[kPlSlots];
     __shared__ uint32_t red[32];
     __shared__ volatile int abort_flag;
     uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
@@ -136,7 +139,9 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                     while (wi < kPlWidths - 1 && (int64_t)plane_box_width(wi) < need) ++wi;
                 }
                 const int W = wi < 0 ? 0 : plane_box_width(wi);
-                meta[s] = make_int4(py0, px0, px1, W | (ph << 8));
+                const int64_t off = (((int64_t)px1 - 1) * side + py0) * side + px0;
+                meta[s] = make_int4((int)(uint32_t)off, (int)(uint32_t)((uint64_t)off >> 32),
+                                    (int)(n - px1 + 2 - py0 - px0), W | (ph << 8));
                 if (wi < 0) {
                     mbar_arrive(&full[s]);  // nothing to load: the phase completes with no bytes
                 } else {
@@ -158,6 +163,8 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
         int slot = 0;
         uint32_t parity = 0;
         const int ho = c == 0 ? 12 : 16 + kPlaneTX;  // this lane's halo word (left or right of the brick)
+        const int64_t toff = (int64_t)(2 * p) * side + 16 * c;  // first output cell of the thread in a brick plane
+        const int tq = 2 * p + 16 * c;                         // its offsets inside the brick, summed
         for (;;) {
             bool stop = false;
 #pragma unroll
@@ -214,14 +221,11 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                 sf[j][4] = h[0] + h[1] + h[2];
                 ss[j][4] = h[1] + h[2] + h[3];
                 if (ph == kPhOut) {
-                    // output plane md.z - 1 from the sets of planes md.z - 2
-                    // (j + 1), md.z - 1 (j + 2) and md.z (j)
+                    // output plane x1 - 1 (x1 the staged plane) from the sets
+                    // of planes x1 - 2 (j + 1), x1 - 1 (j + 2) and x1 (j)
                     const int P = (j + 1) % 3, Q = (j + 2) % 3;
-                    const int64_t x1 = (int64_t)md.z - 1;
-                    const int yf = md.x + 2 * p, xc = md.y + 16 * c;
-                    const bool partial = x1 + md.x + md.y + (kPlaneTY - 1) + (kPlaneTX - 1) > n;
-                    const int lim = (int)(n - x1) + 1;  // a cell is in the domain iff x2 + x3 < lim
-                    uint8_t *dst = out + ((x1 * side + yf) * side + xc);
+                    const bool partial = md.z < kPlaneTY + kPlaneTX - 1;  // not every cell of the brick plane
+                    uint8_t *dst = out + (int64_t)(((uint64_t)(uint32_t)md.y << 32) | (uint32_t)md.x) + toff;
                     uint32_t acc = 0;
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -234,7 +238,7 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                         hsum4(V, c == 0 ? V[4] : lft, c == 7 ? V[4] : rgt, S);
                         next_state4<ORK>(S, r == 0 ? af[Q] : as[Q], rule, nw);
                         if (partial) {
-                            const int cnt = lim - (yf + r) - xc;  // cells of the chunk in the domain
+                            const int cnt = md.z - tq - r;  // cells of the chunk in the domain
                             if (cnt < 16) {
                                 const int c8 = 8 * cnt;
 #pragma unroll
