@@ -223,6 +223,8 @@ def _workload(name, args=None):
         wl = inputs.CA_M3
     elif name == "write2":
         wl = inputs.WRITE_M2
+    elif name == "write2hbm":
+        wl = inputs.WRITE_M2_HBM
     elif name == "write4":
         wl = inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
     elif name == "accum2":
@@ -687,8 +689,8 @@ def run_ours(args, rank, world, local):
         reps = 100
 
         accum = args.workload in ("accum2", "accum3")
-        if accum:
-            reps = 10  # the ACCUM arrays are 1 and 4 GiB: a launch moves 1.1 / 1.4 GB
+        if accum or args.workload == "write2hbm":
+            reps = 10  # 1 to 4 GiB arrays: a launch moves 1.1 to 2.1 GB
 
         def launch(mode):
             if accum:
@@ -905,12 +907,15 @@ def _oracle_sample(wl, steps_sample):
             data = oracle.accum(wl.m, ns, data, 1)
         dt = time.perf_counter() - t0
         return cells * steps_sample / dt, f"{steps_sample} ACCUM pass(es) of n={ns} (array copy included)", cores, dt
-    cells = oracle.count_cells(wl.m, wl.n)
+    # the write of a smaller array of the same simplex dimension past n = 8191
+    # (the 4 GiB array would spend the time allocating and zeroing)
+    ns = min(wl.n, 8191)
+    cells = oracle.count_cells(wl.m, ns)
     t0 = time.perf_counter()
     for _ in range(steps_sample):
-        oracle.write(wl.m, wl.n, wl.seed)
+        oracle.write(wl.m, ns, wl.seed)
     dt = time.perf_counter() - t0
-    return cells * steps_sample / dt, f"{steps_sample} full write(s) of n={wl.n}", cores, dt
+    return cells * steps_sample / dt, f"{steps_sample} full write(s) of n={ns}", cores, dt
 
 
 def _oracle_edm_sample(n_sample):
@@ -998,7 +1003,7 @@ def run_reference(args, rank, world):
     wl = _workload(args.workload, args)
     if wl in ("batch", "serve") or args.workload in ("map2", "map3"):
         return {"impl": "reference", "unavailable": f"the oracle arm times the single-instance workloads "
-                f"(ca2, ca3, write2, write4, accum2, accum3, edm), not {args.workload}"}
+                f"(ca2, ca3, write2, write2hbm, write4, accum2, accum3, edm), not {args.workload}"}
     unit = UNIT if isinstance(wl, inputs.CAWorkload) else "cells/s"
     if args.workload == "edm":
         sample = lambda k: _oracle_edm_sample(8191)  # noqa: E731
@@ -1031,7 +1036,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ca2",
-                    choices=["ca2", "ca3", "write2", "write4", "accum2", "accum3", "map2", "map3", "edm", "batch",
+                    choices=["ca2", "ca3", "write2", "write2hbm", "write4", "accum2", "accum3", "map2", "map3", "edm", "batch",
                              "serve"])
     ap.add_argument("--serve-seconds", type=float, default=inputs.SERVE_SECONDS, help="serve: trace length")
     ap.add_argument("--serve-sample", type=int, default=400, help="serve: jobs re-run alone for the serial baseline")
