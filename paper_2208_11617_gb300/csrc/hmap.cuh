@@ -200,7 +200,9 @@ SX_HD bool xrun_decode(const Plan &p, int kind, uint64_t w, XRun &r)
 // past the domain exit (kMapBB) or run with every store masked
 // (kMapBBThread).  Segments shrink towards the apex so that the last units
 // of a launch are short: a segment starting at plane b has
-// clamp(2^floor(log2((n + 1 - b) / 32)), 4, 64) planes.
+// clamp(2^floor(log2((n + 1 - b) / 64)), 4, 64) planes (16 at the base of
+// the n = 1023 tetrahedron; twice and four times as long were 2 % and 16 %
+// slower).
 constexpr int kPlaneTY = 32, kPlaneTX = 128;
 constexpr int kPlaneMaxSegs = 320;
 
@@ -217,7 +219,7 @@ struct PlaneSched {
 // Planes of the segment that starts at plane b.
 SX_HD int32_t plane_seg_len(int64_t n, int64_t b)
 {
-    const int64_t q = (n + 1 - b) / 32;
+    const int64_t q = (n + 1 - b) / 64;
     int32_t s = 4;
     while (s < 64 && (int64_t)(2 * s) <= q) s *= 2;
     return s;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
             bool have = false;
             for (uint64_t k = 0;; ++k) {
                 const int s = (int)(k % kPlSlots);
-                if (k >= (uint64_t)kPlSlots &&
+                if (k >= (uint64_t)kPlSlots && !mbar_try_wait(&empty[s], (uint32_t)((k / kPlSlots - 1) & 1)) &&
                     !mbar_wait_bounded(&empty[s], (uint32_t)((k / kPlSlots - 1) & 1), kWaitLimitNs)) {
                     abort_flag = 1;
                     break;

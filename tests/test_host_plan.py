@@ -308,10 +308,13 @@ def test_plane_units_cover_each_brick_plane_exactly_once(n):
         else:
             np.testing.assert_array_equal(got, want)
     if n == 1023:
-        # slab lengths: 2^floor(log2((n + 1 - b) / 32)) clamped to [4, 64]
+        # slab lengths: 2^floor(log2((n + 1 - b) / 64)) clamped to [4, 64]
         starts = sorted({u[2] for u, _ in _plane_units(mp, sx.SIMPLEX_MODE_H)})
         lens = np.diff(starts + [n + 1])
-        assert lens[0] == 32 and lens[-1] == 4 and all(np.diff(lens) <= 0)
+        assert lens[0] == 16 and lens[-1] == 4 and all(np.diff(lens) <= 0)
+        for b, ln in zip(starts, lens[:-1]):
+            q = (n + 1 - b) // 64
+            assert ln == min(64, max(4, 1 << (q.bit_length() - 1) if q else 4))
 
 
 # ---------------------------------------------------------------- fully efficient H3 (layout 1)
