@@ -370,7 +370,9 @@ typedef struct simplex_batch *simplex_batch_t;
 
 typedef struct simplex_instance {
     int32_t m;          /* 2 or 3 */
-    int32_t block;      /* tile side: m = 2: 64 or 128; m = 3: 16 or 32 (32^3 tiles run in a second launch per step) */
+    int32_t block;      /* tile side: m = 2: 64 or 128; m = 3: 16 or 32 (32^3 tiles run in a second launch per
+                           step), or 128: the plane stream (32 x 128 bricks streamed along x1, as launch 3 of
+                           simplex_map_create_ex; all such instances run in one more launch per step) */
     int32_t beta;       /* m = 3: 2 (hinge) or 3; m = 2: 2 */
     int32_t band;       /* m = 2 trapezoid band (power of two); 0: automatic */
     int64_t n;          /* simplex size, >= 0 */
@@ -466,7 +468,8 @@ int simplex_batch_grid(simplex_batch_t batch, int i, uint8_t **grid, int64_t *si
  * host threads -- race and give wrong results: serialise them.  A batch whose
  * descriptors, work items and counters exceed 8 MiB (about 1.2 KB per
  * instance: several thousand instances; the 2,304-instance batched workload
- * needs 2.8 MB) is rejected with SIMPLEX_EINVAL.
+ * needs 2.8 MB) is rejected with SIMPLEX_EINVAL.  Batches holding plane-stream
+ * instances (m = 3, block 128) are refused with SIMPLEX_EUNSUPPORTED.
  */
 int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, uint64_t grids_bytes, int parity, int steps,
                              unsigned long long *live, void *stream);

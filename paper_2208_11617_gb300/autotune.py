@@ -5,7 +5,9 @@ Size class of an instance: (m, floor(log2 n)).  Candidates (r = 1/2 is the
 only scale factor implemented):
   m = 2: tile 64 or 128 (H in trapezoid form, band chosen by the plan);
   m = 3: tile 16 or 32 with beta = 2 (H3 with the hinge) or beta = 3 (every
-         corner recursed); 32^3 tiles run in a second launch per step.
+         corner recursed); 32^3 tiles run in a second launch per step; or
+         block 128, the plane stream (bricks of 32 x 128 cells streamed along
+         x1), in a launch of its own.
 For each class the tuner builds a batch of that class's instances alone for
 every candidate, runs a few graph-captured steps, and keeps the candidate with
 the most cell-updates per second.  Results can be cached in a JSON file.
@@ -18,7 +20,8 @@ import os
 import time
 
 CANDIDATES = {2: [dict(block=64, beta=2), dict(block=128, beta=2)],
-              3: [dict(block=16, beta=2), dict(block=16, beta=3), dict(block=32, beta=2), dict(block=32, beta=3)]}
+              3: [dict(block=16, beta=2), dict(block=16, beta=3), dict(block=32, beta=2), dict(block=32, beta=3),
+                  dict(block=128, beta=2)]}
 
 
 def size_class(m: int, n: int):

@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <new>
@@ -38,8 +39,12 @@ struct RunGraph {
 struct simplex_batch {
     std::vector<simplex_instance_t> spec;
     std::vector<sx::BatchInst> insts;
-    std::vector<sx::BatchItem> items;  // set 0 items, then set 1 items
-    size_t nitems0 = 0;
+    std::vector<sx::BatchItem> items;  // set 0 items, then set 1 items, then count-only items
+    size_t nitems0 = 0, nitems1 = 0;   // end of set 0's items, of set 1's
+    // plane-stream instances (kBody3plane): their work units, in instance order
+    std::vector<sx::BatchPlaneUnit> punits;
+    size_t nplane = 0;
+    uint64_t off_punits = 0, off_ptmaps = 0, off_pqueue = 0;
     std::vector<uint64_t> grid_bytes;
     uint64_t blocks = 0, cells = 0;
     // arena layout (byte offsets)
@@ -53,6 +58,9 @@ struct simplex_batch {
 };
 
 namespace {
+
+// Planes per slab of a batched plane-stream instance.
+constexpr int32_t kBatchPlaneSlab = 16;
 
 int check_batch(simplex_batch_t b, bool bound)
 {
@@ -74,8 +82,18 @@ int enqueue_batch_run(simplex_batch_t b, int steps, unsigned long long *live, in
         e = cudaMemsetAsync(live, 0, sizeof(unsigned long long) * b->insts.size() * (size_t)(steps + 1), st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(live)");
     }
+    sx::PlaneBatch pb = {};
+    if (!b->punits.empty()) {
+        pb.insts = insts;
+        pb.units = reinterpret_cast<const sx::BatchPlaneUnit *>(b->arena + b->off_punits);
+        pb.nunits = (uint32_t)b->punits.size();
+        pb.ptmaps = reinterpret_cast<const CUtensorMap *>(b->arena + b->off_ptmaps);
+        pb.arena = b->arena;
+    }
     return enqueue_batch_passes(insts, items, b->items.size(), b->nitems0, tmaps, b->arena, queue,
-                                queue + steps + 1, steps, live, parity, st);
+                                queue + steps + 1, steps, live, parity, st, b->nitems1,
+                                b->punits.empty() ? nullptr : &pb,
+                                reinterpret_cast<unsigned long long *>(b->arena + b->off_pqueue));
 }
 
 }  // namespace
@@ -84,9 +102,11 @@ namespace sxh {
 
 int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items, size_t nitems, size_t nitems0,
                          const CUtensorMap *tmaps, uint8_t *arena, unsigned int *q0, unsigned int *q1, int steps,
-                         unsigned long long *live, int parity, cudaStream_t st)
+                         unsigned long long *live, int parity, cudaStream_t st, size_t nitems1,
+                         const sx::PlaneBatch *planes, unsigned long long *pqueue)
 {
     cudaError_t e;
+    if (nitems1 == (size_t)-1) nitems1 = nitems;
     if (live) {
         e = sx::launch_batch_pass(insts, items, (uint32_t)nitems, tmaps, arena, parity, q0, live, steps + 1, 0, true,
                                   st);
@@ -99,10 +119,19 @@ int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items,
                                       false, st, nullptr, 0);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
         }
-        if (nitems > nitems0) {
-            e = sx::launch_batch_pass(insts, items + nitems0, (uint32_t)(nitems - nitems0), tmaps, arena, in, q1 + s,
+        if (nitems1 > nitems0) {
+            e = sx::launch_batch_pass(insts, items + nitems0, (uint32_t)(nitems1 - nitems0), tmaps, arena, in, q1 + s,
                                       live, steps + 1, s, false, st, nullptr, 1);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch (32^3 tiles)");
+        }
+        if (planes && planes->nunits) {
+            sx::PlaneBatch pb = *planes;
+            pb.in_parity = in;
+            pb.live = live;
+            pb.live_stride = steps + 1;
+            pb.live_index = s;
+            e = sx::launch_batch_planes(pb, pqueue, st);
+            if (e != cudaSuccess) return cuda_fail(e, "batch step launch (plane stream)");
         }
     }
     return SIMPLEX_OK;
@@ -119,6 +148,7 @@ int batch_view(simplex_batch_t b, BatchView *out)
     out->grids_offset = b->off_grids;
     out->grids_bytes = b->bytes - b->off_grids;
     out->serial = b->serial;
+    out->has_planes = !b->punits.empty();
     return SIMPLEX_OK;
 }
 
@@ -144,6 +174,7 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
     }
     uint64_t grid_off = 0;
     std::vector<sx::BatchItem> items1;  // items of launch set 1, appended after set 0's
+    std::vector<sx::BatchItem> items2;  // count-only items (plane-stream instances), appended last
     for (int i = 0; i < count; ++i) {
         const simplex_instance_t &in = instances[i];
         sx::BatchInst &bi = b->insts[i];
@@ -153,10 +184,12 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         if (in.m == 2 && in.block == 128) body = sx::kBody2x128;
         if (in.m == 3 && in.block == 16) body = sx::kBody3x16;
         if (in.m == 3 && in.block == 32) body = sx::kBody3x32;
+        if (in.m == 3 && in.block == 128) body = sx::kBody3plane;
         if (body < 0) {
             delete b;
             return fail(SIMPLEX_EINVAL, "instance %d: the batched engine runs m = 2 with block 64 or 128 and m = 3 "
-                                        "with block 16 or 32 (got m = %d, block = %d)", i, in.m, in.block);
+                                        "with block 16, 32 or 128 (the plane stream) (got m = %d, block = %d)",
+                        i, in.m, in.block);
         }
         const int64_t side = (in.n + 16) / 16 * 16;  // round_up(n + 1, 16)
         int band = 0;
@@ -168,7 +201,9 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
                 while (band < 8 && band * 2 <= nb) band *= 2;
             }
         }
-        int rc = build_plan(in.m, in.n, 2, in.beta, in.block, side, band, &bi.plan);
+        // plane-stream instances keep a 32^3 H3 plan for the count pass (live[0], digests)
+        const int rho = body == sx::kBody3plane ? 32 : in.block;
+        int rc = build_plan(in.m, in.n, 2, in.beta, rho, side, band, &bi.plan);
         if (rc) {
             std::string msg = g_last_error;
             delete b;
@@ -177,6 +212,26 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         bi.rule = make_rule(in.m, in.birth, in.survive);
         bi.body = body;
         bi.tmap = 2 * i;
+        if (body == sx::kBody3plane) {
+            sx::PlaneSched ps;
+            if (!sx::plane_sched_build(in.n, sx::kMapH, &ps, kBatchPlaneSlab) || in.n >= 65535) {
+                delete b;
+                return fail(SIMPLEX_EINVAL, "instance %d: n = %lld is too large for a batched plane stream", i,
+                            (long long)in.n);
+            }
+            bi.tmap = (int32_t)(2 * sx::kPlWidths * b->nplane++);
+            try {
+                for (uint64_t w = 0; w < ps.units; ++w) {
+                    sx::PlaneUnit u;
+                    sx::plane_unit_decode(ps, w, u);
+                    b->punits.push_back(sx::BatchPlaneUnit{(uint32_t)i, (uint32_t)u.y0 | ((uint32_t)u.x0 << 16), u.b,
+                                                           u.e});
+                }
+            } catch (...) {
+                delete b;
+                return fail(SIMPLEX_ENOMEM, "host allocation failed");
+            }
+        }
         uint64_t gb = 1;
         for (int d = 0; d < in.m; ++d) gb *= (uint64_t)side;
         b->grid_bytes[i] = gb;
@@ -202,7 +257,8 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
             for (int d = 0; d < bi.plan.m; ++d) sum += X[d];
             return ok && sum * bi.plan.rho <= bi.plan.n;
         };
-        std::vector<sx::BatchItem> &dst = body == sx::kBody3x32 ? items1 : b->items;
+        // plane-stream instances: block items for the count pass only
+        std::vector<sx::BatchItem> &dst = body == sx::kBody3x32 ? items1 : (body == sx::kBody3plane ? items2 : b->items);
         for (uint64_t v = 0; v < bi.plan.h_blocks;) {
             if (!holds_cells(v)) {
                 ++v;
@@ -213,8 +269,14 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
             dst.push_back(sx::BatchItem{(uint32_t)i, (uint32_t)v0, (uint32_t)(v - v0), 0u});
         }
     }
+    // plane units longest first (the queue's last units are the short ones);
+    // equal lengths keep instance and slab order
+    std::stable_sort(b->punits.begin(), b->punits.end(),
+                     [](const sx::BatchPlaneUnit &x, const sx::BatchPlaneUnit &y) { return x.e - x.b > y.e - y.b; });
     b->nitems0 = b->items.size();
     b->items.insert(b->items.end(), items1.begin(), items1.end());
+    b->nitems1 = b->items.size();
+    b->items.insert(b->items.end(), items2.begin(), items2.end());
     if (b->items.size() >= 0xffffff00ull) {
         delete b;
         return fail(SIMPLEX_EINVAL, "too many work items (%zu)", b->items.size());
@@ -229,6 +291,12 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
     off = align_up(off + sizeof(CUtensorMap) * 2ull * (uint64_t)count, 256);
     b->off_queue = off;
     off = align_up(off + sizeof(unsigned int) * 2ull * (uint64_t)(sx::kBatchMaxSteps + 1), 256);
+    b->off_punits = off;
+    off = align_up(off + sizeof(sx::BatchPlaneUnit) * b->punits.size(), 256);
+    b->off_ptmaps = off;
+    off = align_up(off + sizeof(CUtensorMap) * 2ull * sx::kPlWidths * b->nplane, 256);
+    b->off_pqueue = off;
+    off = align_up(off + 2 * sizeof(unsigned long long), 256);
     b->off_grids = off;
     for (auto &bi : b->insts) {
         bi.grid[0] += off;
@@ -285,8 +353,25 @@ int simplex_batch_bind(simplex_batch_t b, void *arena, uint64_t arena_bytes, voi
                                  b->insts[i].plan.rho + 2);
             if (rc) return rc;
         }
+    std::vector<sx::PlaneMaps> pmaps(2 * b->nplane);
+    for (size_t i = 0; i < b->insts.size(); ++i) {
+        if (b->insts[i].body != sx::kBody3plane) continue;
+        for (int g = 0; g < 2; ++g) {
+            rc = make_plane_maps(b->insts[i].plan, base + b->insts[i].grid[g],
+                                 &pmaps[b->insts[i].tmap / sx::kPlWidths + g]);
+            if (rc) return rc;
+        }
+    }
+    static_assert(sizeof(sx::PlaneMaps) == sizeof(CUtensorMap) * sx::kPlWidths, "plane maps must be contiguous");
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(base + b->off_insts, b->insts.data(), sizeof(sx::BatchInst) * b->insts.size(),
+    if (!b->punits.empty() &&
+        ((e = cudaMemcpyAsync(base + b->off_punits, b->punits.data(), sizeof(sx::BatchPlaneUnit) * b->punits.size(),
+                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+         (e = cudaMemcpyAsync(base + b->off_ptmaps, pmaps.data(), sizeof(sx::PlaneMaps) * pmaps.size(),
+                              cudaMemcpyHostToDevice, st)) != cudaSuccess))
+        return cuda_fail(e, "binding the batch arena (plane stream)");
+    if ((e = cudaMemsetAsync(base + b->off_pqueue, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(base + b->off_insts, b->insts.data(), sizeof(sx::BatchInst) * b->insts.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(base + b->off_items, b->items.data(), sizeof(sx::BatchItem) * b->items.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||

@@ -23,6 +23,7 @@ enum BatchBody : int32_t {
     kBody2x128 = 1,  // m = 2, 128 x 128 tiles
     kBody3x16 = 2,   // m = 3, 16^3 tiles
     kBody3x32 = 3,   // m = 3, 32^3 tiles (a launch of its own: 74 KB stage)
+    kBody3plane = 4, // m = 3, plane stream: 32 x 128 bricks streamed along x1 (a launch of its own)
 };
 
 constexpr int kBatchThreads = 128;
@@ -41,12 +42,32 @@ struct BatchItem {
 // Salt of the result digest: sum over live cells x of splitmix32(kDigestSalt ^ lin(x)).
 constexpr uint32_t kDigestSalt = 0x00D16E57u;
 
+// One plane-stream work unit of a batch: instance `inst`, brick rows
+// y0 = yx & 0xffff ..., cells x0 = yx >> 16 ..., output planes b ... e.
+struct BatchPlaneUnit {
+    uint32_t inst, yx;
+    int32_t b, e;
+};
+
 struct BatchInst {
     Plan plan;
     Rule rule;
     uint64_t grid[2];  // byte offsets of the two grids in the arena
     int32_t body;      // BatchBody
-    int32_t tmap;      // index of the tensor map of grid 0 (grid 1 follows)
+    int32_t tmap;      // index of the tensor map of grid 0 (grid 1 follows); kBody3plane: of the first
+                       // of grid 0's plane maps in the plane-map array (kPlWidths per grid)
+};
+
+// One pass of the plane-stream kernel over a batch's plane units (k_ca3p.cu).
+struct PlaneBatch {
+    const BatchInst *insts;
+    const BatchPlaneUnit *units;
+    uint32_t nunits;
+    int32_t in_parity;           // grid each instance reads; the result goes to the other
+    const CUtensorMap *ptmaps;   // the plane maps of every kBody3plane instance
+    uint8_t *arena;              // grid offsets count from here
+    unsigned long long *live;    // live[inst * live_stride + live_index] += live cells written
+    int32_t live_stride, live_index;
 };
 
 }  // namespace sx

@@ -235,8 +235,10 @@ SX_HD uint64_t plane_tri_bricks(int64_t K)
 }
 
 // Fills s for a map of side n; false if n needs more than kPlaneMaxSegs
-// segments or more than 2^32 units.
-inline bool plane_sched_build(int64_t n, int kind, PlaneSched *s)
+// segments or more than 2^32 units.  fixed_len > 0: every segment has that
+// many planes (the batched engine's small instances, where the length of the
+// whole batch's queue, not of one instance, decides the tail).
+inline bool plane_sched_build(int64_t n, int kind, PlaneSched *s, int32_t fixed_len = 0)
 {
     s->n = n;
     s->kind = kind;
@@ -244,7 +246,7 @@ inline bool plane_sched_build(int64_t n, int kind, PlaneSched *s)
     s->ntx = (int32_t)((n + kPlaneTX) / kPlaneTX);
     uint64_t u = 0;
     int32_t k = 0;
-    for (int64_t b = 0; b <= n; b += plane_seg_len(n, b)) {
+    for (int64_t b = 0; b <= n; b += fixed_len > 0 ? fixed_len : plane_seg_len(n, b)) {
         if (k >= kPlaneMaxSegs) return false;
         s->seg_b[k] = (int32_t)b;
         s->seg_u[k] = (uint32_t)u;

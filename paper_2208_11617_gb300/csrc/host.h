@@ -47,15 +47,20 @@ struct BatchView {
     size_t nitems0;  // items of launch set 0 come first, then those of set 1 (32^3 tiles of m = 3)
     uint64_t grids_offset, grids_bytes;
     uint64_t serial;  // unique per batch of this process: equal serials mean equal plans and items
+    bool has_planes;  // the batch holds plane-stream instances (kBody3plane)
 };
 
 // The step passes of a run: per step, launch set 0 over items [0, nitems0)
 // with queue counter q0[s] and set 1 over the rest with q1[s]; a count pass
 // over every item first (queue q0[0]) when `live` is given.  The counters
 // must be zero.
+// Items of set 1 end at nitems1 (the rest, up to nitems, count passes only);
+// with `planes`, every step also runs one plane-stream pass (work counters
+// `pqueue`, zero and left zero).
 int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items, size_t nitems, size_t nitems0,
                          const CUtensorMap *tmaps, uint8_t *arena, unsigned int *q0, unsigned int *q1, int steps,
-                         unsigned long long *live, int parity, cudaStream_t st);
+                         unsigned long long *live, int parity, cudaStream_t st, size_t nitems1 = (size_t)-1,
+                         const sx::PlaneBatch *planes = nullptr, unsigned long long *pqueue = nullptr);
 int batch_view(struct simplex_batch *b, BatchView *out);
 
 }  // namespace sxh

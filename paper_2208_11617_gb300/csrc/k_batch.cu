@@ -408,6 +408,9 @@ extern "C" int simplex_batch_run_static(simplex_batch_t batch, uint8_t *grids, u
     if (parity != 0 && parity != 1) return fail(SIMPLEX_EINVAL, "parity must be 0 or 1 (got %d)", parity);
     if (steps < 1 || steps > sx::kBatchMaxSteps)
         return fail(SIMPLEX_EINVAL, "steps must be in [1, %d] (got %d)", sx::kBatchMaxSteps, steps);
+    if (bv.has_planes)
+        return fail(SIMPLEX_EUNSUPPORTED, "the fixed scratch does not hold plane-stream instances (m = 3, block 128): "
+                                          "use simplex_batch_bind / simplex_batch_run");
     // scratch layout: descriptors, work items, tensor maps, queue counters
     auto up = [](uint64_t x) { return (x + 255) / 256 * 256; };
     const uint64_t off_items = up(sizeof(sx::BatchInst) * bv.count);

@@ -65,18 +65,26 @@ constexpr int kPhFirst = 0, kPhSecond = 1, kPhOut = 2, kPhEnd = 3;
 
 __host__ __device__ constexpr int plane_box_width(int i) { return i < kPlWidths - 1 ? 48 + 32 * i : kPlMaxW; }
 
-template <bool ORK>
+// BATCH: one pass of the batched engine over the plane-stream units of many
+// m = 3 instances (bt.units, each naming its instance); every instance has its
+// own size, grids, tensor maps (bt.ptmaps + its BatchInst::tmap: the widths of
+// grid 0, then those of grid 1), rule and live counter.  Otherwise one
+// instance: the units come from `sched` and the maps from `maps`.
+template <bool ORK, bool BATCH>
 __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
     ca3_step_planes(const __grid_constant__ PlaneMaps maps, uint8_t *__restrict__ out, const int64_t n,
                     const int64_t side, const Rule rule, const __grid_constant__ PlaneSched sched,
-                    unsigned long long *__restrict__ live, unsigned long long *__restrict__ queue)
+                    unsigned long long *__restrict__ live, unsigned long long *__restrict__ queue,
+                    const PlaneBatch bt)
 {
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t full[kPlSlots], empty[kPlSlots];
-    // per stage: the output row offset (x1 - 1, y0, x0) in the grid as two 32-bit
+    // per stage: the address of the output row (x1 - 1, y0, x0) as two 32-bit
     // halves; n - (x1 - 1) + 1 - y0 - x0 (a cell of that plane is in the
     // domain iff its offsets inside the brick sum below it); width | phase << 8
     __shared__ int4 meta[kPlSlots];
+    // BATCH: the stage's instance, its or-k rule word (0: the general tables) and its side
+    __shared__ int4 meta2[BATCH ? kPlSlots : 1];
     __shared__ uint32_t red[32];
     __shared__ volatile int abort_flag;
     uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
@@ -85,7 +93,8 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
     uint64_t issued = 0;  // producer: stages filled (loads and markers)
 
     if (tid == 0) {
-        for (int i = 0; i < kPlWidths; ++i) prefetch_tmap(&maps.m[i]);
+        if (!BATCH)
+            for (int i = 0; i < kPlWidths; ++i) prefetch_tmap(&maps.m[i]);
         for (int s = 0; s < kPlSlots; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kPlConsumerWarps);
@@ -101,6 +110,13 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
             unsigned long long next_w = atomicAdd(queue, 1ull);
             int32_t py0 = 0, px0 = 0, pb = 0, pe = -1, px1 = 0;
             bool have = false;
+            // the unit's instance (BATCH; else the launch's own)
+            int64_t pn = n, pside = side;
+            uint8_t *pout = out;
+            const CUtensorMap *ptm = maps.m;
+            int32_t pinst = 0;
+            uint32_t pork = 0;
+            const uint64_t nunits = BATCH ? (uint64_t)bt.nunits : sched.units;
             for (uint64_t k = 0;; ++k) {
                 const int s = (int)(k % kPlSlots);
                 if (k >= (uint64_t)kPlSlots && !mbar_try_wait(&empty[s], (uint32_t)((k / kPlSlots - 1) & 1)) &&
@@ -110,10 +126,22 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                 }
                 while (!have) {
                     const unsigned long long w = next_w;
-                    if (w >= sched.units) break;
+                    if (w >= nunits) break;
                     next_w = atomicAdd(queue, 1ull);
                     PlaneUnit u;
-                    if (!plane_unit_decode(sched, w, u)) continue;
+                    if constexpr (BATCH) {
+                        const BatchPlaneUnit bu = bt.units[w];
+                        const BatchInst &bi = bt.insts[bu.inst];
+                        u = PlaneUnit{(int32_t)(bu.yx & 0xffffu), (int32_t)(bu.yx >> 16), bu.b, bu.e};
+                        pinst = (int32_t)bu.inst;
+                        pn = bi.plan.n;
+                        pside = bi.plan.side;
+                        pout = bt.arena + bi.grid[bt.in_parity ^ 1];
+                        ptm = bt.ptmaps + bi.tmap + bt.in_parity * kPlWidths;
+                        pork = bi.rule.or_k;
+                    } else {
+                        if (!plane_unit_decode(sched, w, u)) continue;
+                    }
                     py0 = u.y0;
                     px0 = u.x0;
                     pb = u.b;
@@ -130,24 +158,26 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                 const int ph = px1 == pb - 1 ? kPhFirst : (px1 == pb ? kPhSecond : kPhOut);
                 // bytes of the box that can hold domain cells: from x0 - 16 up to
                 // n - x1 - (y0 - 1) inclusive
-                const int64_t need = (n - px1 - py0 + 2) - (int64_t)(px0 - 16);
+                const int64_t need = (pn - px1 - py0 + 2) - (int64_t)(px0 - 16);
                 int wi = -1;
-                if (px1 >= 0 && px1 <= n && sched.kind == kMapBBThread) {
+                if (!BATCH && px1 >= 0 && px1 <= pn && sched.kind == kMapBBThread) {
                     wi = kPlWidths - 1;  // the paper's bounding box: every brick staged in full
-                } else if (px1 >= 0 && px1 <= n && need > 16) {
+                } else if (px1 >= 0 && px1 <= pn && need > 16) {
                     wi = 0;
                     while (wi < kPlWidths - 1 && (int64_t)plane_box_width(wi) < need) ++wi;
                 }
                 const int W = wi < 0 ? 0 : plane_box_width(wi);
-                const int64_t off = (((int64_t)px1 - 1) * side + py0) * side + px0;
-                meta[s] = make_int4((int)(uint32_t)off, (int)(uint32_t)((uint64_t)off >> 32),
-                                    (int)(n - px1 + 2 - py0 - px0), W | (ph << 8));
+                const uint64_t orow =
+                    reinterpret_cast<uint64_t>(pout + ((((int64_t)px1 - 1) * pside + py0) * pside + px0));
+                meta[s] = make_int4((int)(uint32_t)orow, (int)(uint32_t)(orow >> 32), (int)(pn - px1 + 2 - py0 - px0),
+                                    W | (ph << 8));
+                if (BATCH) meta2[s] = make_int4(pinst, (int)pork, (int)pside, 0);
                 if (wi < 0) {
                     mbar_arrive(&full[s]);  // nothing to load: the phase completes with no bytes
                 } else {
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(&full[s], (uint32_t)(kPlRows * W));
-                    tma_load_3d(ring + s * kPlSlotBytes, &maps.m[wi], px0 - 16, py0 - 1, px1, &full[s]);
+                    tma_load_3d(ring + s * kPlSlotBytes, ptm + wi, px0 - 16, py0 - 1, px1, &full[s]);
                 }
                 issued = k + 1;
                 if (++px1 > pe + 1) have = false;
@@ -165,6 +195,14 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
         const int ho = c == 0 ? 12 : 16 + kPlaneTX;  // this lane's halo word (left or right of the brick)
         const int64_t toff = (int64_t)(2 * p) * side + 16 * c;  // first output cell of the thread in a brick plane
         const int tq = 2 * p + 16 * c;                         // its offsets inside the brick, summed
+        int cur = -1;  // BATCH: the instance lsum counts for
+        auto flush = [&]() {  // BATCH: the warp's live cells of instance `cur` to its counter
+            const uint32_t tot = __reduce_add_sync(0xffffffffu, lsum);
+            if (lane == 0 && tot && cur >= 0 && bt.live)
+                atomicAdd(bt.live + (uint64_t)cur * (uint64_t)bt.live_stride + (uint64_t)bt.live_index,
+                          (unsigned long long)tot);
+            lsum = 0;
+        };
         for (;;) {
             bool stop = false;
 #pragma unroll
@@ -176,6 +214,7 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                     break;
                 }
                 const int4 md = meta[slot];
+                const int4 md2 = BATCH ? meta2[slot] : make_int4(0, 0, 0, 0);
                 const int W = md.w & 255, ph = md.w >> 8;
                 if (ph == kPhEnd) {
                     stop = true;
@@ -225,7 +264,13 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                     // of planes x1 - 2 (j + 1), x1 - 1 (j + 2) and x1 (j)
                     const int P = (j + 1) % 3, Q = (j + 2) % 3;
                     const bool partial = md.z < kPlaneTY + kPlaneTX - 1;  // not every cell of the brick plane
-                    uint8_t *dst = out + (int64_t)(((uint64_t)(uint32_t)md.y << 32) | (uint32_t)md.x) + toff;
+                    const int64_t rs = BATCH ? (int64_t)md2.z : side;  // row stride of the output grid
+                    uint8_t *dst = reinterpret_cast<uint8_t *>(((uint64_t)(uint32_t)md.y << 32) | (uint32_t)md.x) +
+                                   (BATCH ? (int64_t)(2 * p) * rs + 16 * c : toff);
+                    if (BATCH && md2.x != cur) {
+                        flush();
+                        cur = md2.x;
+                    }
                     uint32_t acc = 0;
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
@@ -236,7 +281,14 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                         const uint32_t lft = __shfl_up_sync(0xffffffffu, V[3], 1, 8);
                         const uint32_t rgt = __shfl_down_sync(0xffffffffu, V[0], 1, 8);
                         hsum4(V, c == 0 ? V[4] : lft, c == 7 ? V[4] : rgt, S);
-                        next_state4<ORK>(S, r == 0 ? af[Q] : as[Q], rule, nw);
+                        if constexpr (BATCH) {
+                            if (md2.y)
+                                apply_rule4_ork(S, r == 0 ? af[Q] : as[Q], (uint32_t)md2.y, nw);
+                            else
+                                apply_rule4(S, r == 0 ? af[Q] : as[Q], bt.insts[md2.x].rule, nw);
+                        } else {
+                            next_state4<ORK>(S, r == 0 ? af[Q] : as[Q], rule, nw);
+                        }
                         if (partial) {
                             const int cnt = md.z - tq - r;  // cells of the chunk in the domain
                             if (cnt < 16) {
@@ -245,9 +297,9 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                                 for (int w = 0; w < 4; ++w)
                                     nw[w] &= __funnelshift_rc(0xffffffffu, 0u, (uint32_t)max(0, 32 * w + 32 - c8));
                             }
-                            if (cnt > 0) store16(dst + r * side, nw);
+                            if (cnt > 0) store16(dst + r * rs, nw);
                         } else {
-                            store16(dst + r * side, nw);
+                            store16(dst + r * rs, nw);
                         }
                         acc += (nw[0] + nw[1]) + (nw[2] + nw[3]);
                     }
@@ -260,6 +312,7 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
             }
             if (stop) break;
         }
+        if (BATCH) flush();
     }
 
     __syncthreads();
@@ -280,10 +333,10 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
             __threadfence();
         }
     }
-    if (live) block_add_u64(live, lsum, red);
+    if (!BATCH && live) block_add_u64(live, lsum, red);
 }
 
-template <bool ORK>
+template <bool ORK, bool BATCH>
 static cudaError_t prepare_planes_one()
 {
     static bool attr_set[64] = {false};
@@ -291,15 +344,16 @@ static cudaError_t prepare_planes_one()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(ca3_step_planes<ORK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlSmem);
+    e = cudaFuncSetAttribute(ca3_step_planes<ORK, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlSmem);
     if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
     return e;
 }
 
 cudaError_t ca3_planes_prepare()
 {
-    cudaError_t e = prepare_planes_one<false>();
-    return e != cudaSuccess ? e : prepare_planes_one<true>();
+    cudaError_t e = prepare_planes_one<false, false>();
+    if (e == cudaSuccess) e = prepare_planes_one<true, false>();
+    return e != cudaSuccess ? e : prepare_planes_one<false, true>();
 }
 
 int plane_box_widths(int *w)
@@ -308,25 +362,52 @@ int plane_box_widths(int *w)
     return kPlWidths;
 }
 
+// Resident CTAs of the plane-stream kernel on the current device (SMs x occupancy).
+static cudaError_t planes_resident(uint64_t *out)
+{
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ca3_step_planes<true, false>, kPlThreads,
+                                                           kPlSmem)) != cudaSuccess)
+        return e;
+    *out = (uint64_t)sms * (uint64_t)(occ < 1 ? 1 : occ);
+    return cudaSuccess;
+}
+
 cudaError_t launch_ca3_planes(const PlaneSched &sched, const PlaneMaps &maps, int64_t n, int64_t side, uint8_t *out,
                               const Rule &rule, unsigned long long *live, unsigned long long *queue, cudaStream_t st)
 {
     if (!queue) return cudaErrorInvalidValue;
     cudaError_t e = ca3_planes_prepare();
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, occ = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ca3_step_planes<true>, kPlThreads, kPlSmem)) !=
-        cudaSuccess)
-        return e;
-    if (occ < 1) occ = 1;
-    const uint64_t resident = (uint64_t)sms * (uint64_t)occ;
+    uint64_t resident = 0;
+    if ((e = planes_resident(&resident)) != cudaSuccess) return e;
     const uint64_t g = sched.units < resident ? (sched.units ? sched.units : 1) : resident;
+    const PlaneBatch none = {};
     if (rule.or_k)
-        ca3_step_planes<true><<<(unsigned)g, kPlThreads, kPlSmem, st>>>(maps, out, n, side, rule, sched, live, queue);
+        ca3_step_planes<true, false><<<(unsigned)g, kPlThreads, kPlSmem, st>>>(maps, out, n, side, rule, sched, live,
+                                                                               queue, none);
     else
-        ca3_step_planes<false><<<(unsigned)g, kPlThreads, kPlSmem, st>>>(maps, out, n, side, rule, sched, live, queue);
+        ca3_step_planes<false, false><<<(unsigned)g, kPlThreads, kPlSmem, st>>>(maps, out, n, side, rule, sched,
+                                                                                live, queue, none);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_planes(const PlaneBatch &bt, unsigned long long *queue, cudaStream_t st)
+{
+    if (!queue || !bt.nunits) return bt.nunits ? cudaErrorInvalidValue : cudaSuccess;
+    cudaError_t e = ca3_planes_prepare();
+    if (e != cudaSuccess) return e;
+    uint64_t resident = 0;
+    if ((e = planes_resident(&resident)) != cudaSuccess) return e;
+    const uint64_t g = (uint64_t)bt.nunits < resident ? (uint64_t)bt.nunits : resident;
+    static const PlaneMaps no_maps = {};
+    static const PlaneSched no_sched = {};
+    static const Rule no_rule = {};
+    ca3_step_planes<false, true><<<(unsigned)g, kPlThreads, kPlSmem, st>>>(no_maps, nullptr, 0, 0, no_rule, no_sched,
+                                                                           nullptr, queue, bt);
     return cudaGetLastError();
 }
 

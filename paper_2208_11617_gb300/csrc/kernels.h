@@ -59,6 +59,8 @@ cudaError_t launch_ca3_planes(const PlaneSched &sched, const PlaneMaps &maps, in
                               const Rule &rule, unsigned long long *live, unsigned long long *queue, cudaStream_t st);
 cudaError_t ca3_planes_prepare();
 cudaError_t ca3p_read_status(uint32_t *out);
+// One step of every plane-stream instance of a batch (kBody3plane units).
+cudaError_t launch_batch_planes(const PlaneBatch &bt, unsigned long long *queue, cudaStream_t st);
 
 // Sets the kernels' shared-memory limits for the current device (before any
 // stream capture).

@@ -129,3 +129,20 @@ def test_static_run_checks_arguments_before_any_device_work():
         rc = sx._lib.simplex_batch_run_static(b.handle, ctypes.c_void_p(ptr) if ptr else None, nbytes, parity,
                                               steps, None, None)
         assert rc == sx.SIMPLEX_EINVAL and what in sx.simplex_last_error(), (ptr, nbytes, parity, steps)
+
+
+def test_plane_stream_instances_are_planned():
+    """m = 3 instances with block 128 run as plane streams: the batch plans
+    them (host only), counts their cells, and the allocation-free run refuses
+    them before any device work."""
+    import ctypes
+    insts = [_inst(2, 100, 64), _inst(3, 200, 128), _inst(3, 0, 128), _inst(3, 63, 16)]
+    b = sx.simplex_batch_create(insts)
+    info = sx.simplex_batch_info(b)
+    assert info["cells"] == sum(math.comb(d["n"] + d["m"], d["m"]) for d in insts)
+    assert info["arena_bytes"] > info["grids_bytes"]
+    fake = 1 << 40
+    rc = sx._lib.simplex_batch_run_static(b.handle, ctypes.c_void_p(fake), info["grids_bytes"], 0, 3, None, None)
+    assert rc == sx.SIMPLEX_EUNSUPPORTED and "plane-stream" in sx.simplex_last_error()
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_batch_create([_inst(3, 70000, 128)])

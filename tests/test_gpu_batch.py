@@ -27,9 +27,15 @@ MIXED = [
     _inst(2, 4095, 128, seed=14), _inst(3, 255, 16, seed=15, p=0.3),
     _inst(3, 0, 32, seed=16), _inst(3, 31, 32, seed=17, p=0.3), _inst(3, 100, 32, beta=3, seed=18, p=0.3),
     _inst(3, 200, 32, seed=19, p=0.3), _inst(3, 150, 32, rule=(1 << 4, 1 << 2 | 1 << 3 | 1 << 4), seed=20),
+    # plane-stream instances (block 128): a launch of their own per step
+    _inst(3, 0, 128, seed=24), _inst(3, 1, 128, seed=25), _inst(3, 64, 128, seed=26, p=0.3),
+    _inst(3, 200, 128, seed=27, p=0.3), _inst(3, 150, 128, rule=(1 << 4, 1 << 2 | 1 << 3 | 1 << 4), seed=28),
+    _inst(3, 255, 128, beta=3, seed=29, p=0.3), _inst(3, 300, 128, seed=30, p=0.3),
 ]
 
 ONLY32 = [_inst(3, 64, 32, seed=21, p=0.3), _inst(3, 255, 32, seed=22, p=0.3), _inst(3, 17, 32, seed=23)]
+ONLYPLANE = [_inst(3, 64, 128, seed=31, p=0.3), _inst(3, 255, 128, seed=32, p=0.3), _inst(3, 17, 128, seed=33),
+             _inst(3, 500, 128, seed=34, p=0.3), _inst(3, 2, 128, rule=(1, 0), seed=35, p=0.3)]
 
 
 def _logical(t, n):
@@ -56,8 +62,11 @@ def test_mixed_batch_matches_oracle(use_graph):
     assert sx.simplex_device_status() == 0
 
 
-def test_batch_of_32_cubed_tiles_only_matches_oracle():
-    """A batch whose every instance runs in the second launch set (32^3 tiles)."""
+@pytest.mark.parametrize("insts", [ONLY32, ONLYPLANE], ids=["32cubed", "plane"])
+def test_batch_of_one_launch_set_matches_oracle(insts):
+    """A batch whose every instance runs in the second launch set (32^3 tiles),
+    or in the plane-stream launch (m = 3, block 128)."""
+    ONLY32 = insts
     b = sx.simplex_batch_create(ONLY32)
     sx.simplex_batch_bind(b)
     sx.simplex_batch_init(b)
