@@ -366,7 +366,9 @@ def run_batch(args, rank, world, compact=False):
     maps = []
     for d in ([] if args.no_loop else insts):
         side = (d["n"] + 16) // 16 * 16
-        mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], d["block"], side=side)
+        plane = d["m"] == 3 and d["block"] == 128  # the plane stream: launch 3 of a single instance
+        mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], 32 if plane else d["block"], side=side,
+                                   launch=3 if plane else 0)
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
         bb = torch.zeros_like(a)
         sx.simplex_ca_init(mp, a, d["seed"], d["threshold"])
@@ -574,8 +576,11 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_kind = _peaks()
     res = {}
     if isinstance(wl, inputs.CAWorkload):
+        # m = 3: the plane stream (the fastest form) unless --launch says otherwise;
+        # the other forms are timed beside it below
+        launch = args.launch if (args.launch or wl.m != 3) else 3
         mp = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, band=args.band if wl.m == 2 else None,
-                                   launch=args.launch, layout=args.layout if wl.m == 3 else 0, side=args.side)
+                                   launch=launch, layout=args.layout if wl.m == 3 else 0, side=args.side)
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
@@ -646,6 +651,15 @@ def run_ours(args, rank, world, local):
                                    "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint("ca3_step_planes"),
                                                                    "ca3_step_planes", wl.n)),
                                    "note": "same step, plane-stream form (launch 3)"}
+        if wl.m == 3 and info["launch"] != 1:
+            # the paper's execution model on the same grids: one CTA per block of H3
+            mpg = sx.simplex_map_create(wl.m, wl.n, 2, 2, wl.block, launch=1, layout=args.layout, side=args.side)
+            mg_ms = _per_launch_ms(lambda: sx.simplex_ca_step(mpg, a, nxt, birth, survive, None), 20)[0]
+            ach_g = alg_bytes / (mg_ms * 1e-3) / 1e9
+            kg = f"ca3_step_kernel<{wl.block}>"
+            res["grid_form"] = {"kernel": kg, "launch_ms_mean": mg_ms, "achieved": ach_g, "frac": ach_g / hbm_peak,
+                                "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint(kg), kg, wl.n)),
+                                "note": "same step, one CTA per block of H3 (launch 1, Sec. 4.3 map)"}
         if wl.m == 3 and wl.block == 32 and info["launch"] != 2:
             # the other m = 3 step form on the same grids: persistent CTAs streaming
             # slab columns along x3 (H2 over the tile columns)
@@ -1064,7 +1078,8 @@ def main():
                     help="automaton: padded array side (cells per row, a multiple of 16; default n + 1 rounded up)")
     ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
     ap.add_argument("--launch", type=int, default=0,
-                    help="automaton step form: 0 auto, 1 grid, 2 x-stream, 3 plane stream (m = 3)")
+                    help="automaton step form: 0 auto (m = 3: the plane stream), 1 grid, 2 x-stream, "
+                         "3 plane stream (m = 3)")
     ap.add_argument("--ca-steps", type=int, default=None, help="override automaton steps per bench step")
     ap.add_argument("--layout", type=int, default=0,
                     help="m = 3 H3 layout: 0 packed grid (Sec. 4.3), 1 one block range per stack level")
