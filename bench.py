@@ -48,10 +48,13 @@ _KERNEL_SOURCES = {
     "ca3_step_kernel<32>": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
     "ca3_step_stream": ["k_ca3.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
     "ca3_step_planes": ["k_ca3p.cu", "ca_tiles.cuh", "common.cuh", "hmap.cuh", "rule.h", "tmap.cpp", "kernels.h"],
+    "write_kernel<2>": ["k_write.cu", "common.cuh", "hmap.cuh", "tile.cuh", "kernels.h"],
 }
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (mean of 3 launches
 # at full size), for the kernel sources with the given fingerprint
-_KERNEL_TRAFFIC = {("aec6365a50ef8a26", "ca2_step_kernel<128>", 32767): 1_032_545_877,
+_KERNEL_TRAFFIC = {("7702123f7ad67f6f", "ca2_step_kernel<128>", 32767): 1_032_780_885,
+                   ("ca5d6bc19247a0b1", "ca3_step_planes", 1023): 386_007_979,
+                   ("a64bb17afbc61e81", "write_kernel<2>", 32767): 2_086_039_467,
                    ("464ecdb6afbca9f1", "ca3_step_kernel<32>", 1023): 521_488_810,
                    ("464ecdb6afbca9f1", "ca3_step_stream", 1023): 399_034_453}
 
@@ -752,7 +755,9 @@ def run_ours(args, rank, world, local):
                     "l2": ("arrays of 1 / 4 GiB >> 129 MB L2, no flush" if accum
                            else "array re-written back to back (L2-resident when it fits)")},
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                      "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                      "traffic": None if accum else _KERNEL_TRAFFIC.get(
+                          (_kernel_fingerprint(f"write_kernel<{wl.m}>"), f"write_kernel<{wl.m}>", wl.n)),
                       "kernel": f"{'accum' if accum else 'write'}_kernel<{wl.m}>", "alg_bytes_per_launch": alg_bytes,
                       "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
             clocks=clk, gpu_launches=args.steps * reps,
