@@ -39,8 +39,12 @@ struct RunGraph {
 struct simplex_batch {
     std::vector<simplex_instance_t> spec;
     std::vector<sx::BatchInst> insts;
-    std::vector<sx::BatchItem> items;  // set 0 items, then set 1 items, then count-only items
-    size_t nitems0 = 0, nitems1 = 0;   // end of set 0's items, of set 1's
+    // items of set 0 (m = 3 16^3 tiles, then m = 2 tiles), set 1, count passes only
+    std::vector<sx::BatchItem> items;
+    size_t nitems0_step = 0, nitems0 = 0, nitems1 = 0;  // end of set 0's m = 3 items, of set 0's, of set 1's
+    // m = 2 instances: their blocks holding cells, for the flat pass of a bound batch
+    std::vector<sx::BatchTile> tiles2;
+    uint64_t off_tiles2 = 0;
     // plane-stream instances (kBody3plane): their work units, in instance order
     std::vector<sx::BatchPlaneUnit> punits;
     size_t nplane = 0;
@@ -83,17 +87,24 @@ int enqueue_batch_run(simplex_batch_t b, int steps, unsigned long long *live, in
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(live)");
     }
     sx::PlaneBatch pb = {};
+    BatchExtras ex;
+    ex.nitems1 = b->nitems1;
     if (!b->punits.empty()) {
         pb.insts = insts;
         pb.units = reinterpret_cast<const sx::BatchPlaneUnit *>(b->arena + b->off_punits);
         pb.nunits = (uint32_t)b->punits.size();
         pb.ptmaps = reinterpret_cast<const CUtensorMap *>(b->arena + b->off_ptmaps);
         pb.arena = b->arena;
+        ex.planes = &pb;
+        ex.pqueue = reinterpret_cast<unsigned long long *>(b->arena + b->off_pqueue);
+    }
+    if (!b->tiles2.empty()) {
+        ex.nitems0_step = b->nitems0_step;
+        ex.tiles = reinterpret_cast<const sx::BatchTile *>(b->arena + b->off_tiles2);
+        ex.ntiles = (uint32_t)b->tiles2.size();
     }
     return enqueue_batch_passes(insts, items, b->items.size(), b->nitems0, tmaps, b->arena, queue,
-                                queue + steps + 1, steps, live, parity, st, b->nitems1,
-                                b->punits.empty() ? nullptr : &pb,
-                                reinterpret_cast<unsigned long long *>(b->arena + b->off_pqueue));
+                                queue + steps + 1, steps, live, parity, st, &ex);
 }
 
 }  // namespace
@@ -102,11 +113,14 @@ namespace sxh {
 
 int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items, size_t nitems, size_t nitems0,
                          const CUtensorMap *tmaps, uint8_t *arena, unsigned int *q0, unsigned int *q1, int steps,
-                         unsigned long long *live, int parity, cudaStream_t st, size_t nitems1,
-                         const sx::PlaneBatch *planes, unsigned long long *pqueue)
+                         unsigned long long *live, int parity, cudaStream_t st, const BatchExtras *ex)
 {
     cudaError_t e;
-    if (nitems1 == (size_t)-1) nitems1 = nitems;
+    const BatchExtras none;
+    if (!ex) ex = &none;
+    const size_t nitems1 = ex->nitems1 == (size_t)-1 ? nitems : ex->nitems1;
+    const size_t nstep0 = ex->tiles && ex->nitems0_step != (size_t)-1 ? ex->nitems0_step : nitems0;
+    const sx::PlaneBatch *planes = ex->planes;
     if (live) {
         e = sx::launch_batch_pass(insts, items, (uint32_t)nitems, tmaps, arena, parity, q0, live, steps + 1, 0, true,
                                   st);
@@ -114,10 +128,14 @@ int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items,
     }
     for (int s = 1; s <= steps; ++s) {
         const int in = (parity + s - 1) & 1;
-        if (nitems0) {
-            e = sx::launch_batch_pass(insts, items, (uint32_t)nitems0, tmaps, arena, in, q0 + s, live, steps + 1, s,
+        if (nstep0) {
+            e = sx::launch_batch_pass(insts, items, (uint32_t)nstep0, tmaps, arena, in, q0 + s, live, steps + 1, s,
                                       false, st, nullptr, 0);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
+        }
+        if (ex->tiles && ex->ntiles) {
+            e = sx::launch_batch_flat2(insts, ex->tiles, ex->ntiles, tmaps, arena, in, live, steps + 1, s, st);
+            if (e != cudaSuccess) return cuda_fail(e, "batch step launch (m = 2 tiles)");
         }
         if (nitems1 > nitems0) {
             e = sx::launch_batch_pass(insts, items + nitems0, (uint32_t)(nitems1 - nitems0), tmaps, arena, in, q1 + s,
@@ -130,7 +148,7 @@ int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items,
             pb.live = live;
             pb.live_stride = steps + 1;
             pb.live_index = s;
-            e = sx::launch_batch_planes(pb, pqueue, st);
+            e = sx::launch_batch_planes(pb, ex->pqueue, st);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch (plane stream)");
         }
     }
@@ -173,8 +191,9 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
         return fail(SIMPLEX_ENOMEM, "host allocation failed");
     }
     uint64_t grid_off = 0;
-    std::vector<sx::BatchItem> items1;  // items of launch set 1, appended after set 0's
-    std::vector<sx::BatchItem> items2;  // count-only items (plane-stream instances), appended last
+    std::vector<sx::BatchItem> items0m2;  // set 0 items of m = 2 instances, after set 0's m = 3 items
+    std::vector<sx::BatchItem> items1;    // items of launch set 1, appended after set 0's
+    std::vector<sx::BatchItem> items2;    // count-only items (plane-stream instances), appended last
     for (int i = 0; i < count; ++i) {
         const simplex_instance_t &in = instances[i];
         sx::BatchInst &bi = b->insts[i];
@@ -258,7 +277,10 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
             return ok && sum * bi.plan.rho <= bi.plan.n;
         };
         // plane-stream instances: block items for the count pass only
-        std::vector<sx::BatchItem> &dst = body == sx::kBody3x32 ? items1 : (body == sx::kBody3plane ? items2 : b->items);
+        std::vector<sx::BatchItem> &dst = body == sx::kBody3x32     ? items1
+                                          : body == sx::kBody3plane ? items2
+                                          : in.m == 2               ? items0m2
+                                                                    : b->items;
         for (uint64_t v = 0; v < bi.plan.h_blocks;) {
             if (!holds_cells(v)) {
                 ++v;
@@ -268,11 +290,16 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
             while (v < bi.plan.h_blocks && v - v0 < (uint64_t)sx::kBatchChunk && holds_cells(v)) ++v;
             dst.push_back(sx::BatchItem{(uint32_t)i, (uint32_t)v0, (uint32_t)(v - v0), 0u});
         }
+        if (in.m == 2)
+            for (uint64_t v = 0; v < bi.plan.h_blocks; ++v)
+                if (holds_cells(v)) b->tiles2.push_back(sx::BatchTile{(uint32_t)i, (uint32_t)v});
     }
     // plane units longest first (the queue's last units are the short ones);
     // equal lengths keep instance and slab order
     std::stable_sort(b->punits.begin(), b->punits.end(),
                      [](const sx::BatchPlaneUnit &x, const sx::BatchPlaneUnit &y) { return x.e - x.b > y.e - y.b; });
+    b->nitems0_step = b->items.size();
+    b->items.insert(b->items.end(), items0m2.begin(), items0m2.end());
     b->nitems0 = b->items.size();
     b->items.insert(b->items.end(), items1.begin(), items1.end());
     b->nitems1 = b->items.size();
@@ -291,6 +318,8 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
     off = align_up(off + sizeof(CUtensorMap) * 2ull * (uint64_t)count, 256);
     b->off_queue = off;
     off = align_up(off + sizeof(unsigned int) * 2ull * (uint64_t)(sx::kBatchMaxSteps + 1), 256);
+    b->off_tiles2 = off;
+    off = align_up(off + sizeof(sx::BatchTile) * b->tiles2.size(), 256);
     b->off_punits = off;
     off = align_up(off + sizeof(sx::BatchPlaneUnit) * b->punits.size(), 256);
     b->off_ptmaps = off;
@@ -370,6 +399,10 @@ int simplex_batch_bind(simplex_batch_t b, void *arena, uint64_t arena_bytes, voi
          (e = cudaMemcpyAsync(base + b->off_ptmaps, pmaps.data(), sizeof(sx::PlaneMaps) * pmaps.size(),
                               cudaMemcpyHostToDevice, st)) != cudaSuccess))
         return cuda_fail(e, "binding the batch arena (plane stream)");
+    if (!b->tiles2.empty() &&
+        (e = cudaMemcpyAsync(base + b->off_tiles2, b->tiles2.data(), sizeof(sx::BatchTile) * b->tiles2.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "binding the batch arena (m = 2 tiles)");
     if ((e = cudaMemsetAsync(base + b->off_pqueue, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(base + b->off_insts, b->insts.data(), sizeof(sx::BatchInst) * b->insts.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||

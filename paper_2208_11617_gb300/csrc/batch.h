@@ -42,6 +42,12 @@ struct BatchItem {
 // Salt of the result digest: sum over live cells x of splitmix32(kDigestSalt ^ lin(x)).
 constexpr uint32_t kDigestSalt = 0x00D16E57u;
 
+// One CTA of the batched engine's flat m = 2 launch: block v of instance
+// `inst`'s map (H in trapezoid form, decoded on the device).
+struct BatchTile {
+    uint32_t inst, v;
+};
+
 // One plane-stream work unit of a batch: instance `inst`, brick rows
 // y0 = yx & 0xffff ..., cells x0 = yx >> 16 ..., output planes b ... e.
 struct BatchPlaneUnit {

@@ -54,13 +54,22 @@ struct BatchView {
 // with queue counter q0[s] and set 1 over the rest with q1[s]; a count pass
 // over every item first (queue q0[0]) when `live` is given.  The counters
 // must be zero.
-// Items of set 1 end at nitems1 (the rest, up to nitems, count passes only);
-// with `planes`, every step also runs one plane-stream pass (work counters
-// `pqueue`, zero and left zero).
+// Optional parts of a bound batch's passes.  Items of set 1 end at nitems1
+// (the rest, up to nitems, take part in count passes only).  With `tiles`,
+// set 0's step passes run items [0, nitems0_step) and the m = 2 items after
+// them run as one flat pass over `tiles` instead.  With `planes`, every step
+// also runs one plane-stream pass (work counters `pqueue`, zero and left zero).
+struct BatchExtras {
+    size_t nitems1 = (size_t)-1;
+    size_t nitems0_step = (size_t)-1;
+    const sx::BatchTile *tiles = nullptr;
+    uint32_t ntiles = 0;
+    const sx::PlaneBatch *planes = nullptr;
+    unsigned long long *pqueue = nullptr;
+};
 int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items, size_t nitems, size_t nitems0,
                          const CUtensorMap *tmaps, uint8_t *arena, unsigned int *q0, unsigned int *q1, int steps,
-                         unsigned long long *live, int parity, cudaStream_t st, size_t nitems1 = (size_t)-1,
-                         const sx::PlaneBatch *planes = nullptr, unsigned long long *pqueue = nullptr);
+                         unsigned long long *live, int parity, cudaStream_t st, const BatchExtras *ex = nullptr);
 int batch_view(struct simplex_batch *b, BatchView *out);
 
 }  // namespace sxh

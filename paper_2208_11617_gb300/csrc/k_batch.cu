@@ -280,6 +280,90 @@ __global__ void __launch_bounds__(kBatchThreads, SET ? 3 : 5)
     }
 }
 
+// Flat m = 2 pass: one CTA per block of every m = 2 instance's map that holds
+// cells (tiles[blockIdx.x] names the instance and the block), the launch model
+// of the single-instance step: the CTA decodes its block with the instance's H
+// (trapezoid form), stages the tile plus halo with one TMA load and runs the
+// instance's tile body (64^2 or 128^2).  Consecutive passes are launched with
+// programmatic stream serialization: a CTA decodes before it waits for the
+// previous pass, and lets the next one start once past that wait.
+constexpr int kFlatStage = 160 * 130;  // the 128 x 128 box, the larger of the two bodies
+
+__global__ void __launch_bounds__(kBatchThreads, 10)
+    batch_flat2_kernel(const BatchInst *__restrict__ insts, const BatchTile *__restrict__ tiles,
+                       const CUtensorMap *__restrict__ tmaps, uint8_t *__restrict__ arena, int in_parity,
+                       unsigned long long *__restrict__ live, int live_stride, int live_index)
+{
+    extern __shared__ uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t red[32];
+    uint8_t *tile = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x;
+    const BatchTile bt = tiles[blockIdx.x];
+    const BatchInst &bi = insts[bt.inst];
+    const Plan &p = bi.plan;
+    int32_t X[2] = {0, 0};
+    const bool ok_map = decode<2>(p, kMapH, bt.v, X);
+    const int rho = p.rho;
+    const int64_t y0 = (int64_t)X[0] * rho, x0 = (int64_t)X[1] * rho;
+    const bool partial = y0 + x0 + 2 * (rho - 1) > p.n;
+    const int64_t n = p.n, side = p.side;
+    const CUtensorMap *tm = tmaps + bi.tmap + in_parity;
+    uint8_t *gout = arena + bi.grid[in_parity ^ 1];
+    const bool body128 = bi.body == kBody2x128;
+    if (tid == 0) {
+        prefetch_tmap(tm);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    grid_dep_wait();     // the previous pass writes this pass's input and reads its output
+    grid_dep_trigger();  // the next pass may start (at most one pass ahead)
+    if (!ok_map || y0 + x0 > n) return;  // never listed: every tile of the table holds cells
+    if (tid == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, body128 ? 160u * 130u : 96u * 66u);
+        tma_load_2d(tile, tm, (int32_t)(x0 - 16), (int32_t)(y0 - 1), &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0u, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicOr(&g_batch_status, 4u);
+            mbar_wait_bounded(&bar, 0u, kWaitLimitNs);
+        }
+        return;
+    }
+    const bool ork = bi.rule.or_k != 0;
+    uint32_t my_live;
+    if (body128)
+        my_live = ork ? ca2_tile<128, 8, true>(tile, n, side, bi.rule, gout, x0, y0, partial, tid & 7, tid >> 3)
+                      : ca2_tile<128, 8, false>(tile, n, side, bi.rule, gout, x0, y0, partial, tid & 7, tid >> 3);
+    else
+        my_live = ork ? ca2_tile<64, 2, true>(tile, n, side, bi.rule, gout, x0, y0, partial, tid & 3, tid >> 2)
+                      : ca2_tile<64, 2, false>(tile, n, side, bi.rule, gout, x0, y0, partial, tid & 3, tid >> 2);
+    if (live)
+        block_add_u64(live + (uint64_t)bt.inst * (uint64_t)live_stride + (uint64_t)live_index, my_live, red);
+}
+
+cudaError_t launch_batch_flat2(const BatchInst *insts, const BatchTile *tiles, uint32_t ntiles,
+                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned long long *live,
+                               int live_stride, int live_index, cudaStream_t st)
+{
+    if (!ntiles) return cudaSuccess;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    constexpr int smem = kFlatStage + 128;
+    if (!(dev >= 0 && dev < 64 && attr_set[dev])) {
+        e = cudaFuncSetAttribute(batch_flat2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    return launch_pdl(batch_flat2_kernel, dim3(ntiles), dim3(kBatchThreads), (size_t)smem, st, insts, tiles, tmaps,
+                      arena, in_parity, live, live_stride, live_index);
+}
+
 cudaError_t batch_prepare()
 {
     static bool attr_set[64] = {false};

@@ -89,6 +89,10 @@ cudaError_t launch_batch_pass(const BatchInst *insts, const BatchItem *items, ui
                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned int *queue,
                               unsigned long long *live, int live_stride, int live_index, bool count_only,
                               cudaStream_t st, unsigned long long *digest = nullptr, int set = 0, int pass = 0);
+// The flat m = 2 pass of a bound batch: one CTA per tiles[] entry.
+cudaError_t launch_batch_flat2(const BatchInst *insts, const BatchTile *tiles, uint32_t ntiles,
+                               const CUtensorMap *tmaps, uint8_t *arena, int in_parity, unsigned long long *live,
+                               int live_stride, int live_index, cudaStream_t st);
 cudaError_t batch_read_status(uint32_t *out);
 // CTAs of the batched kernel's launch set resident at once on the current device (SMs x occupancy).
 cudaError_t batch_resident_ctas(uint64_t *out, int set = 0);
