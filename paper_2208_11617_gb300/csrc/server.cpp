@@ -610,8 +610,9 @@ int check_job(const simplex_server *s, const simplex_job_t &sp, int64_t i)
     return SIMPLEX_OK;
 }
 
-// One turn of the serving loop.  Admission: jobs that have arrived, first
-// come first served, as slots and pool memory allow.  Work: with at most
+// One turn of the serving loop.  Retirement of the rounds and chunks that have
+// completed.  Admission: jobs that have arrived, first come first served, as
+// slots and pool memory allow.  Work: with at most
 // direct_jobs jobs resident, a direct chunk for every resident job that has
 // none in flight; otherwise one batched round over those jobs when fewer than
 // max_inflight rounds are queued.  Retirement of the rounds and chunks that
@@ -619,6 +620,15 @@ int check_job(const simplex_server *s, const simplex_job_t &sp, int64_t i)
 // else can progress.  *done += the jobs that finished (done or rejected).
 int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, int64_t *done)
 {
+    // retire what has completed first: a job's results become readable before
+    // this turn spends host time on admissions and launches, and its memory
+    // and slot are free for them
+    int completed = 0;
+    int r = retire(s, false, &completed);
+    if (r < 0) return SIMPLEX_ECUDA;
+    *done += r;
+    if ((r = retire_chunks(s, &completed)) < 0) return SIMPLEX_ECUDA;
+    *done += r;
     const double now = host_ms(s);
     while (!s->pending.empty()) {
         const int64_t j = s->pending.front();
@@ -646,6 +656,10 @@ int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, in
             if (!s->jobs[j].busy) {
                 const int rc = launch_chunk(s, j, st);
                 if (rc) return rc;
+                // a chunk is tens of launches of host time: chunks that complete
+                // meanwhile are retired (their jobs seen done) between two chunks
+                if ((r = retire_chunks(s, &completed)) < 0) return SIMPLEX_ECUDA;
+                *done += r;
             }
         idle_job = false;
     } else if (idle_job && (int)s->inflight.size() < s->prm.max_inflight) {
@@ -655,9 +669,7 @@ int serve_turn(simplex_server *s, cudaStream_t st, bool realtime, bool block, in
         for (int64_t j : s->active) idle_job |= !s->jobs[j].busy;
         idle_job = idle_job && (int)s->inflight.size() < s->prm.max_inflight;
     }
-    int completed = 0;
-    int r = retire(s, false, &completed);
-    if (r < 0) return SIMPLEX_ECUDA;
+    if ((r = retire(s, false, &completed)) < 0) return SIMPLEX_ECUDA;
     *done += r;
     if ((r = retire_chunks(s, &completed)) < 0) return SIMPLEX_ECUDA;
     *done += r;
@@ -811,9 +823,12 @@ int simplex_server_run(simplex_server_t s, const simplex_job_t *jobs, const doub
     int64_t done = 0;
     while (done < count) {
         if ((rc = serve_turn(s, st, realtime != 0, true, &done))) return rc;
-        if (s->active.empty() && s->inflight.empty() && !s->pending.empty() && realtime) {
-            // sleep until 0.2 ms before the next arrival, then spin: a sleep can
-            // overshoot by tens of microseconds, which would add to that job's latency
+        if (s->active.empty() && s->inflight.empty() && s->chunks.empty() && !s->pending.empty() && realtime) {
+            // nothing on the GPU (a job's last chunk is not in the active set,
+            // so chunks are checked too: sleeping past one would hold its
+            // completion until the next arrival): sleep until 0.2 ms before the
+            // next arrival, then spin: a sleep can overshoot by tens of
+            // microseconds, which would add to that job's latency
             const double wait_ms = s->jobs[s->pending.front()].arrival_ms - host_ms(s);
             if (wait_ms > 0.3)
                 std::this_thread::sleep_for(std::chrono::microseconds((int64_t)((wait_ms - 0.2) * 1000)));
