@@ -262,7 +262,19 @@ def _workload(name, args=None):
     return wl
 
 
+def _single_grid_blocks(info):
+    """CUDA blocks of the write, ACCUM, MAP and EDM launches: they take the
+    single Eq. map2d grid on the power-of-two side for m = 2 and r = 1/2,
+    whatever the plan's trapezoid band (which the automaton uses)."""
+    if info["m"] == 2 and info["r_inv"] == 2 and info["band"]:
+        N = info["N"]
+        return (N // 2) * (N - 1) + N
+    return info["h_blocks"]
+
+
 def _map_name(info):
+    if info["m"] == 2 and info.get("r_inv") == 3:
+        return "H with r=1/3, beta=3: three squares and three triangles per split, power-of-three lattice"
     if info["m"] == 2 and info["band"]:
         return f"H, trapezoid bands of {info['band']} tile rows (r=1/2, beta=2)"
     if info["m"] == 2:
@@ -696,8 +708,10 @@ def run_ours(args, rank, world, local):
                       "array_bytes": mp.numel}
         assert sx.simplex_device_status() == 0
     else:
-        beta = 2 if wl.m <= 3 else wl.m
-        mp = sx.simplex_map_create(wl.m, wl.n, 2, beta, wl.block, band=args.band if wl.m == 2 else None)
+        r_inv = args.r_inv if wl.m == 2 else 2
+        beta = 3 if r_inv == 3 else (2 if wl.m <= 3 else wl.m)
+        mp = sx.simplex_map_create(wl.m, wl.n, r_inv, beta, wl.block,
+                                   band=(args.band if r_inv == 2 else -1) if wl.m == 2 else None)
         info = sx.simplex_map_info(mp)
         cells = info["cells"]
         out = torch.zeros(mp.numel, dtype=torch.int32, device="cuda")
@@ -765,7 +779,7 @@ def run_ours(args, rank, world, local):
                 "kernel_speedup_h_over_bb": mean_bb / mean_ms},
             bb_thread={"launch_ms_mean": mean_bbt, "kernel_speedup_h_over_bb_thread": mean_bbt / mean_ms,
                        "note": "bounding box with a per-thread filter only (the paper's baseline)"},
-            blocks={"h": info["h_blocks"], "bb": info["bb_blocks"], "useful": info["useful_blocks"]},
+            blocks={"h": _single_grid_blocks(info), "bb": info["bb_blocks"], "useful": info["useful_blocks"]},
         )
         meter = EnergyMeter(torch.cuda.current_device())
         res["energy"] = {
@@ -814,8 +828,10 @@ def run_diag(args, wl, rank, world):
     import torch
     from paper_2208_11617_gb300 import simplex as sx
     hbm_peak, peak_kind = _peaks()
-    beta = 2 if wl.m <= 3 else wl.m
-    mp = sx.simplex_map_create(wl.m, wl.n, 2, beta, wl.block, band=args.band if wl.m == 2 else None,
+    r_inv = args.r_inv if wl.m == 2 else 2
+    beta = 3 if r_inv == 3 else (2 if wl.m <= 3 else wl.m)
+    mp = sx.simplex_map_create(wl.m, wl.n, r_inv, beta, wl.block,
+                               band=(args.band if r_inv == 2 else -1) if wl.m == 2 else None,
                                layout=args.layout if wl.m == 3 else 0)
     info = sx.simplex_map_info(mp)
     cells = info["cells"]
@@ -861,8 +877,8 @@ def run_diag(args, wl, rank, world):
             "kernel_speedup_h_over_bb": mean_bb / mean_ms},
         bb_thread={"launch_ms_mean": mean_bbt, "kernel_speedup_h_over_bb_thread": mean_bbt / mean_ms,
                    "note": "bounding box with a per-thread filter only (the paper's baseline)"},
-        blocks={"h": info["h_blocks"], "bb": info["bb_blocks"], "useful": info["useful_blocks"],
-                "bb_over_h": info["bb_blocks"] / info["h_blocks"]},
+        blocks={"h": _single_grid_blocks(info), "bb": info["bb_blocks"], "useful": info["useful_blocks"],
+                "bb_over_h": info["bb_blocks"] / _single_grid_blocks(info)},
     )
     meter = EnergyMeter(torch.cuda.current_device())
     res["energy"] = {
@@ -1082,6 +1098,8 @@ def main():
     ap.add_argument("--side", type=int, default=None,
                     help="automaton: padded array side (cells per row, a multiple of 16; default n + 1 rounded up)")
     ap.add_argument("--band", type=int, default=None, help="m = 2: trapezoid band height (-1: single H2 grid)")
+    ap.add_argument("--r-inv", type=int, default=2, choices=[2, 3],
+                    help="write, ACCUM, MAP, EDM with m = 2: scale factor 1/r of the map (3: the r = 1/3, beta = 3 map)")
     ap.add_argument("--launch", type=int, default=0,
                     help="automaton step form: 0 auto (m = 3: the plane stream), 1 grid, 2 x-stream, "
                          "3 plane stream (m = 3)")

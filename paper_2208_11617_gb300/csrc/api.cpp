@@ -106,12 +106,18 @@ int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, i
 {
     if (m < 2 || m > 4) return fail(SIMPLEX_EINVAL, "m must be 2, 3 or 4 (got %d)", m);
     if (n < 0) return fail(SIMPLEX_EINVAL, "n must be >= 0 (got %lld)", (long long)n);
-    if (r_inv != 2)
-        return fail(SIMPLEX_EUNSUPPORTED, "only r = 1/2 (r_inv = 2) is implemented (got r_inv = %d)", r_inv);
-    const bool beta_ok = (m == 2 && beta == 2) || (m == 3 && (beta == 2 || beta == 3)) || (m == 4 && beta == 4);
+    if (r_inv != 2 && !(r_inv == 3 && m == 2))
+        return fail(SIMPLEX_EUNSUPPORTED,
+                    "r = 1/%d is not implemented for m = %d (r = 1/2 for every m, r = 1/3 for m = 2)", r_inv, m);
+    const bool beta_ok = r_inv == 3 ? beta == 3
+                                    : (m == 2 && beta == 2) || (m == 3 && (beta == 2 || beta == 3)) ||
+                                          (m == 4 && beta == 4);
     if (!beta_ok)
         return fail(SIMPLEX_EUNSUPPORTED,
-                    "beta = %d does not give a covering map for m = %d (m=2: 2; m=3: 2 or 3; m=4: 4)", beta, m);
+                    "beta = %d does not give a covering map for m = %d, r = 1/%d (r = 1/2: m=2: 2; m=3: 2 or 3; "
+                    "m=4: 4; r = 1/3, m = 2: 3)", beta, m, r_inv);
+    if (r_inv == 3 && band > 0)
+        return fail(SIMPLEX_EINVAL, "the trapezoid form (band > 0) is an r = 1/2 map; r = 1/3 takes band 0 or -1");
     if (!is_pow2(block) || block < 4 || block > 256)
         return fail(SIMPLEX_EINVAL, "block must be a power of two in [4, 256] (got %d)", block);
     if (side < n + 1) return fail(SIMPLEX_EINVAL, "side (%lld) must be >= n + 1", (long long)side);
@@ -140,11 +146,22 @@ int build_plan(int m, int64_t n, int r_inv, int beta, int block, int64_t side, i
     p->n = n;
     p->side = side;
     p->bb_blocks = ipow((uint64_t)N, m);
+    p->rinv = r_inv;
     p->seg_len = (int32_t)(N < kStreamRun ? N : kStreamRun);
     const uint64_t h2 = sx::h2_cover_blocks((int32_t)N);
     if (m != 2 && band > 0)
         return fail(SIMPLEX_EINVAL, "band (trapezoid height) applies to m = 2 only (got %d for m = %d)", band, m);
-    if (m == 2 && band > 0) {
+    if (r_inv == 3) {
+        int64_t N3 = 1;
+        int L3 = 0;
+        while (N3 < nb) {
+            N3 *= 3;
+            ++L3;
+        }
+        p->N3 = (int32_t)N3;
+        p->L3 = L3;
+        p->h_blocks = (uint64_t)N3 * (uint64_t)(N3 + 1) / 2;
+    } else if (m == 2 && band > 0) {
         if (!is_pow2(band) || band > 32768)
             return fail(SIMPLEX_EINVAL, "band must be a power of two <= 32768 (got %d)", band);
         const int64_t Ne = (nb + band - 1) / band * band;
@@ -412,7 +429,7 @@ int simplex_map_create_ex(const simplex_map_params_t *params, simplex_map_t *out
                     params->launch);
     const int64_t side = params->side ? params->side : params->n + 1;
     int band = params->band;
-    if (band == 0) band = params->m == 2 ? kDefaultBand : 0;  // automatic
+    if (band == 0) band = (params->m == 2 && params->r_inv == 2) ? kDefaultBand : 0;  // automatic
     if (band < 0) band = 0;                                   // single H2 grid
     sx::Plan p;
     if (params->layout != 0 && !(params->layout == 1 && params->m == 3 && params->beta == 2))
@@ -495,9 +512,14 @@ int simplex_map_info(simplex_map_t map, simplex_map_info_t *out)
     }
     out->h_blocks = p.h_blocks;
     out->bb_blocks = p.bb_blocks;
-    // Eq. generic-m with r = 1/2: (N^m - beta^log2 N) / (2^m - beta)
-    out->h_set_blocks = (ipow((uint64_t)p.N, p.m) - ipow((uint64_t)p.beta, p.logN)) /
-                        ((uint64_t(1) << p.m) - (uint64_t)p.beta);
+    // Eq. generic-m with r = 1/2: (N^m - beta^log2 N) / (2^m - beta); the
+    // r = 1/3 map of m = 2 lays three squares per split instead of one:
+    // 3 (N3^2 - 3^L3) / (3^2 - 3)
+    if (p.rinv == 3)
+        out->h_set_blocks = 3 * ((uint64_t)p.N3 * (uint64_t)p.N3 - ipow(3, p.L3)) / 6;
+    else
+        out->h_set_blocks = (ipow((uint64_t)p.N, p.m) - ipow((uint64_t)p.beta, p.logN)) /
+                            ((uint64_t(1) << p.m) - (uint64_t)p.beta);
     return SIMPLEX_OK;
 }
 

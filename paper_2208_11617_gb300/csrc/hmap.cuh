@@ -77,7 +77,12 @@ struct Plan {
     // m = 3, beta = 2: 0 = the single packed grid of Sec. 4.3 (the layer of
     // height N/4 with per-level exits), 1 = one block range per stack level
     // (the fully efficient form of Sec. 4.3: no waste)
-    int32_t h3_exact, pad2_;
+    int32_t h3_exact;
+    // scale factor of the map: rinv = 1/r, 2 (every map above) or 3 (m = 2,
+    // beta = 3: h2_r3 on the lattice of N3 = 3^L3 tiles per axis; the bounding
+    // box keeps the power-of-two lattice N)
+    int32_t rinv;
+    int32_t N3, L3;
     uint64_t h_blocks;   // CUDA blocks of one H launch
     uint64_t bb_blocks;  // N^m
     // H3 (beta = 2): region sizes
@@ -134,14 +139,64 @@ SX_HD bool h2_cover(uint64_t v, int32_t N, int32_t logN, int32_t *X)
     return true;
 }
 
+// m = 2 with r = 1/3, beta = 3 (Sec. 6 with 1/r = 3): the block triangle
+// X1 + X2 <= N3 - 1 of side N3 = 3s is three squares of side s -- at (0, 0),
+// (s, 0) and (0, s) -- and three triangles of side s at (2s, 0), (0, 2s) and
+// (s, s), each split the same way; the triangles of side 1 are the blocks of
+// the diagonal X1 + X2 = N3 - 1.  Level k (1 ... L3) holds 3^k squares of
+// side b = N3 / 3^k, numbered triangle by triangle (the triangle's index in
+// base 3, least significant digit = the last split, picks its corner at each
+// split) and square by square; the N3 diagonal blocks follow.  The squares
+// and the diagonal cover the triangle exactly once: N3 (N3 + 1) / 2 blocks.
+// Integer arithmetic only (divisions by powers of three, no roots).
+SX_HD bool h2_r3(int32_t N3, int32_t L3, uint64_t v, int32_t *X)
+{
+    uint64_t tris = 1;  // triangles the level's squares lie in: 3^(k-1)
+    int64_t b = N3;
+    for (int k = 1; k <= L3; ++k) {
+        b /= 3;  // side of this level's squares
+        const uint64_t bb = (uint64_t)b * (uint64_t)b, level = 3 * tris * bb;
+        if (v < level) {
+            const uint64_t sq = v / bb, loc = v - sq * bb;
+            uint64_t t = sq / 3;
+            const int q = (int)(sq - 3 * t);
+            int64_t o1 = q == 1 ? b : 0, o2 = q == 2 ? b : 0;
+            for (int64_t s = 3 * b, i = 1; i < k; ++i, s *= 3) {  // the triangle's corners, last split first
+                const uint64_t d = t % 3;
+                t /= 3;
+                o1 += d == 0 ? 2 * s : (d == 2 ? s : 0);
+                o2 += d == 1 ? 2 * s : (d == 2 ? s : 0);
+            }
+            X[0] = (int32_t)(o1 + (int64_t)(loc / (uint64_t)b));
+            X[1] = (int32_t)(o2 + (int64_t)(loc % (uint64_t)b));
+            return true;
+        }
+        v -= level;
+        tris *= 3;
+    }
+    if (v >= (uint64_t)N3) return false;
+    int64_t o1 = 0, o2 = 0;
+    uint64_t t = v;
+    for (int64_t s = 1, i = 0; i < L3; ++i, s *= 3) {
+        const uint64_t d = t % 3;
+        t /= 3;
+        o1 += d == 0 ? 2 * s : (d == 2 ? s : 0);
+        o2 += d == 1 ? 2 * s : (d == 2 ? s : 0);
+    }
+    X[0] = (int32_t)o1;
+    X[1] = (int32_t)o2;
+    return true;
+}
+
 // The plan with the single Eq. map2d grid (plus its diagonal row) on the
 // power-of-two side N for m = 2, whatever its band: the kernels without a
 // stencil (write, MAP, EDM) have no halo to keep in L2, so they take the
 // paper's map and its clz-only decode instead of the trapezoid form's search.
+// (An r = 1/3 plan has no band and keeps its own map.)
 SX_HD Plan single_grid(const Plan &p)
 {
     Plan q = p;
-    if (q.m == 2 && q.band) {
+    if (q.m == 2 && q.band && q.rinv != 3) {
         q.band = 0;
         q.log_band = 0;
         q.h_blocks = h2_cover_blocks(q.N);
@@ -512,7 +567,10 @@ SX_HD bool decode(const Plan &p, int kind, uint64_t v, int32_t *X)
             X[M - 1 - i] = (int32_t)((v >> (i * p.logN)) & (uint64_t)(p.N - 1));
         return true;
     }
-    if (M == 2) return p.band ? h2_trapezoids(p, v, X) : h2_cover(v, p.N, p.logN, X);
+    if (M == 2) {
+        if (p.rinv == 3) return h2_r3(p.N3, p.L3, v, X);
+        return p.band ? h2_trapezoids(p, v, X) : h2_cover(v, p.N, p.logN, X);
+    }
     if (M == 3 && p.beta == 2) return p.h3_exact ? h3_exact(p, v, X) : h3_cover(p, v, X);
     return Cover<M>::run(p, v, X);
 }

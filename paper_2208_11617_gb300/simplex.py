@@ -243,7 +243,8 @@ class SimplexMap:
 def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, block: int = 16,
                        side: int | None = None, band: int | None = None, launch: int = 0,
                        layout: int = 0) -> SimplexMap:
-    """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4).
+    """Plan H for Delta_n^m (beta defaults to the paper's 2 for m <= 3, m for m = 4, and to 3 for the
+    r = 1/3 map of m = 2, r_inv = 3).
 
     band (m = 2): None/0 automatic trapezoid bands, > 0 band height, -1 the
     single grid of Eq. map2d.  launch: 0 automatic, 1 grid, 2 x-stream
@@ -251,7 +252,7 @@ def simplex_map_create(m: int, n: int, r_inv: int = 2, beta: int | None = None, 
     persistent CTAs streaming bricks along x1).  layout (m = 3, beta = 2): 0 packed grid, 1 one block
     range per stack level."""
     if beta is None:
-        beta = 2 if m <= 3 else m
+        beta = 3 if r_inv == 3 else (2 if m <= 3 else m)
     h = _vp()
     if band is not None or launch or layout:
         prm = SimplexMapParams(m, r_inv, beta, block, n, side or 0, band or 0, launch, layout)

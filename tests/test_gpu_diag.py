@@ -54,6 +54,15 @@ def test_map_test_maps_every_cell_once(m, n, block, mode):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("n,block", [(1023, 16), (1295, 16), (32767, 16), (17, 4)])
+def test_map_test_r_third_maps_every_cell_once(n, block):
+    """MAP on the r = 1/3 map of m = 2: C(n + 2, 2) cells, each once."""
+    mp = sx.simplex_map_create(2, n, 3, 3, block)
+    cells = torch.zeros(1, dtype=torch.int64, device=DEV)
+    sx.simplex_map_test(mp, cells)
+    assert int(cells.item()) == math.comb(n + 2, 2)
+
+
 def test_map_test_rejects_blocks_over_1024_threads():
     mp = sx.simplex_map_create(3, 100, 2, 2, 16)
     with pytest.raises(sx.SimplexError):

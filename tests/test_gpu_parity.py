@@ -610,3 +610,41 @@ def test_h3_level_layout_matches_oracle(n, block, side):
         got, rest = _logical(out, mp, n)
         np.testing.assert_array_equal(got.view(np.uint32), oracle.write(3, n, 5))
         assert not rest.any()
+
+
+# ---------------------------------------------------------------- r = 1/3, beta = 3 (m = 2)
+@pytest.mark.parametrize("n,block,side", [(1023, 16, None), (1000, 16, 1004), (1295, 16, None), (35, 4, None),
+                                          (0, 16, None), (400, 8, None)])
+def test_r_third_write_and_visits_match_oracle(n, block, side):
+    """The m = 2 map with r = 1/3, beta = 3: the write test gives the
+    oracle's array, every block holding cells is visited once and every cell
+    of the domain once (nothing outside)."""
+    mp = sx.simplex_map_create(2, n, 3, 3, block, side=side)
+    assert mp.info.r_inv == 3
+    out = torch.zeros(mp.numel, dtype=torch.int32, device=DEV)
+    sx.simplex_write(mp, out, 91)
+    got, rest = _logical(out, mp, n)
+    np.testing.assert_array_equal(got.view(np.uint32), oracle.write(2, n, 91))
+    assert not rest.any()
+    nb = (n + block) // block
+    blk = torch.zeros(nb * nb, dtype=torch.int32, device=DEV)
+    sx.simplex_visit_count(mp, blk, sx.SIMPLEX_LEVEL_BLOCK)
+    np.testing.assert_array_equal(blk.view(nb, nb).cpu().numpy().astype(np.uint32), oracle.block_indicator(2, n, block))
+    cell = torch.zeros(mp.numel, dtype=torch.int32, device=DEV)
+    sx.simplex_visit_count(mp, cell, sx.SIMPLEX_LEVEL_CELL)
+    c = cell.view(mp.shape).cpu().numpy()
+    np.testing.assert_array_equal(c, (np.indices(c.shape).sum(0) <= n).astype(np.int32))
+
+
+@pytest.mark.parametrize("n,block,side", [(1023, 64, None), (500, 32, 512), (1295, 128, 1296)])
+def test_r_third_automaton_matches_oracle(n, block, side):
+    """The automaton step on the r = 1/3 map (one CTA per block of the map)
+    gives the oracle's grids and live counts."""
+    mp = sx.simplex_map_create(2, n, 3, 3, block, side=side)
+    thr = inputs.bernoulli_threshold(0.5)
+    fin, live = _gpu_run(mp, n, 9, inputs.B3S23, 41, thr, sx.SIMPLEX_MODE_H)
+    got, rest = _logical(fin, mp, n)
+    ref, ref_live = oracle.ca_run(2, n, 9, *inputs.B3S23, oracle.ca_init(2, n, 41, thr))
+    np.testing.assert_array_equal(got, ref)
+    assert not rest.any()
+    np.testing.assert_array_equal(live, ref_live)

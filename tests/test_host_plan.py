@@ -454,3 +454,62 @@ def test_null_handles_and_outputs_are_rejected():
     for name, rc in got.items():
         want = sx.SIMPLEX_OK if name.endswith("_destroy") else sx.SIMPLEX_EINVAL
         assert rc == want, (name, rc)
+
+
+
+# ---------------------------------------------------------------- r = 1/3, beta = 3 (m = 2)
+def _n3(n, rho):
+    nb, N3 = (n + rho) // rho, 1
+    while N3 < nb:
+        N3 *= 3
+    return N3
+
+
+@pytest.mark.parametrize("n,rho", [(0, 4), (3, 4), (11, 4), (35, 4), (100, 4), (107, 4), (323, 4), (400, 8),
+                                   (1295, 16)])
+def test_r_third_map_covers_each_block_exactly_once(n, rho):
+    """The m = 2 map with r = 1/3, beta = 3 (three squares and three triangles
+    per split) sends its N3 (N3 + 1) / 2 CUDA blocks one-to-one onto the block
+    triangle X1 + X2 <= N3 - 1 of the power-of-three lattice, the diagonal
+    blocks last; a block holds cells iff rho (X1 + X2) <= n."""
+    mp = sx.simplex_map_create(2, n, 3, 3, rho)
+    info = mp.info
+    N3 = _n3(n, rho)
+    assert info.r_inv == 3 and info.h_blocks == N3 * (N3 + 1) // 2
+    assert info.h_set_blocks == (N3 * N3 - N3) // 2
+    seen = collections.Counter()
+    valid = 0
+    for v in range(info.h_blocks):
+        X, ok = sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)
+        assert X[0] >= 0 and X[1] >= 0 and X[0] + X[1] <= N3 - 1
+        assert ok == (rho * (X[0] + X[1]) <= n)
+        if v >= info.h_blocks - N3:
+            assert X[0] + X[1] == N3 - 1  # the diagonal comes last
+        seen[X] += 1
+        valid += ok
+    assert len(seen) == info.h_blocks and max(seen.values()) == 1
+    assert valid == info.useful_blocks == math.comb(n // rho + 2, 2)
+
+
+def test_r_third_map_first_level_layout():
+    """N3 = 9: the first 27 blocks are the three 3 x 3 squares at (0, 0),
+    (3, 0), (0, 3) -- the split of Sec. 6 with 1/r = 3 -- row by row."""
+    mp = sx.simplex_map_create(2, 35, 3, 3, 4)  # 9 tiles per axis
+    got = [sx.simplex_map_block(mp, sx.SIMPLEX_MODE_H, v)[0] for v in range(27)]
+    want = [(o1 + i, o2 + j) for (o1, o2) in ((0, 0), (3, 0), (0, 3)) for i in range(3) for j in range(3)]
+    assert got == want
+
+
+def test_r_third_refusals_and_padding():
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_map_create(3, 100, 3, 3, 16)
+    assert ei.value.code == sx.SIMPLEX_EUNSUPPORTED
+    with pytest.raises(sx.SimplexError) as ei:
+        sx.simplex_map_create(2, 100, 3, 2, 16)
+    assert ei.value.code == sx.SIMPLEX_EUNSUPPORTED
+    with pytest.raises(sx.SimplexError):
+        sx.simplex_map_create(2, 100, 3, 3, 16, band=4)
+    # n + 1 = 81 tiles: r = 1/3 needs no padding, r = 1/2 pads to 128 tiles
+    third, half = sx.simplex_map_create(2, 1295, 3, 3, 16), sx.simplex_map_create(2, 1295, 2, 2, 16, band=-1)
+    assert third.info.h_blocks == third.info.useful_blocks == 3321
+    assert half.info.h_blocks == 64 * 127 + 128
