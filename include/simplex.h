@@ -88,7 +88,13 @@ typedef struct simplex_map_info {
  *   m      2, 3 or 4.
  *   n      >= 0.
  *   r_inv  1/r, the scale factor of the self-similar set (Sec. 6, Eq.
- *          generic-m); only 2 (r = 1/2, the paper's value) is implemented.
+ *          generic-m): 2 (r = 1/2, the paper's value) for every m, or 3 for
+ *          m = 2 with beta = 3: the block triangle of side 3s is split into
+ *          three squares of side s, at (0, 0), (s, 0) and (0, s), and three
+ *          triangles of side s, at (2s, 0), (0, 2s) and (s, s), each split
+ *          again; the lattice side is the power of three at or above
+ *          ceil((n+1)/rho) and the map covers its triangle, diagonal
+ *          included, with N3 (N3 + 1) / 2 blocks (band must be 0 or -1).
  *   beta   replication factor (Sec. 6).  m = 2: 2 (Eq. map2d, Thm. 1).
  *          m = 3: 2 (the packed map with the hinge of Sec. 4.3) or 3 (every
  *          corner recursed, no hinge).  m = 4: 4 (every corner recursed;
@@ -96,10 +102,10 @@ typedef struct simplex_map_info {
  *   block  tile side rho in cells, a power of two in [4, 256].
  *   out    receives the new map.
  * Allocates host memory only.  The lattice side N is the power of two at or
- * above ceil((n+1)/rho) (n padded from above, Sec. 4.2); tiles past the
- * domain exit at once.  Errors: SIMPLEX_EINVAL for a bad argument,
- * SIMPLEX_EUNSUPPORTED for r_inv != 2 or a beta the library does not map,
- * SIMPLEX_ENOMEM.
+ * above ceil((n+1)/rho) (n padded from above, Sec. 4.2; the bounding box uses
+ * it for either r); tiles past the domain exit at once.  Errors:
+ * SIMPLEX_EINVAL for a bad argument, SIMPLEX_EUNSUPPORTED for an (m, r_inv,
+ * beta) the library does not map, SIMPLEX_ENOMEM.
  */
 int simplex_map_create(int m, int64_t n, int r_inv, int beta, int block, simplex_map_t *out);
 
