@@ -2,8 +2,8 @@
 // the tetrahedron, fixed-dead boundary, Sec. 5.1), plane-stream form
 // (launch 3).
 //
-// Persistent CTAs (kPlCtasPerSm per SM, 128 threads each) take work units
-// from a device counter; a unit is one brick of kPlaneTY rows x2 by kPlaneTX
+// Persistent CTAs (kPlCtasPerSm per SM: four consumer warps and one producer
+// warp each) take work units from a device counter; a unit is one brick of kPlaneTY rows x2 by kPlaneTX
 // cells x3 over one segment of planes x1 (plane_unit_decode).  The CTA
 // streams the brick along x1: every input plane of the brick (its 32 rows and
 // 128 cells plus the one-cell halo: 34 rows of up to 160 bytes, the box
@@ -32,13 +32,18 @@
 // with no domain cell in reach (before x1 = 0, past the brick's apex) is not
 // loaded at all.
 //
-// The producer is thread 0: after the CTA's barrier that ends the reads of
-// stage s it refills s with the plane kPlSlots ahead, fetching the next unit
-// from the counter one unit in advance.  A unit of output planes b ... e
-// stages planes b - 1 ... e + 1; the first two only fill the sums.  Every
-// wait is bounded: a CTA whose wait runs out sets the status word, waits
-// (bounded) for the loads it issued and leaves.  The last CTA to finish puts
-// the counter back to zero.
+// The producer is lane 0 of the last warp.  Each stage has a `full` mbarrier
+// (the producer's arrival with the load's bytes, or a plain arrival for a
+// plane it does not load) and an `empty` one (one arrival per consumer warp
+// once the warp has read the stage); the producer refills stage s with the
+// plane kPlSlots ahead as soon as `empty` says every consumer warp is done
+// with it, fetching the next unit from the counter one unit in advance, so
+// the consumer warps never wait for one another.  A unit of output planes
+// b ... e stages planes b - 1 ... e + 1; the first two only fill the sums.
+// Every wait is bounded: a warp whose wait runs out sets an abort flag that
+// stops the others, the CTA records the status word, waits (bounded) for the
+// loads it issued and leaves.  The last CTA to finish puts the counter back
+// to zero.
 #include "ca_tiles.cuh"
 #include "common.cuh"
 #include "hmap.cuh"
