@@ -275,11 +275,28 @@ int ensure_queue(simplex_map_t map)
             return fail(SIMPLEX_EINVAL, "the map's work counters live on device %d, not %d", map->queue_device, dev);
         return SIMPLEX_OK;
     }
+    // two counters, then (plane stream) the segment tables of the three map
+    // kinds, which the kernel's producer searches through L1
+    const size_t tables = map->plan.persistent == 2 ? 3 * sx::kPlaneSegWords * sizeof(int32_t) : 0;
     void *q = nullptr;
-    if ((e = cudaMalloc(&q, 2 * sizeof(unsigned long long))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(work counters)");
+    if ((e = cudaMalloc(&q, 2 * sizeof(unsigned long long) + tables)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(work counters)");
     if ((e = cudaMemset(q, 0, 2 * sizeof(unsigned long long))) != cudaSuccess) {
         cudaFree(q);
         return cuda_fail(e, "cudaMemset(work counters)");
+    }
+    if (tables) {
+        std::vector<int32_t> h(3 * sx::kPlaneSegWords, 0);
+        for (int k = 0; k < 3; ++k) {
+            std::memcpy(h.data() + k * sx::kPlaneSegWords, map->sched[k]->seg_b, sizeof(map->sched[k]->seg_b));
+            std::memcpy(h.data() + k * sx::kPlaneSegWords + sx::kPlaneSegTable, map->sched[k]->seg_u,
+                        sizeof(map->sched[k]->seg_u));
+        }
+        e = cudaMemcpy(static_cast<unsigned long long *>(q) + 2, h.data(), tables, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(q);
+            return cuda_fail(e, "cudaMemcpy(plane-stream segment tables)");
+        }
     }
     map->queue = static_cast<unsigned long long *>(q);
     map->queue_device = dev;
@@ -295,7 +312,9 @@ int step_once(simplex_map_t map, const uint8_t *in, uint8_t *out, const sx::Rule
     if (p.m == 3 && p.persistent == 2) {
         sx::PlaneMaps maps;
         if ((rc = make_plane_maps(p, in, &maps))) return rc;
-        cudaError_t e = sx::launch_ca3_planes(*map->sched[mode], maps, p.n, p.side, out, rule, live, map->queue, st);
+        const int32_t *segs = reinterpret_cast<const int32_t *>(map->queue + 2) + mode * sx::kPlaneSegWords;
+        cudaError_t e =
+            sx::launch_ca3_planes(*map->sched[mode], segs, maps, p.n, p.side, out, rule, live, map->queue, st);
         if (e != cudaSuccess) return cuda_fail(e, "automaton step launch");
         return SIMPLEX_OK;
     }

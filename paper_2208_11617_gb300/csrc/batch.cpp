@@ -95,6 +95,9 @@ int enqueue_batch_run(simplex_batch_t b, int steps, unsigned long long *live, in
         pb.nunits = (uint32_t)b->punits.size();
         pb.ptmaps = reinterpret_cast<const CUtensorMap *>(b->arena + b->off_ptmaps);
         pb.arena = b->arena;
+        pb.all_ork = 1;
+        for (const auto &bi : b->insts)
+            if (bi.body == sx::kBody3plane && !bi.rule.or_k) pb.all_ork = 0;
         ex.planes = &pb;
         ex.pqueue = reinterpret_cast<unsigned long long *>(b->arena + b->off_pqueue);
     }

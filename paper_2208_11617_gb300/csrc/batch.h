@@ -70,6 +70,7 @@ struct PlaneBatch {
     const BatchPlaneUnit *units;
     uint32_t nunits;
     int32_t in_parity;           // grid each instance reads; the result goes to the other
+    int32_t all_ork;             // every plane-stream instance has an or-k rule (Rule::or_k)
     const CUtensorMap *ptmaps;   // the plane maps of every kBody3plane instance
     uint8_t *arena;              // grid offsets count from here
     unsigned long long *live;    // live[inst * live_stride + live_index] += live cells written

@@ -227,6 +227,48 @@ __device__ __forceinline__ void next_state4(const uint32_t s[4], const uint32_t 
         apply_rule4(s, alive, r, nw);
 }
 
+// Dead-byte words of a 16-cell chunk of which the first `cnt` cells lie in the
+// domain: bit 7 of byte i of dead[w] is set iff 4 w + i >= cnt.  Byte i of
+// word w holds 4 w + i + 128 - min(max(cnt, 0), 16), which stays in
+// 112 ... 143 (no carries) and reaches 128 exactly from cell cnt on.
+__device__ __forceinline__ void chunk_dead4(int cnt, uint32_t dead[4])
+{
+    const uint32_t k = (uint32_t)(128 - min(max(cnt, 0), 16)) * 0x01010101u;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) dead[w] = k + (0x03020100u + 0x04040404u * (uint32_t)w);
+}
+
+// apply_rule4_ork / apply_rule4 with the bytes whose bit 7 is set in dead[]
+// forced to 0 (cells past the domain's edge).
+__device__ __forceinline__ void apply_rule4_ork_masked(const uint32_t s[4], const uint32_t alive[4], uint32_t kbytes,
+                                                       const uint32_t dead[4], uint32_t nw[4])
+{
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t c = s[w] - alive[w];
+        const uint32_t y = ((c | alive[w]) ^ kbytes) + 0x7F7F7F7Fu;  // bit 7 set iff byte != k
+        nw[w] = (~(y | dead[w]) >> 7) & 0x01010101u;
+    }
+}
+
+__device__ __forceinline__ void apply_rule4_masked(const uint32_t s[4], const uint32_t alive[4], const Rule &r,
+                                                   const uint32_t dead[4], uint32_t nw[4])
+{
+    apply_rule4(s, alive, r, nw);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) nw[w] &= ~(dead[w] >> 7);
+}
+
+template <bool ORK>
+__device__ __forceinline__ void next_state4_masked(const uint32_t s[4], const uint32_t alive[4], const Rule &r,
+                                                   const uint32_t dead[4], uint32_t nw[4])
+{
+    if (ORK)
+        apply_rule4_ork_masked(s, alive, r.or_k, dead, nw);
+    else
+        apply_rule4_masked(s, alive, r, dead, nw);
+}
+
 // Sum of the four bytes of a word (each byte <= 255, no overflow).
 __device__ __forceinline__ uint32_t byte_sum(uint32_t v)
 {

@@ -247,8 +247,8 @@ SX_HD bool xrun_decode(const Plan &p, int kind, uint64_t w, XRun &r)
 // brick's planes along x1 (see k_ca3p.cu).  Units are numbered segment by
 // segment (the whole cross-section of one slab before the next, so the
 // bricks processed at the same time are neighbours and their halos meet in
-// L2); within a segment brick column X (x3 = 128 X ...) comes before X + 1,
-// and inside a column the rows Y = 0, 1, ... (a compact numbering: every
+// L2); within a segment the row band Y (x2 = 32 Y ...) comes before Y + 1,
+// and inside a band the bricks X = 0, 1, ... (a compact numbering: every
 // unit index names a brick that holds cells of the segment's first plane,
 // found from prefix counts instead of a map with padding).  The bounding box
 // numbers every brick of the (n+1) x (n+1) square in every segment; bricks
@@ -325,30 +325,34 @@ struct PlaneUnit {
 // Unit w -> its brick and planes.  False when the brick has no cell in the
 // segment (bounding box only; kMapBBThread keeps such bricks, with e the
 // segment's last plane, and their stores are all masked).
-SX_HD bool plane_unit_decode(const PlaneSched &s, uint64_t w, PlaneUnit &u)
+// seg_b / seg_u: the schedule's segment tables (s.seg_b, s.seg_u, or a copy
+// of them in device memory, where the kernel reads them through L1).
+SX_HD bool plane_unit_decode(const PlaneSched &s, const int32_t *seg_b, const uint32_t *seg_u, uint64_t w,
+                             PlaneUnit &u)
 {
     // segment: the last s with seg_u[s] <= w
     int32_t lo = 0, hi = s.nseg - 1;
     while (lo < hi) {
         const int32_t mid = (lo + hi + 1) >> 1;
-        if ((uint64_t)s.seg_u[mid] <= w) lo = mid; else hi = mid - 1;
+        if ((uint64_t)seg_u[mid] <= w) lo = mid; else hi = mid - 1;
     }
-    const int64_t b = s.seg_b[lo], e = (int64_t)s.seg_b[lo + 1] - 1;
-    uint64_t r = w - (uint64_t)s.seg_u[lo];
+    const int64_t b = seg_b[lo], e = (int64_t)seg_b[lo + 1] - 1;
+    uint64_t r = w - (uint64_t)seg_u[lo];
     int64_t Y, X;
     if (is_bb(s.kind)) {
-        X = (int64_t)(r / (uint64_t)s.nty);
-        Y = (int64_t)(r - (uint64_t)X * (uint64_t)s.nty);
+        Y = (int64_t)(r / (uint64_t)s.ntx);
+        X = (int64_t)(r - (uint64_t)Y * (uint64_t)s.ntx);
     } else {
+        // row band Y holds the bricks X with TX X <= K - TY Y
         const int64_t K = s.n - b;
-        X = 0;
+        Y = 0;
         for (;;) {
-            const uint64_t rows = (uint64_t)((K - X * kPlaneTX) / kPlaneTY + 1);
-            if (r < rows) break;
-            r -= rows;
-            ++X;
+            const uint64_t cols = (uint64_t)((K - Y * kPlaneTY) / kPlaneTX + 1);
+            if (r < cols) break;
+            r -= cols;
+            ++Y;
         }
-        Y = (int64_t)r;
+        X = (int64_t)r;
     }
     u.y0 = (int32_t)(Y * kPlaneTY);
     u.x0 = (int32_t)(X * kPlaneTX);
@@ -361,6 +365,16 @@ SX_HD bool plane_unit_decode(const PlaneSched &s, uint64_t w, PlaneUnit &u)
     u.e = (int32_t)(last < e ? last : e);
     return last >= b;
 }
+
+SX_HD bool plane_unit_decode(const PlaneSched &s, uint64_t w, PlaneUnit &u)
+{
+    return plane_unit_decode(s, s.seg_b, s.seg_u, w, u);
+}
+
+// Device copy of a schedule's segment tables: seg_b[kPlaneSegTable] then
+// seg_u[kPlaneSegTable] (int32 / uint32), kPlaneSegWords words per mode.
+constexpr int kPlaneSegTable = kPlaneMaxSegs + 1;
+constexpr int kPlaneSegWords = 2 * kPlaneSegTable;
 
 // Blocks before band k of the trapezoid form: sum over j < k of
 // h (Ne - (j+1) h) + h (h+1) / 2 = k h (2 Ne - k h + 1) / 2.

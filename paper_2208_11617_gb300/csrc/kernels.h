@@ -46,17 +46,21 @@ cudaError_t launch_ca3_step(const Plan &p, const CUtensorMap &tin, uint8_t *out,
                             int kind, unsigned long long *live, unsigned long long *queue, cudaStream_t st);
 
 // m = 3 plane-stream form (launch 3, k_ca3p.cu): bricks of kPlaneTY x
-// kPlaneTX cells streamed along x1.  Each staged plane is one TMA box of 34
-// rows by one of kPlWidths widths (plane_box_widths: 48 ... 160 bytes);
+// kPlaneTX cells streamed along x1.  Each stage is one TMA box of kPlPlanes
+// planes of 34 rows by one of kPlWidths widths (plane_box_widths: 48 ... 160
+// bytes);
 // maps.m[i] maps the input grid with box width i.  queue: two zeroed 64-bit
-// counters, left zeroed.
+// counters, left zeroed.  segs: sched's segment tables in device memory
+// (kPlaneSegWords words: seg_b, then seg_u).
 constexpr int kPlWidths = 5;
+constexpr int kPlPlanes = 2;  // planes x1 per TMA box (the box's depth)
 struct PlaneMaps {
     CUtensorMap m[kPlWidths];
 };
 int plane_box_widths(int *w);  // fills kPlWidths widths in bytes, returns kPlWidths
-cudaError_t launch_ca3_planes(const PlaneSched &sched, const PlaneMaps &maps, int64_t n, int64_t side, uint8_t *out,
-                              const Rule &rule, unsigned long long *live, unsigned long long *queue, cudaStream_t st);
+cudaError_t launch_ca3_planes(const PlaneSched &sched, const int32_t *segs, const PlaneMaps &maps, int64_t n,
+                              int64_t side, uint8_t *out, const Rule &rule, unsigned long long *live,
+                              unsigned long long *queue, cudaStream_t st);
 cudaError_t ca3_planes_prepare();
 cudaError_t ca3p_read_status(uint32_t *out);
 // One step of every plane-stream instance of a batch (kBody3plane units).

@@ -79,7 +79,7 @@ int make_plane_maps(const sx::Plan &p, const void *base, sx::PlaneMaps *maps)
     cuuint64_t strides[2] = {(cuuint64_t)p.side, (cuuint64_t)(p.side * p.side)};
     cuuint32_t estr[3] = {1, 1, 1};
     for (int i = 0; i < sx::kPlWidths; ++i) {
-        cuuint32_t box[3] = {(cuuint32_t)widths[i], (cuuint32_t)(sx::kPlaneTY + 2), 1};
+        cuuint32_t box[3] = {(cuuint32_t)widths[i], (cuuint32_t)(sx::kPlaneTY + 2), (cuuint32_t)sx::kPlPlanes};
         CUresult r = fn(&maps->m[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
