@@ -57,7 +57,7 @@ namespace sx {
 
 static __device__ uint32_t g_ca3p_status;
 
-constexpr int kPlStages = 5;
+constexpr int kPlStages = 4;
 constexpr int kPlCtasPerSm = 4;
 constexpr int kPlConsumerWarps = (kPlaneTX / 16) * (kPlaneTY / 2) / 32;  // 8 chunks x 16 row pairs
 constexpr int kPlThreads = 32 * (kPlConsumerWarps + 1);                  // plus the producer warp
