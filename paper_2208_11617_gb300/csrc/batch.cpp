@@ -57,6 +57,9 @@ struct simplex_batch {
     int device = -1;
     int parity = 0;
     cudaStream_t capture = nullptr;
+    // the m = 3 chain's stream and its fork / join events (created on the first run)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     std::vector<RunGraph> graphs;
     uint64_t serial = 0;  // unique per batch created in this process (never reused)
 };
@@ -101,6 +104,9 @@ int enqueue_batch_run(simplex_batch_t b, int steps, unsigned long long *live, in
         ex.planes = &pb;
         ex.pqueue = reinterpret_cast<unsigned long long *>(b->arena + b->off_pqueue);
     }
+    ex.side = b->side;
+    ex.fork = b->fork;
+    ex.join = b->join;
     if (!b->tiles2.empty()) {
         ex.nitems0_step = b->nitems0_step;
         ex.tiles = reinterpret_cast<const sx::BatchTile *>(b->arena + b->off_tiles2);
@@ -129,20 +135,34 @@ int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items,
                                   st);
         if (e != cudaSuccess) return cuda_fail(e, "batch count launch");
     }
+    // With m = 2 tiles and m = 3 work both present, the two chains of launches
+    // (m = 2: the flat tile pass; m = 3: set 0's 16^3 items, set 1, the plane
+    // stream) touch disjoint instances, counters and live slots, so the m = 3
+    // chain may run on a second stream beside the m = 2 one: each fills the
+    // SMs the other leaves idle (its tail, its latency-bound stretches).
+    const bool has_m2 = ex->tiles && ex->ntiles;
+    const bool has_m3 = nstep0 || nitems1 > nitems0 || (planes && planes->nunits);
+    cudaStream_t s3 = st;
+    if (ex->side && ex->fork && ex->join && has_m2 && has_m3) {
+        if ((e = cudaEventRecord(ex->fork, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord(fork)");
+        if ((e = cudaStreamWaitEvent(ex->side, ex->fork, 0)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamWaitEvent(fork)");
+        s3 = ex->side;
+    }
     for (int s = 1; s <= steps; ++s) {
         const int in = (parity + s - 1) & 1;
         if (nstep0) {
             e = sx::launch_batch_pass(insts, items, (uint32_t)nstep0, tmaps, arena, in, q0 + s, live, steps + 1, s,
-                                      false, st, nullptr, 0);
+                                      false, s3, nullptr, 0);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
         }
-        if (ex->tiles && ex->ntiles) {
+        if (has_m2) {
             e = sx::launch_batch_flat2(insts, ex->tiles, ex->ntiles, tmaps, arena, in, live, steps + 1, s, st);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch (m = 2 tiles)");
         }
         if (nitems1 > nitems0) {
             e = sx::launch_batch_pass(insts, items + nitems0, (uint32_t)(nitems1 - nitems0), tmaps, arena, in, q1 + s,
-                                      live, steps + 1, s, false, st, nullptr, 1);
+                                      live, steps + 1, s, false, s3, nullptr, 1);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch (32^3 tiles)");
         }
         if (planes && planes->nunits) {
@@ -151,9 +171,13 @@ int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items,
             pb.live = live;
             pb.live_stride = steps + 1;
             pb.live_index = s;
-            e = sx::launch_batch_planes(pb, ex->pqueue, st);
+            e = sx::launch_batch_planes(pb, ex->pqueue, s3);
             if (e != cudaSuccess) return cuda_fail(e, "batch step launch (plane stream)");
         }
+    }
+    if (s3 != st) {
+        if ((e = cudaEventRecord(ex->join, s3)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord(join)");
+        if ((e = cudaStreamWaitEvent(st, ex->join, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent(join)");
     }
     return SIMPLEX_OK;
 }
@@ -346,6 +370,9 @@ int simplex_batch_destroy(simplex_batch_t b)
     if (!b) return SIMPLEX_OK;
     for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     delete b;
     return SIMPLEX_OK;
 }
@@ -447,6 +474,13 @@ int simplex_batch_run(simplex_batch_t b, int steps, unsigned long long *live, in
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = sx::batch_prepare();
     if (e != cudaSuccess) return cuda_fail(e, "setting the batch kernel's shared-memory limit");
+    if (!b->side) {
+        if ((e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreateWithFlags(side)");
+        if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreateWithFlags");
+    }
     if (!use_graph) {
         rc = enqueue_batch_run(b, steps, live, b->parity, st);
         if (rc) return rc;

@@ -66,6 +66,11 @@ struct BatchExtras {
     uint32_t ntiles = 0;
     const sx::PlaneBatch *planes = nullptr;
     unsigned long long *pqueue = nullptr;
+    // a second stream and two events: when set and the batch holds both m = 2
+    // tiles and m = 3 work, the m = 3 launches of every step run on `side`,
+    // forked from and joined back to the main stream, beside the m = 2 ones
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 int enqueue_batch_passes(const sx::BatchInst *insts, const sx::BatchItem *items, size_t nitems, size_t nitems0,
                          const CUtensorMap *tmaps, uint8_t *arena, unsigned int *q0, unsigned int *q1, int steps,
