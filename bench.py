@@ -51,12 +51,13 @@ _KERNEL_SOURCES = {
     "write_kernel<2>": ["k_write.cu", "common.cuh", "hmap.cuh", "tile.cuh", "kernels.h"],
 }
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (mean of 3 launches
-# at full size), for the kernel sources with the given fingerprint
-_KERNEL_TRAFFIC = {("7702123f7ad67f6f", "ca2_step_kernel<128>", 32767): 1_032_780_885,
-                   ("ca5d6bc19247a0b1", "ca3_step_planes", 1023): 386_007_979,
-                   ("a64bb17afbc61e81", "write_kernel<2>", 32767): 2_086_039_467,
-                   ("464ecdb6afbca9f1", "ca3_step_kernel<32>", 1023): 521_488_810,
-                   ("464ecdb6afbca9f1", "ca3_step_stream", 1023): 399_034_453}
+# at full size), for the kernel sources with the given fingerprint, at the
+# given n and tile size
+_KERNEL_TRAFFIC = {("32f88cfef9b587ce", "ca2_step_kernel<128>", 32767, 128): 1_032_765_866,
+                   ("3fdcfdfcfb16cbda", "ca3_step_planes", 1023, 32): 382_589_354,
+                   ("8d3bcc26f6e4db16", "write_kernel<2>", 32767, 128): 2_086_079_658,
+                   ("509b2c66697ba39c", "ca3_step_kernel<32>", 1023, 32): 520_881_749,
+                   ("509b2c66697ba39c", "ca3_step_stream", 1023, 32): 398_068_906}
 
 
 def _kernel_fingerprint(kname):
@@ -638,7 +639,7 @@ def run_ours(args, rank, world, local):
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                       "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                       "kernel": kname, "alg_bytes_per_launch": alg_bytes,
-                      "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint(kname), kname, wl.n)),
+                      "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint(kname), kname, wl.n, wl.block)),
                       "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
             clocks=clk,
             gpu_launches=args.steps * (wl.steps + 1),
@@ -664,7 +665,7 @@ def run_ours(args, rank, world, local):
             res["plane_stream"] = {"kernel": "ca3_step_planes", "launch_ms_mean": mq_ms, "achieved": ach_q,
                                    "frac": ach_q / hbm_peak,
                                    "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint("ca3_step_planes"),
-                                                                   "ca3_step_planes", wl.n)),
+                                                                   "ca3_step_planes", wl.n, wl.block)),
                                    "note": "same step, plane-stream form (launch 3)"}
         if wl.m == 3 and info["launch"] != 1:
             # the paper's execution model on the same grids: one CTA per block of H3
@@ -673,7 +674,7 @@ def run_ours(args, rank, world, local):
             ach_g = alg_bytes / (mg_ms * 1e-3) / 1e9
             kg = f"ca3_step_kernel<{wl.block}>"
             res["grid_form"] = {"kernel": kg, "launch_ms_mean": mg_ms, "achieved": ach_g, "frac": ach_g / hbm_peak,
-                                "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint(kg), kg, wl.n)),
+                                "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint(kg), kg, wl.n, wl.block)),
                                 "note": "same step, one CTA per block of H3 (launch 1, Sec. 4.3 map)"}
         if wl.m == 3 and wl.block == 32 and info["launch"] != 2:
             # the other m = 3 step form on the same grids: persistent CTAs streaming
@@ -684,7 +685,7 @@ def run_ours(args, rank, world, local):
             res["x_stream"] = {"kernel": "ca3_step_stream", "launch_ms_mean": mx_ms, "achieved": ach_x,
                                "frac": ach_x / hbm_peak,
                                "traffic": _KERNEL_TRAFFIC.get((_kernel_fingerprint("ca3_step_stream"),
-                                                               "ca3_step_stream", wl.n)),
+                                                               "ca3_step_stream", wl.n, wl.block)),
                                "note": "same step, x-stream form (launch 2)"}
         # end to end through the C ABI from pinned host memory
         e2e_steps = 0 if args.no_e2e else max(1, min(3, args.steps))
@@ -771,7 +772,7 @@ def run_ours(args, rank, world, local):
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                       "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                       "traffic": None if accum else _KERNEL_TRAFFIC.get(
-                          (_kernel_fingerprint(f"write_kernel<{wl.m}>"), f"write_kernel<{wl.m}>", wl.n)),
+                          (_kernel_fingerprint(f"write_kernel<{wl.m}>"), f"write_kernel<{wl.m}>", wl.n, wl.block)),
                       "kernel": f"{'accum' if accum else 'write'}_kernel<{wl.m}>", "alg_bytes_per_launch": alg_bytes,
                       "launch_ms_mean": mean_ms, "launch_ms_median": med_ms},
             clocks=clk, gpu_launches=args.steps * reps,
