@@ -38,6 +38,11 @@ ONLYPLANE = [_inst(3, 64, 128, seed=31, p=0.3), _inst(3, 255, 128, seed=32, p=0.
              _inst(3, 500, 128, seed=34, p=0.3), _inst(3, 2, 128, rule=(1, 0), seed=35, p=0.3)]
 
 
+def _batch_side(d):
+    """The batch's grid side: whole 128-byte rows for m = 2, round_up(n + 1, 16) for m = 3."""
+    return (d["n"] + 128) // 128 * 128 if d["m"] == 2 else (d["n"] + 16) // 16 * 16
+
+
 def _logical(t, n):
     return t[tuple(slice(0, n + 1) for _ in range(t.dim()))].cpu().numpy()
 
@@ -98,7 +103,7 @@ def test_batch_workload_equals_single_instance_path():
     rng = np.random.default_rng(5)
     oracle_check = set(rng.choice(len(insts), size=12, replace=False).tolist())
     for i, d in enumerate(insts):
-        side = (d["n"] + 16) // 16 * 16
+        side = _batch_side(d)
         mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], 32 if d["m"] == 3 else d["block"], side=side)
         a = torch.zeros(mp.numel, dtype=torch.uint8, device="cuda")
         bb = torch.zeros_like(a)
