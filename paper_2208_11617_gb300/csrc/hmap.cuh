@@ -520,21 +520,11 @@ template <int D>
 SX_HD bool cubes_generic(const Plan &p, uint64_t v, int32_t *X)
 {
     const int32_t N = p.N, logN = p.logN;
-    // level k holds D^(k-1) cubes of side N / 2^k; walk the levels with the
-    // running block count in registers (p.level_end holds the same sums, but
-    // a table indexed by a loop variable costs a dependent memory load a level)
     int k = 1;
-    uint64_t start = 0, cubes = 1;  // blocks before level k; cubes in level k
-    for (;;) {
-        const uint64_t lev = cubes << (D * (logN - k));
-        if (k >= logN || v < start + lev) break;
-        start += lev;
-        cubes *= (uint64_t)D;
-        ++k;
-    }
+    while (k < logN && v >= p.level_end[D - 3][k]) ++k;
     const int lb = logN - k;
     const int32_t b = 1 << lb;
-    const uint64_t local = v - start;
+    const uint64_t local = v - p.level_end[D - 3][k - 1];
     uint64_t c = local >> (D * lb);
     const uint64_t l = local & ((1ull << (D * lb)) - 1ull);
     int32_t corner[D];
