@@ -50,7 +50,8 @@ def _time_batch(sx, torch, insts, steps: int, reps: int) -> float:
     b = sx.simplex_batch_create(insts)
     sx.simplex_batch_bind(b)
     sx.simplex_batch_init(b)
-    sx.simplex_batch_run(b, steps)          # capture + warm up
+    for _ in range(2):                      # capture + warm up
+        sx.simplex_batch_run(b, steps)
     torch.cuda.synchronize()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.record()
@@ -63,8 +64,10 @@ def _time_batch(sx, torch, insts, steps: int, reps: int) -> float:
     return cells * steps * reps / (s.elapsed_time(e) * 1e-3)
 
 
-def tune(instances, steps: int = 4, reps: int = 3, max_per_class: int = 256, cache: str | None = None):
-    """Returns {size class: config}; reads/writes `cache` (JSON) when given."""
+def tune(instances, steps: int = 16, reps: int = 3, max_per_class: int = 256, cache: str | None = None):
+    """Returns {size class: config}; reads/writes `cache` (JSON) when given.  Each
+    candidate runs `steps` steps per graph (the batched workload's 16: with fewer,
+    a small class's fixed graph-launch cost decides the choice)."""
     import torch
     from . import simplex as sx
     if cache and os.path.exists(cache):
