@@ -16,13 +16,22 @@
 // x1 - 1, x1, x1 + 1) plus one horizontal 3-sum, all byte-parallel in 32-bit
 // words (cells are 0/1, sums stay below 32: no carries between bytes).
 //
-// Thread (c, p) -- c = tid & 7, p = tid >> 3 -- owns the 16-byte chunk c of
-// the brick's rows 2p and 2p + 1: per plane it loads its chunk of the four
-// staged rows 2p ... 2p + 3 and one halo word (lane c = 0 the word left of
-// the brick, c = 7 the word right of it), and takes the neighbouring
-// chunks' edge words from lanes c - 1 and c + 1 by shuffle.  The register
-// sets of three consecutive planes rotate through a loop unrolled over three
-// stages (six planes), so nothing is copied between planes.
+// Consumer warp w owns the warp tile of 16 rows (wy = w / 2) by 64 cells
+// (wx = w % 2) of the brick; its lane (c, p) -- c = lane & 3, p = lane >> 2
+// -- owns the 16-byte chunk C = 4 wx + c of the brick rows 2P and 2P + 1,
+// P = 8 wy + p.  Per plane a lane loads its chunk of the four staged rows
+// 2P ... 2P + 3 and one halo word (c = 0 the word left of the warp tile, c =
+// 3 the word right of it: inside the box, or the box's halo at the brick's
+// edges) and takes the neighbouring chunks' edge words from lanes c - 1 and
+// c + 1 by shuffle.  A warp whose tile holds no domain cell on an output
+// plane (on the bricks along the diagonal) skips that plane's output: 2-3 %
+// faster than warps of 8 rows by the whole brick width, which never skip,
+// although the narrower boxes now cost some shared-memory bank conflicts
+// (a quarter warp reads two row pairs 2W bytes apart; boxes narrowed to
+// widths 32 modulo 64 only, which avoid them, read more and were 5 %
+// slower).  The register sets of three consecutive planes rotate through a
+// loop unrolled over three stages (six planes), so nothing is copied between
+// planes.
 //
 // Box width.  The cells of a staged plane x1 that lie in the domain have
 // x3 <= n - x1 - (y0 - 1), so the box only has to reach that far: the
@@ -59,7 +68,8 @@ static __device__ uint32_t g_ca3p_status;
 
 constexpr int kPlStages = 4;
 constexpr int kPlCtasPerSm = 4;
-constexpr int kPlConsumerWarps = (kPlaneTX / 16) * (kPlaneTY / 2) / 32;  // 8 chunks x 16 row pairs
+constexpr int kPlTileRows = 16, kPlTileCols = 64;  // a consumer warp's tile of the brick
+constexpr int kPlConsumerWarps = (kPlaneTY / kPlTileRows) * (kPlaneTX / kPlTileCols);
 constexpr int kPlThreads = 32 * (kPlConsumerWarps + 1);                  // plus the producer warp
 constexpr int kPlRows = kPlaneTY + 2;
 constexpr int kPlMaxW = kPlaneTX + 32;
@@ -69,7 +79,8 @@ constexpr int kPlRingSmem = kPlStages * (int)kPlStageBytes + 128;  // plus 128 b
 constexpr int kPlMaxSmem = kPlRingSmem + kPlaneSegWords * (int)sizeof(int32_t);
 static_assert(kPlPlanes == 2, "the consumer loop handles two planes per stage");
 static_assert(kPlStageBytes % 128 == 0, "every stage starts on a 128-byte boundary");
-static_assert(kPlConsumerWarps == 4, "the thread layout assumes 8 chunks x 16 row pairs");
+static_assert(kPlConsumerWarps == 4 && kPlTileRows * kPlTileCols == 32 * 2 * 16,
+              "a warp tile is 8 row pairs x 4 chunks, one chunk pair per lane");
 static_assert(kPlMaxW == 160 && kPlaneTY == 32, "the halo-word offsets assume 160-byte rows");
 
 // Phase codes of a staged plane (meta .w: first plane bits 8..9, second
@@ -266,21 +277,27 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
         }
     } else {
         // ---------------------------------------------------------------- consumers
-        const int c = tid & 7, p = tid >> 3;
+        const int wx = warp % (kPlaneTX / kPlTileCols), wy = warp / (kPlaneTX / kPlTileCols);
+        const int c = lane & 3, C = 4 * wx + c;              // chunk inside the warp tile / the brick
+        const int P = (kPlTileRows / 2) * wy + (lane >> 2);  // row pair inside the brick
         // column sums of the three newest staged planes (rotating): words 0..3
-        // of row 2p (f) and of row 2p + 1 (s), [4] the halo word; and the
+        // of row 2P (f) and of row 2P + 1 (s), [4] the halo word; and the
         // centre rows (the cells' own states)
         uint32_t sf[3][5], ss[3][5], af[3][4], as[3][4];
         int slot = 0;
         uint32_t parity = 0;
-        // this lane's halo word (left of the brick for c = 0, right of it
-        // otherwise; only c = 0 and c = 7 use theirs), as a byte offset in a
-        // staged row
-        const int ho = c == 0 ? 12 : 16 + kPlaneTX;
+        // this lane's halo word as a byte offset in a staged row (c = 0: the
+        // word left of the warp tile, c = 3: the word right of it) and the box
+        // width from which it lies inside the box; lanes c = 1, 2 read zeros
+        // and do not use theirs
+        const int ho = c == 0 ? 12 + kPlTileCols * wx : 16 + kPlTileCols * (wx + 1);
+        const int hw = c == 0 || c == 3 ? ho + 4 : 1 << 20;
+        const int cw = 16 * C + 32;  // box width from which this lane's chunk lies inside the box
         const uint32_t ring_sa = smem_u32(ring), zb_sa = smem_u32(zb);
-        const int64_t toff = (int64_t)(2 * p) * side + 16 * c;  // first output cell of the thread in a brick plane
+        const int64_t toff = (int64_t)(2 * P) * side + 16 * C;  // first output cell of the thread in a brick plane
         const int64_t pstride = side * side;                   // bytes per output plane
-        const int tq = 2 * p + 16 * c;                         // its offsets inside the brick, summed
+        const int tq = 2 * P + 16 * C;                         // its offsets inside the brick, summed
+        const int tmin = kPlTileRows * wy + kPlTileCols * wx;  // the warp tile's least offset sum
         int cur = -1;  // BATCH: the instance lsum counts for
         uint32_t acc = 0;  // live cells written, per byte, over at most six planes (bytes <= 48)
         auto flush = [&]() {  // BATCH: the warp's live cells of instance `cur` to its counter
@@ -314,10 +331,9 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                 // halo word) outside the box reads the 16 zero bytes zb with
                 // stride 0 (the grid is zero there: outside the domain).  Every
                 // lane thus loads unconditionally.
-                const uint32_t rowb = ring_sa + (uint32_t)(slot * (int)kPlStageBytes + 2 * p * W);
-                const bool has_c = 16 * c + 32 <= W;
-                const bool has_h = c == 0 ? W > 0 : W == kPlMaxW;
-                const uint32_t pc = has_c ? rowb + (uint32_t)(16 + 16 * c) : zb_sa;
+                const uint32_t rowb = ring_sa + (uint32_t)(slot * (int)kPlStageBytes + 2 * P * W);
+                const bool has_c = cw <= W, has_h = hw <= W;
+                const uint32_t pc = has_c ? rowb + (uint32_t)(16 + 16 * C) : zb_sa;
                 const uint32_t hc = has_h ? rowb + (uint32_t)ho : zb_sa;
                 const uint32_t sc = has_c ? (uint32_t)W : 0u, sh = has_h ? (uint32_t)W : 0u;
                 const uint64_t dbase = ((uint64_t)(uint32_t)md.y << 32) | (uint32_t)md.x;
@@ -343,7 +359,7 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                         if (lane == 0) mbar_arrive(&empty[slot]);
                     }
                     // sums of this plane into set j; only lanes c = 0 (left)
-                    // and c = 7 (right) use their halo word
+                    // and c = 3 (right) use their halo word
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         sf[j][w] = v[0][w] + v[1][w] + v[2][w];
@@ -353,23 +369,24 @@ __global__ void __launch_bounds__(kPlThreads, kPlCtasPerSm)
                     }
                     sf[j][4] = h[0] + h[1] + h[2];
                     ss[j][4] = h[1] + h[2] + h[3];
-                    if (ph == kPhOut) {
+                    const int qz = md.z - q;  // n - (x1 - 1) + 1 - y0 - x0 of this plane
+                    if (ph == kPhOut && tmin < qz) {
                         // output plane x1 - 1 (x1 the staged plane) from the
-                        // sets of planes x1 - 2 (j + 1), x1 - 1 (j + 2) and x1 (j)
-                        const int P = (j + 1) % 3, Q = (j + 2) % 3;
-                        const int qz = md.z - q;  // n - (x1 - 1) + 1 - y0 - x0 of this plane
+                        // sets of planes x1 - 2 (j + 1), x1 - 1 (j + 2) and x1
+                        // (j); a warp tile with no domain cell skips it
+                        const int P3 = (j + 1) % 3, Q = (j + 2) % 3;
                         const bool partial = qz < kPlaneTY + kPlaneTX - 1;  // not every cell of the brick plane
                         uint8_t *dst = reinterpret_cast<uint8_t *>(dbase) + q * ps +
-                                       (BATCH ? (int64_t)(2 * p) * rs + 16 * c : toff);
+                                       (BATCH ? (int64_t)(2 * P) * rs + 16 * C : toff);
 #pragma unroll
                         for (int r = 0; r < 2; ++r) {
                             uint32_t V[5], S[4], nw[4];
 #pragma unroll
                             for (int w = 0; w < 5; ++w)
-                                V[w] = r == 0 ? sf[P][w] + sf[Q][w] + sf[j][w] : ss[P][w] + ss[Q][w] + ss[j][w];
-                            const uint32_t lft = __shfl_up_sync(0xffffffffu, V[3], 1, 8);
-                            const uint32_t rgt = __shfl_down_sync(0xffffffffu, V[0], 1, 8);
-                            hsum4(V, c == 0 ? V[4] : lft, c == 7 ? V[4] : rgt, S);
+                                V[w] = r == 0 ? sf[P3][w] + sf[Q][w] + sf[j][w] : ss[P3][w] + ss[Q][w] + ss[j][w];
+                            const uint32_t lft = __shfl_up_sync(0xffffffffu, V[3], 1, 4);
+                            const uint32_t rgt = __shfl_down_sync(0xffffffffu, V[0], 1, 4);
+                            hsum4(V, c == 0 ? V[4] : lft, c == 3 ? V[4] : rgt, S);
                             const uint32_t *A = r == 0 ? af[Q] : as[Q];
                             if constexpr (BATCH) {
                                 // ORK: every instance's rule is or-k (its word in
