@@ -54,7 +54,7 @@ _KERNEL_SOURCES = {
 # at full size), for the kernel sources with the given fingerprint, at the
 # given n and tile size
 _KERNEL_TRAFFIC = {("32f88cfef9b587ce", "ca2_step_kernel<128>", 32767, 128): 1_032_765_866,
-                   ("3fdcfdfcfb16cbda", "ca3_step_planes", 1023, 32): 382_589_354,
+                   ("ff5e3aa57fa66250", "ca3_step_planes", 1023, 32): 384_356_864,
                    ("8d3bcc26f6e4db16", "write_kernel<2>", 32767, 128): 2_086_079_658,
                    ("509b2c66697ba39c", "ca3_step_kernel<32>", 1023, 32): 520_881_749,
                    ("509b2c66697ba39c", "ca3_step_stream", 1023, 32): 398_068_906}
