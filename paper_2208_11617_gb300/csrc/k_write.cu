@@ -280,7 +280,9 @@ cudaError_t launch_write(const Plan &plan, uint32_t *out, uint32_t seed, int kin
     // m >= 3: tiles of fewer than 256 chunks one per warp (kWriteWarps per
     // CTA: 1.8x faster for 4^4 tiles); larger ones one per CTA (a warp per
     // tile, or persistent CTAs decoding the next tile ahead, were 1.4x slower
-    // for 8^4 tiles)
+    // for 8^4 tiles).  m = 4 CTAs have 128 threads: as fast as 256 for H, and
+    // the bounding box's mostly empty CTAs retire 1.3x faster (64 threads: H
+    // 13 % slower)
     const bool small = (1ull << (p.m * p.log_rho - 2)) < 256;
     const unsigned gw = grid_for((nb + kWriteWarps - 1) / kWriteWarps);
     switch (p.m * 2 + (small ? 1 : 0)) {
@@ -288,7 +290,7 @@ cudaError_t launch_write(const Plan &plan, uint32_t *out, uint32_t seed, int kin
     case 5: write_kernel<2><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
     case 6: write_kernel<3><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
     case 7: write_kernel_w<3><<<gw, 32 * kWriteWarps, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
-    case 8: write_kernel<4><<<g, t, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
+    case 8: write_kernel<4><<<g, t < 128u ? t : 128u, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
     case 9: write_kernel_w<4><<<gw, 32 * kWriteWarps, 0, st>>>(p, out, seed, kind, nb, vec ? 1 : 0); break;
     default: return cudaErrorInvalidValue;
     }
