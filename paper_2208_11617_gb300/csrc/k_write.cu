@@ -47,14 +47,32 @@ __global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__re
 {
     const uint32_t nchunks = 1u << (M * p.log_rho - 2);
     __shared__ int32_t sX[M + 1];  // block_decode's shared copy of the tile (m >= 3)
+    // m >= 3: when a block's chunks (4 cells each) span whole x1-slabs of the
+    // tile (rho^(m-1) cells), a thread's chunks c, c + blockDim.x, ... differ
+    // only in x1: their positions follow from the first by three adds
+    const int lslab = (M - 1) * p.log_rho;
+    const uint32_t step_cells = blockDim.x * 4u;
+    const bool stepped = M >= 3 && (step_cells & ((1u << lslab) - 1u)) == 0;
     for (uint64_t v = blockIdx.x; v < nblocks; v += gridDim.x) {
         int32_t X[M];
         if (!block_decode<M>(p, kind, v, X, sX)) continue;
         const int64_t s0 = tile_base_sum<M>(p, X);
         if (s0 > p.n && kind != kMapBBThread) continue;  // tile past the domain
         const bool partial = s0 + (int64_t)M * (p.rho - 1) > p.n;
+        int64_t dx = 0, dlin = 0, daddr = 0;
+        if (stepped) {
+            dx = (int64_t)(step_cells >> lslab);
+            dlin = dx;
+            daddr = dx;
+#pragma unroll
+            for (int i = 0; i < M - 1; ++i) {
+                dlin *= p.n + 1;
+                daddr *= p.side;
+            }
+        }
+        ChunkPos<M> q = chunk_pos<M>(p, X, threadIdx.x, 2);
         for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
-            const ChunkPos<M> q = chunk_pos<M>(p, X, c, 2);
+            if (M < 3 || (!stepped && c != threadIdx.x)) q = chunk_pos<M>(p, X, c, 2);
             const uint32_t l0 = (uint32_t)q.lin;
             if (!partial) {
                 const uint32_t h0 = splitmix32(seed ^ l0), h1 = splitmix32(seed ^ (l0 + 1u));
@@ -79,6 +97,11 @@ __global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__re
                     for (int j = 0; j < 4; ++j)
                         if (j < rem) out[q.addr + j] = splitmix32(seed ^ (l0 + (uint32_t)j));
                 }
+            }
+            if (M >= 3) {
+                q.lin += dlin;
+                q.addr += daddr;
+                q.sum += dx;
             }
         }
     }
@@ -280,9 +303,10 @@ cudaError_t launch_write(const Plan &plan, uint32_t *out, uint32_t seed, int kin
     // m >= 3: tiles of fewer than 256 chunks one per warp (kWriteWarps per
     // CTA: 1.8x faster for 4^4 tiles); larger ones one per CTA (a warp per
     // tile, or persistent CTAs decoding the next tile ahead, were 1.4x slower
-    // for 8^4 tiles).  m = 4 CTAs have 128 threads: as fast as 256 for H, and
-    // the bounding box's mostly empty CTAs retire 1.3x faster (64 threads: H
-    // 13 % slower)
+    // for 8^4 tiles).  m = 4 CTAs have 128 threads: with the per-thread
+    // position steps (a thread's 8 chunks then lie in consecutive x1-slabs)
+    // 1.22x faster than 256 threads, and the bounding box's mostly empty CTAs
+    // retire 1.3x faster (64 threads: 13 % slower)
     const bool small = (1ull << (p.m * p.log_rho - 2)) < 256;
     const unsigned gw = grid_for((nb + kWriteWarps - 1) / kWriteWarps);
     switch (p.m * 2 + (small ? 1 : 0)) {
