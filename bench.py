@@ -357,8 +357,12 @@ def run_batch(args, rank, world, compact=False):
     from paper_2208_11617_gb300 import simplex as sx
 
     base = inputs.batch_instances(n2=args.batch_m2, n3=args.batch_m3)
+    if args.batch_nmin is not None or args.batch_nmax is not None:
+        lo = args.batch_nmin if args.batch_nmin is not None else 0
+        hi = args.batch_nmax if args.batch_nmax is not None else 1 << 62
+        base = [d for d in base if lo <= d["n"] <= hi]
     t0 = time.perf_counter()
-    table = {} if args.no_tune else autotune.tune(base)
+    table = {} if args.no_tune else autotune.tune(base, cache=args.tune_cache)
     tune_s = time.perf_counter() - t0
     insts = autotune.apply(base, table)
     steps = inputs.BATCH_STEPS
@@ -1085,9 +1089,13 @@ def main():
                     help="serve: rounds with at most this many resident jobs launch each job's steps directly "
                          "(0: the default, 24; -1: never)")
     ap.add_argument("--no-tune", action="store_true", help="batch: untuned tile choices")
+    ap.add_argument("--tune-cache", default=None,
+                    help="batch: JSON file of tuned tile choices, read if it exists, else written after tuning")
     ap.add_argument("--no-loop", action="store_true", help="batch: skip the single-instance loop baseline")
     ap.add_argument("--batch-m2", type=int, default=2048, help="batch: number of m = 2 instances")
     ap.add_argument("--batch-m3", type=int, default=256, help="batch: number of m = 3 instances")
+    ap.add_argument("--batch-nmin", type=int, default=None, help="batch: keep only the instances with n >= this")
+    ap.add_argument("--batch-nmax", type=int, default=None, help="batch: keep only the instances with n <= this")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
