@@ -400,7 +400,7 @@ typedef struct simplex_batch_info {
 } simplex_batch_info_t;
 
 /* Plans every instance (host memory only).  Each instance's grids have side
- * round_up(n + 1, 128) for m = 2 and round_up(n + 1, 16) for m = 3.  Errors: SIMPLEX_EINVAL (an instance's parameters; the
+ * round_up(n + 1, 128).  Errors: SIMPLEX_EINVAL (an instance's parameters; the
  * message names it), SIMPLEX_ENOMEM. */
 int simplex_batch_create(const simplex_instance_t *instances, int count, simplex_batch_t *out);
 

@@ -237,9 +237,10 @@ int simplex_batch_create(const simplex_instance_t *instances, int count, simplex
                                         "with block 16, 32 or 128 (the plane stream) (got m = %d, block = %d)",
                         i, in.m, in.block);
         }
-        // m = 2 rows start on 128-byte lines (the flat pass ran 3 % faster than
-        // with rows only 16-byte aligned); m = 3 keeps round_up(n + 1, 16)
-        const int64_t side = in.m == 2 ? (in.n + 128) / 128 * 128 : (in.n + 16) / 16 * 16;
+        // rows start on 128-byte lines: a box row then touches only the
+        // 32-byte sectors it reads (with rows 16-byte aligned the m = 2 flat
+        // pass ran 3 % slower, the whole batch 4 %)
+        const int64_t side = (in.n + 128) / 128 * 128;
         int band = 0;
         if (in.m == 2) {
             band = in.band;

@@ -22,7 +22,7 @@ def test_batch_counts_and_layout():
     blocks = 0
     items = 0
     for d in insts:
-        side = (d["n"] + 128) // 128 * 128 if d["m"] == 2 else (d["n"] + 16) // 16 * 16
+        side = (d["n"] + 128) // 128 * 128
         mp = sx.simplex_map_create(d["m"], d["n"], 2, d["beta"], d["block"], side=side,
                                    band=(min(8, 1 << ((d["n"] + d["block"]) // d["block"]).bit_length() - 1)
                                          if d["m"] == 2 else None))
@@ -40,7 +40,7 @@ def test_batch_counts_and_layout():
         items += 1 if run else 0
     assert info["blocks"] == blocks
     assert info["items"] == items
-    sides = [(d["n"] + 128) // 128 * 128 if d["m"] == 2 else (d["n"] + 16) // 16 * 16 for d in insts]
+    sides = [(d["n"] + 128) // 128 * 128 for d in insts]
     grids = sum(2 * (-(-s ** d["m"] // 256) * 256) for s, d in zip(sides, insts))
     assert info["arena_bytes"] >= grids
 

@@ -39,8 +39,8 @@ ONLYPLANE = [_inst(3, 64, 128, seed=31, p=0.3), _inst(3, 255, 128, seed=32, p=0.
 
 
 def _batch_side(d):
-    """The batch's grid side: whole 128-byte rows for m = 2, round_up(n + 1, 16) for m = 3."""
-    return (d["n"] + 128) // 128 * 128 if d["m"] == 2 else (d["n"] + 16) // 16 * 16
+    """The batch's grid side: whole 128-byte rows, round_up(n + 1, 128)."""
+    return (d["n"] + 128) // 128 * 128
 
 
 def _logical(t, n):
