@@ -66,7 +66,7 @@ namespace sx {
 
 static __device__ uint32_t g_ca3p_status;
 
-constexpr int kPlStages = 4;
+constexpr int kPlStages = 4;  // five per CTA were 5 % slower, three or six (three CTAs per SM) no faster
 constexpr int kPlCtasPerSm = 4;
 constexpr int kPlTileRows = 16, kPlTileCols = 64;  // a consumer warp's tile of the brick
 constexpr int kPlConsumerWarps = (kPlaneTY / kPlTileRows) * (kPlaneTX / kPlTileCols);
