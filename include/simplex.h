@@ -155,9 +155,9 @@ typedef struct simplex_map_params {
  *     into bricks of 32 rows x2 by 128 cells x3; a unit is one brick of one
  *     slab (simplex_map_unit), numbered slab by slab so that bricks in
  *     flight are neighbours.  The CTA streams the brick along x1, staging
- *     each plane (the brick plus its one-cell halo, a box only as wide as
- *     the plane's domain cells reach) by one TMA load into a ring of stages,
- *     and reads every staged byte once.  Slabs hold 64 planes at most and
+ *     its planes two at a time (the brick plus its one-cell halo, a box only
+ *     as wide as the first plane's domain cells reach) by one TMA load into a
+ *     ring of stages, and reads every staged byte once.  Slabs hold 64 planes at most and
  *     shrink towards the apex (x1 = n) to 4, so the last units of a step are
  *     short.  Mode H numbers only bricks holding cells of their slab;
  *     SIMPLEX_MODE_BB numbers every brick of the (n+1)^2 square in every slab
