@@ -61,6 +61,8 @@ WRITE_CASES = [
     (4, 127, 8, None, 4),          # 128^4, the m = 4 write workload
     (4, 127, 4, None, 4),
     (4, 40, 4, 44, 4),
+    (4, 100, 8, 104, 4),           # ragged n, 8^4 tiles: multi-tile blocks, early stop on the diagonal
+    (4, 60, 8, 62, 4),             # 8^4 tiles, side not a multiple of 4 (4-byte stores)
 ]
 
 
