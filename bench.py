@@ -55,7 +55,7 @@ _KERNEL_SOURCES = {
 # given n and tile size
 _KERNEL_TRAFFIC = {("32f88cfef9b587ce", "ca2_step_kernel<128>", 32767, 128): 1_032_765_866,
                    ("ff5e3aa57fa66250", "ca3_step_planes", 1023, 32): 384_356_864,
-                   ("6f15e8800e8651f8", "write_kernel<2>", 32767, 128): 2_085_767_509,
+                   ("afe643cc8e1992fd", "write_kernel<2>", 32767, 128): 2_085_882_453,
                    ("509b2c66697ba39c", "ca3_step_kernel<32>", 1023, 32): 520_881_749,
                    ("509b2c66697ba39c", "ca3_step_stream", 1023, 32): 398_068_906}
 

@@ -74,28 +74,51 @@ __global__ void __launch_bounds__(256) write_kernel(const Plan p, uint32_t *__re
         for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
             if (M < 3 || (!stepped && c != threadIdx.x)) q = chunk_pos<M>(p, X, c, 2);
             const uint32_t l0 = (uint32_t)q.lin;
-            if (!partial) {
-                const uint32_t h0 = splitmix32(seed ^ l0), h1 = splitmix32(seed ^ (l0 + 1u));
-                const uint32_t h2 = splitmix32(seed ^ (l0 + 2u)), h3 = splitmix32(seed ^ (l0 + 3u));
-                if (vec) {
-                    *reinterpret_cast<uint4 *>(out + q.addr) = make_uint4(h0, h1, h2, h3);
+            if (M < 3) {
+                // m = 2 (HBM-bound at full size): the two store forms apart
+                if (!partial) {
+                    const uint32_t h0 = splitmix32(seed ^ l0), h1 = splitmix32(seed ^ (l0 + 1u));
+                    const uint32_t h2 = splitmix32(seed ^ (l0 + 2u)), h3 = splitmix32(seed ^ (l0 + 3u));
+                    if (vec) {
+                        *reinterpret_cast<uint4 *>(out + q.addr) = make_uint4(h0, h1, h2, h3);
+                    } else {
+                        out[q.addr] = h0;
+                        out[q.addr + 1] = h1;
+                        out[q.addr + 2] = h2;
+                        out[q.addr + 3] = h3;
+                    }
                 } else {
-                    out[q.addr] = h0;
-                    out[q.addr + 1] = h1;
-                    out[q.addr + 2] = h2;
-                    out[q.addr + 3] = h3;
+                    // diagonal tile: most chunks lie wholly inside or outside the domain
+                    const int64_t rem = p.n - q.sum + 1;  // cells of the chunk in the domain
+                    if (rem >= 4 && vec) {
+                        *reinterpret_cast<uint4 *>(out + q.addr) =
+                            make_uint4(splitmix32(seed ^ l0), splitmix32(seed ^ (l0 + 1u)),
+                                       splitmix32(seed ^ (l0 + 2u)), splitmix32(seed ^ (l0 + 3u)));
+                    } else if (rem > 0) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (j < rem) out[q.addr + j] = splitmix32(seed ^ (l0 + (uint32_t)j));
+                    }
                 }
             } else {
-                // diagonal tile: most chunks lie wholly inside or outside the domain
-                const int64_t rem = p.n - q.sum + 1;  // cells of the chunk in the domain
-                if (rem >= 4 && vec) {
-                    *reinterpret_cast<uint4 *>(out + q.addr) =
-                        make_uint4(splitmix32(seed ^ l0), splitmix32(seed ^ (l0 + 1u)), splitmix32(seed ^ (l0 + 2u)),
-                                   splitmix32(seed ^ (l0 + 3u)));
-                } else if (rem > 0) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (j < rem) out[q.addr + j] = splitmix32(seed ^ (l0 + (uint32_t)j));
+                // m >= 3 (instruction-bound): cells of the chunk in the domain,
+                // 4 off the diagonal band; one hash sequence for every lane
+                // with a cell, so a warp whose chunks straddle the diagonal
+                // hashes once, not once per store form (7 % faster for the
+                // m = 4 write)
+                const int64_t rem = partial ? p.n - q.sum + 1 : 4;
+                if (rem > 0) {
+                    const uint32_t h0 = splitmix32(seed ^ l0), h1 = splitmix32(seed ^ (l0 + 1u));
+                    const uint32_t h2 = splitmix32(seed ^ (l0 + 2u)), h3 = splitmix32(seed ^ (l0 + 3u));
+                    uint32_t *dst = out + q.addr;
+                    if (rem >= 4 && vec) {
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(h0, h1, h2, h3);
+                    } else {
+                        dst[0] = h0;
+                        if (rem > 1) dst[1] = h1;
+                        if (rem > 2) dst[2] = h2;
+                        if (rem > 3) dst[3] = h3;
+                    }
                 }
             }
             if (M >= 3) {
@@ -168,28 +191,20 @@ __global__ void __launch_bounds__(32 * kWriteWarps) write_kernel_w(const Plan p,
                 l0 += (uint32_t)t[i] * sl[i];
                 tsum += t[i];
             }
-            if (!partial) {
+            // cells of the chunk in the domain (4 off the diagonal band), one
+            // hash sequence for every store form as in write_kernel
+            const int64_t rem = partial ? p.n - (s0 + tsum) + 1 : 4;
+            if (rem > 0) {
                 const uint32_t h0 = splitmix32(seed ^ l0), h1 = splitmix32(seed ^ (l0 + 1u));
                 const uint32_t h2 = splitmix32(seed ^ (l0 + 2u)), h3 = splitmix32(seed ^ (l0 + 3u));
-                if (vec) {
-                    *reinterpret_cast<uint4 *>(out + addr) = make_uint4(h0, h1, h2, h3);
-                } else {
-                    out[addr] = h0;
-                    out[addr + 1] = h1;
-                    out[addr + 2] = h2;
-                    out[addr + 3] = h3;
-                }
-            } else {
-                // diagonal tile: most chunks lie wholly inside or outside the domain
-                const int64_t rem = p.n - (s0 + tsum) + 1;  // cells of the chunk in the domain
+                uint32_t *dst = out + addr;
                 if (rem >= 4 && vec) {
-                    *reinterpret_cast<uint4 *>(out + addr) =
-                        make_uint4(splitmix32(seed ^ l0), splitmix32(seed ^ (l0 + 1u)), splitmix32(seed ^ (l0 + 2u)),
-                                   splitmix32(seed ^ (l0 + 3u)));
-                } else if (rem > 0) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (j < rem) out[addr + j] = splitmix32(seed ^ (l0 + (uint32_t)j));
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(h0, h1, h2, h3);
+                } else {
+                    dst[0] = h0;
+                    if (rem > 1) dst[1] = h1;
+                    if (rem > 2) dst[2] = h2;
+                    if (rem > 3) dst[3] = h3;
                 }
             }
         }
