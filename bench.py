@@ -230,7 +230,7 @@ def _workload(name, args=None):
     elif name == "write2hbm":
         wl = inputs.WRITE_M2_HBM
     elif name == "write4":
-        wl = inputs.WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
+        wl = inputs.WRITE_M4
     elif name == "accum2":
         wl = inputs.ACCUM_M2
     elif name == "accum3":

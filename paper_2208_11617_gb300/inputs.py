@@ -59,8 +59,9 @@ WRITE_M2 = WriteWorkload("write m=2 n=1023 rho=16", m=2, n=1023, block=16)
 # Write test on the 2-simplex at a size past the L2: n = 32767 (536,887,296
 # cells, 2.1 GB of stores) in a 32768^2 uint32 array (4 GiB), 128 x 128 tiles.
 WRITE_M2_HBM = WriteWorkload("write m=2 n=32767 rho=128", m=2, n=32767, block=128)
-# Write test on the 4-simplex: n = 127 (11,716,640 cells) in a 128^4 uint32 array.
-WRITE_M4 = WriteWorkload("write m=4 n=127 rho=4", m=4, n=127, block=4)
+# Write test on the 4-simplex: n = 127 (11,716,640 cells) in a 128^4 uint32 array,
+# 8^4 tiles.
+WRITE_M4 = WriteWorkload("write m=4 n=127 rho=8", m=4, n=127, block=8)
 # ACCUM test (Table 1, read-add-write of one uint32 per cell) at sizes well
 # past the L2: the 2-simplex n = 16383 (134,225,920 cells, 16384^2 array) in
 # 64 x 64 tiles and the 3-simplex n = 1023 (179,481,600 cells, 1024^3 array)
